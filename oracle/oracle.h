@@ -1,0 +1,54 @@
+/*
+ * oracle.h -- plain, slow, obviously correct FP64 CPU reference for the LSQR
+ * hot path of the Gaia AVU-GSR solver (arXiv 2308.00778).
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library. The GPU library never
+ * links, includes or calls it, and it shares no code with the GPU path.
+ *
+ * Every routine is single-threaded, uses binary64 with round-to-nearest and no
+ * FMA contraction (built with -ffp-contract=off), and follows the paper's data
+ * layout: the dense-per-row coefficient matrix A_d (Sec. 2) holds 24 values
+ * per row, row-major (row i, slot j at A[i*24 + j]); slots [0,5) astrometric,
+ * [5,17) attitude (3 axes x 4 knots), [17,23) instrumental, [23] global.
+ */
+#ifndef GSR_ORACLE_H
+#define GSR_ORACLE_H
+
+#include <stdint.h>
+
+#define ORACLE_NPAR 24
+
+typedef struct {
+    int64_t n_rows;
+    int64_t n_stars;
+    const int64_t *star_ptr; /* [n_stars+1], rows of star s are [star_ptr[s], star_ptr[s+1]) */
+    int32_t n_dfa;           /* attitude degrees of freedom per axis                       */
+    int32_t n_instr;         /* instrumental unknowns                                        */
+    int32_t n_glob;          /* global unknowns, 0 or 1                                      */
+    const double *A;         /* A_d, n_rows x 24, row-major                                  */
+    const int32_t *knot;     /* first attitude knot of each row (same for the 3 axes)        */
+    const int32_t *instr;    /* n_rows x 6 instrumental column indices in [0, n_instr)       */
+} oracle_sys;
+
+typedef struct {
+    int32_t itnlim;
+    double atol, btol, conlim, damp;
+    int32_t precond; /* 1: column-norm preconditioning (Alg. 1), 0: none */
+} oracle_lsqr_params;
+
+typedef struct {
+    int32_t istop, itn;
+    double anorm, acond, rnorm, r1norm, r2norm, arnorm, xnorm, bnorm;
+} oracle_lsqr_info;
+
+int64_t oracle_ncols(const oracle_sys *s);
+void oracle_aprod1(const oracle_sys *s, const double *x, double *y);
+void oracle_aprod2(const oracle_sys *s, const double *y, double *x);
+double oracle_norm2(int64_t n, const double *a);
+void oracle_precond(const oracle_sys *s, double *p);
+void oracle_scale_columns(const oracle_sys *s, const double *p, double *A_out);
+int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
+                oracle_lsqr_info *info);
+
+#endif
