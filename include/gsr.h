@@ -1,0 +1,197 @@
+/*
+ * gsr.h -- C ABI of libgsr: the LSQR hot path of the Gaia AVU-GSR solver
+ * (Cesare et al., arXiv 2308.00778) on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Sec. 1, Eq. 1): an overdetermined sparse system A x = b solved
+ * in the least-squares sense by LSQR. Each row (observation) of A has 24
+ * nonzeros (Sec. 2): 5 astrometric coefficients of the observed star, 3 axes x
+ * 4 consecutive attitude B-spline coefficients (axis stride n_dfa), 6
+ * instrumental coefficients at arbitrary instrumental columns and 1 global
+ * (PPN gamma) coefficient. Rows are grouped by star (the block-diagonal
+ * astrometric part). The unknowns are laid out as
+ *     [astro 5*n_stars | attitude axis0 | axis1 | axis2 (n_dfa each) | instr n_instr | glob n_glob].
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a gsr_status and never aborts; on failure
+ *     gsr_last_error(ctx) holds a one-line message. Nothing is written on
+ *     GSR_EINVAL.
+ *   - The context owns all device memory it allocates; caller pointers are
+ *     borrowed for the duration of the call only.
+ *   - "where" arguments say whether a caller pointer is host (GSR_HOST) or
+ *     device (GSR_DEVICE) memory; device pointers must be on the context's
+ *     device.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls that take a stream are asynchronous with respect to the
+ *     host unless stated otherwise.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsr_ctx gsr_ctx;
+
+typedef enum {
+    GSR_OK = 0,
+    GSR_EINVAL = 1,   /* bad argument: sizes, indices, ordering, null pointers   */
+    GSR_ENOMEM = 2,   /* a device or pinned-host allocation failed               */
+    GSR_ECUDA = 3,    /* a CUDA runtime call failed                              */
+    GSR_ESTATE = 4,   /* call out of order (e.g. solve before the system is set) */
+    GSR_ENUMERIC = 5, /* NaN/Inf in the inputs or in the LSQR scalars            */
+    GSR_ETIMEOUT = 6  /* the solve exceeded gsr_solve_params.timeout_s           */
+} gsr_status;
+
+enum { GSR_FP64 = 0, GSR_FP32 = 1 };   /* storage precision of the coefficients  */
+enum { GSR_HOST = 0, GSR_DEVICE = 1 }; /* where a caller pointer lives            */
+enum { GSR_AOS = 0, GSR_SOA = 1 };     /* layout of caller coefficient arrays     */
+enum { GSR_PLAIN = 0, GSR_MIXED = 1 }; /* solver mode                             */
+enum { GSR_WARM_NONE = 0, GSR_WARM_JACOBI = 1, GSR_WARM_LEARNED = 2 };
+
+/*
+ * gsr_create -- size a context for one system and allocate its device memory.
+ *   n_stars       number of stars (>= 1); astrometric unknowns are 5*n_stars (Sec. 2).
+ *   obs_per_star  observations per star when every star has the same count (>= 1),
+ *                 or 0 when star_ptr gives the grouping.
+ *   star_ptr      host array [n_stars+1] of first rows, star_ptr[0] = 0,
+ *                 nondecreasing; NULL when obs_per_star > 0. Copied.
+ *   n_dfa         attitude degrees of freedom per axis (>= 4): N_DFA of Sec. 2.
+ *   n_instr       instrumental unknowns (>= 6).
+ *   n_glob        global unknowns: 0 or 1 (PPN gamma).
+ *   value_precision GSR_FP64 or GSR_FP32: how the coefficients are stored.
+ *                 FP32 storage is required for GSR_MIXED solves.
+ *   device        CUDA device ordinal.
+ * Errors: GSR_EINVAL (sizes, star_ptr), GSR_ENOMEM, GSR_ECUDA. On failure
+ * *out is NULL.
+ */
+gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr, int32_t n_dfa,
+                      int32_t n_instr, int32_t n_glob, int32_t value_precision, int32_t device);
+
+/* gsr_destroy -- free everything the context owns. NULL is accepted. */
+gsr_status gsr_destroy(gsr_ctx *ctx);
+
+/* gsr_last_error -- message of the last failed call on ctx ("" if none; a
+ * static message when ctx is NULL). Valid until the next call on ctx. */
+const char *gsr_last_error(const gsr_ctx *ctx);
+
+/* gsr_dims -- rows and unknowns of the system (either pointer may be NULL). */
+gsr_status gsr_dims(const gsr_ctx *ctx, int64_t *n_rows, int64_t *n_cols);
+
+/*
+ * gsr_set_rows -- load rows [row0, row0+nrows) of the coefficient matrix in the
+ * paper's storage (Sec. 2: A_d with 24 values per row, the attitude index map
+ * M_i and the instrumental map I_c) and convert them to the context's layout.
+ *   values      coefficients, binary64 (values_fp32 = 0) or binary32 (= 1).
+ *               GSR_AOS: row-major nrows x 24 (A_d: element (i, j) at i*24 + j).
+ *               GSR_SOA: 24 planes, plane j at values + j*plane_stride elements.
+ *               Slots [0,5) astro, [5,17) attitude axis-major (4 knots each),
+ *               [17,23) instrumental, 23 global (ignored when n_glob = 0).
+ *   att_knot    nrows first attitude knots, each in [0, n_dfa-4]; slot
+ *               5+4a+k of a row multiplies unknown 5*n_stars + a*n_dfa + knot + k.
+ *   instr_col   instrumental columns in [0, n_instr): GSR_AOS nrows x 6 row-major,
+ *               GSR_SOA 6 planes at instr_col + j*plane_stride.
+ *   where       GSR_HOST or GSR_DEVICE (all three arrays).
+ * FP64 values into an FP32 context are rounded to nearest; FP32 values into an
+ * FP64 context are widened exactly. Indices are validated on the device before
+ * anything is committed: GSR_EINVAL on an out-of-range index (the rows are
+ * left unchanged), GSR_ENUMERIC on a NaN or Inf coefficient.
+ * Synchronous: returns after the rows are in place.
+ */
+gsr_status gsr_set_rows(gsr_ctx *ctx, int64_t row0, int64_t nrows, const void *values, int32_t values_fp32,
+                        int32_t layout, int64_t plane_stride, const int32_t *att_knot, const int32_t *instr_col,
+                        int32_t where, void *stream);
+
+/*
+ * gsr_set_rhs -- load the known terms b (n_rows binary64; Eq. 1). Copied.
+ * GSR_ENUMERIC if b holds a NaN or Inf. Synchronous.
+ */
+gsr_status gsr_set_rhs(gsr_ctx *ctx, const double *b, int32_t where, void *stream);
+
+/*
+ * gsr_set_system -- gsr_set_rows over all rows (AoS, like the paper's A_d),
+ * then gsr_set_rhs(b) when b is not NULL.
+ */
+gsr_status gsr_set_system(gsr_ctx *ctx, const void *values, int32_t values_fp32, const int32_t *att_knot,
+                          const int32_t *instr_col, const double *b, int32_t where, void *stream);
+
+/*
+ * gsr_aprod1 -- y += A x (aprod 1, Eq. 2; Alg. 2).
+ *   x  device array of n_cols binary64 (read only).
+ *   y  device array of n_rows binary64, updated in place.
+ * Runs on stream; does not synchronise. Arithmetic is binary64 whatever the
+ * storage precision. GSR_ESTATE before every row has been set.
+ */
+gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
+
+/*
+ * gsr_aprod2 -- x += A^T y (aprod 2, Eq. 3; Alg. 3).
+ *   y  device array of n_rows binary64 (read only).
+ *   x  device array of n_cols binary64, updated in place.
+ * Runs on stream. Attitude, instrumental and global unknowns are accumulated
+ * with atomic adds, so the low bits of those results can differ from run to
+ * run (sums are reordered); astrometric unknowns are reproducible.
+ */
+gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
+
+typedef struct {
+    int32_t itnlim;     /* maximum LSQR iterations (>= 0)                               */
+    double atol, btol;  /* Paige-Saunders tolerances (0 disables the test)              */
+    double conlim;      /* condition limit (0 disables)                                 */
+    double damp;        /* damping of the scaled problem (>= 0)                         */
+    int32_t precond;    /* 1: column-norm preconditioning (Alg. 1), 0: none             */
+    int32_t mode;       /* GSR_PLAIN or GSR_MIXED                                       */
+    int32_t warm;       /* GSR_WARM_NONE / _JACOBI / _LEARNED                           */
+    const char *weights_path; /* learned warm start: weights file (see gsr_warm.h)      */
+    double timeout_s;   /* wall-clock limit of the solve (0 = none)                     */
+    int32_t graph_k;    /* LSQR iterations per CUDA-graph launch (0 = automatic)        */
+    int32_t where;      /* GSR_HOST / GSR_DEVICE: x0, x_out and se_out                  */
+    int32_t inner_itn;  /* MIXED: iterations per inner FP32 solve (0 = automatic)       */
+    double inner_tol;   /* MIXED: inner relative tolerance (0 = 1e-6)                    */
+    double refine_tol;  /* MIXED: stop when every block's |dx|/|x| < refine_tol (0 = 1e-10) */
+    int32_t max_outer;  /* MIXED: maximum refinement steps (0 = 20)                     */
+} gsr_solve_params;
+
+typedef struct {
+    int32_t istop;      /* Paige-Saunders stop reason 0..7 (7 = itnlim reached)          */
+    int32_t itn;        /* LSQR iterations run (all inner iterations in MIXED)          */
+    int32_t outer_itn;  /* MIXED: refinement steps                                      */
+    double r1norm;      /* |b - A x|                                                    */
+    double r2norm;      /* sqrt(|b - A x|^2 + damp^2 |y|^2)                             */
+    double anorm;       /* Frobenius-norm estimate of the scaled [A; damp I]            */
+    double acond;       /* condition estimate                                           */
+    double arnorm;      /* |A~^T r - damp^2 y| estimate                                  */
+    double xnorm;       /* |y| estimate (scaled unknowns)                               */
+    double ms_total;    /* wall time of the call                                        */
+    double ms_warm;     /* part of ms_total spent on the warm start                     */
+} gsr_solve_info;
+
+/* gsr_default_params -- fill p with the defaults (itnlim 2000, atol = btol =
+ * 1e-12, conlim 1e12, damp 0, precond 1, PLAIN, no warm start, host buffers). */
+void gsr_default_params(gsr_solve_params *p);
+
+/*
+ * gsr_lsqr_solve -- damped LSQR (Paige & Saunders 1982, the solver of Sec. 1-2)
+ * on the column-preconditioned system (Alg. 1), with every step on the GPU:
+ * aprod 1/2, the Eq. 4 norms, the vector updates and the scalar recurrences,
+ * one iteration per CUDA-graph segment and no per-iteration host copies
+ * (replacing the copies of Alg. 1 and Sec. 4.4).
+ *   x0      NULL or n_cols starting guess; LSQR then solves for the correction
+ *           of r0 = b - A x0 and returns x0 + correction.
+ *   x_out   n_cols solution (required).
+ *   se_out  NULL or n_cols standard errors of the unknowns.
+ *   info    NULL or filled on return (also on GSR_ETIMEOUT / GSR_ENUMERIC).
+ * Synchronous (returns after x_out is written). GSR_ESTATE if the rows or b
+ * are missing; GSR_EINVAL for MIXED on an FP64-stored context.
+ */
+gsr_status gsr_lsqr_solve(gsr_ctx *ctx, const gsr_solve_params *params, const double *x0, double *x_out,
+                          double *se_out, gsr_solve_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

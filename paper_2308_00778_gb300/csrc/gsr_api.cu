@@ -1,0 +1,438 @@
+// gsr_api.cu -- the C ABI of libgsr (include/gsr.h): contexts, loading the
+// system into SoA device planes, aprod 1/2 on caller buffers, and the solve.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gsr_internal.cuh"
+
+#define GSR_API extern "C" __attribute__((visibility("default")))
+
+namespace gsr {
+
+gsr_status fail(gsr_ctx *c, gsr_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+gsr_status cuda_fail(gsr_ctx *c, cudaError_t e, const char *what)
+{
+    const std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(c, GSR_ENOMEM, m);
+    return fail(c, GSR_ECUDA, m);
+}
+
+bool rows_complete(const gsr_ctx *c)
+{
+    if (c->n_rows == 0) return true;
+    return c->rows_set.size() == 1 && c->rows_set[0].first == 0 && c->rows_set[0].second == c->n_rows;
+}
+
+static void mark_rows(gsr_ctx *c, int64_t lo, int64_t hi)
+{
+    if (hi <= lo) return;
+    auto &v = c->rows_set;
+    v.emplace_back(lo, hi);
+    std::sort(v.begin(), v.end());
+    std::vector<std::pair<int64_t, int64_t>> m;
+    for (auto &r : v) {
+        if (!m.empty() && r.first <= m.back().second)
+            m.back().second = std::max(m.back().second, r.second);
+        else
+            m.push_back(r);
+    }
+    v.swap(m);
+}
+
+// ---------------------------------------------------------------- conversion kernels
+// error words: [0] knot out of range, [1] instr out of range, [2] non-finite value
+template <typename ST>
+__global__ void k_validate(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
+                           const int32_t *__restrict__ instr, int64_t n, int32_t n_dfa, int32_t n_instr,
+                           int32_t *__restrict__ errw)
+{
+    int32_t bk = 0, bi = 0, bv = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = knot[r];
+        bk |= (k < 0 || k > n_dfa - 4);
+        for (int j = 0; j < NINSTR; ++j) {
+            const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+            bi |= (ic < 0 || ic >= n_instr);
+        }
+        for (int j = 0; j < NPAR; ++j) {
+            const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
+            bv |= !isfinite(v);
+        }
+    }
+    if (bk) atomicOr(errw + 0, 1);
+    if (bi) atomicOr(errw + 1, 1);
+    if (bv) atomicOr(errw + 2, 1);
+}
+
+template <typename ST, typename DT>
+__global__ void k_convert(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
+                          const int32_t *__restrict__ instr, int64_t n, int32_t n_glob, DT *__restrict__ dvals,
+                          int32_t *__restrict__ dknot, int32_t *__restrict__ dinstr, int64_t plane, int64_t row0)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = row0 + r;
+        for (int j = 0; j < NPAR; ++j) {
+            ST v = layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r];
+            if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
+            dvals[j * plane + o] = (DT)v;
+        }
+        dknot[o] = knot[r];
+        for (int j = 0; j < NINSTR; ++j)
+            dinstr[j * plane + o] = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+    }
+}
+
+__global__ void k_check_finite(const double *__restrict__ a, int64_t n, int32_t *__restrict__ errw)
+{
+    int32_t bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]);
+    if (bad) atomicOr(errw + 2, 1);
+}
+
+static int grid_for(const gsr_ctx *c, int64_t n, int threads = 256)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)c->sm_count * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename ST>
+static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, int32_t layout,
+                                  int64_t vstride, const int32_t *knot, const int32_t *instr, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->errw, 0, 4 * sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    const int g = grid_for(c, nrows);
+    k_validate<ST><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_dfa, c->n_instr, c->errw);
+    int32_t hw[4];
+    if ((e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "validation");
+    if (hw[0]) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
+    if (hw[1]) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
+    if (hw[2]) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
+    if (c->prec == GSR_FP32)
+        k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob, (float *)c->vals,
+                                                c->knot, c->instr, c->plane, row0);
+    else
+        k_convert<ST, double><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
+                                                 (double *)c->vals, c->knot, c->instr, c->plane, row0);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "conversion");
+    return GSR_OK;
+}
+
+// host input: validate on the host first (nothing is written on error), then
+// stage chunks to the device and convert them there.
+template <typename ST>
+static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, int32_t layout,
+                                int64_t vstride, const int32_t *knot, const int32_t *instr, cudaStream_t s)
+{
+    for (int64_t r = 0; r < nrows; ++r) {
+        if (knot[r] < 0 || knot[r] > c->n_dfa - 4) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
+        for (int j = 0; j < NINSTR; ++j) {
+            const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+            if (ic < 0 || ic >= c->n_instr) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
+        }
+        for (int j = 0; j < NPAR; ++j) {
+            const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
+            if (!std::isfinite(v)) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
+        }
+    }
+    const int64_t chunk = std::min<int64_t>(nrows, 1 << 21);
+    ST *dv = nullptr;
+    int32_t *dk = nullptr, *di = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&dv, sizeof(ST) * NPAR * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&dk, sizeof(int32_t) * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&di, sizeof(int32_t) * NINSTR * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess) {
+        cudaFree(dv);
+        cudaFree(dk);
+        cudaFree(di);
+        return cuda_fail(c, e, "staging allocation");
+    }
+    gsr_status rc = GSR_OK;
+    for (int64_t r = 0; r < nrows && rc == GSR_OK; r += chunk) {
+        const int64_t m = std::min(chunk, nrows - r);
+        if (layout == GSR_AOS) {
+            e = cudaMemcpyAsync(dv, vals + r * NPAR, sizeof(ST) * NPAR * m, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(di, instr + r * NINSTR, sizeof(int32_t) * NINSTR * m, cudaMemcpyHostToDevice, s);
+        } else {
+            e = cudaMemcpy2DAsync(dv, sizeof(ST) * m, vals + r, sizeof(ST) * vstride, sizeof(ST) * m, NPAR,
+                                  cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(di, sizeof(int32_t) * m, instr + r, sizeof(int32_t) * vstride,
+                                      sizeof(int32_t) * m, NINSTR, cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dk, knot + r, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(c, e, "row upload");
+            break;
+        }
+        const int g = grid_for(c, m);
+        if (c->prec == GSR_FP32)
+            k_convert<ST, float><<<g, 256, 0, s>>>(dv, layout, m, dk, di, m, c->n_glob, (float *)c->vals, c->knot,
+                                                    c->instr, c->plane, row0 + r);
+        else
+            k_convert<ST, double><<<g, 256, 0, s>>>(dv, layout, m, dk, di, m, c->n_glob, (double *)c->vals, c->knot,
+                                                     c->instr, c->plane, row0 + r);
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            rc = cuda_fail(c, e, "conversion");
+    }
+    cudaFree(dv);
+    cudaFree(dk);
+    cudaFree(di);
+    return rc;
+}
+
+}  // namespace gsr
+
+using namespace gsr;
+
+// ---------------------------------------------------------------- entry points
+GSR_API const char *gsr_last_error(const gsr_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+GSR_API void gsr_default_params(gsr_solve_params *p)
+{
+    if (p) default_params(p);
+}
+
+GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
+                              int32_t n_dfa, int32_t n_instr, int32_t n_glob, int32_t value_precision, int32_t device)
+{
+    if (!out) return GSR_EINVAL;
+    *out = nullptr;
+    if (n_stars < 1 || n_dfa < 4 || n_instr < NINSTR || (n_glob != 0 && n_glob != 1) ||
+        (value_precision != GSR_FP64 && value_precision != GSR_FP32) || obs_per_star < 0 ||
+        (obs_per_star == 0) != (star_ptr != nullptr))
+        return GSR_EINVAL;
+    gsr_ctx *c = new gsr_ctx();
+    c->device = device;
+    c->prec = value_precision;
+    c->n_stars = n_stars;
+    c->n_dfa = n_dfa;
+    c->n_instr = n_instr;
+    c->n_glob = n_glob;
+    c->star_ptr_h.resize((size_t)n_stars + 1);
+    if (star_ptr) {
+        if (star_ptr[0] != 0) {
+            delete c;
+            return GSR_EINVAL;
+        }
+        for (int64_t s = 0; s < n_stars; ++s) {
+            if (star_ptr[s + 1] < star_ptr[s]) {
+                delete c;
+                return GSR_EINVAL;
+            }
+        }
+        std::memcpy(c->star_ptr_h.data(), star_ptr, sizeof(int64_t) * (size_t)(n_stars + 1));
+    } else {
+        for (int64_t s = 0; s <= n_stars; ++s) c->star_ptr_h[s] = s * (int64_t)obs_per_star;
+    }
+    c->n_rows = c->star_ptr_h[n_stars];
+    for (int64_t s = 0; s < n_stars; ++s)
+        c->max_obs = std::max<int64_t>(c->max_obs, c->star_ptr_h[s + 1] - c->star_ptr_h[s]);
+    c->n_cols = (int64_t)NASTRO * n_stars + (int64_t)NAXES * n_dfa + n_instr + n_glob;
+    c->plane = ((std::max<int64_t>(c->n_rows, 1) + 63) / 64) * 64;
+
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return GSR_ECUDA;
+    }
+    const size_t vbytes = (c->prec == GSR_FP32 ? sizeof(float) : sizeof(double)) * NPAR * (size_t)c->plane;
+    if ((e = cudaMalloc(&c->vals, vbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->knot, sizeof(int32_t) * (size_t)c->plane)) != cudaSuccess ||
+        (e = cudaMalloc(&c->instr, sizeof(int32_t) * NINSTR * (size_t)c->plane)) != cudaSuccess ||
+        (e = cudaMalloc(&c->star_ptr, sizeof(int64_t) * (size_t)(n_stars + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->b, sizeof(double) * (size_t)std::max<int64_t>(c->n_rows, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->errw, 4 * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess) {
+        cudaGetLastError();
+        gsr_destroy(c);
+        return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
+    }
+    // padding rows (plane tail) hold zeros so that vectorised readers see finite values
+    e = cudaMemset(c->vals, 0, vbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->knot, 0, sizeof(int32_t) * (size_t)c->plane);
+    if (e == cudaSuccess) e = cudaMemset(c->instr, 0, sizeof(int32_t) * NINSTR * (size_t)c->plane);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->star_ptr, c->star_ptr_h.data(), sizeof(int64_t) * (size_t)(n_stars + 1),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gsr_destroy(c);
+        return GSR_ECUDA;
+    }
+    *out = c;
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_destroy(gsr_ctx *c)
+{
+    if (!c) return GSR_OK;
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    cudaFree(c->vals);
+    cudaFree(c->knot);
+    cudaFree(c->instr);
+    cudaFree(c->star_ptr);
+    cudaFree(c->b);
+    cudaFree(c->errw);
+    if (c->own) cudaStreamDestroy(c->own);
+    if (c->ev) cudaEventDestroy(c->ev);
+    cudaGetLastError();
+    delete c;
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_dims(const gsr_ctx *c, int64_t *n_rows, int64_t *n_cols)
+{
+    if (!c) return GSR_EINVAL;
+    if (n_rows) *n_rows = c->n_rows;
+    if (n_cols) *n_cols = c->n_cols;
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_set_rows(gsr_ctx *c, int64_t row0, int64_t nrows, const void *values, int32_t values_fp32,
+                                int32_t layout, int64_t plane_stride, const int32_t *att_knot,
+                                const int32_t *instr_col, int32_t where, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (row0 < 0 || nrows < 0 || row0 + nrows > c->n_rows) return fail(c, GSR_EINVAL, "row range outside the system");
+    if (layout != GSR_AOS && layout != GSR_SOA) return fail(c, GSR_EINVAL, "layout must be GSR_AOS or GSR_SOA");
+    if (where != GSR_HOST && where != GSR_DEVICE) return fail(c, GSR_EINVAL, "where must be GSR_HOST or GSR_DEVICE");
+    if (values_fp32 != 0 && values_fp32 != 1) return fail(c, GSR_EINVAL, "values_fp32 must be 0 or 1");
+    if (nrows == 0) return GSR_OK;
+    if (!values || !att_knot || !instr_col) return fail(c, GSR_EINVAL, "null array");
+    if (layout == GSR_SOA && plane_stride < nrows) return fail(c, GSR_EINVAL, "plane_stride < nrows");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    gsr_status rc;
+    if (where == GSR_DEVICE)
+        rc = values_fp32 ? set_rows_device<float>(c, row0, nrows, (const float *)values, layout, plane_stride,
+                                                  att_knot, instr_col, s)
+                         : set_rows_device<double>(c, row0, nrows, (const double *)values, layout, plane_stride,
+                                                   att_knot, instr_col, s);
+    else
+        rc = values_fp32 ? set_rows_host<float>(c, row0, nrows, (const float *)values, layout, plane_stride, att_knot,
+                                                instr_col, s)
+                         : set_rows_host<double>(c, row0, nrows, (const double *)values, layout, plane_stride,
+                                                 att_knot, instr_col, s);
+    if (rc == GSR_OK) mark_rows(c, row0, row0 + nrows);
+    return rc;
+}
+
+GSR_API gsr_status gsr_set_rhs(gsr_ctx *c, const double *b, int32_t where, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (!b && c->n_rows > 0) return fail(c, GSR_EINVAL, "null b");
+    if (where != GSR_HOST && where != GSR_DEVICE) return fail(c, GSR_EINVAL, "where must be GSR_HOST or GSR_DEVICE");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->n_rows == 0) {
+        c->rhs_set = true;
+        return GSR_OK;
+    }
+    if (where == GSR_HOST) {
+        for (int64_t i = 0; i < c->n_rows; ++i)
+            if (!std::isfinite(b[i])) return fail(c, GSR_ENUMERIC, "non-finite b");
+        e = cudaMemcpyAsync(c->b, b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyHostToDevice, s);
+    } else {
+        int32_t hw[4];
+        e = cudaMemsetAsync(c->errw, 0, sizeof(hw), s);
+        if (e == cudaSuccess) {
+            k_check_finite<<<grid_for(c, c->n_rows), 256, 0, s>>>(b, c->n_rows, c->errw);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && hw[2]) return fail(c, GSR_ENUMERIC, "non-finite b");
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->b, b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "b upload");
+    c->rhs_set = true;
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_set_system(gsr_ctx *c, const void *values, int32_t values_fp32, const int32_t *att_knot,
+                                  const int32_t *instr_col, const double *b, int32_t where, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    gsr_status rc = gsr_set_rows(c, 0, c->n_rows, values, values_fp32, GSR_AOS, 0, att_knot, instr_col, where, stream);
+    if (rc != GSR_OK || !b) return rc;
+    return gsr_set_rhs(c, b, where, stream);
+}
+
+GSR_API gsr_status gsr_aprod1(gsr_ctx *c, const double *x, double *y, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = launch_aprod1(c, x, y, nullptr, nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "aprod1");
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_aprod2(gsr_ctx *c, const double *y, double *x, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "aprod2");
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, const double *x0, double *x_out,
+                                  double *se_out, gsr_solve_info *info, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (!x_out) return fail(c, GSR_EINVAL, "null x_out");
+    gsr_solve_params prm;
+    if (params)
+        prm = *params;
+    else
+        default_params(&prm);
+    if (prm.itnlim < 0 || prm.damp < 0.0 || prm.atol < 0.0 || prm.btol < 0.0 || prm.conlim < 0.0 ||
+        (prm.where != GSR_HOST && prm.where != GSR_DEVICE) || (prm.mode != GSR_PLAIN && prm.mode != GSR_MIXED) ||
+        prm.warm < GSR_WARM_NONE || prm.warm > GSR_WARM_LEARNED)
+        return fail(c, GSR_EINVAL, "invalid solve parameters");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if (!c->rhs_set) return fail(c, GSR_ESTATE, "b not loaded");
+    if (prm.mode == GSR_MIXED && c->prec != GSR_FP32)
+        return fail(c, GSR_EINVAL, "GSR_MIXED needs an FP32-stored context");
+    if (prm.mode == GSR_MIXED || prm.warm != GSR_WARM_NONE)
+        return fail(c, GSR_EINVAL, "mode/warm start not available in this build");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    // run on the context's own stream (graph capture needs a non-legacy stream), after the caller's work
+    if ((e = cudaEventRecord(c->ev, (cudaStream_t)stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->own, c->ev, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "stream ordering");
+    return lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
+}

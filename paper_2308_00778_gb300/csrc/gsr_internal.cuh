@@ -1,0 +1,171 @@
+// gsr_internal.cuh -- context, device views and helpers shared by the libgsr translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/gsr.h"
+
+namespace gsr {
+
+constexpr int NPAR = 24;     // coefficients per observation row (Sec. 2)
+constexpr int NASTRO = 5;    // astrometric unknowns per star
+constexpr int NAXES = 3;     // attitude axes
+constexpr int NPARAXIS = 4;  // attitude B-spline knots per axis touched by a row
+constexpr int NINSTR = 6;    // instrumental coefficients per row
+constexpr int MAX_PARTIALS = 4096;  // per-block partial sums kept for the norms
+
+// ---------------------------------------------------------------- device views
+// Coefficients are stored as 24 SoA planes of VT (double or float), plane j at
+// val + j*plane. knot: one int32 plane. instr: 6 int32 planes (instrumental
+// index in [0, n_instr)). Rows of star s are [star_ptr[s], star_ptr[s+1]).
+template <typename VT>
+struct SysView {
+    const VT *__restrict__ val;
+    const int32_t *__restrict__ knot;
+    const int32_t *__restrict__ instr;
+    const int64_t *__restrict__ star_ptr;
+    int64_t plane;
+    int64_t n_stars, n_rows;
+    int32_t n_dfa, n_instr, n_glob;
+    int64_t att0, instr0, glob0;  // first column of each section
+};
+
+// LSQR scalars shared between the kernels of one solve (one instance in device
+// memory). Written only by the single-thread scalar kernels; read by all.
+struct LsqrState {
+    double alpha, beta;          // current alpha_i, beta_i
+    double rhobar, phibar;
+    double anorm, acond, ddnorm, res2, xnorm, xxnorm, zeta, cs2, sn2;
+    double bnorm, rnorm, r1norm, r2norm, arnorm;
+    double damp, atol, btol, ctol;
+    double coef_u;     // aprod1: u_next = A pv + coef_u * u   (= -alpha/beta)
+    double inv_alpha;  // colB: v = vhat * inv_alpha
+    double t1, t2;     // colB: x += t1 w, w = v + t2 w
+    double inv_rho;    // colB: var += (w * inv_rho)^2
+    int32_t itn, itnlim, istop, done, colb_skip, numeric;
+};
+
+struct Workspace {
+    int64_t n_rows = 0, n_cols = 0;
+    double *u = nullptr;        // n_rows: unnormalised bidiagonalisation vector beta*u
+    double *z = nullptr;        // n_cols: aprod2 accumulator (kept zero between uses)
+    double *v = nullptr;        // n_cols: v (holds vhat between colA and colB)
+    double *w = nullptr;        // n_cols
+    double *x = nullptr;        // n_cols: solution of the scaled problem
+    double *pv = nullptr;       // n_cols: p * v, the vector aprod1 gathers
+    double *p = nullptr;        // n_cols: preconditioner, 1/|A_:,j|
+    double *var = nullptr;      // n_cols: sum of (w/rho)^2
+    double *tmp = nullptr;      // n_cols scratch
+    double *part_u = nullptr;   // MAX_PARTIALS: per-block sums of squares of u
+    double *part_v = nullptr;   // MAX_PARTIALS: of vhat
+    double *part_w = nullptr;   // MAX_PARTIALS: of w
+    LsqrState *st = nullptr;    // device
+    int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
+    int32_t *flag_d = nullptr;  // device alias of flag_h
+};
+
+}  // namespace gsr
+
+struct gsr_ctx {
+    int device = 0;
+    int prec = GSR_FP64;
+    int sm_count = 0;
+    int64_t n_stars = 0, n_rows = 0, n_cols = 0;
+    int32_t n_dfa = 0, n_instr = 0, n_glob = 0;
+    int64_t plane = 0;               // padded plane length (elements)
+    void *vals = nullptr;            // 24 planes of double or float
+    int32_t *knot = nullptr;         // 1 plane
+    int32_t *instr = nullptr;        // 6 planes
+    int64_t *star_ptr = nullptr;     // device copy
+    std::vector<int64_t> star_ptr_h; // host copy
+    int32_t max_obs = 0;             // longest star
+    double *b = nullptr;             // n_rows
+    bool rhs_set = false;
+    std::vector<std::pair<int64_t, int64_t>> rows_set;  // merged [lo, hi) ranges of loaded rows
+    int32_t *errw = nullptr;         // device error words for validation (4 int32)
+    cudaStream_t own = nullptr;      // non-blocking stream the solve runs (and captures) on
+    cudaEvent_t ev = nullptr;        // orders `own` after the caller's stream
+    gsr::Workspace ws;
+    std::string err;
+};
+
+namespace gsr {
+
+// ---------------------------------------------------------------- host helpers
+gsr_status fail(gsr_ctx *c, gsr_status s, const std::string &msg);
+gsr_status cuda_fail(gsr_ctx *c, cudaError_t e, const char *what);
+bool rows_complete(const gsr_ctx *c);
+
+template <typename VT>
+SysView<VT> view(const gsr_ctx *c)
+{
+    SysView<VT> s;
+    s.val = static_cast<const VT *>(c->vals);
+    s.knot = c->knot;
+    s.instr = c->instr;
+    s.star_ptr = c->star_ptr;
+    s.plane = c->plane;
+    s.n_stars = c->n_stars;
+    s.n_rows = c->n_rows;
+    s.n_dfa = c->n_dfa;
+    s.n_instr = c->n_instr;
+    s.n_glob = c->n_glob;
+    s.att0 = (int64_t)NASTRO * c->n_stars;
+    s.instr0 = s.att0 + (int64_t)NAXES * c->n_dfa;
+    s.glob0 = s.instr0 + c->n_instr;
+    return s;
+}
+
+// kernels launchers (aprod.cu)
+cudaError_t launch_aprod1(const gsr_ctx *c, const double *x, double *y, const LsqrState *st, double *part,
+                          cudaStream_t s);
+cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool square, const LsqrState *st,
+                          cudaStream_t s);
+int aprod1_grid(const gsr_ctx *c);
+
+// LSQR driver (lsqr.cu)
+gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,
+                      gsr_solve_info *info, cudaStream_t s);
+gsr_status ensure_workspace(gsr_ctx *c);
+void free_workspace(gsr_ctx *c);
+void default_params(gsr_solve_params *p);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic sum of n partials by one warp (lane-strided, then a fixed tree).
+__device__ __forceinline__ double warp_sum_partials(const double *__restrict__ part, int n)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) acc += part[i];
+    return warp_sum(acc);
+}
+
+// Block-wide sum; every thread must call it; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sm32)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm32[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? sm32[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+}  // namespace gsr

@@ -1,0 +1,559 @@
+// lsqr.cu -- the LSQR iteration (Paige & Saunders 1982; the solver of Sec. 1-2) on the GPU.
+//
+// One iteration is five kernels, captured once into a CUDA graph and replayed
+// (replacing the per-iteration host synchronisations and copies of Alg. 1 and
+// Sec. 4.4):
+//   aprod1  u <- A (p v) - (alpha/beta) u, per-block sums of squares of u
+//   aprod2  z <- A^T u (z is zero on entry)
+//   colA    beta = |u| (from the partials), vhat = p z / beta - beta v,
+//           z <- 0, per-block sums of squares of vhat and of w
+//   scalar  alpha = |vhat|, the two plane rotations, the norm / condition /
+//           residual estimates and the stopping tests (one thread)
+//   colB    v = vhat / alpha, pv = p v, x += t1 w, w = v + t2 w, var += (w/rho)^2
+// The LSQR vectors u and v are kept unnormalised where that saves a pass: u is
+// stored as beta*u (its scale folded into the aprod1 coefficient), and the
+// preconditioner p (column norms, Alg. 1) is applied to column vectors rather
+// than to A. Norms (alpha, beta) are exact 2-norms from per-block FP64 sums of
+// squares reduced in a fixed order (Eq. 4's scaling only guards against
+// overflow; a non-finite sum stops the solve with GSR_ENUMERIC).
+//
+// Stopping: the scalar kernel sets st->done when a test fires (after setting
+// the coefficients of that iteration's x update). Later kernels read done and
+// return at once; colB of the stopping iteration still runs (it reads
+// st->colb_skip, which the scalar kernel clears when it ran). The host reads
+// a pinned mapped flag after each graph launch.
+#include <chrono>
+#include <cmath>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+static constexpr int kColThreads = 256;
+
+// ---------------------------------------------------------------- column kernels
+// u <- b - (A x0 is added by a separate aprod1 on -x0); here: u <- src, partial sums of squares
+__global__ void k_copy_ssq(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
+                           double *__restrict__ part)
+{
+    __shared__ double sm32[32];
+    double ssq = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        dst[i] = v;
+        ssq = fma(v, v, ssq);
+    }
+    const double t = block_sum(ssq, sm32);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// sums of squares of a row vector (used after u <- b - A x0)
+__global__ void k_ssq(const double *__restrict__ a, int64_t n, double *__restrict__ part)
+{
+    __shared__ double sm32[32];
+    double ssq = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        ssq = fma(v, v, ssq);
+    }
+    const double t = block_sum(ssq, sm32);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p_j = 1/sqrt(colsq_j) (1 for an empty column), colsq reset to zero
+__global__ void k_precond_finish(double *__restrict__ colsq, double *__restrict__ p, int64_t n, int32_t use)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double q = colsq[j];
+        p[j] = (use && q > 0.0) ? 1.0 / sqrt(q) : 1.0;
+        colsq[j] = 0.0;
+    }
+}
+
+// colA: beta from the aprod1 partials; vhat = p z / beta - beta v (first=1: no v term); z <- 0;
+// per-block sums of squares of vhat (alpha) and of w (for the condition estimate).
+__global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *__restrict__ z,
+                       const double *__restrict__ p, double *__restrict__ v, const double *__restrict__ w, int64_t n,
+                       LsqrState *__restrict__ st, double *__restrict__ part_v, double *__restrict__ part_w,
+                       int32_t first)
+{
+    __shared__ double sm32[32];
+    __shared__ double s_beta;
+    if (!first && st->done) return;
+    if (threadIdx.x < 32) {
+        const double ssq = warp_sum_partials(part_u, n_part_u);
+        if (threadIdx.x == 0) s_beta = sqrt(ssq);
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    double sv = 0.0, sw = 0.0;
+    if (beta > 0.0 && isfinite(beta)) {
+        const double ib = 1.0 / beta;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const double zj = z[j];
+            z[j] = 0.0;
+            double vh = p[j] * zj * ib;
+            if (!first) vh = fma(-beta, v[j], vh);
+            v[j] = vh;
+            sv = fma(vh, vh, sv);
+            if (!first) {
+                const double wj = w[j];
+                sw = fma(wj, wj, sw);
+            }
+        }
+    } else {
+        // beta = 0 (b in the range of A already reached) or non-finite: leave v as alpha*v,
+        // so that colB restores it; the scalar kernel keeps alpha.
+        const double a = first ? 0.0 : st->alpha;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            z[j] = 0.0;
+            const double vh = a * v[j];
+            v[j] = vh;
+            sv = fma(vh, vh, sv);
+            if (!first) {
+                const double wj = w[j];
+                sw = fma(wj, wj, sw);
+            }
+        }
+    }
+    const double tv = block_sum(sv, sm32);
+    const double tw = block_sum(sw, sm32);
+    if (threadIdx.x == 0) {
+        part_v[blockIdx.x] = tv;
+        part_w[blockIdx.x] = tw;
+        if (blockIdx.x == 0) st->beta = beta;
+    }
+}
+
+// The start of LSQR: beta_1 u_1 = b, alpha_1 v_1 = A~^T u_1, w_1 = v_1, x_0 = 0,
+// phibar_1 = beta_1, rhobar_1 = alpha_1 (one warp; thread 0 writes).
+__global__ void k_scalar_init(LsqrState *__restrict__ st, const double *__restrict__ part_v, int n_part,
+                              int32_t *__restrict__ flag)
+{
+    const double ssq = warp_sum_partials(part_v, n_part);
+    if (threadIdx.x != 0) return;
+    const double beta = st->beta;
+    const double alpha = sqrt(ssq);
+    st->alpha = alpha;
+    st->rhobar = alpha;
+    st->phibar = beta;
+    st->anorm = 0.0;
+    st->acond = 0.0;
+    st->ddnorm = 0.0;
+    st->res2 = 0.0;
+    st->xnorm = 0.0;
+    st->xxnorm = 0.0;
+    st->zeta = 0.0;
+    st->cs2 = -1.0;
+    st->sn2 = 0.0;
+    st->bnorm = beta;
+    st->rnorm = beta;
+    st->r1norm = beta;
+    st->r2norm = beta;
+    st->arnorm = alpha * beta;
+    st->itn = 0;
+    st->istop = 0;
+    st->numeric = !(isfinite(alpha) && isfinite(beta));
+    st->done = (st->arnorm == 0.0 || st->numeric || st->itnlim <= 0) ? 1 : 0;
+    st->colb_skip = 0;
+    st->inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    st->t1 = 0.0;
+    st->t2 = 0.0;
+    st->inv_rho = 0.0;
+    st->coef_u = beta > 0.0 ? -alpha / beta : 0.0;
+    *flag = st->done;
+}
+
+// One step of the recurrence. Thread 0 of one warp.
+__global__ void k_scalar(LsqrState *__restrict__ st, const double *__restrict__ part_v,
+                         const double *__restrict__ part_w, int n_part, int32_t *__restrict__ flag)
+{
+    const double ssq_v = warp_sum_partials(part_v, n_part);
+    const double ssq_w = warp_sum_partials(part_w, n_part);
+    if (threadIdx.x != 0) return;
+    if (st->done) {
+        st->colb_skip = 1;
+        return;
+    }
+    st->colb_skip = 0;
+    const double damp = st->damp, dampsq = damp * damp;
+    const double beta = st->beta;
+    double alpha = st->alpha;
+    double anorm = st->anorm;
+    if (beta > 0.0) {
+        anorm = sqrt(anorm * anorm + alpha * alpha + beta * beta + dampsq);
+        alpha = sqrt(ssq_v);
+    }
+    // rotation eliminating damp
+    const double rhobar = st->rhobar;
+    double phibar = st->phibar;
+    const double rhobar1 = sqrt(rhobar * rhobar + dampsq);
+    const double cs1 = rhobar / rhobar1;
+    const double sn1 = damp / rhobar1;
+    const double psi = sn1 * phibar;
+    phibar = cs1 * phibar;
+    // rotation eliminating beta
+    const double rho = sqrt(rhobar1 * rhobar1 + beta * beta);
+    const double cs = rhobar1 / rho;
+    const double sn = beta / rho;
+    const double theta = sn * alpha;
+    const double rhobar_n = -cs * alpha;
+    const double phi = cs * phibar;
+    phibar = sn * phibar;
+    const double tau = sn * phi;
+    // coefficients of the x and w updates
+    st->t1 = phi / rho;
+    st->t2 = -theta / rho;
+    st->inv_rho = 1.0 / rho;
+    const double ddnorm = st->ddnorm + ssq_w / (rho * rho);
+    // |x| estimate
+    const double delta = st->sn2 * rho;
+    const double gambar = -st->cs2 * rho;
+    const double rhs = phi - delta * st->zeta;
+    const double zbar = rhs / gambar;
+    const double xnorm = sqrt(st->xxnorm + zbar * zbar);
+    const double gamma = sqrt(gambar * gambar + theta * theta);
+    st->cs2 = gambar / gamma;
+    st->sn2 = theta / gamma;
+    st->zeta = rhs / gamma;
+    st->xxnorm = st->xxnorm + st->zeta * st->zeta;
+    // estimates
+    const double acond = anorm * sqrt(ddnorm);
+    const double res1 = phibar * phibar;
+    const double res2 = st->res2 + psi * psi;
+    const double rnorm = sqrt(res1 + res2);
+    const double arnorm = alpha * fabs(tau);
+    const double r1sq = rnorm * rnorm - dampsq * st->xxnorm;
+    double r1norm = sqrt(fabs(r1sq));
+    if (r1sq < 0.0) r1norm = -r1norm;
+    const int itn = st->itn + 1;
+    // stopping tests
+    const double bnorm = st->bnorm;
+    const double test1 = rnorm / bnorm;
+    const double test2 = arnorm / (anorm * rnorm);
+    const double test3 = 1.0 / acond;
+    const double tt1 = test1 / (1.0 + anorm * xnorm / bnorm);
+    const double rtol = st->btol + st->atol * anorm * xnorm / bnorm;
+    int istop = 0;
+    if (itn >= st->itnlim) istop = 7;
+    if (1.0 + test3 <= 1.0) istop = 6;
+    if (1.0 + test2 <= 1.0) istop = 5;
+    if (1.0 + tt1 <= 1.0) istop = 4;
+    if (test3 <= st->ctol) istop = 3;
+    if (test2 <= st->atol) istop = 2;
+    if (test1 <= rtol) istop = 1;
+    const bool bad = !(isfinite(alpha) && isfinite(rho) && isfinite(phi) && isfinite(theta) && isfinite(rnorm));
+    // store
+    st->alpha = alpha;
+    st->anorm = anorm;
+    st->rhobar = rhobar_n;
+    st->phibar = phibar;
+    st->ddnorm = ddnorm;
+    st->xnorm = xnorm;
+    st->acond = acond;
+    st->res2 = res2;
+    st->rnorm = rnorm;
+    st->r1norm = r1norm;
+    st->r2norm = rnorm;
+    st->arnorm = arnorm;
+    st->itn = itn;
+    st->inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    st->coef_u = beta > 0.0 ? -alpha / beta : 0.0;
+    if (bad) {
+        st->numeric = 1;
+        st->colb_skip = 1;
+        istop = istop ? istop : 7;
+    }
+    st->istop = istop;
+    if (istop) {
+        st->done = 1;
+        *flag = 1;
+    }
+}
+
+// colB (first=1: the start, w = v and x = 0)
+__global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, const double *__restrict__ p,
+                       double *__restrict__ w, double *__restrict__ x, double *__restrict__ var, int64_t n,
+                       const LsqrState *__restrict__ st, int32_t first)
+{
+    if (!first && st->colb_skip) return;
+    if (first && st->done) return;
+    const double ia = st->inv_alpha;
+    const double t1 = st->t1, t2 = st->t2, ir = st->inv_rho;
+    const bool has_alpha = st->alpha > 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double vh = v[j];
+        const double vj = has_alpha ? vh * ia : vh;
+        v[j] = vj;
+        pv[j] = p[j] * vj;
+        if (first) {
+            w[j] = vj;
+            x[j] = 0.0;
+            if (var) var[j] = 0.0;
+        } else {
+            const double wj = w[j];
+            if (var) {
+                const double d = wj * ir;
+                var[j] = fma(d, d, var[j]);
+            }
+            x[j] = fma(t1, wj, x[j]);
+            w[j] = fma(t2, wj, vj);
+        }
+    }
+}
+
+// x_out = p * x (+ x0); se = sqrt(var) * p * s (s = |r| / sqrt(max(m - n, 1)))
+__global__ void k_finish(const double *__restrict__ x, const double *__restrict__ p, const double *__restrict__ x0,
+                         double *__restrict__ out, const double *__restrict__ var, double *__restrict__ se,
+                         const LsqrState *__restrict__ st, int64_t n, double dof)
+{
+    const double s = fabs(st->r1norm) / sqrt(dof);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double xv = x[j] * p[j];
+        if (x0) xv += x0[j];
+        out[j] = xv;
+        if (se) se[j] = sqrt(var[j]) * p[j] * s;
+    }
+}
+
+__global__ void k_negate(const double *__restrict__ a, double *__restrict__ out, int64_t n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = -a[j];
+}
+
+// ---------------------------------------------------------------- host side
+static int col_grid(const gsr_ctx *c, int64_t n)
+{
+    int64_t g = (n + kColThreads - 1) / kColThreads;
+    const int64_t cap = (int64_t)c->sm_count * 4;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+gsr_status ensure_workspace(gsr_ctx *c)
+{
+    Workspace &ws = c->ws;
+    if (ws.u) return GSR_OK;
+    const size_t nr = (size_t)(c->n_rows > 0 ? c->n_rows : 1), nc = (size_t)c->n_cols;
+    cudaError_t e = cudaSuccess;
+    double **cols[] = {&ws.z, &ws.v, &ws.w, &ws.x, &ws.pv, &ws.p, &ws.var, &ws.tmp};
+    if ((e = cudaMalloc(&ws.u, nr * sizeof(double))) != cudaSuccess) goto oom;
+    for (double **pp : cols)
+        if ((e = cudaMalloc(pp, nc * sizeof(double))) != cudaSuccess) goto oom;
+    if ((e = cudaMalloc(&ws.part_u, 3 * MAX_PARTIALS * sizeof(double))) != cudaSuccess) goto oom;
+    ws.part_v = ws.part_u + MAX_PARTIALS;
+    ws.part_w = ws.part_v + MAX_PARTIALS;
+    if ((e = cudaMalloc(&ws.st, sizeof(LsqrState))) != cudaSuccess) goto oom;
+    if ((e = cudaHostAlloc(&ws.flag_h, sizeof(int32_t), cudaHostAllocMapped)) != cudaSuccess) goto oom;
+    if ((e = cudaHostGetDevicePointer(&ws.flag_d, ws.flag_h, 0)) != cudaSuccess) goto oom;
+    if ((e = cudaMemset(ws.z, 0, nc * sizeof(double))) != cudaSuccess) goto oom;
+    if ((e = cudaMemset(ws.part_u, 0, 3 * MAX_PARTIALS * sizeof(double))) != cudaSuccess) goto oom;
+    ws.n_rows = c->n_rows;
+    ws.n_cols = c->n_cols;
+    return GSR_OK;
+oom:
+    free_workspace(c);
+    cudaGetLastError();
+    return fail(c, GSR_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+}
+
+void free_workspace(gsr_ctx *c)
+{
+    Workspace &ws = c->ws;
+    double *ptrs[] = {ws.u, ws.z, ws.v, ws.w, ws.x, ws.pv, ws.p, ws.var, ws.tmp, ws.part_u};
+    for (double *p : ptrs)
+        if (p) cudaFree(p);
+    if (ws.st) cudaFree(ws.st);
+    if (ws.flag_h) cudaFreeHost(ws.flag_h);
+    ws = Workspace();
+}
+
+// Capture `k` LSQR iterations (5 kernels each) into an executable graph.
+static cudaError_t capture_iterations(gsr_ctx *c, int k, bool want_var, cudaStream_t s, cudaGraphExec_t *exec)
+{
+    Workspace &ws = c->ws;
+    const int gu = aprod1_grid(c);
+    const int gc = col_grid(c, c->n_cols);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < k && e == cudaSuccess; ++i) {
+        if ((e = launch_aprod1(c, ws.pv, ws.u, ws.st, ws.part_u, s)) != cudaSuccess) break;
+        if ((e = launch_aprod2(c, ws.u, ws.z, false, ws.st, s)) != cudaSuccess) break;
+        k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gu, ws.z, ws.p, ws.v, ws.w, c->n_cols, ws.st, ws.part_v,
+                                          ws.part_w, 0);
+        k_scalar<<<1, 32, 0, s>>>(ws.st, ws.part_v, ws.part_w, gc, ws.flag_d);
+        k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, c->n_cols,
+                                          ws.st, 0);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+void default_params(gsr_solve_params *p)
+{
+    *p = gsr_solve_params();
+    p->itnlim = 2000;
+    p->atol = 1e-12;
+    p->btol = 1e-12;
+    p->conlim = 1e12;
+    p->damp = 0.0;
+    p->precond = 1;
+    p->mode = GSR_PLAIN;
+    p->warm = GSR_WARM_NONE;
+    p->weights_path = nullptr;
+    p->timeout_s = 0.0;
+    p->graph_k = 0;
+    p->where = GSR_HOST;
+}
+
+gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,
+                      gsr_solve_info *info, cudaStream_t s)
+{
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    gsr_status rc = ensure_workspace(c);
+    if (rc != GSR_OK) return rc;
+    Workspace &ws = c->ws;
+    const int64_t nc = c->n_cols, nr = c->n_rows;
+    const bool dev_io = prm->where == GSR_DEVICE;
+    const bool want_var = se_out != nullptr;
+    const int gc = col_grid(c, nc);
+    const int gr = col_grid(c, nr);
+    cudaError_t e;
+
+    // preconditioner p = 1/|A_:,j| (Alg. 1): one pass over A per solve
+    if ((e = cudaMemsetAsync(ws.tmp, 0, nc * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if (prm->precond) {
+        if ((e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s)) != cudaSuccess)
+            return cuda_fail(c, e, "column norms");
+    }
+    k_precond_finish<<<gc, kColThreads, 0, s>>>(ws.tmp, ws.p, nc, prm->precond ? 1 : 0);
+
+    // x0: u = b - A x0 ; otherwise u = b
+    const double *x0d = nullptr;
+    double *x0_buf = nullptr;
+    if (x0) {
+        if (dev_io) {
+            x0d = x0;
+        } else {
+            if ((e = cudaMalloc(&x0_buf, nc * sizeof(double))) != cudaSuccess)
+                return fail(c, GSR_ENOMEM, "x0 buffer allocation failed");
+            if ((e = cudaMemcpyAsync(x0_buf, x0, nc * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+                cudaFree(x0_buf);
+                return cuda_fail(c, e, "x0 copy");
+            }
+            x0d = x0_buf;
+        }
+    }
+    LsqrState init = LsqrState();
+    init.damp = prm->damp;
+    init.atol = prm->atol;
+    init.btol = prm->btol;
+    init.ctol = prm->conlim > 0.0 ? 1.0 / prm->conlim : 0.0;
+    init.itnlim = prm->itnlim;
+    if ((e = cudaMemcpyAsync(ws.st, &init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "state upload");
+    if (x0d) {
+        k_negate<<<gc, kColThreads, 0, s>>>(x0d, ws.x, nc);
+        k_copy_ssq<<<gr, kColThreads, 0, s>>>(c->b, ws.u, nr, ws.part_u);
+        launch_aprod1(c, ws.x, ws.u, nullptr, nullptr, s);  // u = b - A x0
+        k_ssq<<<gr, kColThreads, 0, s>>>(ws.u, nr, ws.part_u);
+    } else {
+        k_copy_ssq<<<gr, kColThreads, 0, s>>>(c->b, ws.u, nr, ws.part_u);
+    }
+    // alpha_1 v_1 = A~^T u_1: z = A^T u (unnormalised), colA with first=1 divides by beta
+    launch_aprod2(c, ws.u, ws.z, false, nullptr, s);
+    k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gr, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1);
+    k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);
+    k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, nc, ws.st, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        if (x0_buf) cudaFree(x0_buf);
+        return cuda_fail(c, e, "LSQR start");
+    }
+    // the u partials of the start were written with grid gr; the iterations use aprod1's grid
+    // (k_colA inside the graph reads aprod1_grid partials)
+
+    int k = prm->graph_k > 0 ? prm->graph_k : 8;
+    if (k > prm->itnlim && prm->itnlim > 0) k = prm->itnlim;
+    if (k < 1) k = 1;
+    cudaGraphExec_t exec = nullptr;
+    gsr_status status = GSR_OK;
+    if ((e = capture_iterations(c, k, want_var, s, &exec)) != cudaSuccess) {
+        if (x0_buf) cudaFree(x0_buf);
+        return cuda_fail(c, e, "graph capture");
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        if (x0_buf) cudaFree(x0_buf);
+        return cuda_fail(c, e, "LSQR start");
+    }
+    int launched = 0;
+    const int max_launch = prm->itnlim > 0 ? (prm->itnlim + k - 1) / k : 0;
+    while (!*(volatile int32_t *)ws.flag_h && launched < max_launch) {
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+            status = cuda_fail(c, e, "graph launch");
+            break;
+        }
+        ++launched;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            status = cuda_fail(c, e, "LSQR iteration");
+            break;
+        }
+        if (prm->timeout_s > 0.0 &&
+            std::chrono::duration<double>(clk::now() - t0).count() > prm->timeout_s) {
+            status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
+            break;
+        }
+    }
+    cudaGraphExecDestroy(exec);
+
+    LsqrState fin;
+    if ((e = cudaMemcpyAsync(&fin, ws.st, sizeof(fin), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        if (x0_buf) cudaFree(x0_buf);
+        return cuda_fail(c, e, "state download");
+    }
+    // result
+    double *out_d = dev_io ? x_out : ws.tmp;
+    double *se_d = nullptr;
+    if (se_out) se_d = dev_io ? se_out : ws.z;  // z is free after the loop (kept zero below)
+    const double dof = (double)(nr - nc > 1 ? nr - nc : 1);
+    k_finish<<<gc, kColThreads, 0, s>>>(ws.x, ws.p, x0d, out_d, ws.var, se_d, ws.st, nc, dof);
+    if ((e = cudaGetLastError()) == cudaSuccess && !dev_io) {
+        e = cudaMemcpyAsync(x_out, out_d, nc * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && se_out) e = cudaMemcpyAsync(se_out, se_d, nc * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && se_d == ws.z) e = cudaMemsetAsync(ws.z, 0, nc * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (x0_buf) cudaFree(x0_buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "result");
+
+    if (info) {
+        info->istop = fin.istop;
+        info->itn = fin.itn;
+        info->outer_itn = 0;
+        info->r1norm = fin.r1norm;
+        info->r2norm = fin.r2norm;
+        info->anorm = fin.anorm;
+        info->acond = fin.acond;
+        info->arnorm = fin.arnorm;
+        info->xnorm = fin.xnorm;
+        info->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+        info->ms_warm = 0.0;
+    }
+    if (status != GSR_OK) return status;
+    if (fin.numeric) return fail(c, GSR_ENUMERIC, "non-finite value in the LSQR scalars");
+    return GSR_OK;
+}
+
+}  // namespace gsr

@@ -1,0 +1,243 @@
+"""ctypes binding of libgsr (include/gsr.h), same names as the C entry points.
+
+Each ``gsr_*`` function forwards its arguments to the C function of the same
+name and returns the integer status; ``Context`` is a small convenience
+wrapper that raises ``GsrError`` on a non-zero status. Pointers are plain
+integers: ``tensor.data_ptr()``, ``ndarray.ctypes.data`` or 0 for NULL; a
+stream is ``torch.cuda.Stream.cuda_stream`` (0 = legacy default stream).
+The library must have been built (``__graft_entry__.build()``); importing
+this module without it raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libgsr.so")
+
+GSR_FP64, GSR_FP32 = 0, 1
+GSR_HOST, GSR_DEVICE = 0, 1
+GSR_AOS, GSR_SOA = 0, 1
+GSR_PLAIN, GSR_MIXED = 0, 1
+GSR_WARM_NONE, GSR_WARM_JACOBI, GSR_WARM_LEARNED = 0, 1, 2
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    EINVAL = 1
+    ENOMEM = 2
+    ECUDA = 3
+    ESTATE = 4
+    ENUMERIC = 5
+    ETIMEOUT = 6
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [
+        ("itnlim", ctypes.c_int32),
+        ("atol", ctypes.c_double),
+        ("btol", ctypes.c_double),
+        ("conlim", ctypes.c_double),
+        ("damp", ctypes.c_double),
+        ("precond", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("warm", ctypes.c_int32),
+        ("weights_path", ctypes.c_char_p),
+        ("timeout_s", ctypes.c_double),
+        ("graph_k", ctypes.c_int32),
+        ("where", ctypes.c_int32),
+        ("inner_itn", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double),
+        ("refine_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int32),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("istop", ctypes.c_int32),
+        ("itn", ctypes.c_int32),
+        ("outer_itn", ctypes.c_int32),
+        ("r1norm", ctypes.c_double),
+        ("r2norm", ctypes.c_double),
+        ("anorm", ctypes.c_double),
+        ("acond", ctypes.c_double),
+        ("arnorm", ctypes.c_double),
+        ("xnorm", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("ms_warm", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libgsr.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(f"libgsr.so not built ({library_path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(library_path)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "gsr_create": (I32, [ctypes.POINTER(P), I64, I32, P, I32, I32, I32, I32, I32]),
+            "gsr_destroy": (I32, [P]),
+            "gsr_last_error": (ctypes.c_char_p, [P]),
+            "gsr_dims": (I32, [P, P, P]),
+            "gsr_set_rows": (I32, [P, I64, I64, P, I32, I32, I64, P, P, I32, P]),
+            "gsr_set_rhs": (I32, [P, P, I32, P]),
+            "gsr_set_system": (I32, [P, P, I32, P, P, P, I32, P]),
+            "gsr_aprod1": (I32, [P, P, P, P]),
+            "gsr_aprod2": (I32, [P, P, P, P]),
+            "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
+            "gsr_lsqr_solve": (I32, [P, ctypes.POINTER(SolveParams), P, P, P, ctypes.POINTER(SolveInfo), P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- same-name functions
+def gsr_create(n_stars, obs_per_star, star_ptr, n_dfa, n_instr, n_glob, value_precision, device):
+    """Returns (status, ctx handle). star_ptr: host pointer (int) or 0."""
+    h = ctypes.c_void_p()
+    st = lib().gsr_create(ctypes.byref(h), n_stars, obs_per_star, star_ptr or None, n_dfa, n_instr, n_glob,
+                          value_precision, device)
+    return st, h.value
+
+
+def gsr_destroy(ctx):
+    return lib().gsr_destroy(ctx)
+
+
+def gsr_last_error(ctx) -> str:
+    r = lib().gsr_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def gsr_dims(ctx):
+    nr, nc = ctypes.c_int64(), ctypes.c_int64()
+    st = lib().gsr_dims(ctx, ctypes.byref(nr), ctypes.byref(nc))
+    return st, nr.value, nc.value
+
+
+def gsr_set_rows(ctx, row0, nrows, values, values_fp32, layout, plane_stride, att_knot, instr_col, where, stream=0):
+    return lib().gsr_set_rows(ctx, row0, nrows, values or None, values_fp32, layout, plane_stride, att_knot or None,
+                              instr_col or None, where, stream or None)
+
+
+def gsr_set_rhs(ctx, b, where, stream=0):
+    return lib().gsr_set_rhs(ctx, b or None, where, stream or None)
+
+
+def gsr_set_system(ctx, values, values_fp32, att_knot, instr_col, b, where, stream=0):
+    return lib().gsr_set_system(ctx, values or None, values_fp32, att_knot or None, instr_col or None, b or None,
+                                where, stream or None)
+
+
+def gsr_aprod1(ctx, x, y, stream=0):
+    return lib().gsr_aprod1(ctx, x or None, y or None, stream or None)
+
+
+def gsr_aprod2(ctx, y, x, stream=0):
+    return lib().gsr_aprod2(ctx, y or None, x or None, stream or None)
+
+
+def gsr_default_params() -> SolveParams:
+    p = SolveParams()
+    lib().gsr_default_params(ctypes.byref(p))
+    return p
+
+
+def gsr_lsqr_solve(ctx, params: SolveParams, x0, x_out, se_out, info: SolveInfo, stream=0):
+    return lib().gsr_lsqr_solve(ctx, ctypes.byref(params), x0 or None, x_out or None, se_out or None,
+                                ctypes.byref(info), stream or None)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class GsrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{Status(status).name}: {msg}")
+        self.status = Status(status)
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _where(a) -> int:
+    return GSR_DEVICE if hasattr(a, "is_cuda") and a.is_cuda else GSR_HOST
+
+
+class Context:
+    """Owns one gsr_ctx. Arrays may be numpy arrays (host) or torch tensors (host or CUDA)."""
+
+    def __init__(self, n_stars, obs_per_star=0, star_ptr=None, n_dfa=4, n_instr=6, n_glob=1, fp32=False, device=0):
+        import numpy as np
+
+        self._sp = None if star_ptr is None else np.ascontiguousarray(star_ptr, dtype=np.int64)
+        st, h = gsr_create(n_stars, obs_per_star, _ptr(self._sp), n_dfa, n_instr, n_glob,
+                           GSR_FP32 if fp32 else GSR_FP64, device)
+        if st != 0:
+            raise GsrError(st, "gsr_create failed")
+        self.h = h
+        _, self.n_rows, self.n_cols = gsr_dims(h)
+
+    def _check(self, st):
+        if st != 0:
+            raise GsrError(st, gsr_last_error(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            gsr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_system(self, A, knot, instr, b=None, stream=0):
+        fp32 = 1 if str(A.dtype).endswith("float32") else 0
+        self._check(gsr_set_system(self.h, _ptr(A), fp32, _ptr(knot), _ptr(instr), _ptr(b), _where(A), stream))
+
+    def set_rows(self, row0, nrows, vals, knot, instr, layout=GSR_AOS, plane_stride=0, stream=0):
+        fp32 = 1 if str(vals.dtype).endswith("float32") else 0
+        self._check(gsr_set_rows(self.h, row0, nrows, _ptr(vals), fp32, layout, plane_stride, _ptr(knot),
+                                 _ptr(instr), _where(vals), stream))
+
+    def set_rhs(self, b, stream=0):
+        self._check(gsr_set_rhs(self.h, _ptr(b), _where(b), stream))
+
+    def aprod1(self, x, y, stream=0):
+        self._check(gsr_aprod1(self.h, _ptr(x), _ptr(y), stream))
+
+    def aprod2(self, y, x, stream=0):
+        self._check(gsr_aprod2(self.h, _ptr(y), _ptr(x), stream))
+
+    def solve(self, x_out, x0=None, se_out=None, stream=0, **kw):
+        p = gsr_default_params()
+        for k, v in kw.items():
+            if k == "weights_path" and isinstance(v, str):
+                v = v.encode()
+            setattr(p, k, v)
+        p.where = _where(x_out)
+        info = SolveInfo()
+        st = gsr_lsqr_solve(self.h, p, _ptr(x0), _ptr(x_out), _ptr(se_out), info, stream)
+        if st != 0:
+            raise GsrError(st, gsr_last_error(self.h) + f" (info: {info.as_dict()})")
+        return info.as_dict()

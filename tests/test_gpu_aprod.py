@@ -1,0 +1,162 @@
+"""aprod 1 / aprod 2 on the GPU against the CPU oracle, element by element.
+
+Tolerance: |gpu - oracle| <= 1e-13 * (sum of |terms|) per element: both sides
+compute in binary64 and differ only in summation order and FMA contraction.
+Cases span many blocks and warps, ragged stars (including empty stars and
+single-row stars), no global column, and attitude / instrumental widths that
+select each accumulator placement (shared memory or global atomics).
+"""
+import numpy as np
+import pytest
+import torch
+
+import gsrgen
+import oracle
+import paper_2308_00778_gb300 as g
+from gpu_util import abs_system, context_for
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tiny": gsrgen.make_cfg(7, 20, 30, 12, 8),
+    "ragged_noglob": gsrgen.make_cfg(21, 13, (1, 37), 9, 6, n_glob=0),
+    "empty_stars": gsrgen.make_cfg(23, 50, (0, 4), 4, 6),
+    "c1": gsrgen.workloads()["c1"].cfg,
+    "ragged_many": gsrgen.make_cfg(31, 3000, (1, 300), 250, 40),
+    "wide_att_global": gsrgen.make_cfg(33, 400, 100, 20000, 15000),   # accumulators too big for shared memory
+    "wide_att_instr_smem": gsrgen.make_cfg(34, 400, 100, 6000, 2000),  # attitude global, instr shared
+}
+
+
+def _check(got, want, scale, tol=1e-13):
+    err = np.abs(got - want)
+    bound = tol * (scale + np.abs(want)) + 1e-300
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound):.3g}"
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("fp32", [False, True])
+def test_aprod_vs_oracle(name, fp32):
+    cfg = CASES[name]
+    h = gsrgen.generate(cfg, fp32=fp32)
+    s = oracle.from_host_system(h)
+    ctx = context_for(h, fp32=fp32)
+    ctx.set_system(h.A32 if fp32 else h.A, h.knot, h.instr)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(s.n_cols)
+    y0 = rng.standard_normal(s.n_rows)
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.tensor(y0, device="cuda")
+    ctx.aprod1(xd, yd)
+    want = oracle.aprod1(s, x, y0.copy())
+    scale = oracle.aprod1(abs_system(s), np.abs(x), np.abs(y0).copy())
+    _check(yd.cpu().numpy(), want, scale)
+
+    u = rng.standard_normal(s.n_rows)
+    x0 = rng.standard_normal(s.n_cols)
+    ud = torch.tensor(u, device="cuda")
+    zd = torch.tensor(x0, device="cuda")
+    ctx.aprod2(ud, zd)
+    want2 = oracle.aprod2(s, u, x0.copy())
+    scale2 = oracle.aprod2(abs_system(s), np.abs(u), np.abs(x0).copy())
+    _check(zd.cpu().numpy(), want2, scale2)
+    ctx.close()
+
+
+def test_aprod2_astro_reproducible_rest_close():
+    h = gsrgen.generate(CASES["c1"])
+    s = oracle.from_host_system(h)
+    ctx = context_for(h)
+    ctx.set_system(h.A, h.knot, h.instr)
+    u = torch.randn(s.n_rows, dtype=torch.float64, device="cuda")
+    outs = []
+    for _ in range(3):
+        z = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+        ctx.aprod2(u, z)
+        outs.append(z.cpu().numpy())
+    a = 5 * s.n_stars
+    for o in outs[1:]:
+        assert np.array_equal(o[:a], outs[0][:a])  # astro: one warp per star, no atomics
+        np.testing.assert_allclose(o[a:], outs[0][a:], rtol=1e-13, atol=1e-13)
+    ctx.close()
+
+
+def test_device_soa_input_and_chunks():
+    """Rows loaded from device SoA planes in two chunks equal the host AoS load."""
+    cfg = CASES["ragged_many"]
+    h = gsrgen.generate(cfg)
+    s = oracle.from_host_system(h)
+    ctx = context_for(h)
+    n = s.n_rows
+    stride = n + 5
+    vals = torch.zeros(24 * stride, dtype=torch.float64, device="cuda")
+    ins = torch.zeros(6 * stride, dtype=torch.int32, device="cuda")
+    A = torch.tensor(h.A, device="cuda")
+    I = torch.tensor(h.instr, device="cuda")
+    for j in range(24):
+        vals[j * stride:j * stride + n] = A[:, j]
+    for j in range(6):
+        ins[j * stride:j * stride + n] = I[:, j]
+    knot = torch.tensor(h.knot, device="cuda")
+    cut = n // 3
+    ctx.set_rows(cut, n - cut, vals[cut:], knot[cut:], ins[cut:], layout=g.GSR_SOA, plane_stride=stride)
+    with pytest.raises(g.GsrError) as e:
+        ctx.aprod1(torch.zeros(s.n_cols, dtype=torch.float64, device="cuda"),
+                   torch.zeros(n, dtype=torch.float64, device="cuda"))
+    assert e.value.status == g.Status.ESTATE
+    ctx.set_rows(0, cut, vals, knot, ins, layout=g.GSR_SOA, plane_stride=stride)
+    x = np.random.default_rng(4).standard_normal(s.n_cols)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.aprod1(torch.tensor(x, device="cuda"), y)
+    want = oracle.aprod1(s, x, np.zeros(n))
+    scale = oracle.aprod1(abs_system(s), np.abs(x), np.zeros(n))
+    _check(y.cpu().numpy(), want, scale)
+    ctx.close()
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_validation_rejects_bad_rows(where):
+    cfg = CASES["tiny"]
+    h = gsrgen.generate(cfg)
+    ctx = context_for(h)
+
+    def put(A, knot, instr):
+        if where == "device":
+            A, knot, instr = (torch.tensor(a, device="cuda") for a in (A, knot, instr))
+        ctx.set_system(A, knot, instr)
+
+    bad = h.knot.copy()
+    bad[17] = cfg.n_dfa - 3
+    with pytest.raises(g.GsrError) as e:
+        put(h.A, bad, h.instr)
+    assert e.value.status == g.Status.EINVAL
+    bad = h.knot.copy()
+    bad[3] = -1
+    with pytest.raises(g.GsrError) as e:
+        put(h.A, bad, h.instr)
+    assert e.value.status == g.Status.EINVAL
+    badi = h.instr.copy()
+    badi[5, 2] = cfg.n_instr
+    with pytest.raises(g.GsrError) as e:
+        put(h.A, h.knot, badi)
+    assert e.value.status == g.Status.EINVAL
+    badA = h.A.copy()
+    badA[9, 11] = np.nan
+    with pytest.raises(g.GsrError) as e:
+        put(badA, h.knot, h.instr)
+    assert e.value.status == g.Status.ENUMERIC
+    # nothing was committed: aprod still refuses
+    with pytest.raises(g.GsrError) as e:
+        ctx.aprod1(torch.zeros(ctx.n_cols, dtype=torch.float64, device="cuda"),
+                   torch.zeros(ctx.n_rows, dtype=torch.float64, device="cuda"))
+    assert e.value.status == g.Status.ESTATE
+    put(h.A, h.knot, h.instr)
+    b = np.ones(ctx.n_rows)
+    b[4] = np.inf
+    with pytest.raises(g.GsrError) as e:
+        ctx.set_rhs(b)
+    assert e.value.status == g.Status.ENUMERIC
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(np.zeros(ctx.n_cols))
+    assert e.value.status == g.Status.ESTATE
+    ctx.close()

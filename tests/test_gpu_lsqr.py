@@ -1,0 +1,127 @@
+"""The GPU LSQR solve against the CPU oracle.
+
+Fixed iteration counts (tolerances off) compare the same iterate; converged
+runs compare the solutions. Bar: relative error per block (astro, attitude,
+instrumental, global) <= 1e-10, |x_blk - x_oracle_blk| / max(|x_oracle_blk|, 1e-3).
+Both sides compute in binary64; atomics reorder the attitude / instrumental /
+global sums in the GPU aprod 2, so iterates agree to rounding, not bitwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gsrgen
+import oracle
+import paper_2308_00778_gb300 as g
+from gpu_util import block_errors, context_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(cfg, fp32=False):
+    h = gsrgen.generate(cfg, fp32=fp32)
+    s = oracle.from_host_system(h)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    ctx = context_for(h, fp32=fp32)
+    ctx.set_system(h.A32 if fp32 else h.A, h.knot, h.instr, b)
+    return h, s, b, ctx
+
+
+@pytest.mark.parametrize("itn", [1, 2, 10, 50])
+def test_fixed_iterations_c1(itn):
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup(w.cfg)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, itnlim=itn, atol=0.0, btol=0.0, conlim=0.0, damp=w.damp)
+    xo, io = oracle.lsqr(s, b, itn, 0.0, 0.0, 0.0, w.damp)
+    assert info["itn"] == itn and info["istop"] == 7
+    for k, e in block_errors(x, xo, s).items():
+        assert e <= 1e-10, (k, e)
+    for key in ("r1norm", "r2norm", "anorm", "acond", "arnorm", "xnorm"):
+        assert info[key] == pytest.approx(io[key], rel=1e-9), key
+    ctx.close()
+
+
+def test_converged_c1():
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup(w.cfg)
+    x = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, itnlim=w.itnlim, atol=w.atol, btol=w.btol, conlim=1e12, damp=w.damp)
+    xo, io = oracle.lsqr(s, b, w.itnlim, w.atol, w.btol, 1e12, w.damp)
+    assert info["istop"] in (1, 2) and abs(info["itn"] - io["itn"]) <= 1
+    for k, e in block_errors(x.cpu().numpy(), xo, s).items():
+        assert e <= 1e-10, (k, e)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["ragged_damped", "noprecond", "fp32_storage", "many_blocks"])
+def test_variants_vs_oracle(case):
+    damp, precond, fp32, itn = 1e-6, True, False, 60
+    cfg = gsrgen.make_cfg(41, 300, (1, 120), 40, 17)
+    if case == "ragged_damped":
+        damp = 0.3
+    elif case == "noprecond":
+        precond = False
+    elif case == "fp32_storage":
+        fp32 = True
+    elif case == "many_blocks":
+        cfg = gsrgen.make_cfg(42, 20000, (20, 60), 600, 300, att_kind=1)
+        itn = 30
+    h, s, b, ctx = _setup(cfg, fp32=fp32)
+    x = np.zeros(s.n_cols)
+    ctx.solve(x, itnlim=itn, atol=0.0, btol=0.0, conlim=0.0, damp=damp, precond=1 if precond else 0, graph_k=7)
+    xo, _ = oracle.lsqr(s, b, itn, 0.0, 0.0, 0.0, damp, precond=precond)
+    for k, e in block_errors(x, xo, s).items():
+        assert e <= 1e-10, (case, k, e)
+    ctx.close()
+
+
+def test_standard_errors_and_warm_start():
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup(w.cfg)
+    x = np.zeros(s.n_cols)
+    se = np.zeros(s.n_cols)
+    info = ctx.solve(x, se_out=se, itnlim=40, atol=0.0, btol=0.0, conlim=0.0, damp=w.damp)
+    xo, io, var = oracle.lsqr(s, b, 40, 0.0, 0.0, 0.0, w.damp, want_var=True)
+    se_o = np.sqrt(var) * abs(io["r1norm"]) / np.sqrt(s.n_rows - s.n_cols)
+    np.testing.assert_allclose(se, se_o, rtol=1e-9)
+    # warm start from x0: LSQR solves for the correction; the converged result matches the cold solve
+    x0 = xo + 1e-3 * np.random.default_rng(0).standard_normal(s.n_cols)
+    x1 = np.zeros(s.n_cols)
+    ctx.solve(x1, x0=x0, itnlim=w.itnlim, atol=w.atol, btol=w.btol, conlim=1e12, damp=w.damp)
+    xc, _ = oracle.lsqr(s, b, w.itnlim, w.atol, w.btol, 1e12, w.damp)
+    for k, e in block_errors(x1, xc, s).items():
+        assert e <= 1e-9, (k, e)
+    ctx.close()
+
+
+def test_edge_cases():
+    cfg = gsrgen.make_cfg(7, 20, 30, 12, 8)
+    h, s, b, ctx = _setup(cfg)
+    x = np.ones(s.n_cols)
+    info = ctx.solve(x, itnlim=0)
+    assert info["itn"] == 0 and not x.any()
+    ctx.set_rhs(np.zeros(s.n_rows))
+    x = np.ones(s.n_cols)
+    info = ctx.solve(x, itnlim=10)
+    assert info["istop"] == 0 and info["itn"] == 0 and not x.any()
+    ctx.set_rhs(b)
+    info = ctx.solve(x, itnlim=5, atol=0.0, btol=0.0)
+    assert info["istop"] == 7 and info["itn"] == 5
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(x, itnlim=1000, atol=0.0, btol=0.0, timeout_s=1e-9, graph_k=1)
+    assert e.value.status == g.Status.ETIMEOUT
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(x, mode=g.GSR_MIXED)  # FP64-stored context
+    assert e.value.status == g.Status.EINVAL
+    ctx.close()
+
+
+def test_noise_free_planted_recovery():
+    cfg = gsrgen.make_cfg(8, 40, 40, 20, 10, noise_sigma=0.0)
+    h, s, b, ctx = _setup(cfg)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, itnlim=2000, atol=1e-15, btol=1e-15, damp=0.0)
+    for k, e in block_errors(x, h.x_true, s).items():
+        assert e <= 1e-10, (k, e)
+    ctx.close()
