@@ -11,14 +11,17 @@
 // LSQR form it computes u <- A (p v) + coef * u and emits per-block sums of
 // squares of the new u (the norm beta).
 //
-// aprod 2: the astrometric part is a per-star register accumulation and one
-// warp reduction per star, written without atomics (one warp owns a star).
-// Attitude and instrumental products go to block-private shared-memory
-// accumulators when they fit (flushed once per block with atomic adds),
-// otherwise straight to global memory with atomic adds resolved in L2. The
-// global column is reduced per block in registers and added once per block
-// (the two-stage reduction of the paper's global kernels, Sec. 4.2, folded
-// into one pass).
+// aprod 2 runs as two passes. The star-ordered pass reads the astrometric,
+// instrumental and global coefficients: the astrometric part is a per-star
+// register accumulation and one warp reduction per star, written without
+// atomics (one warp owns a star); instrumental products go to block-private
+// shared-memory accumulators flushed once per block (global atomic adds when
+// n_instr is too large); the global column is reduced per block and added
+// once per block (the two-stage reduction of the paper's global kernels,
+// Sec. 4.2, folded into one pass). The attitude pass reads the knot-ordered
+// copy of the 12 attitude coefficients (layout.cu) and gathers y through the
+// row permutation: runs of equal knot are summed in registers and added once
+// per run, instead of 12 atomic adds per row.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -89,34 +92,36 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const double *__r
     }
 }
 
-template <typename VT, bool ATT_SMEM, bool INSTR_SMEM, bool SQUARE, bool LSQR>
-__global__ void __launch_bounds__(256) k_aprod2(SysView<VT> S, const double *__restrict__ y, double *__restrict__ z,
-                                                const LsqrState *__restrict__ st)
+// aprod 2, star-ordered pass: astrometric (per-star warp reduction, no atomics),
+// instrumental (block-private shared-memory accumulators, or global atomics
+// when n_instr is too large) and global (block reduction) parts.
+template <typename VT, bool INSTR_SMEM, bool SQUARE, bool LSQR>
+__global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const double *__restrict__ y,
+                                                     double *__restrict__ z, const LsqrState *__restrict__ st)
 {
     extern __shared__ double smem[];
     __shared__ double sm32[32];
     if (LSQR && st->done) return;
-    const int32_t n_att = NAXES * S.n_dfa;
-    double *sm_att = smem;
-    double *sm_ins = smem + (ATT_SMEM ? n_att : 0);
-    const int32_t nsm = (ATT_SMEM ? n_att : 0) + (INSTR_SMEM ? S.n_instr : 0);
+    double *sm_ins = smem;
+    const int32_t nsm = INSTR_SMEM ? S.n_instr : 0;
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0.0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double *__restrict__ zt = z + S.att0;
     double *__restrict__ zi = z + S.instr0;
     double gsum = 0.0;
     for (int64_t s = gw; s < S.n_stars; s += nw) {
         const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
         double acc[NASTRO] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int64_t r = r0 + lane; r < r1; r += 32) {
-            double a[NPAR];
+            double a[NASTRO], ai[NINSTR];
 #pragma unroll
-            for (int j = 0; j < NPAR; ++j) a[j] = (double)ld_stream(S.val + j * S.plane + r);
-            const int32_t k = ld_stream(S.knot + r);
+            for (int j = 0; j < NASTRO; ++j) a[j] = (double)ld_stream(S.val + j * S.plane + r);
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) ai[j] = (double)ld_stream(S.val + (17 + j) * S.plane + r);
+            double ag = (double)ld_stream(S.val + 23 * S.plane + r);
             int32_t ic[NINSTR];
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) ic[j] = ld_stream(S.instr + j * S.plane + r);
@@ -124,33 +129,24 @@ __global__ void __launch_bounds__(256) k_aprod2(SysView<VT> S, const double *__r
             if (SQUARE) {
                 yr = 1.0;
 #pragma unroll
-                for (int j = 0; j < NPAR; ++j) a[j] = a[j] * a[j];
+                for (int j = 0; j < NASTRO; ++j) a[j] = a[j] * a[j];
+#pragma unroll
+                for (int j = 0; j < NINSTR; ++j) ai[j] = ai[j] * ai[j];
+                ag = ag * ag;
             } else {
                 yr = y[r];
             }
 #pragma unroll
             for (int j = 0; j < NASTRO; ++j) acc[j] = fma(a[j], yr, acc[j]);
 #pragma unroll
-            for (int ax = 0; ax < NAXES; ++ax) {
-                const int32_t base = ax * S.n_dfa + k;
-#pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) {
-                    const double pr = a[NASTRO + NPARAXIS * ax + j] * yr;
-                    if (ATT_SMEM)
-                        atomicAdd(sm_att + base + j, pr);
-                    else
-                        atomicAdd(zt + base + j, pr);
-                }
-            }
-#pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
-                const double pr = a[17 + j] * yr;
+                const double pr = ai[j] * yr;
                 if (INSTR_SMEM)
                     atomicAdd(sm_ins + ic[j], pr);
                 else
                     atomicAdd(zi + ic[j], pr);
             }
-            gsum = fma(a[23], yr, gsum);
+            gsum = fma(ag, yr, gsum);
         }
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) acc[j] = warp_sum(acc[j]);
@@ -164,17 +160,94 @@ __global__ void __launch_bounds__(256) k_aprod2(SysView<VT> S, const double *__r
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
         const double v = smem[i];
-        if (v != 0.0) {
-            if (ATT_SMEM && i < n_att)
-                atomicAdd(zt + i, v);
-            else
-                atomicAdd(zi + (i - (ATT_SMEM ? n_att : 0)), v);
-        }
+        if (v != 0.0) atomicAdd(zi + i, v);
     }
     if (S.n_glob) {
         const double t = block_sum(gsum, sm32);
         if (threadIdx.x == 0 && t != 0.0) atomicAdd(z + S.glob0, t);
     }
+}
+
+// Add a warp's run sums of the 12 attitude columns of knot k (warp-collective).
+__device__ __forceinline__ void flush_att_run(double (&acc)[NAXES * NPARAXIS], int32_t k, int32_t n_dfa,
+                                              double *__restrict__ zt)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NAXES * NPARAXIS; ++j) {
+        const double t = warp_sum(acc[j]);
+        if (lane == 0 && t != 0.0) atomicAdd(zt + (j / NPARAXIS) * n_dfa + k + (j % NPARAXIS), t);
+        acc[j] = 0.0;
+    }
+}
+
+// aprod 2, attitude pass over the knot-ordered copy: each warp owns a
+// contiguous range of positions; runs of equal knot are summed in registers
+// and added once per run (one atomic add per column per run).
+template <typename VT, bool SQUARE, bool LSQR>
+__global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const double *__restrict__ y,
+                                                    double *__restrict__ z, const LsqrState *__restrict__ st,
+                                                    int64_t per_warp)
+{
+    if (LSQR && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n = S.n_rows;
+    const int64_t p0 = gw * per_warp;
+    if (p0 >= n) return;
+    const int64_t p1 = min(n, p0 + per_warp);
+    const int32_t nk = S.n_dfa - 3;
+    // knot of p0: the largest k with knot_ptr[k] <= p0
+    int32_t lo = 0, hi = nk - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (S.knot_ptr[mid] <= p0)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int32_t k = lo;
+    int64_t next = S.knot_ptr[k + 1];
+    double *__restrict__ zt = z + S.att0;
+    double acc[NAXES * NPARAXIS];
+#pragma unroll
+    for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = 0.0;
+    for (int64_t q = p0; q < p1; q += 32) {
+        const int64_t i = q + lane;
+        const bool active = i < p1;
+        const int64_t last = min(q + 31, p1 - 1);
+        double a[NAXES * NPARAXIS];
+        double yr = 0.0;
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = (double)ld_stream(S.att_k + j * S.plane + i);
+            if (SQUARE) {
+                yr = 1.0;
+#pragma unroll
+                for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = a[j] * a[j];
+            } else {
+                yr = y[ld_stream(S.perm + i)];
+            }
+        }
+        if (last < next) {  // every position of this step is on knot k
+            if (active) {
+#pragma unroll
+                for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = fma(a[j], yr, acc[j]);
+            }
+        } else {  // the step crosses knot boundaries
+            flush_att_run(acc, k, S.n_dfa, zt);
+            int32_t kl = k;
+            if (active) {
+                while (S.knot_ptr[kl + 1] <= i) ++kl;
+#pragma unroll
+                for (int j = 0; j < NAXES * NPARAXIS; ++j)
+                    atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), a[j] * yr);
+            }
+            k = __shfl_sync(0xffffffffu, kl, (int)(last - q));
+            next = S.knot_ptr[k + 1];
+        }
+    }
+    flush_att_run(acc, k, S.n_dfa, zt);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -224,11 +297,12 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const double *x, double *y, const Ls
     return c->prec == GSR_FP32 ? aprod1_t<float>(c, x, y, st, part, s) : aprod1_t<double>(c, x, y, st, part, s);
 }
 
-template <typename VT, bool ATT, bool INS, bool SQ, bool LS>
-static cudaError_t aprod2_launch(const gsr_ctx *c, const double *y, double *x, const LsqrState *st, cudaStream_t s)
+template <typename VT, bool INS, bool SQ, bool LS>
+static cudaError_t aprod2_star_launch(const gsr_ctx *c, const double *y, double *x, const LsqrState *st,
+                                      cudaStream_t s)
 {
-    auto kern = k_aprod2<VT, ATT, INS, SQ, LS>;
-    const size_t dyn = sizeof(double) * ((ATT ? (size_t)NAXES * c->n_dfa : 0) + (INS ? (size_t)c->n_instr : 0));
+    auto kern = k_aprod2_star<VT, INS, SQ, LS>;
+    const size_t dyn = INS ? sizeof(double) * (size_t)c->n_instr : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -239,13 +313,27 @@ static cudaError_t aprod2_launch(const gsr_ctx *c, const double *y, double *x, c
 }
 
 template <typename VT, bool SQ, bool LS>
-static cudaError_t aprod2_modes(const gsr_ctx *c, const double *y, double *x, const LsqrState *st, cudaStream_t s)
+static cudaError_t aprod2_t(const gsr_ctx *c, const double *y, double *x, const LsqrState *st, cudaStream_t s)
 {
-    const size_t att_b = sizeof(double) * (size_t)NAXES * c->n_dfa;
-    const size_t ins_b = sizeof(double) * (size_t)c->n_instr;
-    if (att_b + ins_b <= kSmemBudget) return aprod2_launch<VT, true, true, SQ, LS>(c, y, x, st, s);
-    if (ins_b <= kSmemBudget) return aprod2_launch<VT, false, true, SQ, LS>(c, y, x, st, s);
-    return aprod2_launch<VT, false, false, SQ, LS>(c, y, x, st, s);
+    cudaError_t e;
+    if (sizeof(double) * (size_t)c->n_instr <= kSmemBudget)
+        e = aprod2_star_launch<VT, true, SQ, LS>(c, y, x, st, s);
+    else
+        e = aprod2_star_launch<VT, false, SQ, LS>(c, y, x, st, s);
+    if (e != cudaSuccess) return e;
+    // attitude pass: at least 256 positions per warp
+    auto kern = k_aprod2_att<VT, SQ, LS>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t wpb = kThreads / 32;
+    const int64_t max_warps = (int64_t)per_sm * c->sm_count * wpb;
+    int64_t per = (c->n_rows + max_warps - 1) / max_warps;
+    if (per < 256) per = 256;
+    const int64_t warps = (c->n_rows + per - 1) / per;
+    const int64_t blocks = (warps + wpb - 1) / wpb;
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), y, x, st, per);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool square, const LsqrState *st,
@@ -253,13 +341,13 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool squ
 {
     if (c->n_rows == 0) return cudaSuccess;
     if (c->prec == GSR_FP32) {
-        if (square) return aprod2_modes<float, true, false>(c, y, x, nullptr, s);
-        if (st) return aprod2_modes<float, false, true>(c, y, x, st, s);
-        return aprod2_modes<float, false, false>(c, y, x, nullptr, s);
+        if (square) return aprod2_t<float, true, false>(c, y, x, nullptr, s);
+        if (st) return aprod2_t<float, false, true>(c, y, x, st, s);
+        return aprod2_t<float, false, false>(c, y, x, nullptr, s);
     }
-    if (square) return aprod2_modes<double, true, false>(c, y, x, nullptr, s);
-    if (st) return aprod2_modes<double, false, true>(c, y, x, st, s);
-    return aprod2_modes<double, false, false>(c, y, x, nullptr, s);
+    if (square) return aprod2_t<double, true, false>(c, y, x, nullptr, s);
+    if (st) return aprod2_t<double, false, true>(c, y, x, st, s);
+    return aprod2_t<double, false, false>(c, y, x, nullptr, s);
 }
 
 }  // namespace gsr

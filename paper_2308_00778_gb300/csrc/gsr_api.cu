@@ -132,24 +132,33 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
     return GSR_OK;
 }
 
-// host input: validate on the host first (nothing is written on error), then
-// stage chunks to the device and convert them there.
+// host input. When the rows fit in a quarter of the free device memory they
+// are staged whole, validated on the device and converted (nothing is written
+// on error). Otherwise they are validated on the host first, then staged and
+// converted chunk by chunk.
 template <typename ST>
 static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, int32_t layout,
                                 int64_t vstride, const int32_t *knot, const int32_t *instr, cudaStream_t s)
 {
-    for (int64_t r = 0; r < nrows; ++r) {
-        if (knot[r] < 0 || knot[r] > c->n_dfa - 4) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
-        for (int j = 0; j < NINSTR; ++j) {
-            const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
-            if (ic < 0 || ic >= c->n_instr) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
-        }
-        for (int j = 0; j < NPAR; ++j) {
-            const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
-            if (!std::isfinite(v)) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
+    const size_t row_bytes = sizeof(ST) * NPAR + sizeof(int32_t) * (1 + NINSTR);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const bool whole = (size_t)nrows * row_bytes <= free_b / 4;
+    if (!whole) {
+        for (int64_t r = 0; r < nrows; ++r) {
+            if (knot[r] < 0 || knot[r] > c->n_dfa - 4)
+                return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
+            for (int j = 0; j < NINSTR; ++j) {
+                const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+                if (ic < 0 || ic >= c->n_instr) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
+            }
+            for (int j = 0; j < NPAR; ++j) {
+                const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
+                if (!std::isfinite(v)) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
+            }
         }
     }
-    const int64_t chunk = std::min<int64_t>(nrows, 1 << 21);
+    const int64_t chunk = whole ? nrows : std::min<int64_t>(nrows, 1 << 21);
     ST *dv = nullptr;
     int32_t *dk = nullptr, *di = nullptr;
     cudaError_t e;
@@ -180,15 +189,8 @@ static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const S
             rc = cuda_fail(c, e, "row upload");
             break;
         }
-        const int g = grid_for(c, m);
-        if (c->prec == GSR_FP32)
-            k_convert<ST, float><<<g, 256, 0, s>>>(dv, layout, m, dk, di, m, c->n_glob, (float *)c->vals, c->knot,
-                                                    c->instr, c->plane, row0 + r);
-        else
-            k_convert<ST, double><<<g, 256, 0, s>>>(dv, layout, m, dk, di, m, c->n_glob, (double *)c->vals, c->knot,
-                                                     c->instr, c->plane, row0 + r);
-        if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
-            rc = cuda_fail(c, e, "conversion");
+        // device-resident staged rows: validate then convert, exactly as for device input
+        rc = set_rows_device<ST>(c, row0 + r, m, dv, layout, m, dk, di, s);
     }
     cudaFree(dv);
     cudaFree(dk);
@@ -264,6 +266,9 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
         (e = cudaMalloc(&c->star_ptr, sizeof(int64_t) * (size_t)(n_stars + 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->b, sizeof(double) * (size_t)std::max<int64_t>(c->n_rows, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->errw, 4 * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&c->att_k, vbytes / NPAR * (NAXES * NPARAXIS))) != cudaSuccess ||
+        (e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)c->plane)) != cudaSuccess ||
+        (e = cudaMalloc(&c->knot_ptr, sizeof(int64_t) * (size_t)(n_dfa - 2))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess) {
         cudaGetLastError();
@@ -297,6 +302,9 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->star_ptr);
     cudaFree(c->b);
     cudaFree(c->errw);
+    cudaFree(c->att_k);
+    cudaFree(c->perm);
+    cudaFree(c->knot_ptr);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->ev) cudaEventDestroy(c->ev);
     cudaGetLastError();
@@ -338,7 +346,10 @@ GSR_API gsr_status gsr_set_rows(gsr_ctx *c, int64_t row0, int64_t nrows, const v
                                                 instr_col, s)
                          : set_rows_host<double>(c, row0, nrows, (const double *)values, layout, plane_stride,
                                                  att_knot, instr_col, s);
-    if (rc == GSR_OK) mark_rows(c, row0, row0 + nrows);
+    if (rc == GSR_OK) {
+        mark_rows(c, row0, row0 + nrows);
+        c->att_valid = false;
+    }
     return rc;
 }
 
@@ -403,8 +414,11 @@ GSR_API gsr_status gsr_aprod2(gsr_ctx *c, const double *y, double *x, void *stre
     if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
     if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
     cudaError_t e = cudaSetDevice(c->device);
-    if (e == cudaSuccess) e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "aprod2");
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream);
+    if (rc != GSR_OK) return rc;
+    if ((e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(c, e, "aprod2");
     return GSR_OK;
 }
 
@@ -434,5 +448,13 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     if ((e = cudaEventRecord(c->ev, (cudaStream_t)stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(c->own, c->ev, 0)) != cudaSuccess)
         return cuda_fail(c, e, "stream ordering");
-    return lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
+    {
+        const gsr_status rl = ensure_att_layout(c, c->own);
+        if (rl != GSR_OK) return rl;
+    }
+    const gsr_status rc = lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
+    // the caller's stream continues after the solve's last kernel
+    if (cudaEventRecord(c->ev, c->own) == cudaSuccess) cudaStreamWaitEvent((cudaStream_t)stream, c->ev, 0);
+    cudaGetLastError();
+    return rc;
 }

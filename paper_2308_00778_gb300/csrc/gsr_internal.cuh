@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -29,6 +30,9 @@ struct SysView {
     const int32_t *__restrict__ knot;
     const int32_t *__restrict__ instr;
     const int64_t *__restrict__ star_ptr;
+    const VT *__restrict__ att_k;         // 12 knot-ordered attitude planes (layout.cu)
+    const int32_t *__restrict__ perm;     // row of each knot-ordered position
+    const int64_t *__restrict__ knot_ptr; // first position of each knot, [n_dfa-2]
     int64_t plane;
     int64_t n_stars, n_rows;
     int32_t n_dfa, n_instr, n_glob;
@@ -81,6 +85,10 @@ struct gsr_ctx {
     void *vals = nullptr;            // 24 planes of double or float
     int32_t *knot = nullptr;         // 1 plane
     int32_t *instr = nullptr;        // 6 planes
+    void *att_k = nullptr;           // 12 knot-ordered attitude planes (same type as vals)
+    int32_t *perm = nullptr;         // row of each knot-ordered position
+    int64_t *knot_ptr = nullptr;     // [n_dfa-2] first position of each knot
+    bool att_valid = false;          // att_k / perm / knot_ptr match the loaded rows
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -109,6 +117,9 @@ SysView<VT> view(const gsr_ctx *c)
     s.knot = c->knot;
     s.instr = c->instr;
     s.star_ptr = c->star_ptr;
+    s.att_k = static_cast<const VT *>(c->att_k);
+    s.perm = c->perm;
+    s.knot_ptr = c->knot_ptr;
     s.plane = c->plane;
     s.n_stars = c->n_stars;
     s.n_rows = c->n_rows;
@@ -127,6 +138,9 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const double *x, double *y, const Ls
 cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool square, const LsqrState *st,
                           cudaStream_t s);
 int aprod1_grid(const gsr_ctx *c);
+
+// knot-ordered attitude copy (layout.cu); built once per loaded system
+gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s);
 
 // LSQR driver (lsqr.cu)
 gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,

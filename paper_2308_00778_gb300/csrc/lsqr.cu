@@ -279,7 +279,6 @@ __global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, const do
                        const LsqrState *__restrict__ st, int32_t first)
 {
     if (!first && st->colb_skip) return;
-    if (first && st->done) return;
     const double ia = st->inv_alpha;
     const double t1 = st->t1, t2 = st->t2, ir = st->inv_rho;
     const bool has_alpha = st->alpha > 0.0;
