@@ -137,6 +137,30 @@ gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
  */
 gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
 
+/*
+ * gsr_aprod1_f32 -- y += A x in binary32 arithmetic (the kernel of the inner
+ * solves of GSR_MIXED; Eq. 2). FP32-stored contexts only (GSR_EINVAL
+ * otherwise).
+ *   x  device array of n_cols binary32.   y  device array of n_rows binary32.
+ */
+gsr_status gsr_aprod1_f32(gsr_ctx *ctx, const float *x, float *y, void *stream);
+
+/*
+ * gsr_aprod2_f32 -- x += A^T y with binary32 products and per-block binary32
+ * partial sums added into binary64 x (Eq. 3). FP32-stored contexts only.
+ *   y  device array of n_rows binary32.   x  device array of n_cols binary64.
+ */
+gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream);
+
+/*
+ * gsr_residual -- r = b - A x for the loaded b, with every product and sum
+ * carried in double-float (pairs of binary32 with error-free transforms:
+ * about 2^-44 relative to the sum of |terms|), the outer residual of the
+ * GSR_MIXED refinement. FP32-stored contexts only; b must be loaded.
+ *   x  device array of n_cols binary64.   r  device array of n_rows binary32.
+ */
+gsr_status gsr_residual(gsr_ctx *ctx, const double *x, float *r, void *stream);
+
 typedef struct {
     int32_t itnlim;     /* maximum LSQR iterations (>= 0)                               */
     double atol, btol;  /* Paige-Saunders tolerances (0 disables the test)              */

@@ -11,6 +11,12 @@
 // LSQR form it computes u <- A (p v) + coef * u and emits per-block sums of
 // squares of the new u (the norm beta).
 //
+// Every kernel is templated on the stored value type VT, the type of the
+// gathered / streamed vectors (XT for x in aprod 1, UT for the row vector) and
+// the arithmetic type AT: binary64 for the plain solver (on FP64- or
+// FP32-stored values) and binary32 throughout for the inner solve of the
+// mixed-precision solver. Column accumulators (z) are always binary64.
+//
 // aprod 2 runs as two passes. The star-ordered pass reads the astrometric,
 // instrumental and global coefficients: the astrometric part is a per-star
 // register accumulation and one warp reduction per star, written without
@@ -32,62 +38,82 @@ __device__ __forceinline__ T ld_stream(const T *p)
     return __ldcs(p);
 }
 
-template <typename VT, bool LSQR>
-__global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const double *__restrict__ x, double *__restrict__ y,
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// STAGE: the attitude and instrumental parts of x (3 n_dfa + n_instr values)
+// are copied into shared memory once per block; the per-row gathers then hit
+// shared memory instead of issuing scattered L1 requests.
+template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool STAGE>
+__global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm32[32];
-    double coef = 1.0;
+    AT coef = (AT)1;
     if (LSQR) {
         if (st->done) return;  // same value for every thread of the grid
-        coef = st->coef_u;
+        coef = (AT)st->coef_u;
     }
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double *__restrict__ xt = x + S.att0;
-    const double *__restrict__ xi = x + S.instr0;
-    const double xg = S.n_glob ? __ldg(x + S.glob0) : 0.0;
-    double ssq = 0.0;
+    const XT *__restrict__ xt = x + S.att0;
+    const XT *__restrict__ xi = x + S.instr0;
+    if (STAGE) {
+        XT *sx = reinterpret_cast<XT *>(smem_raw);
+        const int32_t n_att = NAXES * S.n_dfa, n_st = n_att + S.n_instr;
+        for (int32_t i = threadIdx.x; i < n_st; i += blockDim.x) sx[i] = x[S.att0 + i];
+        __syncthreads();
+        xt = sx;
+        xi = sx + n_att;
+    }
+    const AT xg = S.n_glob ? (AT)__ldg(x + S.glob0) : (AT)0;
+    AT ssq = (AT)0;
     for (int64_t s = gw; s < S.n_stars; s += nw) {
         const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        const double *__restrict__ xa = x + NASTRO * s;
-        const double xa0 = __ldg(xa + 0), xa1 = __ldg(xa + 1), xa2 = __ldg(xa + 2), xa3 = __ldg(xa + 3),
-                     xa4 = __ldg(xa + 4);
+        const XT *__restrict__ xa = x + NASTRO * s;
+        const AT xa0 = (AT)__ldg(xa + 0), xa1 = (AT)__ldg(xa + 1), xa2 = (AT)__ldg(xa + 2),
+                 xa3 = (AT)__ldg(xa + 3), xa4 = (AT)__ldg(xa + 4);
         for (int64_t r = r0 + lane; r < r1; r += 32) {
-            double a[NPAR];
+            AT a[NPAR];
 #pragma unroll
-            for (int j = 0; j < NPAR; ++j) a[j] = (double)ld_stream(S.val + j * S.plane + r);
+            for (int j = 0; j < NPAR; ++j) a[j] = (AT)ld_stream(S.val + j * S.plane + r);
             const int32_t k = ld_stream(S.knot + r);
             int32_t ic[NINSTR];
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) ic[j] = ld_stream(S.instr + j * S.plane + r);
-            double sum = a[0] * xa0;
+            AT sum = a[0] * xa0;
             sum = fma(a[1], xa1, sum);
             sum = fma(a[2], xa2, sum);
             sum = fma(a[3], xa3, sum);
             sum = fma(a[4], xa4, sum);
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
-                const double *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + k;
+                const XT *xk = xt + (int64_t)ax * S.n_dfa + k;
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) sum = fma(a[NASTRO + NPARAXIS * ax + j], __ldg(xk + j), sum);
+                for (int j = 0; j < NPARAXIS; ++j) sum = fma(a[NASTRO + NPARAXIS * ax + j], (AT)xk[j], sum);
             }
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) sum = fma(a[17 + j], __ldg(xi + ic[j]), sum);
+            for (int j = 0; j < NINSTR; ++j) sum = fma(a[17 + j], (AT)xi[ic[j]], sum);
             sum = fma(a[23], xg, sum);
-            double yn;
+            AT yn;
             if (LSQR) {
-                yn = fma(coef, y[r], sum);
+                yn = fma(coef, (AT)y[r], sum);
                 ssq = fma(yn, yn, ssq);
             } else {
-                yn = y[r] + sum;
+                yn = (AT)y[r] + sum;
             }
-            y[r] = yn;
+            y[r] = (UT)yn;
         }
     }
     if (LSQR) {
-        const double t = block_sum(ssq, sm32);
+        const double t = block_sum((double)ssq, sm32);
         if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
 }
@@ -95,97 +121,98 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const double *__r
 // aprod 2, star-ordered pass: astrometric (per-star warp reduction, no atomics),
 // instrumental (block-private shared-memory accumulators, or global atomics
 // when n_instr is too large) and global (block reduction) parts.
-template <typename VT, bool INSTR_SMEM, bool SQUARE, bool LSQR>
-__global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const double *__restrict__ y,
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, bool SQUARE, bool LSQR>
+__global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
                                                      double *__restrict__ z, const LsqrState *__restrict__ st)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm32[32];
     if (LSQR && st->done) return;
-    double *sm_ins = smem;
+    AT *sm_ins = reinterpret_cast<AT *>(smem_raw);
     const int32_t nsm = INSTR_SMEM ? S.n_instr : 0;
-    for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) smem[i] = 0.0;
+    for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double *__restrict__ zi = z + S.instr0;
-    double gsum = 0.0;
+    AT gsum = (AT)0;
     for (int64_t s = gw; s < S.n_stars; s += nw) {
         const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        double acc[NASTRO] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        AT acc[NASTRO] = {(AT)0, (AT)0, (AT)0, (AT)0, (AT)0};
         for (int64_t r = r0 + lane; r < r1; r += 32) {
-            double a[NASTRO], ai[NINSTR];
+            AT a[NASTRO], ai[NINSTR];
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) a[j] = (double)ld_stream(S.val + j * S.plane + r);
+            for (int j = 0; j < NASTRO; ++j) a[j] = (AT)ld_stream(S.val + j * S.plane + r);
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ai[j] = (double)ld_stream(S.val + (17 + j) * S.plane + r);
-            double ag = (double)ld_stream(S.val + 23 * S.plane + r);
+            for (int j = 0; j < NINSTR; ++j) ai[j] = (AT)ld_stream(S.val + (17 + j) * S.plane + r);
+            AT ag = (AT)ld_stream(S.val + 23 * S.plane + r);
             int32_t ic[NINSTR];
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) ic[j] = ld_stream(S.instr + j * S.plane + r);
-            double yr;
+            AT yr;
             if (SQUARE) {
-                yr = 1.0;
+                yr = (AT)1;
 #pragma unroll
                 for (int j = 0; j < NASTRO; ++j) a[j] = a[j] * a[j];
 #pragma unroll
                 for (int j = 0; j < NINSTR; ++j) ai[j] = ai[j] * ai[j];
                 ag = ag * ag;
             } else {
-                yr = y[r];
+                yr = (AT)y[r];
             }
 #pragma unroll
             for (int j = 0; j < NASTRO; ++j) acc[j] = fma(a[j], yr, acc[j]);
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
-                const double pr = ai[j] * yr;
+                const AT pr = ai[j] * yr;
                 if (INSTR_SMEM)
                     atomicAdd(sm_ins + ic[j], pr);
                 else
-                    atomicAdd(zi + ic[j], pr);
+                    atomicAdd(zi + ic[j], (double)pr);
             }
             gsum = fma(ag, yr, gsum);
         }
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) acc[j] = warp_sum(acc[j]);
+        for (int j = 0; j < NASTRO; ++j) acc[j] = warp_sum_t(acc[j]);
         if (lane < NASTRO) {
-            double mine = acc[0];
+            AT mine = acc[0];
 #pragma unroll
             for (int j = 1; j < NASTRO; ++j) mine = (lane == j) ? acc[j] : mine;
-            z[NASTRO * s + lane] += mine;
+            z[NASTRO * s + lane] += (double)mine;
         }
     }
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
-        const double v = smem[i];
-        if (v != 0.0) atomicAdd(zi + i, v);
+        const AT v = sm_ins[i];
+        if (v != (AT)0) atomicAdd(zi + i, (double)v);
     }
     if (S.n_glob) {
-        const double t = block_sum(gsum, sm32);
+        const double t = block_sum((double)gsum, sm32);
         if (threadIdx.x == 0 && t != 0.0) atomicAdd(z + S.glob0, t);
     }
 }
 
 // Add a warp's run sums of the 12 attitude columns of knot k (warp-collective).
-__device__ __forceinline__ void flush_att_run(double (&acc)[NAXES * NPARAXIS], int32_t k, int32_t n_dfa,
+template <typename AT>
+__device__ __forceinline__ void flush_att_run(AT (&acc)[NAXES * NPARAXIS], int32_t k, int32_t n_dfa,
                                               double *__restrict__ zt)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NAXES * NPARAXIS; ++j) {
-        const double t = warp_sum(acc[j]);
-        if (lane == 0 && t != 0.0) atomicAdd(zt + (j / NPARAXIS) * n_dfa + k + (j % NPARAXIS), t);
-        acc[j] = 0.0;
+        const AT t = warp_sum_t(acc[j]);
+        if (lane == 0 && t != (AT)0) atomicAdd(zt + (j / NPARAXIS) * n_dfa + k + (j % NPARAXIS), (double)t);
+        acc[j] = (AT)0;
     }
 }
 
 // aprod 2, attitude pass over the knot-ordered copy: each warp owns a
 // contiguous range of positions; runs of equal knot are summed in registers
 // and added once per run (one atomic add per column per run).
-template <typename VT, bool SQUARE, bool LSQR>
-__global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const double *__restrict__ y,
+template <typename VT, typename UT, typename AT, bool SQUARE, bool LSQR>
+__global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__restrict__ y,
                                                     double *__restrict__ z, const LsqrState *__restrict__ st,
                                                     int64_t per_warp)
 {
@@ -209,24 +236,24 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const double 
     int32_t k = lo;
     int64_t next = S.knot_ptr[k + 1];
     double *__restrict__ zt = z + S.att0;
-    double acc[NAXES * NPARAXIS];
+    AT acc[NAXES * NPARAXIS];
 #pragma unroll
-    for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = (AT)0;
     for (int64_t q = p0; q < p1; q += 32) {
         const int64_t i = q + lane;
         const bool active = i < p1;
         const int64_t last = min(q + 31, p1 - 1);
-        double a[NAXES * NPARAXIS];
-        double yr = 0.0;
+        AT a[NAXES * NPARAXIS];
+        AT yr = (AT)0;
         if (active) {
 #pragma unroll
-            for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = (double)ld_stream(S.att_k + j * S.plane + i);
+            for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = (AT)ld_stream(S.att_k + j * S.plane + i);
             if (SQUARE) {
-                yr = 1.0;
+                yr = (AT)1;
 #pragma unroll
                 for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = a[j] * a[j];
             } else {
-                yr = y[ld_stream(S.perm + i)];
+                yr = (AT)y[ld_stream(S.perm + i)];
             }
         }
         if (last < next) {  // every position of this step is on knot k
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const double 
                 while (S.knot_ptr[kl + 1] <= i) ++kl;
 #pragma unroll
                 for (int j = 0; j < NAXES * NPARAXIS; ++j)
-                    atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), a[j] * yr);
+                    atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), (double)(a[j] * yr));
             }
             k = __shfl_sync(0xffffffffu, kl, (int)(last - q));
             next = S.knot_ptr[k + 1];
@@ -269,60 +296,95 @@ static int persistent_blocks(const gsr_ctx *c, KernelT kern, size_t dyn_smem)
     return (int)blocks;
 }
 
-int aprod1_grid(const gsr_ctx *c)
+// bytes of shared memory that staging the gathered part of x needs (0 = too large, gather from L1)
+static constexpr size_t kStageBudget = 160 * 1024;
+
+template <typename XT>
+static size_t stage_bytes(const gsr_ctx *c)
 {
-    if (c->prec == GSR_FP32) return persistent_blocks(c, k_aprod1<float, true>, 0);
-    return persistent_blocks(c, k_aprod1<double, true>, 0);
+    const size_t b = sizeof(XT) * ((size_t)NAXES * c->n_dfa + (size_t)c->n_instr);
+    return b <= kStageBudget ? b : 0;
 }
 
-template <typename VT>
-static cudaError_t aprod1_t(const gsr_ctx *c, const double *x, double *y, const LsqrState *st, double *part,
-                            cudaStream_t s)
+template <typename VT, typename XT, typename UT, typename AT>
+static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
+                            cudaStream_t s, int *grid_out)
 {
     const SysView<VT> S = view<VT>(c);
+    const size_t dyn = stage_bytes<XT>(c);
+    auto pick = [&](auto kern) -> cudaError_t {
+        if (dyn > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+        }
+        const int g = persistent_blocks(c, kern, dyn);
+        if (grid_out) {
+            *grid_out = g;
+            return cudaSuccess;
+        }
+        if (!x || !y) return cudaErrorInvalidValue;
+        kern<<<g, kThreads, dyn, s>>>(S, (const XT *)x, (UT *)y, st, part);
+        return cudaGetLastError();
+    };
     if (st) {
-        const int g = persistent_blocks(c, k_aprod1<VT, true>, 0);
-        k_aprod1<VT, true><<<g, kThreads, 0, s>>>(S, x, y, st, part);
-    } else {
-        const int g = persistent_blocks(c, k_aprod1<VT, false>, 0);
-        k_aprod1<VT, false><<<g, kThreads, 0, s>>>(S, x, y, nullptr, nullptr);
+        if (dyn) return pick(k_aprod1<VT, XT, UT, AT, true, true>);
+        return pick(k_aprod1<VT, XT, UT, AT, true, false>);
     }
-    return cudaGetLastError();
+    if (dyn) return pick(k_aprod1<VT, XT, UT, AT, false, true>);
+    return pick(k_aprod1<VT, XT, UT, AT, false, false>);
 }
 
-cudaError_t launch_aprod1(const gsr_ctx *c, const double *x, double *y, const LsqrState *st, double *part,
-                          cudaStream_t s)
+static cudaError_t aprod1_dispatch(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
+                                   cudaStream_t s, bool inner32, int *grid_out)
+{
+    if (inner32) return aprod1_t<float, float, float, float>(c, x, y, st, part, s, grid_out);
+    if (c->prec == GSR_FP32) return aprod1_t<float, double, double, double>(c, x, y, st, part, s, grid_out);
+    return aprod1_t<double, double, double, double>(c, x, y, st, part, s, grid_out);
+}
+
+int aprod1_grid(const gsr_ctx *c, bool inner32)
+{
+    int g = 1;
+    static LsqrState dummy;  // only selects the LSQR kernel variant; never dereferenced on the host
+    aprod1_dispatch(c, nullptr, nullptr, &dummy, nullptr, nullptr, inner32, &g);
+    return g;
+}
+
+cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
+                          cudaStream_t s, bool inner32)
 {
     if (c->n_rows == 0) return cudaSuccess;
-    return c->prec == GSR_FP32 ? aprod1_t<float>(c, x, y, st, part, s) : aprod1_t<double>(c, x, y, st, part, s);
+    return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, bool INS, bool SQ, bool LS>
-static cudaError_t aprod2_star_launch(const gsr_ctx *c, const double *y, double *x, const LsqrState *st,
+template <typename VT, typename UT, typename AT, bool INS, bool SQ, bool LS>
+static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, const LsqrState *st,
                                       cudaStream_t s)
 {
-    auto kern = k_aprod2_star<VT, INS, SQ, LS>;
-    const size_t dyn = INS ? sizeof(double) * (size_t)c->n_instr : 0;
+    auto kern = k_aprod2_star<VT, UT, AT, INS, SQ, LS>;
+    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
     const int g = persistent_blocks(c, kern, dyn);
-    kern<<<g, kThreads, dyn, s>>>(view<VT>(c), y, x, st);
+    kern<<<g, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, st);
     return cudaGetLastError();
 }
 
-template <typename VT, bool SQ, bool LS>
-static cudaError_t aprod2_t(const gsr_ctx *c, const double *y, double *x, const LsqrState *st, cudaStream_t s)
+template <typename VT, typename UT, typename AT, bool SQ, bool LS>
+static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, const LsqrState *st, cudaStream_t s)
 {
+    if (LS != (st != nullptr)) return cudaErrorInvalidValue;  // the LSQR variants read the solver state
+    if (!SQ && !y) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (sizeof(double) * (size_t)c->n_instr <= kSmemBudget)
-        e = aprod2_star_launch<VT, true, SQ, LS>(c, y, x, st, s);
+    if (sizeof(AT) * (size_t)c->n_instr <= kSmemBudget)
+        e = aprod2_star_launch<VT, UT, AT, true, SQ, LS>(c, y, x, st, s);
     else
-        e = aprod2_star_launch<VT, false, SQ, LS>(c, y, x, st, s);
+        e = aprod2_star_launch<VT, UT, AT, false, SQ, LS>(c, y, x, st, s);
     if (e != cudaSuccess) return e;
     // attitude pass: at least 256 positions per warp
-    auto kern = k_aprod2_att<VT, SQ, LS>;
+    auto kern = k_aprod2_att<VT, UT, AT, SQ, LS>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -332,22 +394,26 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const double *y, double *x, const 
     if (per < 256) per = 256;
     const int64_t warps = (c->n_rows + per - 1) / per;
     const int64_t blocks = (warps + wpb - 1) / wpb;
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), y, x, st, per);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, st, per);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool square, const LsqrState *st,
-                          cudaStream_t s)
+cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool square, const LsqrState *st,
+                          cudaStream_t s, bool inner32)
 {
     if (c->n_rows == 0) return cudaSuccess;
-    if (c->prec == GSR_FP32) {
-        if (square) return aprod2_t<float, true, false>(c, y, x, nullptr, s);
-        if (st) return aprod2_t<float, false, true>(c, y, x, st, s);
-        return aprod2_t<float, false, false>(c, y, x, nullptr, s);
+    if (inner32) {
+        if (st) return aprod2_t<float, float, float, false, true>(c, y, x, st, s);
+        return aprod2_t<float, float, float, false, false>(c, y, x, nullptr, s);
     }
-    if (square) return aprod2_t<double, true, false>(c, y, x, nullptr, s);
-    if (st) return aprod2_t<double, false, true>(c, y, x, st, s);
-    return aprod2_t<double, false, false>(c, y, x, nullptr, s);
+    if (c->prec == GSR_FP32) {
+        if (square) return aprod2_t<float, double, double, true, false>(c, y, x, nullptr, s);
+        if (st) return aprod2_t<float, double, double, false, true>(c, y, x, st, s);
+        return aprod2_t<float, double, double, false, false>(c, y, x, nullptr, s);
+    }
+    if (square) return aprod2_t<double, double, double, true, false>(c, y, x, nullptr, s);
+    if (st) return aprod2_t<double, double, double, false, true>(c, y, x, st, s);
+    return aprod2_t<double, double, double, false, false>(c, y, x, nullptr, s);
 }
 
 }  // namespace gsr

@@ -422,6 +422,45 @@ GSR_API gsr_status gsr_aprod2(gsr_ctx *c, const double *y, double *x, void *stre
     return GSR_OK;
 }
 
+GSR_API gsr_status gsr_aprod1_f32(gsr_ctx *c, const float *x, float *y, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (c->prec != GSR_FP32) return fail(c, GSR_EINVAL, "binary32 kernels need an FP32-stored context");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = launch_aprod1(c, x, y, nullptr, nullptr, (cudaStream_t)stream, true);
+    if (e != cudaSuccess) return cuda_fail(c, e, "aprod1_f32");
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_aprod2_f32(gsr_ctx *c, const float *y, double *x, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (c->prec != GSR_FP32) return fail(c, GSR_EINVAL, "binary32 kernels need an FP32-stored context");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream);
+    if (rc != GSR_OK) return rc;
+    if ((e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream, true)) != cudaSuccess)
+        return cuda_fail(c, e, "aprod2_f32");
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_residual(gsr_ctx *c, const double *x, float *r, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (c->prec != GSR_FP32) return fail(c, GSR_EINVAL, "gsr_residual needs an FP32-stored context");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if (!c->rhs_set) return fail(c, GSR_ESTATE, "b not loaded");
+    if ((!x || !r) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    const cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return residual_f32(c, x, r, (cudaStream_t)stream);
+}
+
 GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, const double *x0, double *x_out,
                                   double *se_out, gsr_solve_info *info, void *stream)
 {
@@ -440,8 +479,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     if (!c->rhs_set) return fail(c, GSR_ESTATE, "b not loaded");
     if (prm.mode == GSR_MIXED && c->prec != GSR_FP32)
         return fail(c, GSR_EINVAL, "GSR_MIXED needs an FP32-stored context");
-    if (prm.mode == GSR_MIXED || prm.warm != GSR_WARM_NONE)
-        return fail(c, GSR_EINVAL, "mode/warm start not available in this build");
+    if (prm.warm != GSR_WARM_NONE) return fail(c, GSR_EINVAL, "warm start not available in this build");
+    if (prm.mode == GSR_MIXED && se_out) return fail(c, GSR_EINVAL, "se_out is computed by GSR_PLAIN solves only");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // run on the context's own stream (graph capture needs a non-legacy stream), after the caller's work
@@ -452,7 +491,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         const gsr_status rl = ensure_att_layout(c, c->own);
         if (rl != GSR_OK) return rl;
     }
-    const gsr_status rc = lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
+    const gsr_status rc = prm.mode == GSR_MIXED ? mixed_solve(c, &prm, x0, x_out, info, c->own)
+                                                : lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
     // the caller's stream continues after the solve's last kernel
     if (cudaEventRecord(c->ev, c->own) == cudaSuccess) cudaStreamWaitEvent((cudaStream_t)stream, c->ev, 0);
     cudaGetLastError();

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 #include <utility>
 #include <vector>
@@ -54,6 +55,12 @@ struct LsqrState {
     int32_t itn, itnlim, istop, done, colb_skip, numeric;
 };
 
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int k = 0;
+    bool var = false, inner32 = false;
+};
+
 struct Workspace {
     int64_t n_rows = 0, n_cols = 0;
     double *u = nullptr;        // n_rows: unnormalised bidiagonalisation vector beta*u
@@ -68,6 +75,13 @@ struct Workspace {
     double *part_u = nullptr;   // MAX_PARTIALS: per-block sums of squares of u
     double *part_v = nullptr;   // MAX_PARTIALS: of vhat
     double *part_w = nullptr;   // MAX_PARTIALS: of w
+    float *u32 = nullptr;       // n_rows: binary32 row vector of the inner solves (FP32-stored systems)
+    float *pv32 = nullptr;      // n_cols: binary32 copy of p * v for the inner aprod1
+    double *xo = nullptr;       // n_cols: refined solution (unscaled) of the mixed solver
+    float2 *xhl = nullptr;      // n_cols: xo split into two binary32 parts
+    float2 *bhl = nullptr;      // n_rows: b split into two binary32 parts
+    double *blk = nullptr;      // 16: per-block sums of squares of the correction and of x
+    std::vector<GraphCache> graphs;
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
     int32_t *flag_d = nullptr;  // device alias of flag_h
@@ -133,11 +147,12 @@ SysView<VT> view(const gsr_ctx *c)
 }
 
 // kernels launchers (aprod.cu)
-cudaError_t launch_aprod1(const gsr_ctx *c, const double *x, double *y, const LsqrState *st, double *part,
-                          cudaStream_t s);
-cudaError_t launch_aprod2(const gsr_ctx *c, const double *y, double *x, bool square, const LsqrState *st,
-                          cudaStream_t s);
-int aprod1_grid(const gsr_ctx *c);
+// inner32: the binary32 kernels of the mixed solver's inner LSQR (x / y are float*)
+cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
+                          cudaStream_t s, bool inner32 = false);
+cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool square, const LsqrState *st,
+                          cudaStream_t s, bool inner32 = false);
+int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 
 // knot-ordered attitude copy (layout.cu); built once per loaded system
 gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s);
@@ -148,6 +163,16 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
 gsr_status ensure_workspace(gsr_ctx *c);
 void free_workspace(gsr_ctx *c);
 void default_params(gsr_solve_params *p);
+int col_grid(const gsr_ctx *c, int64_t n);
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s);
+LsqrState initial_state(const gsr_solve_params *prm);
+gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
+                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
+void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
+// mixed-precision solver (mixed.cu)
+gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
+gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out,
+                       gsr_solve_info *info, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v)

@@ -274,9 +274,9 @@ __global__ void k_scalar(LsqrState *__restrict__ st, const double *__restrict__ 
 }
 
 // colB (first=1: the start, w = v and x = 0)
-__global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, const double *__restrict__ p,
-                       double *__restrict__ w, double *__restrict__ x, double *__restrict__ var, int64_t n,
-                       const LsqrState *__restrict__ st, int32_t first)
+__global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, float *__restrict__ pv32,
+                       const double *__restrict__ p, double *__restrict__ w, double *__restrict__ x,
+                       double *__restrict__ var, int64_t n, const LsqrState *__restrict__ st, int32_t first)
 {
     if (!first && st->colb_skip) return;
     const double ia = st->inv_alpha;
@@ -286,7 +286,9 @@ __global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, const do
         const double vh = v[j];
         const double vj = has_alpha ? vh * ia : vh;
         v[j] = vj;
-        pv[j] = p[j] * vj;
+        const double pvj = p[j] * vj;
+        pv[j] = pvj;
+        if (pv32) pv32[j] = (float)pvj;
         if (first) {
             w[j] = vj;
             x[j] = 0.0;
@@ -324,7 +326,7 @@ __global__ void k_negate(const double *__restrict__ a, double *__restrict__ out,
 }
 
 // ---------------------------------------------------------------- host side
-static int col_grid(const gsr_ctx *c, int64_t n)
+int col_grid(const gsr_ctx *c, int64_t n)
 {
     int64_t g = (n + kColThreads - 1) / kColThreads;
     const int64_t cap = (int64_t)c->sm_count * 4;
@@ -351,6 +353,15 @@ gsr_status ensure_workspace(gsr_ctx *c)
     if ((e = cudaHostGetDevicePointer(&ws.flag_d, ws.flag_h, 0)) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.z, 0, nc * sizeof(double))) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.part_u, 0, 3 * MAX_PARTIALS * sizeof(double))) != cudaSuccess) goto oom;
+    if (c->prec == GSR_FP32) {
+        // mixed-precision solver: binary32 row vector, gathered column vector, split x and b
+        if ((e = cudaMalloc(&ws.u32, nr * sizeof(float))) != cudaSuccess) goto oom;
+        if ((e = cudaMalloc(&ws.pv32, nc * sizeof(float))) != cudaSuccess) goto oom;
+        if ((e = cudaMalloc(&ws.xo, nc * sizeof(double))) != cudaSuccess) goto oom;
+        if ((e = cudaMalloc(&ws.xhl, nc * sizeof(float2))) != cudaSuccess) goto oom;
+        if ((e = cudaMalloc(&ws.bhl, nr * sizeof(float2))) != cudaSuccess) goto oom;
+        if ((e = cudaMalloc(&ws.blk, 16 * sizeof(double))) != cudaSuccess) goto oom;
+    }
     ws.n_rows = c->n_rows;
     ws.n_cols = c->n_cols;
     return GSR_OK;
@@ -363,38 +374,65 @@ oom:
 void free_workspace(gsr_ctx *c)
 {
     Workspace &ws = c->ws;
-    double *ptrs[] = {ws.u, ws.z, ws.v, ws.w, ws.x, ws.pv, ws.p, ws.var, ws.tmp, ws.part_u};
+    double *ptrs[] = {ws.u, ws.z, ws.v, ws.w, ws.x, ws.pv, ws.p, ws.var, ws.tmp, ws.part_u, ws.xo, ws.blk};
     for (double *p : ptrs)
         if (p) cudaFree(p);
+    if (ws.u32) cudaFree(ws.u32);
+    if (ws.pv32) cudaFree(ws.pv32);
+    if (ws.xhl) cudaFree(ws.xhl);
+    if (ws.bhl) cudaFree(ws.bhl);
     if (ws.st) cudaFree(ws.st);
     if (ws.flag_h) cudaFreeHost(ws.flag_h);
+    for (auto &gc : ws.graphs)
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
     ws = Workspace();
 }
 
-// Capture `k` LSQR iterations (5 kernels each) into an executable graph.
-static cudaError_t capture_iterations(gsr_ctx *c, int k, bool want_var, cudaStream_t s, cudaGraphExec_t *exec)
+// The executable graph of `k` LSQR iterations (5 kernels each), captured on
+// first use and cached on the context (kernel arguments are the context's
+// fixed buffers; the iteration state lives in device memory).
+static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner32, cudaStream_t s,
+                                   cudaGraphExec_t *out)
 {
     Workspace &ws = c->ws;
-    const int gu = aprod1_grid(c);
+    for (auto &gc : ws.graphs) {
+        if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32) {
+            *out = gc.exec;
+            return cudaSuccess;
+        }
+    }
+    const int gu = aprod1_grid(c, inner32);
     const int gc = col_grid(c, c->n_cols);
+    void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
+    const void *pv = inner32 ? (const void *)ws.pv32 : (const void *)ws.pv;
+    float *pv32 = c->prec == GSR_FP32 ? ws.pv32 : nullptr;
     cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < k && e == cudaSuccess; ++i) {
-        if ((e = launch_aprod1(c, ws.pv, ws.u, ws.st, ws.part_u, s)) != cudaSuccess) break;
-        if ((e = launch_aprod2(c, ws.u, ws.z, false, ws.st, s)) != cudaSuccess) break;
+        if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
+        if ((e = launch_aprod2(c, u, ws.z, false, ws.st, s, inner32)) != cudaSuccess) break;
         k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gu, ws.z, ws.p, ws.v, ws.w, c->n_cols, ws.st, ws.part_v,
                                           ws.part_w, 0);
         k_scalar<<<1, 32, 0, s>>>(ws.st, ws.part_v, ws.part_w, gc, ws.flag_d);
-        k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, c->n_cols,
-                                          ws.st, 0);
+        k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr,
+                                          c->n_cols, ws.st, 0);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    return e;
+    if (e != cudaSuccess) return e;
+    GraphCache gcache;
+    gcache.exec = exec;
+    gcache.k = k;
+    gcache.var = want_var;
+    gcache.inner32 = inner32;
+    ws.graphs.push_back(gcache);
+    *out = exec;
+    return cudaSuccess;
 }
 
 void default_params(gsr_solve_params *p)
@@ -412,13 +450,108 @@ void default_params(gsr_solve_params *p)
     p->timeout_s = 0.0;
     p->graph_k = 0;
     p->where = GSR_HOST;
+    p->inner_itn = 0;
+    p->inner_tol = 0.0;
+    p->refine_tol = 0.0;
+    p->max_outer = 0;
+}
+
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s)
+{
+    Workspace &ws = c->ws;
+    const int64_t nc = c->n_cols;
+    cudaError_t e = cudaMemsetAsync(ws.tmp, 0, nc * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+    if (use && (e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s)) != cudaSuccess)
+        return cuda_fail(c, e, "column norms");
+    k_precond_finish<<<col_grid(c, nc), kColThreads, 0, s>>>(ws.tmp, ws.p, nc, use ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "preconditioner");
+    return GSR_OK;
+}
+
+// LSQR from a prepared start: the row vector (ws.u, or ws.u32 when inner32)
+// holds the right-hand side and part_u[0..n_part_u) its per-block sums of
+// squares. Runs the start (alpha_1 v_1 = A~^T u_1) and the iterations; leaves
+// the scaled solution in ws.x and the final scalars in *fin.
+gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
+                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin)
+{
+    using clk = std::chrono::steady_clock;
+    Workspace &ws = c->ws;
+    const int64_t nc = c->n_cols;
+    const int gc = col_grid(c, nc);
+    float *pv32 = c->prec == GSR_FP32 ? ws.pv32 : nullptr;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ws.st, &init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "state upload");
+    void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
+    if ((e = launch_aprod2(c, u, ws.z, false, nullptr, s, inner32)) != cudaSuccess) return cuda_fail(c, e, "start");
+    k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, n_part_u, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1);
+    k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);
+    k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, nc, ws.st, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "LSQR start");
+
+    int k = graph_k > 0 ? graph_k : 8;
+    if (k > init.itnlim && init.itnlim > 0) k = init.itnlim;
+    if (k < 1) k = 1;
+    cudaGraphExec_t exec = nullptr;
+    if ((e = iteration_graph(c, k, want_var, inner32, s, &exec)) != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "LSQR start");
+    gsr_status status = GSR_OK;
+    int launched = 0;
+    const int max_launch = init.itnlim > 0 ? (init.itnlim + k - 1) / k : 0;
+    while (!*(volatile int32_t *)ws.flag_h && launched < max_launch) {
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+            status = cuda_fail(c, e, "graph launch");
+            break;
+        }
+        ++launched;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            status = cuda_fail(c, e, "LSQR iteration");
+            break;
+        }
+        if (timeout_s > 0.0 && std::chrono::duration<double>(clk::now() - t0).count() > timeout_s) {
+            status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
+            break;
+        }
+    }
+    if ((e = cudaMemcpyAsync(fin, ws.st, sizeof(*fin), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "state download");
+    return status;
+}
+
+LsqrState initial_state(const gsr_solve_params *prm)
+{
+    LsqrState init = LsqrState();
+    init.damp = prm->damp;
+    init.atol = prm->atol;
+    init.btol = prm->btol;
+    init.ctol = prm->conlim > 0.0 ? 1.0 / prm->conlim : 0.0;
+    init.itnlim = prm->itnlim;
+    return init;
+}
+
+void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0)
+{
+    if (!info) return;
+    info->istop = fin.istop;
+    info->itn = fin.itn;
+    info->outer_itn = 0;
+    info->r1norm = fin.r1norm;
+    info->r2norm = fin.r2norm;
+    info->anorm = fin.anorm;
+    info->acond = fin.acond;
+    info->arnorm = fin.arnorm;
+    info->xnorm = fin.xnorm;
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->ms_warm = 0.0;
 }
 
 gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,
                       gsr_solve_info *info, cudaStream_t s)
 {
-    using clk = std::chrono::steady_clock;
-    const auto t0 = clk::now();
+    const auto t0 = std::chrono::steady_clock::now();
     gsr_status rc = ensure_workspace(c);
     if (rc != GSR_OK) return rc;
     Workspace &ws = c->ws;
@@ -430,12 +563,7 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
     cudaError_t e;
 
     // preconditioner p = 1/|A_:,j| (Alg. 1): one pass over A per solve
-    if ((e = cudaMemsetAsync(ws.tmp, 0, nc * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
-    if (prm->precond) {
-        if ((e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s)) != cudaSuccess)
-            return cuda_fail(c, e, "column norms");
-    }
-    k_precond_finish<<<gc, kColThreads, 0, s>>>(ws.tmp, ws.p, nc, prm->precond ? 1 : 0);
+    if ((rc = precond_pass(c, prm->precond != 0, s)) != GSR_OK) return rc;
 
     // x0: u = b - A x0 ; otherwise u = b
     const double *x0d = nullptr;
@@ -452,16 +580,6 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
             }
             x0d = x0_buf;
         }
-    }
-    LsqrState init = LsqrState();
-    init.damp = prm->damp;
-    init.atol = prm->atol;
-    init.btol = prm->btol;
-    init.ctol = prm->conlim > 0.0 ? 1.0 / prm->conlim : 0.0;
-    init.itnlim = prm->itnlim;
-    if ((e = cudaMemcpyAsync(ws.st, &init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(c, e, "state upload");
-    if (x0d) {
         k_negate<<<gc, kColThreads, 0, s>>>(x0d, ws.x, nc);
         k_copy_ssq<<<gr, kColThreads, 0, s>>>(c->b, ws.u, nr, ws.part_u);
         launch_aprod1(c, ws.x, ws.u, nullptr, nullptr, s);  // u = b - A x0
@@ -469,62 +587,16 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
     } else {
         k_copy_ssq<<<gr, kColThreads, 0, s>>>(c->b, ws.u, nr, ws.part_u);
     }
-    // alpha_1 v_1 = A~^T u_1: z = A^T u (unnormalised), colA with first=1 divides by beta
-    launch_aprod2(c, ws.u, ws.z, false, nullptr, s);
-    k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gr, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1);
-    k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);
-    k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, nc, ws.st, 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) {
-        if (x0_buf) cudaFree(x0_buf);
-        return cuda_fail(c, e, "LSQR start");
-    }
-    // the u partials of the start were written with grid gr; the iterations use aprod1's grid
-    // (k_colA inside the graph reads aprod1_grid partials)
-
-    int k = prm->graph_k > 0 ? prm->graph_k : 8;
-    if (k > prm->itnlim && prm->itnlim > 0) k = prm->itnlim;
-    if (k < 1) k = 1;
-    cudaGraphExec_t exec = nullptr;
-    gsr_status status = GSR_OK;
-    if ((e = capture_iterations(c, k, want_var, s, &exec)) != cudaSuccess) {
-        if (x0_buf) cudaFree(x0_buf);
-        return cuda_fail(c, e, "graph capture");
-    }
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
-        cudaGraphExecDestroy(exec);
-        if (x0_buf) cudaFree(x0_buf);
-        return cuda_fail(c, e, "LSQR start");
-    }
-    int launched = 0;
-    const int max_launch = prm->itnlim > 0 ? (prm->itnlim + k - 1) / k : 0;
-    while (!*(volatile int32_t *)ws.flag_h && launched < max_launch) {
-        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
-            status = cuda_fail(c, e, "graph launch");
-            break;
-        }
-        ++launched;
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
-            status = cuda_fail(c, e, "LSQR iteration");
-            break;
-        }
-        if (prm->timeout_s > 0.0 &&
-            std::chrono::duration<double>(clk::now() - t0).count() > prm->timeout_s) {
-            status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
-            break;
-        }
-    }
-    cudaGraphExecDestroy(exec);
-
     LsqrState fin;
-    if ((e = cudaMemcpyAsync(&fin, ws.st, sizeof(fin), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    gsr_status status = run_lsqr(c, initial_state(prm), false, want_var, gr, prm->graph_k, prm->timeout_s, t0, s, &fin);
+    if (status != GSR_OK && status != GSR_ETIMEOUT) {
         if (x0_buf) cudaFree(x0_buf);
-        return cuda_fail(c, e, "state download");
+        return status;
     }
     // result
     double *out_d = dev_io ? x_out : ws.tmp;
     double *se_d = nullptr;
-    if (se_out) se_d = dev_io ? se_out : ws.z;  // z is free after the loop (kept zero below)
+    if (se_out) se_d = dev_io ? se_out : ws.z;  // z is free after the loop (cleared again below)
     const double dof = (double)(nr - nc > 1 ? nr - nc : 1);
     k_finish<<<gc, kColThreads, 0, s>>>(ws.x, ws.p, x0d, out_d, ws.var, se_d, ws.st, nc, dof);
     if ((e = cudaGetLastError()) == cudaSuccess && !dev_io) {
@@ -536,20 +608,7 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (x0_buf) cudaFree(x0_buf);
     if (e != cudaSuccess) return cuda_fail(c, e, "result");
-
-    if (info) {
-        info->istop = fin.istop;
-        info->itn = fin.itn;
-        info->outer_itn = 0;
-        info->r1norm = fin.r1norm;
-        info->r2norm = fin.r2norm;
-        info->anorm = fin.anorm;
-        info->acond = fin.acond;
-        info->arnorm = fin.arnorm;
-        info->xnorm = fin.xnorm;
-        info->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
-        info->ms_warm = 0.0;
-    }
+    fill_info(info, fin, t0);
     if (status != GSR_OK) return status;
     if (fin.numeric) return fail(c, GSR_ENUMERIC, "non-finite value in the LSQR scalars");
     return GSR_OK;

@@ -95,6 +95,9 @@ def lib():
             "gsr_set_system": (I32, [P, P, I32, P, P, P, I32, P]),
             "gsr_aprod1": (I32, [P, P, P, P]),
             "gsr_aprod2": (I32, [P, P, P, P]),
+            "gsr_aprod1_f32": (I32, [P, P, P, P]),
+            "gsr_aprod2_f32": (I32, [P, P, P, P]),
+            "gsr_residual": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
             "gsr_lsqr_solve": (I32, [P, ctypes.POINTER(SolveParams), P, P, P, ctypes.POINTER(SolveInfo), P]),
         }
@@ -150,6 +153,18 @@ def gsr_aprod1(ctx, x, y, stream=0):
 
 def gsr_aprod2(ctx, y, x, stream=0):
     return lib().gsr_aprod2(ctx, y or None, x or None, stream or None)
+
+
+def gsr_aprod1_f32(ctx, x, y, stream=0):
+    return lib().gsr_aprod1_f32(ctx, x or None, y or None, stream or None)
+
+
+def gsr_aprod2_f32(ctx, y, x, stream=0):
+    return lib().gsr_aprod2_f32(ctx, y or None, x or None, stream or None)
+
+
+def gsr_residual(ctx, x, r, stream=0):
+    return lib().gsr_residual(ctx, x or None, r or None, stream or None)
 
 
 def gsr_default_params() -> SolveParams:
@@ -228,6 +243,15 @@ class Context:
 
     def aprod2(self, y, x, stream=0):
         self._check(gsr_aprod2(self.h, _ptr(y), _ptr(x), stream))
+
+    def aprod1_f32(self, x, y, stream=0):
+        self._check(gsr_aprod1_f32(self.h, _ptr(x), _ptr(y), stream))
+
+    def aprod2_f32(self, y, x, stream=0):
+        self._check(gsr_aprod2_f32(self.h, _ptr(y), _ptr(x), stream))
+
+    def residual(self, x, r, stream=0):
+        self._check(gsr_residual(self.h, _ptr(x), _ptr(r), stream))
 
     def solve(self, x_out, x0=None, se_out=None, stream=0, **kw):
         p = gsr_default_params()

@@ -75,9 +75,10 @@ def test_aprod2_astro_reproducible_rest_close():
         ctx.aprod2(u, z)
         outs.append(z.cpu().numpy())
     a = 5 * s.n_stars
+    scale = oracle.aprod2(abs_system(s), np.abs(u.cpu().numpy()), np.zeros(s.n_cols))
     for o in outs[1:]:
         assert np.array_equal(o[:a], outs[0][:a])  # astro: one warp per star, no atomics
-        np.testing.assert_allclose(o[a:], outs[0][a:], rtol=1e-13, atol=1e-13)
+        assert np.all(np.abs(o[a:] - outs[0][a:]) <= 1e-13 * scale[a:])  # reordered atomic sums
     ctx.close()
 
 

@@ -1,0 +1,129 @@
+"""Mixed precision (binary32 inner LSQR, binary64 refinement) against binary64 solutions.
+
+Both sides solve the same system: coefficients rounded to binary32 once, the
+binary64 references use exactly those values widened. Bar: every block
+within 1e-9 relative (|x_blk - ref_blk| / max(|ref_blk|, 1e-3)) of the
+binary64 solution. The refinement converges to the least-squares solution of
+the undamped problem; with damp 1e-6 the damped reference differs by
+O(damp^2) ~ 1e-12, far below the bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gsrgen
+import oracle
+import paper_2308_00778_gb300 as g
+from gpu_util import block_errors, context_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup32(cfg):
+    h = gsrgen.generate(cfg, fp32=True)
+    s = oracle.from_host_system(h)  # h.A holds the binary32-rounded values, widened
+    b = oracle.rhs(s, h.x_true, h.eps)
+    ctx = context_for(h, fp32=True)
+    ctx.set_system(h.A32, h.knot, h.instr, b)
+    return h, s, b, ctx
+
+
+def test_mixed_c1_vs_oracle():
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup32(w.cfg)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, mode=g.GSR_MIXED, damp=w.damp)
+    xo, io = oracle.lsqr(s, b, 500, 1e-14, 1e-14, 0.0, w.damp)
+    errs = block_errors(x, xo, s)
+    assert max(errs.values()) <= 1e-9, (errs, info)
+    assert 2 <= info["outer_itn"] <= 6, info
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["ragged_sinusoid", "wide_instr_global"])
+def test_mixed_vs_plain_fp64_on_gpu(name):
+    cfg = {"ragged_sinusoid": gsrgen.make_cfg(51, 20000, (50, 150), 1500, 300, att_kind=1),
+           "wide_instr_global": gsrgen.make_cfg(52, 3000, 100, 20000, 15000)}[name]
+    h, s, b, ctx = _setup32(cfg)
+    xp = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    ctx.solve(xp, damp=1e-6, atol=1e-14, btol=1e-14, conlim=0.0, itnlim=5000)  # binary64 arithmetic, same values
+    xm = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    info = ctx.solve(xm, mode=g.GSR_MIXED, damp=1e-6)
+    errs = block_errors(xm.cpu().numpy(), xp.cpu().numpy(), s)
+    assert max(errs.values()) <= 1e-9, (errs, info)
+    ctx.close()
+
+
+def test_mixed_fixed_schedule_and_x0():
+    """A fixed schedule (inner iterations x outer steps) and a warm start x0."""
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup32(w.cfg)
+    xo, _ = oracle.lsqr(s, b, 500, 1e-14, 1e-14, 0.0, w.damp)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, mode=g.GSR_MIXED, damp=w.damp, inner_itn=12, max_outer=3, refine_tol=-1.0,
+                     atol=0.0, btol=0.0, inner_tol=1e-30)
+    assert info["outer_itn"] == 3 and info["itn"] == 36, info
+    assert max(block_errors(x, xo, s).values()) <= 1e-9
+    x1 = np.zeros(s.n_cols)
+    info = ctx.solve(x1, x0=xo, mode=g.GSR_MIXED, damp=w.damp)
+    assert info["outer_itn"] <= 2 and max(block_errors(x1, xo, s).values()) <= 1e-9, info
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(x1, mode=g.GSR_MIXED, se_out=np.zeros(s.n_cols))
+    assert e.value.status == g.Status.EINVAL
+    ctx.close()
+
+
+def _abs_sys(s):
+    return oracle.System(s.star_ptr, np.abs(s.A), s.knot, s.instr, s.n_dfa, s.n_instr, s.n_glob)
+
+
+@pytest.mark.parametrize("name", ["c1", "ragged_wide"])
+def test_binary32_kernels_and_residual(name):
+    """The inner kernels against the oracle on the same (rounded) values.
+
+    aprod1_f32: 24 binary32 products and sums per row, error <= 25 u sum|terms|
+    (u = 2^-24). aprod2_f32: binary32 partial sums of up to ~10^3 terms before
+    the binary64 flush; bound 2e3 u sum|terms|. residual: double-float, then
+    rounded to binary32: |r - r_ref| <= u |r_ref| + 2^-40 sum|terms|."""
+    cfg = {"c1": gsrgen.workloads()["c1"].cfg, "ragged_wide": gsrgen.make_cfg(61, 2000, (10, 300), 9000, 9000)}[name]
+    h, s, b, ctx = _setup32(cfg)
+    u = 2.0 ** -24
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(s.n_cols).astype(np.float32).astype(np.float64)
+    y0 = rng.standard_normal(s.n_rows).astype(np.float32).astype(np.float64)
+    yd = torch.tensor(y0, dtype=torch.float32, device="cuda")
+    ctx.aprod1_f32(torch.tensor(x, dtype=torch.float32, device="cuda"), yd)
+    want = oracle.aprod1(s, x, y0.copy())
+    scale = oracle.aprod1(_abs_sys(s), np.abs(x), np.abs(y0).copy())
+    assert np.all(np.abs(yd.cpu().numpy() - want) <= 25 * u * scale)
+
+    z0 = rng.standard_normal(s.n_cols)
+    zd = torch.tensor(z0, device="cuda")
+    ctx.aprod2_f32(torch.tensor(y0, dtype=torch.float32, device="cuda"), zd)
+    want2 = oracle.aprod2(s, y0, z0.copy())
+    scale2 = oracle.aprod2(_abs_sys(s), np.abs(y0), np.abs(z0).copy())
+    assert np.all(np.abs(zd.cpu().numpy() - want2) <= 2e3 * u * scale2)
+
+    xs = rng.standard_normal(s.n_cols)
+    rd = torch.zeros(s.n_rows, dtype=torch.float32, device="cuda")
+    ctx.residual(torch.tensor(xs, device="cuda"), rd)
+    r_ref = b - oracle.aprod1(s, xs, np.zeros(s.n_rows))
+    rscale = oracle.aprod1(_abs_sys(s), np.abs(xs), np.abs(b).copy())
+    assert np.all(np.abs(rd.cpu().numpy() - r_ref) <= u * np.abs(r_ref) + 2.0 ** -40 * rscale)
+    ctx.close()
+
+
+def test_binary32_entry_points_need_fp32_context():
+    cfg = gsrgen.make_cfg(7, 20, 30, 12, 8)
+    h = gsrgen.generate(cfg)
+    ctx = context_for(h)
+    ctx.set_system(h.A, h.knot, h.instr, np.ones(h.n_rows))
+    with pytest.raises(g.GsrError) as e:
+        ctx.aprod1_f32(torch.zeros(ctx.n_cols, dtype=torch.float32, device="cuda"),
+                       torch.zeros(ctx.n_rows, dtype=torch.float32, device="cuda"))
+    assert e.value.status == g.Status.EINVAL
+    with pytest.raises(g.GsrError) as e:
+        ctx.residual(torch.zeros(ctx.n_cols, dtype=torch.float64, device="cuda"),
+                     torch.zeros(ctx.n_rows, dtype=torch.float32, device="cuda"))
+    assert e.value.status == g.Status.EINVAL
+    ctx.close()
