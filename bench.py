@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["f32", "f64"],
+                    help="profiling mode for ncu: load the system with binary32 (f32) or binary64 (f64) storage "
+                         "and launch each hot kernel --steps times inside an NVTX range 'prof'; prints timings")
     return ap.parse_args()
 
 
@@ -491,8 +494,49 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """A small driver for ncu captures: one context, each hot kernel launched --steps times."""
+    import torch
+
+    import gsrgen
+    import paper_2308_00778_gb300 as g
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    w = gsrgen.workloads()[args.workload]
+    cfg = w.cfg
+    f32 = args.profile == "f32"
+    ctx, b, _ = _device_system(g, gsrgen, torch, cfg, f32, True, dev, sh)
+    n, nc = ctx.n_rows, ctx.n_cols
+    x = torch.randn(nc, dtype=torch.float64, device=dev)
+    u = torch.randn(n, dtype=torch.float64, device=dev)
+    z = torch.zeros(nc, dtype=torch.float64, device=dev)
+    if f32:
+        x32, u32, r32 = x.float(), u.float(), torch.empty(n, dtype=torch.float32, device=dev)
+        ops = {"aprod1_f32": lambda: ctx.aprod1_f32(x32, u32, stream=sh),
+               "aprod2_f32": lambda: ctx.aprod2_f32(u32, z, stream=sh),
+               "residual_df": lambda: ctx.residual(x, r32, stream=sh)}
+    else:
+        ops = {"aprod1_f64": lambda: ctx.aprod1(x, u, stream=sh), "aprod2_f64": lambda: ctx.aprod2(u, z, stream=sh)}
+    for fn in ops.values():  # warm-up outside the profiled range (builds layouts, loads modules)
+        fn()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("prof")
+    out = {}
+    for name, fn in ops.items():
+        out[name] = _time_kernel(torch, fn, stream, reps=max(args.steps, 1))
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile": args.profile, "workload": args.workload, "rows": n, "ms": out}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -69,6 +69,7 @@ def workloads() -> dict:
     tiny : 20 stars x 30 obs, 12 knots, 8 instr, 1 global (600 x 145)
     c1   : 1,000 stars x 100 obs, 100 knots/axis, 60 instr, 1 global, seed 0
     c2   : 100k stars x 200 obs (2e7 rows), 3,000 knots/axis, 1,000 instr, sinusoid attitude, seed 1
+    c2h  : c2 with half the stars (1e7 rows), for profiling captures
     c3   : 1M stars x 200 obs (2e8 rows), 30,000 knots/axis, 10,000 instr, FP32 values, seed 2
     c4   : 50k stars x 200 obs (1e7 rows), 2,000 knots/axis, 500 instr, sinusoid attitude (seed per system)
     c5   : 2M stars x 250 obs (5e8 rows), 60,000 knots/axis, 20,000 instr, sinusoid attitude, FP32 values, seed 5
@@ -77,6 +78,7 @@ def workloads() -> dict:
         "tiny": Workload("tiny", make_cfg(7, 20, 30, 12, 8), False, 1e-6, 1e-12, 1e-12, 400),
         "c1": Workload("c1", make_cfg(0, 1000, 100, 100, 60), False, 1e-6, 1e-12, 1e-12, 200),
         "c2": Workload("c2", make_cfg(1, 100_000, 200, 3000, 1000, att_kind=1), False, 1e-6, 1e-12, 1e-12, 2000),
+        "c2h": Workload("c2h", make_cfg(1, 50_000, 200, 3000, 1000, att_kind=1), False, 1e-6, 1e-12, 1e-12, 2000),
         "c3": Workload("c3", make_cfg(2, 1_000_000, 200, 30000, 10000), True, 1e-6, 1e-12, 1e-12, 2000),
         "c4": Workload("c4", make_cfg(100, 50_000, 200, 2000, 500, att_kind=1), False, 1e-6, 1e-12, 1e-12, 2000),
         "c5": Workload("c5", make_cfg(5, 2_000_000, 250, 60000, 20000, att_kind=1), True, 1e-6, 1e-12, 1e-12, 2000),
