@@ -18,38 +18,16 @@
 // point is the undamped minimiser (it differs from the damped one by
 // O(damp^2), far below the binary32 noise for the damping used here).
 #include "gsr_internal.cuh"
+#include "dfloat.cuh"
 
 namespace gsr {
 
 static constexpr int kThreads = 256;
 
-// s + e = a + b exactly (Knuth's two-sum); explicit roundings, no contraction
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fadd_rn(s, -a);
-    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
-}
-
-// (s, c) += a * (x.x + x.y): the leading product split exactly with an FMA
-// (p + pe = a * x.x), the small product a * x.y and all error terms go to c.
-__device__ __forceinline__ void acc_term(float a, float2 x, float &s, float &c)
-{
-    const float p = __fmul_rn(a, x.x);
-    const float pe = __fmaf_rn(a, x.x, -p);
-    const float q = __fmul_rn(a, x.y);
-    float t, e;
-    two_sum(s, p, t, e);
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(e, __fadd_rn(pe, q)));
-}
-
 __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ out, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = a[i];
-        const float hi = (float)v;
-        out[i] = make_float2(hi, (float)(v - (double)hi));
+        out[i] = split_double(a[i]);
     }
 }
 
