@@ -10,7 +10,7 @@
  * Row structure follows the paper's model of one observation equation
  * (Sec. 2): 24 coefficients per row, 5 astrometric (the observed star),
  * 3 axes x 4 consecutive attitude B-spline knots, 6 instrumental columns
- * "without a particular scheme", 1 global (PPN gamma). Rows are star-major
+ * with no fixed pattern, 1 global (PPN gamma). Rows are star-major
  * (the block-diagonal astrometric part, Sec. 2), with the observation times of
  * each star sorted, so the attitude knot of a row is nondecreasing within a
  * star.
