@@ -161,6 +161,29 @@ gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream)
  */
 gsr_status gsr_residual(gsr_ctx *ctx, const double *x, float *r, void *stream);
 
+/*
+ * gsr_residual_static -- the same r = b - A x as gsr_residual (same arithmetic),
+ * for callers that must not allocate device memory at call time: a process
+ * whose device memory is already reserved by another allocator's pool, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation. (The paper has no counterpart; this is a library
+ * convenience.) gsr_residual takes its scratch from the context's workspace,
+ * allocated on first use; this entry point calls no allocating routine.
+ *   - Its scratch is a file-scope device array of 2^20 binary32 pairs
+ *     (8 MiB), present on every GPU that loads the library until the process
+ *     exits: n_cols above 1048576 is rejected with GSR_EINVAL.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current); make
+ *     that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     each call writes every element it reads first, so nothing needs
+ *     clearing. Calls that overlap on the GPU (different streams, or
+ *     contexts on the same device) race on it: order them.
+ *   x  device array of n_cols binary64.   r  device array of n_rows binary32.
+ * FP32-stored contexts only; b must be loaded. Runs on stream.
+ */
+gsr_status gsr_residual_static(gsr_ctx *ctx, const double *x, float *r, void *stream);
+
 typedef struct {
     int32_t itnlim;     /* maximum LSQR iterations (>= 0)                               */
     double atol, btol;  /* Paige-Saunders tolerances (0 disables the test)              */

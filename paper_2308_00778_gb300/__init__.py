@@ -7,7 +7,7 @@ pointer; their ``data_ptr()`` is forwarded unchanged.
 """
 from .gsr import (  # noqa: F401
     GSR_AOS, GSR_DEVICE, GSR_FP32, GSR_FP64, GSR_HOST, GSR_MIXED, GSR_PLAIN, GSR_SOA, GSR_WARM_JACOBI,
-    GSR_WARM_LEARNED, GSR_WARM_NONE, GsrError, SolveInfo, SolveParams, Status, gsr_aprod1, gsr_aprod1_f32, gsr_aprod2, gsr_aprod2_f32, gsr_residual, gsr_create,
+    GSR_WARM_LEARNED, GSR_WARM_NONE, GsrError, SolveInfo, SolveParams, Status, gsr_aprod1, gsr_aprod1_f32, gsr_aprod2, gsr_aprod2_f32, gsr_residual, gsr_residual_static, gsr_create,
     gsr_default_params, gsr_destroy, gsr_dims, gsr_last_error, gsr_lsqr_solve, gsr_set_rhs, gsr_set_rows,
     gsr_set_system, lib, library_path, Context,
 )

@@ -98,6 +98,7 @@ def lib():
             "gsr_aprod1_f32": (I32, [P, P, P, P]),
             "gsr_aprod2_f32": (I32, [P, P, P, P]),
             "gsr_residual": (I32, [P, P, P, P]),
+            "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
             "gsr_lsqr_solve": (I32, [P, ctypes.POINTER(SolveParams), P, P, P, ctypes.POINTER(SolveInfo), P]),
         }
@@ -165,6 +166,10 @@ def gsr_aprod2_f32(ctx, y, x, stream=0):
 
 def gsr_residual(ctx, x, r, stream=0):
     return lib().gsr_residual(ctx, x or None, r or None, stream or None)
+
+
+def gsr_residual_static(ctx, x, r, stream=0):
+    return lib().gsr_residual_static(ctx, x or None, r or None, stream or None)
 
 
 def gsr_default_params() -> SolveParams:
