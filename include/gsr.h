@@ -131,9 +131,10 @@ gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
  * gsr_aprod2 -- x += A^T y (aprod 2, Eq. 3; Alg. 3).
  *   y  device array of n_rows binary64 (read only).
  *   x  device array of n_cols binary64, updated in place.
- * Runs on stream. Attitude, instrumental and global unknowns are accumulated
- * with atomic adds, so the low bits of those results can differ from run to
- * run (sums are reordered); astrometric unknowns are reproducible.
+ * Runs on stream. Partial sums (per star segment, per attitude knot run,
+ * per block for the instrumental and global unknowns) are added with atomic
+ * adds, so the low bits of the results can differ from run to run (the sums
+ * are reordered).
  */
 gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
 

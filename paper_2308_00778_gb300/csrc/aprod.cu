@@ -1,42 +1,37 @@
-// aprod.cu -- aprod 1 (y += A x, Eq. 2) and aprod 2 (x += A^T y, Eq. 3) on SoA planes.
+// aprod.cu -- aprod 1 (y += A x, Eq. 2) and aprod 2 (x += A^T y, Eq. 3) over row tiles.
 //
-// Both kernels are persistent grids with one warp per star: the rows of a star
-// are contiguous (the block-diagonal astrometric part, Sec. 2), so each warp
-// streams 32 consecutive rows per step with coalesced loads of the 24 value
-// planes, the knot plane and the 6 instrumental planes.
+// All kernels are persistent grids in which a warp handles one tile of
+// T = 32*R rows at a time (tiles.cuh): lane l owns R consecutive rows and reads
+// every plane of the tile with one 16-byte load. Warps take tiles in a
+// grid-stride order, so the warps running at one time stream consecutive
+// tiles of memory.
 //
-// aprod 1: the 5 astrometric unknowns of the star are loaded once per star
-// (broadcast), the 12 attitude and 6 instrumental unknowns are gathered
-// through the read-only cache, and each lane writes its row's result. In the
-// LSQR form it computes u <- A (p v) + coef * u and emits per-block sums of
-// squares of the new u (the norm beta).
+// aprod 1: per row, the 5 astrometric unknowns of the row's star (the star
+// of each row comes from star_ptr, searched from the tile's first star), the
+// 12 attitude and 6 instrumental unknowns gathered through the read-only
+// cache, 1 global. In the LSQR form it computes u <- A (p v) + coef * u and
+// emits per-block sums of squares of the new u (the norm beta).
+//
+// aprod 2 runs as two passes. The star pass reads the astrometric,
+// instrumental and global coefficients. Each warp owns a contiguous range of
+// tiles; astrometric products of the current star accumulate in registers
+// and are added once per star (run) and warp; instrumental products go to
+// block-private shared-memory accumulators flushed once per block (global
+// atomic adds when n_instr is too large); the global column is reduced per
+// block and added once per block (the two-stage reduction of the paper's
+// global kernels, Sec. 4.2, folded into one pass). The attitude pass reads the
+// knot-ordered copy of the 12 attitude coefficients (layout.cu): each warp
+// owns a contiguous range of tiles, sums runs of equal knot in registers and
+// adds each run once, instead of 12 atomic adds per row.
 //
 // Every kernel is templated on the stored value type VT, the type of the
 // gathered / streamed vectors (XT for x in aprod 1, UT for the row vector) and
 // the arithmetic type AT: binary64 for the plain solver (on FP64- or
 // FP32-stored values) and binary32 throughout for the inner solve of the
 // mixed-precision solver. Column accumulators (z) are always binary64.
-//
-// aprod 2 runs as two passes. The star-ordered pass reads the astrometric,
-// instrumental and global coefficients: the astrometric part is a per-star
-// register accumulation and one warp reduction per star, written without
-// atomics (one warp owns a star); instrumental products go to block-private
-// shared-memory accumulators flushed once per block (global atomic adds when
-// n_instr is too large); the global column is reduced per block and added
-// once per block (the two-stage reduction of the paper's global kernels,
-// Sec. 4.2, folded into one pass). The attitude pass reads the knot-ordered
-// copy of the 12 attitude coefficients (layout.cu) and gathers y through the
-// row permutation: runs of equal knot are summed in registers and added once
-// per run, instead of 12 atomic adds per row.
-#include "gsr_internal.cuh"
+#include "tiles.cuh"
 
 namespace gsr {
-
-template <typename T>
-__device__ __forceinline__ T ld_stream(const T *p)
-{
-    return __ldcs(p);
-}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v)
@@ -46,14 +41,12 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-// STAGE: the attitude and instrumental parts of x (3 n_dfa + n_instr values)
-// are copied into shared memory once per block; the per-row gathers then hit
-// shared memory instead of issuing scattered L1 requests.
-template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool STAGE>
+template <typename VT, typename XT, typename UT, typename AT, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
     __shared__ double sm32[32];
     AT coef = (AT)1;
     if (LSQR) {
@@ -65,51 +58,48 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const XT *__restrict__ xt = x + S.att0;
     const XT *__restrict__ xi = x + S.instr0;
-    if (STAGE) {
-        XT *sx = reinterpret_cast<XT *>(smem_raw);
-        const int32_t n_att = NAXES * S.n_dfa, n_st = n_att + S.n_instr;
-        for (int32_t i = threadIdx.x; i < n_st; i += blockDim.x) sx[i] = x[S.att0 + i];
-        __syncthreads();
-        xt = sx;
-        xi = sx + n_att;
-    }
     const AT xg = S.n_glob ? (AT)__ldg(x + S.glob0) : (AT)0;
     AT ssq = (AT)0;
-    for (int64_t s = gw; s < S.n_stars; s += nw) {
-        const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        const XT *__restrict__ xa = x + NASTRO * s;
-        const AT xa0 = (AT)__ldg(xa + 0), xa1 = (AT)__ldg(xa + 1), xa2 = (AT)__ldg(xa + 2),
-                 xa3 = (AT)__ldg(xa + 3), xa4 = (AT)__ldg(xa + 4);
-        for (int64_t r = r0 + lane; r < r1; r += 32) {
-            AT a[NPAR];
+    for (int64_t t = gw; t < S.n_tiles; t += nw) {
+        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
+        const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
+        int32_t kn[R];
+        load_ints<R>(ti, 0, kn);
+        int32_t ic[NINSTR][R];
 #pragma unroll
-            for (int j = 0; j < NPAR; ++j) a[j] = (AT)ld_stream(S.val + j * S.plane + r);
-            const int32_t k = ld_stream(S.knot + r);
-            int32_t ic[NINSTR];
+        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        AT a[NPAR][R];
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ic[j] = ld_stream(S.instr + j * S.plane + r);
-            AT sum = a[0] * xa0;
-            sum = fma(a[1], xa1, sum);
-            sum = fma(a[2], xa2, sum);
-            sum = fma(a[3], xa3, sum);
-            sum = fma(a[4], xa4, sum);
+        for (int j = 0; j < NPAR; ++j) load_vals<VT, AT>(tb, j, a[j]);
+        const int64_t r0 = t * T + lane * R;
+        int64_t sr[R];
+        stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const XT *__restrict__ xa = x + NASTRO * sr[i];
+            AT v = a[0][i] * (AT)__ldg(xa);
+#pragma unroll
+            for (int j = 1; j < NASTRO; ++j) v = fma(a[j][i], (AT)__ldg(xa + j), v);
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
-                const XT *xk = xt + (int64_t)ax * S.n_dfa + k;
+                const XT *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + kn[i];
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) sum = fma(a[NASTRO + NPARAXIS * ax + j], (AT)xk[j], sum);
+                for (int j = 0; j < NPARAXIS; ++j) v = fma(a[NASTRO + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
             }
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) sum = fma(a[17 + j], (AT)xi[ic[j]], sum);
-            sum = fma(a[23], xg, sum);
-            AT yn;
-            if (LSQR) {
-                yn = fma(coef, (AT)y[r], sum);
-                ssq = fma(yn, yn, ssq);
-            } else {
-                yn = (AT)y[r] + sum;
+            for (int j = 0; j < NINSTR; ++j) v = fma(a[17 + j][i], (AT)__ldg(xi + ic[j][i]), v);
+            v = fma(a[23][i], xg, v);
+            const int64_t r = r0 + i;
+            if (r < S.n_rows) {
+                AT yn;
+                if (LSQR) {
+                    yn = fma(coef, (AT)y[r], v);
+                    ssq = fma(yn, yn, ssq);
+                } else {
+                    yn = (AT)y[r] + v;
+                }
+                y[r] = (UT)yn;
             }
-            y[r] = (UT)yn;
         }
     }
     if (LSQR) {
@@ -118,15 +108,46 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     }
 }
 
-// aprod 2, star-ordered pass: astrometric (per-star warp reduction, no atomics),
-// instrumental (block-private shared-memory accumulators, or global atomics
-// when n_instr is too large) and global (block reduction) parts.
+// Add a warp's per-lane partial sums of the 5 astrometric columns of star k:
+// the 32 x 5 partials go through a per-warp shared-memory buffer and lanes
+// 0..4 each sum one column (31 adds per column instead of a 5-step shuffle
+// tree per value on every lane). Warp-collective.
+template <typename AT>
+__device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT *__restrict__ wbuf,
+                                                double *__restrict__ z)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NASTRO; ++j) {
+        wbuf[j * 32 + lane] = acc[j];
+        acc[j] = (AT)0;
+    }
+    __syncwarp();
+    if (lane < NASTRO) {
+        AT t = (AT)0;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
+        atomicAdd(z + NASTRO * k + lane, (double)t);
+    }
+    __syncwarp();
+}
+
+// aprod 2, star pass: astrometric, instrumental and global parts. Each warp
+// owns a contiguous range of tiles; astrometric products of the current star
+// accumulate per lane and are flushed once when the star changes (a tile that
+// crosses a star boundary moves its rows of the next star into a second
+// accumulator; rows of stars that begin and end inside one tile are added
+// directly).
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, bool SQUARE, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
-                                                     double *__restrict__ z, const LsqrState *__restrict__ st)
+                                                     double *__restrict__ z, const LsqrState *__restrict__ st,
+                                                     int64_t tiles_per_warp)
 {
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm32[32];
+    __shared__ AT wred[8][NASTRO * 32];
     if (LSQR && st->done) return;
     AT *sm_ins = reinterpret_cast<AT *>(smem_raw);
     const int32_t nsm = INSTR_SMEM ? S.n_instr : 0;
@@ -134,63 +155,98 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    AT *wbuf = wred[threadIdx.x >> 5];
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t t0 = gw * tiles_per_warp;
+    const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
     double *__restrict__ zi = z + S.instr0;
     AT gsum = (AT)0;
-    for (int64_t s = gw; s < S.n_stars; s += nw) {
-        const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        AT acc[NASTRO] = {(AT)0, (AT)0, (AT)0, (AT)0, (AT)0};
-        for (int64_t r = r0 + lane; r < r1; r += 32) {
-            AT a[NASTRO], ai[NINSTR];
+    AT acc[NASTRO], acc2[NASTRO];
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) a[j] = (AT)ld_stream(S.val + j * S.plane + r);
+    for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = (AT)0;
+    int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current run
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
+        const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
+        int32_t ic[NINSTR][R];
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ai[j] = (AT)ld_stream(S.val + (17 + j) * S.plane + r);
-            AT ag = (AT)ld_stream(S.val + 23 * S.plane + r);
-            int32_t ic[NINSTR];
+        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        AT a[NASTRO][R], ai[NINSTR][R], ag[R];
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ic[j] = ld_stream(S.instr + j * S.plane + r);
-            AT yr;
-            if (SQUARE) {
-                yr = (AT)1;
+        for (int j = 0; j < NASTRO; ++j) load_vals<VT, AT>(tb, j, a[j]);
 #pragma unroll
-                for (int j = 0; j < NASTRO; ++j) a[j] = a[j] * a[j];
+        for (int j = 0; j < NINSTR; ++j) load_vals<VT, AT>(tb, 17 + j, ai[j]);
+        load_vals<VT, AT>(tb, 23, ag);
+        const int64_t r0 = t * T + lane * R;
+        bool in[R];
+        AT yr[R];
 #pragma unroll
-                for (int j = 0; j < NINSTR; ++j) ai[j] = ai[j] * ai[j];
-                ag = ag * ag;
-            } else {
-                yr = (AT)y[r];
-            }
+        for (int i = 0; i < R; ++i) {
+            in[i] = r0 + i < S.n_rows;
+            yr[i] = SQUARE ? (in[i] ? (AT)1 : (AT)0) : (in[i] ? (AT)y[r0 + i] : (AT)0);
+        }
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) acc[j] = fma(a[j], yr, acc[j]);
+        for (int i = 0; i < R; ++i) {
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
-                const AT pr = ai[j] * yr;
-                if (INSTR_SMEM)
-                    atomicAdd(sm_ins + ic[j], pr);
-                else
-                    atomicAdd(zi + ic[j], (double)pr);
+                const AT av = SQUARE ? ai[j][i] * ai[j][i] : ai[j][i];
+                if (in[i]) {
+                    if (INSTR_SMEM)
+                        atomicAdd(sm_ins + ic[j][i], av * yr[i]);
+                    else
+                        atomicAdd(zi + ic[j][i], (double)(av * yr[i]));
+                }
             }
-            gsum = fma(ag, yr, gsum);
+            const AT gv = SQUARE ? ag[i] * ag[i] : ag[i];
+            gsum = fma(gv, yr[i], gsum);
         }
+        // astrometric part: does the whole tile belong to star k?
+        const int64_t tile_end = min((t + 1) * T, S.n_rows);  // one past the tile's last row
+        if (__ldg(S.star_ptr + k + 1) >= tile_end) {
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) acc[j] = warp_sum_t(acc[j]);
-        if (lane < NASTRO) {
-            AT mine = acc[0];
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 1; j < NASTRO; ++j) mine = (lane == j) ? acc[j] : mine;
-            z[NASTRO * s + lane] += (double)mine;
+                for (int j = 0; j < NASTRO; ++j) {
+                    const AT av = SQUARE ? a[j][i] * a[j][i] : a[j][i];
+                    acc[j] = fma(av, yr[i], acc[j]);
+                }
+        } else {
+            // the star of the tile's last row ends the next run
+            const int64_t kn = star_of_row(S.star_ptr, S.first_star, t, tile_end - 1);
+            int64_t sr[R];
+            stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+#pragma unroll
+                for (int j = 0; j < NASTRO; ++j) {
+                    const AT av = SQUARE ? a[j][i] * a[j][i] : a[j][i];
+                    const AT pv = av * yr[i];
+                    if (sr[i] == k)
+                        acc[j] += pv;
+                    else if (sr[i] == kn)
+                        acc2[j] += pv;
+                    else if (in[i])
+                        atomicAdd(z + NASTRO * sr[i] + j, (double)pv);
+                }
+            }
+            flush_astro_run(acc, k, wbuf, z);
+#pragma unroll
+            for (int j = 0; j < NASTRO; ++j) {
+                acc[j] = acc2[j];
+                acc2[j] = (AT)0;
+            }
+            k = kn;
         }
     }
+    if (t0 < t1) flush_astro_run(acc, k, wbuf, z);
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
         const AT v = sm_ins[i];
         if (v != (AT)0) atomicAdd(zi + i, (double)v);
     }
     if (S.n_glob) {
-        const double t = block_sum((double)gsum, sm32);
-        if (threadIdx.x == 0 && t != 0.0) atomicAdd(z + S.glob0, t);
+        const double tot = block_sum((double)gsum, sm32);
+        if (threadIdx.x == 0 && tot != 0.0) atomicAdd(z + S.glob0, tot);
     }
 }
 
@@ -208,22 +264,26 @@ __device__ __forceinline__ void flush_att_run(AT (&acc)[NAXES * NPARAXIS], int32
     }
 }
 
-// aprod 2, attitude pass over the knot-ordered copy: each warp owns a
-// contiguous range of positions; runs of equal knot are summed in registers
-// and added once per run (one atomic add per column per run).
+// aprod 2, attitude pass over the knot-ordered tiles: each warp owns the tiles
+// [w*tiles_per_warp, (w+1)*tiles_per_warp); runs of equal knot are summed in
+// registers and added once per run (one atomic add per column per run).
 template <typename VT, typename UT, typename AT, bool SQUARE, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__restrict__ y,
                                                     double *__restrict__ z, const LsqrState *__restrict__ st,
-                                                    int64_t per_warp)
+                                                    int64_t tiles_per_warp)
 {
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
+    constexpr int NA = NAXES * NPARAXIS;
     if (LSQR && st->done) return;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n = S.n_rows;
-    const int64_t p0 = gw * per_warp;
-    if (p0 >= n) return;
-    const int64_t p1 = min(n, p0 + per_warp);
+    const int64_t t0 = gw * tiles_per_warp;
+    if (t0 >= S.n_tiles) return;
+    const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
     const int32_t nk = S.n_dfa - 3;
+    const int64_t p0 = t0 * T;
     // knot of p0: the largest k with knot_ptr[k] <= p0
     int32_t lo = 0, hi = nk - 1;
     while (lo < hi) {
@@ -236,41 +296,53 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
     int32_t k = lo;
     int64_t next = S.knot_ptr[k + 1];
     double *__restrict__ zt = z + S.att0;
-    AT acc[NAXES * NPARAXIS];
+    AT acc[NA];
 #pragma unroll
-    for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = (AT)0;
-    for (int64_t q = p0; q < p1; q += 32) {
-        const int64_t i = q + lane;
-        const bool active = i < p1;
-        const int64_t last = min(q + 31, p1 - 1);
-        AT a[NAXES * NPARAXIS];
-        AT yr = (AT)0;
-        if (active) {
+    for (int j = 0; j < NA; ++j) acc[j] = (AT)0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint8_t *tb = S.atiles + t * Tile<VT>::ABYTES;
+        const int64_t q = t * T;
+        const int64_t lastp = min(q + T - 1, n - 1);
+        const int64_t pl = q + lane * R;
+        AT a[NA][R];
 #pragma unroll
-            for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = (AT)ld_stream(S.att_k + j * S.plane + i);
-            if (SQUARE) {
-                yr = (AT)1;
+        for (int j = 0; j < NA; ++j) load_vals<VT, AT>(tb, j, a[j]);
+        AT yr[R];
+        if (SQUARE) {
 #pragma unroll
-                for (int j = 0; j < NAXES * NPARAXIS; ++j) a[j] = a[j] * a[j];
-            } else {
-                yr = (AT)y[ld_stream(S.perm + i)];
-            }
+            for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)1 : (AT)0;
+#pragma unroll
+            for (int j = 0; j < NA; ++j)
+#pragma unroll
+                for (int i = 0; i < R; ++i) a[j][i] = a[j][i] * a[j][i];
+        } else {
+            int32_t pr[R];
+            load_ints<R>(tb + NA * Tile<VT>::VBLK, 0, pr);
+#pragma unroll
+            for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)y[pr[i]] : (AT)0;
         }
-        if (last < next) {  // every position of this step is on knot k
-            if (active) {
+        if (lastp < next) {  // every position of this tile is on knot k
 #pragma unroll
-                for (int j = 0; j < NAXES * NPARAXIS; ++j) acc[j] = fma(a[j], yr, acc[j]);
-            }
-        } else {  // the step crosses knot boundaries
+            for (int j = 0; j < NA; ++j)
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc[j] = fma(a[j][i], yr[i], acc[j]);
+        } else {  // the tile crosses knot boundaries: add its products position by position
             flush_att_run(acc, k, S.n_dfa, zt);
-            int32_t kl = k;
-            if (active) {
-                while (S.knot_ptr[kl + 1] <= i) ++kl;
 #pragma unroll
-                for (int j = 0; j < NAXES * NPARAXIS; ++j)
-                    atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), (double)(a[j] * yr));
+            for (int i = 0; i < R; ++i) {
+                const int64_t p = pl + i;
+                if (p < n) {
+                    int32_t kl = k;
+                    while (S.knot_ptr[kl + 1] <= p) ++kl;
+#pragma unroll
+                    for (int j = 0; j < NA; ++j) {
+                        const AT pv = a[j][i] * yr[i];
+                        if (pv != (AT)0)
+                            atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), (double)pv);
+                    }
+                }
             }
-            k = __shfl_sync(0xffffffffu, kl, (int)(last - q));
+            while (S.knot_ptr[k + 1] <= lastp) ++k;
             next = S.knot_ptr[k + 1];
         }
     }
@@ -288,22 +360,29 @@ static int persistent_blocks(const gsr_ctx *c, KernelT kern, size_t dyn_smem)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn_smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * c->sm_count;
-    // no more warps than stars, at least one block
-    const int64_t max_blocks = (c->n_stars + (kThreads / 32) - 1) / (kThreads / 32);
+    // no more warps than tiles, at least one block
+    const int64_t max_blocks = (c->n_tiles + (kThreads / 32) - 1) / (kThreads / 32);
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     if (blocks > MAX_PARTIALS) blocks = MAX_PARTIALS;
     return (int)blocks;
 }
 
-// bytes of shared memory that staging the gathered part of x needs (0 = too large, gather from L1)
-static constexpr size_t kStageBudget = 160 * 1024;
-
-template <typename XT>
-static size_t stage_bytes(const gsr_ctx *c)
+// Contiguous tile ranges for the aprod 2 passes: one range per warp of the
+// resident grid, at least 8 tiles per warp.
+template <typename KernelT>
+static void tile_ranges(const gsr_ctx *c, KernelT kern, size_t dyn_smem, int64_t *per_warp, int64_t *blocks)
 {
-    const size_t b = sizeof(XT) * ((size_t)NAXES * c->n_dfa + (size_t)c->n_instr);
-    return b <= kStageBudget ? b : 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn_smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t wpb = kThreads / 32;
+    const int64_t max_warps = (int64_t)per_sm * c->sm_count * wpb;
+    int64_t per = (c->n_tiles + max_warps - 1) / max_warps;
+    if (per < 8) per = 8;
+    const int64_t warps = (c->n_tiles + per - 1) / per;
+    *per_warp = per;
+    *blocks = std::max<int64_t>((warps + wpb - 1) / wpb, 1);
 }
 
 template <typename VT, typename XT, typename UT, typename AT>
@@ -311,27 +390,18 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
                             cudaStream_t s, int *grid_out)
 {
     const SysView<VT> S = view<VT>(c);
-    const size_t dyn = stage_bytes<XT>(c);
     auto pick = [&](auto kern) -> cudaError_t {
-        if (dyn > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-            if (e != cudaSuccess) return e;
-        }
-        const int g = persistent_blocks(c, kern, dyn);
+        const int g = persistent_blocks(c, kern, 0);
         if (grid_out) {
             *grid_out = g;
             return cudaSuccess;
         }
         if (!x || !y) return cudaErrorInvalidValue;
-        kern<<<g, kThreads, dyn, s>>>(S, (const XT *)x, (UT *)y, st, part);
+        kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part);
         return cudaGetLastError();
     };
-    if (st) {
-        if (dyn) return pick(k_aprod1<VT, XT, UT, AT, true, true>);
-        return pick(k_aprod1<VT, XT, UT, AT, true, false>);
-    }
-    if (dyn) return pick(k_aprod1<VT, XT, UT, AT, false, true>);
-    return pick(k_aprod1<VT, XT, UT, AT, false, false>);
+    if (st) return pick(k_aprod1<VT, XT, UT, AT, true>);
+    return pick(k_aprod1<VT, XT, UT, AT, false>);
 }
 
 static cudaError_t aprod1_dispatch(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
@@ -367,8 +437,9 @@ static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
-    const int g = persistent_blocks(c, kern, dyn);
-    kern<<<g, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, st);
+    int64_t per = 0, blocks = 0;
+    tile_ranges(c, kern, dyn, &per, &blocks);
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, st, per);
     return cudaGetLastError();
 }
 
@@ -383,17 +454,10 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, const Ls
     else
         e = aprod2_star_launch<VT, UT, AT, false, SQ, LS>(c, y, x, st, s);
     if (e != cudaSuccess) return e;
-    // attitude pass: at least 256 positions per warp
+    // attitude pass
     auto kern = k_aprod2_att<VT, UT, AT, SQ, LS>;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const int64_t wpb = kThreads / 32;
-    const int64_t max_warps = (int64_t)per_sm * c->sm_count * wpb;
-    int64_t per = (c->n_rows + max_warps - 1) / max_warps;
-    if (per < 256) per = 256;
-    const int64_t warps = (c->n_rows + per - 1) / per;
-    const int64_t blocks = (warps + wpb - 1) / wpb;
+    int64_t per = 0, blocks = 0;
+    tile_ranges(c, kern, 0, &per, &blocks);
     kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, st, per);
     return cudaGetLastError();
 }
@@ -403,6 +467,7 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
 {
     if (c->n_rows == 0) return cudaSuccess;
     if (inner32) {
+        if (square) return aprod2_t<float, float, float, true, false>(c, y, x, nullptr, s);
         if (st) return aprod2_t<float, float, float, false, true>(c, y, x, st, s);
         return aprod2_t<float, float, float, false, false>(c, y, x, nullptr, s);
     }

@@ -4,7 +4,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "gsr_internal.cuh"
+#include "tiles.cuh"
 
 #define GSR_API extern "C" __attribute__((visibility("default")))
 
@@ -71,21 +71,26 @@ __global__ void k_validate(const ST *__restrict__ vals, int32_t layout, int64_t 
     if (bv) atomicOr(errw + 2, 1);
 }
 
+// rows [0, n) of the caller's arrays -> rows [row0, row0 + n) of the tiled layout (tiles.cuh)
 template <typename ST, typename DT>
 __global__ void k_convert(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
-                          const int32_t *__restrict__ instr, int64_t n, int32_t n_glob, DT *__restrict__ dvals,
-                          int32_t *__restrict__ dknot, int32_t *__restrict__ dinstr, int64_t plane, int64_t row0)
+                          const int32_t *__restrict__ instr, int64_t n, int32_t n_glob, uint8_t *__restrict__ tiles,
+                          int64_t row0)
 {
+    using TL = Tile<DT>;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = row0 + r;
+        uint8_t *tb = tiles + (o / TL::T) * TL::BYTES;
+        const int64_t i = o % TL::T;
         for (int j = 0; j < NPAR; ++j) {
             ST v = layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r];
             if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
-            dvals[j * plane + o] = (DT)v;
+            reinterpret_cast<DT *>(tb + j * TL::VBLK)[i] = (DT)v;
         }
-        dknot[o] = knot[r];
+        int32_t *ti = reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK);
+        ti[i] = knot[r];
         for (int j = 0; j < NINSTR; ++j)
-            dinstr[j * plane + o] = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+            ti[(1 + j) * TL::T + i] = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
     }
 }
 
@@ -122,11 +127,11 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
     if (hw[1]) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
     if (hw[2]) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
     if (c->prec == GSR_FP32)
-        k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob, (float *)c->vals,
-                                                c->knot, c->instr, c->plane, row0);
+        k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
+                                                (uint8_t *)c->tiles, row0);
     else
         k_convert<ST, double><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
-                                                 (double *)c->vals, c->knot, c->instr, c->plane, row0);
+                                                 (uint8_t *)c->tiles, row0);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(c, e, "conversion");
     return GSR_OK;
@@ -250,7 +255,20 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
     for (int64_t s = 0; s < n_stars; ++s)
         c->max_obs = std::max<int64_t>(c->max_obs, c->star_ptr_h[s + 1] - c->star_ptr_h[s]);
     c->n_cols = (int64_t)NASTRO * n_stars + (int64_t)NAXES * n_dfa + n_instr + n_glob;
-    c->plane = ((std::max<int64_t>(c->n_rows, 1) + 63) / 64) * 64;
+    const int64_t rows_per_tile = value_precision == GSR_FP32 ? Tile<float>::T : Tile<double>::T;
+    const int64_t tile_bytes = value_precision == GSR_FP32 ? Tile<float>::BYTES : Tile<double>::BYTES;
+    const int64_t atile_bytes = value_precision == GSR_FP32 ? Tile<float>::ABYTES : Tile<double>::ABYTES;
+    c->n_tiles = (c->n_rows + rows_per_tile - 1) / rows_per_tile;
+    // first star of each tile (host), star of the last row at index n_tiles
+    std::vector<int32_t> first_star((size_t)c->n_tiles + 1, 0);
+    {
+        int64_t st = 0;
+        for (int64_t t = 0; t <= c->n_tiles; ++t) {
+            const int64_t row = std::min(t * rows_per_tile, std::max<int64_t>(c->n_rows - 1, 0));
+            while (st + 1 < n_stars && c->star_ptr_h[st + 1] <= row) ++st;
+            first_star[(size_t)t] = (int32_t)st;
+        }
+    }
 
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -259,15 +277,14 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
         delete c;
         return GSR_ECUDA;
     }
-    const size_t vbytes = (c->prec == GSR_FP32 ? sizeof(float) : sizeof(double)) * NPAR * (size_t)c->plane;
-    if ((e = cudaMalloc(&c->vals, vbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&c->knot, sizeof(int32_t) * (size_t)c->plane)) != cudaSuccess ||
-        (e = cudaMalloc(&c->instr, sizeof(int32_t) * NINSTR * (size_t)c->plane)) != cudaSuccess ||
+    const size_t tbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * (size_t)tile_bytes;
+    const size_t abytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * (size_t)atile_bytes;
+    if ((e = cudaMalloc(&c->tiles, tbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->atiles, abytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->first_star, sizeof(int32_t) * first_star.size())) != cudaSuccess ||
         (e = cudaMalloc(&c->star_ptr, sizeof(int64_t) * (size_t)(n_stars + 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->b, sizeof(double) * (size_t)std::max<int64_t>(c->n_rows, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->errw, 4 * sizeof(int32_t))) != cudaSuccess ||
-        (e = cudaMalloc(&c->att_k, vbytes / NPAR * (NAXES * NPARAXIS))) != cudaSuccess ||
-        (e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)c->plane)) != cudaSuccess ||
         (e = cudaMalloc(&c->knot_ptr, sizeof(int64_t) * (size_t)(n_dfa - 2))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess) {
@@ -275,10 +292,11 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
         gsr_destroy(c);
         return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
     }
-    // padding rows (plane tail) hold zeros so that vectorised readers see finite values
-    e = cudaMemset(c->vals, 0, vbytes);
-    if (e == cudaSuccess) e = cudaMemset(c->knot, 0, sizeof(int32_t) * (size_t)c->plane);
-    if (e == cudaSuccess) e = cudaMemset(c->instr, 0, sizeof(int32_t) * NINSTR * (size_t)c->plane);
+    // padding rows of the last tile hold zeros (zero coefficients contribute nothing)
+    e = cudaMemset(c->tiles, 0, tbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->atiles, 0, abytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->first_star, first_star.data(), sizeof(int32_t) * first_star.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->star_ptr, c->star_ptr_h.data(), sizeof(int64_t) * (size_t)(n_stars + 1),
                        cudaMemcpyHostToDevice);
@@ -296,14 +314,12 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     if (!c) return GSR_OK;
     cudaSetDevice(c->device);
     free_workspace(c);
-    cudaFree(c->vals);
-    cudaFree(c->knot);
-    cudaFree(c->instr);
+    cudaFree(c->tiles);
+    cudaFree(c->atiles);
+    cudaFree(c->first_star);
     cudaFree(c->star_ptr);
     cudaFree(c->b);
     cudaFree(c->errw);
-    cudaFree(c->att_k);
-    cudaFree(c->perm);
     cudaFree(c->knot_ptr);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->ev) cudaEventDestroy(c->ev);

@@ -22,19 +22,18 @@ constexpr int NINSTR = 6;    // instrumental coefficients per row
 constexpr int MAX_PARTIALS = 4096;  // per-block partial sums kept for the norms
 
 // ---------------------------------------------------------------- device views
-// Coefficients are stored as 24 SoA planes of VT (double or float), plane j at
-// val + j*plane. knot: one int32 plane. instr: 6 int32 planes (instrumental
-// index in [0, n_instr)). Rows of star s are [star_ptr[s], star_ptr[s+1]).
+// The coefficient matrix lives in tiles of rows (tiles.cuh): `tiles` holds the
+// star-ordered tile records, `atiles` the knot-ordered attitude tiles
+// (layout.cu). Rows of star s are [star_ptr[s], star_ptr[s+1]); first_star[t]
+// is the star of the first row of tile t (first_star[n_tiles] = last star).
 template <typename VT>
 struct SysView {
-    const VT *__restrict__ val;
-    const int32_t *__restrict__ knot;
-    const int32_t *__restrict__ instr;
+    const uint8_t *__restrict__ tiles;
+    const uint8_t *__restrict__ atiles;
     const int64_t *__restrict__ star_ptr;
-    const VT *__restrict__ att_k;         // 12 knot-ordered attitude planes (layout.cu)
-    const int32_t *__restrict__ perm;     // row of each knot-ordered position
-    const int64_t *__restrict__ knot_ptr; // first position of each knot, [n_dfa-2]
-    int64_t plane;
+    const int32_t *__restrict__ first_star;
+    const int64_t *__restrict__ knot_ptr;  // first knot-ordered position of each knot, [n_dfa-2]
+    int64_t n_tiles;
     int64_t n_stars, n_rows;
     int32_t n_dfa, n_instr, n_glob;
     int64_t att0, instr0, glob0;  // first column of each section
@@ -95,14 +94,12 @@ struct gsr_ctx {
     int sm_count = 0;
     int64_t n_stars = 0, n_rows = 0, n_cols = 0;
     int32_t n_dfa = 0, n_instr = 0, n_glob = 0;
-    int64_t plane = 0;               // padded plane length (elements)
-    void *vals = nullptr;            // 24 planes of double or float
-    int32_t *knot = nullptr;         // 1 plane
-    int32_t *instr = nullptr;        // 6 planes
-    void *att_k = nullptr;           // 12 knot-ordered attitude planes (same type as vals)
-    int32_t *perm = nullptr;         // row of each knot-ordered position
+    int64_t n_tiles = 0;             // row tiles (tiles.cuh); rows per tile depend on the precision
+    void *tiles = nullptr;           // star-ordered tile records
+    void *atiles = nullptr;          // knot-ordered attitude tile records
+    int32_t *first_star = nullptr;   // [n_tiles + 1] star of the first row of each tile
     int64_t *knot_ptr = nullptr;     // [n_dfa-2] first position of each knot
-    bool att_valid = false;          // att_k / perm / knot_ptr match the loaded rows
+    bool att_valid = false;          // atiles / knot_ptr match the loaded rows
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -127,14 +124,12 @@ template <typename VT>
 SysView<VT> view(const gsr_ctx *c)
 {
     SysView<VT> s;
-    s.val = static_cast<const VT *>(c->vals);
-    s.knot = c->knot;
-    s.instr = c->instr;
+    s.tiles = static_cast<const uint8_t *>(c->tiles);
+    s.atiles = static_cast<const uint8_t *>(c->atiles);
     s.star_ptr = c->star_ptr;
-    s.att_k = static_cast<const VT *>(c->att_k);
-    s.perm = c->perm;
+    s.first_star = c->first_star;
     s.knot_ptr = c->knot_ptr;
-    s.plane = c->plane;
+    s.n_tiles = c->n_tiles;
     s.n_stars = c->n_stars;
     s.n_rows = c->n_rows;
     s.n_dfa = c->n_dfa;
@@ -164,13 +159,16 @@ gsr_status ensure_workspace(gsr_ctx *c);
 void free_workspace(gsr_ctx *c);
 void default_params(gsr_solve_params *p);
 int col_grid(const gsr_ctx *c, int64_t n);
-gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s);
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false);
 LsqrState initial_state(const gsr_solve_params *prm);
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
+cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
+                            double *part, cudaStream_t s, int *grid_out);
+cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out,
                        gsr_solve_info *info, cudaStream_t s);
 

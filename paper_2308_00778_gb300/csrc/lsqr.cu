@@ -456,13 +456,16 @@ void default_params(gsr_solve_params *p)
     p->max_outer = 0;
 }
 
-gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s)
+// p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in
+// binary32 (binary32-stored systems; used by the mixed solver, whose
+// refinement does not depend on the exact scaling), otherwise binary64.
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32)
 {
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols;
     cudaError_t e = cudaMemsetAsync(ws.tmp, 0, nc * sizeof(double), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-    if (use && (e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s)) != cudaSuccess)
+    if (use && (e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s, f32)) != cudaSuccess)
         return cuda_fail(c, e, "column norms");
     k_precond_finish<<<col_grid(c, nc), kColThreads, 0, s>>>(ws.tmp, ws.p, nc, use ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "preconditioner");

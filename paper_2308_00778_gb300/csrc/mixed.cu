@@ -17,8 +17,8 @@
 // damped inner solve the damping acts on the correction only, so the fixed
 // point is the undamped minimiser (it differs from the damped one by
 // O(damp^2), far below the binary32 noise for the damping used here).
-#include "gsr_internal.cuh"
 #include "dfloat.cuh"
+#include "tiles.cuh"
 
 namespace gsr {
 
@@ -31,68 +31,78 @@ __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ out, 
     }
 }
 
-// r = b - A x for every row (one warp per star), stored in binary32, with
-// per-block sums of squares of r.
-// STAGE: the attitude and instrumental parts of x are copied to shared memory
-// once per block (as in aprod 1), so the per-row gathers stay on chip.
-template <bool STAGE>
+// r = b - A x for every row, stored in binary32, over the binary32 row tiles
+// (one warp per tile, 4 rows per lane: four independent double-float chains).
+// b comes either pre-split (bhl, two binary32 per row) or as binary64 split
+// here; `part` (may be null) receives per-block sums of squares of r.
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
-                                                  const float2 *__restrict__ bhl, float *__restrict__ r_out,
-                                                  double *__restrict__ part)
+                                                  const float2 *__restrict__ bhl, const double *__restrict__ b64,
+                                                  float *__restrict__ r_out, double *__restrict__ part)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int R = Tile<float>::R;
+    constexpr int T = Tile<float>::T;
     __shared__ double sm32[32];
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float2 *xt = xhl + S.att0;
-    const float2 *xi = xhl + S.instr0;
-    if (STAGE) {
-        float2 *sx = reinterpret_cast<float2 *>(smem_raw);
-        const int32_t n_att = NAXES * S.n_dfa, n_st = n_att + S.n_instr;
-        for (int32_t i = threadIdx.x; i < n_st; i += blockDim.x) sx[i] = xhl[S.att0 + i];
-        __syncthreads();
-        xt = sx;
-        xi = sx + n_att;
-    }
+    const float2 *__restrict__ xt = xhl + S.att0;
+    const float2 *__restrict__ xi = xhl + S.instr0;
     const float2 xg = S.n_glob ? xhl[S.glob0] : make_float2(0.f, 0.f);
     float ssq = 0.f;
-    for (int64_t s = gw; s < S.n_stars; s += nw) {
-        const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        float2 xa[NASTRO];
+    for (int64_t t = gw; t < S.n_tiles; t += nw) {
+        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
+        const uint8_t *ti = tb + NPAR * Tile<float>::VBLK;
+        int32_t kn[R];
+        load_ints<R>(ti, 0, kn);
+        int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) xa[j] = xhl[NASTRO * s + j];
-        for (int64_t r = r0 + lane; r < r1; r += 32) {
-            float a[NPAR];
+        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        float a[NPAR][R];
 #pragma unroll
-            for (int j = 0; j < NPAR; ++j) a[j] = __ldcs(S.val + j * S.plane + r);
-            const int32_t k = __ldcs(S.knot + r);
-            int32_t ic[NINSTR];
+        for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
+        const int64_t r0 = t * T + lane * R;
+        int64_t sr[R];
+        stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+        float sh[R], c[R];
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ic[j] = __ldcs(S.instr + j * S.plane + r);
-            float sh = 0.f, c = 0.f;
+        for (int i = 0; i < R; ++i) {
+            sh[i] = 0.f;
+            c[i] = 0.f;
+        }
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) acc_term(a[j], xa[j], sh, c);
+        for (int j = 0; j < NASTRO; ++j)
 #pragma unroll
-            for (int ax = 0; ax < NAXES; ++ax) {
-                const float2 *xk = xt + (int64_t)ax * S.n_dfa + k;
+            for (int i = 0; i < R; ++i) acc_term(a[j][i], xhl[NASTRO * sr[i] + j], sh[i], c[i]);
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) acc_term(a[NASTRO + NPARAXIS * ax + j], xk[j], sh, c);
+        for (int ax = 0; ax < NAXES; ++ax)
+#pragma unroll
+            for (int j = 0; j < NPARAXIS; ++j)
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    acc_term(a[NASTRO + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j)
+#pragma unroll
+            for (int i = 0; i < R; ++i) acc_term(a[17 + j][i], xi[ic[j][i]], sh[i], c[i]);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            acc_term(a[23][i], xg, sh[i], c[i]);
+            const int64_t r = r0 + i;
+            if (r < S.n_rows) {
+                const float2 bb = bhl ? __ldcs(bhl + r) : split_double(__ldcs(b64 + r));
+                float tt, e;
+                two_sum(bb.x, -sh[i], tt, e);  // b_hi - s exactly
+                const float lo = __fadd_rn(__fadd_rn(e, bb.y), -c[i]);
+                const float rv = __fadd_rn(tt, lo);
+                r_out[r] = rv;
+                ssq = fmaf(rv, rv, ssq);
             }
-#pragma unroll
-            for (int j = 0; j < NINSTR; ++j) acc_term(a[17 + j], xi[ic[j]], sh, c);
-            acc_term(a[23], xg, sh, c);
-            const float2 b = __ldcs(bhl + r);
-            float t, e;
-            two_sum(b.x, -sh, t, e);  // b_hi - s exactly
-            const float lo = __fadd_rn(__fadd_rn(e, b.y), -c);
-            const float rv = __fadd_rn(t, lo);
-            r_out[r] = rv;
-            ssq = fmaf(rv, rv, ssq);
         }
     }
-    const double tot = block_sum((double)ssq, sm32);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (part) {
+        const double tot = block_sum((double)ssq, sm32);
+        if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    }
 }
 
 // x += p * y (the inner solution, scaled back); per-block sums of squares of
@@ -122,37 +132,30 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
     }
 }
 
-static constexpr size_t kStageBudget = 160 * 1024;
-
-static size_t residual_stage_bytes(const gsr_ctx *c)
+// Launch (or, with grid_out, only size) the residual kernel. Allocates nothing.
+cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
+                            double *part, cudaStream_t s, int *grid_out)
 {
-    const size_t b = sizeof(float2) * ((size_t)NAXES * c->n_dfa + (size_t)c->n_instr);
-    return b <= kStageBudget ? b : 0;
-}
-
-// launch (or, with grid_out, only size) the residual kernel
-static cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, float *r, double *part,
-                                   cudaStream_t s, int *grid_out)
-{
-    const size_t dyn = residual_stage_bytes(c);
-    auto kern = dyn ? k_residual<true> : k_residual<false>;
-    if (dyn > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * c->sm_count;
-    const int64_t max_blocks = (c->n_stars + (kThreads / 32) - 1) / (kThreads / 32);
-    blocks = std::min(blocks, max_blocks);
+    blocks = std::min<int64_t>(blocks, (c->n_tiles + (kThreads / 32) - 1) / (kThreads / 32));
     blocks = std::max<int64_t>(blocks, 1);
     blocks = std::min<int64_t>(blocks, MAX_PARTIALS);
     if (grid_out) {
         *grid_out = (int)blocks;
         return cudaSuccess;
     }
-    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<float>(c), xhl, bhl, r, part);
+    k_residual<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, bhl, b64, r, part);
+    return cudaGetLastError();
+}
+
+// x (binary64) -> (hi, lo) binary32 pairs. Allocates nothing.
+cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_split<<<col_grid(c, n), kThreads, 0, s>>>(x, out, n);
     return cudaGetLastError();
 }
 
@@ -164,7 +167,7 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
     Workspace &ws = c->ws;
     k_split<<<col_grid(c, c->n_rows), kThreads, 0, s>>>(c->b, ws.bhl, c->n_rows);
     k_split<<<col_grid(c, c->n_cols), kThreads, 0, s>>>(x, ws.xhl, c->n_cols);
-    const cudaError_t e = residual_launch(c, ws.xhl, ws.bhl, r, ws.part_u, s, nullptr);
+    const cudaError_t e = residual_launch(c, ws.xhl, ws.bhl, nullptr, r, ws.part_u, s, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "residual");
     return GSR_OK;
 }
@@ -182,7 +185,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     const bool dev_io = prm->where == GSR_DEVICE;
     cudaError_t e;
 
-    if ((rc = precond_pass(c, prm->precond != 0, s)) != GSR_OK) return rc;
+    if ((rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
     k_split<<<grow, kThreads, 0, s>>>(c->b, ws.bhl, nr);
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double), dev_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -197,7 +200,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
     const double refine_tol = prm->refine_tol != 0.0 ? prm->refine_tol : 1e-10;
     int gres = 1;
-    residual_launch(c, nullptr, nullptr, nullptr, nullptr, s, &gres);
+    residual_launch(c, nullptr, nullptr, nullptr, nullptr, nullptr, s, &gres);
     const int64_t att0 = (int64_t)NASTRO * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa,
                   glob0 = instr0 + c->n_instr;
 
@@ -206,7 +209,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     gsr_status status = GSR_OK;
     for (; outer < max_outer; ++outer) {
         k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
-        if (nr > 0 && (e = residual_launch(c, ws.xhl, ws.bhl, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
+        if (nr > 0 && (e = residual_launch(c, ws.xhl, ws.bhl, nullptr, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
             return cuda_fail(c, e, "residual");
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
         status = run_lsqr(c, init, true, false, nr > 0 ? gres : 0, prm->graph_k, prm->timeout_s, t0, s, &fin);

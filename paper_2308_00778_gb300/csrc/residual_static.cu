@@ -3,12 +3,12 @@
 //
 // gsr_residual needs scratch for the split copies of x and b and for its
 // partial sums, and takes it from the context's workspace, which is allocated
-// with cudaMalloc on first use. This entry point keeps its only scratch, the
-// split copy of x, in a file-scope __device__ array of fixed size, splits b
-// inside the kernel, and writes no partial sums, so a call allocates nothing.
+// with cudaMalloc on first use. This entry point runs the same kernels but
+// keeps its only scratch, the split copy of x, in a file-scope __device__
+// array of fixed size, has b split inside the residual kernel, and writes no
+// partial sums, so a call allocates nothing.
 #include <mutex>
 
-#include "dfloat.cuh"
 #include "gsr_internal.cuh"
 
 #define GSR_API extern "C" __attribute__((visibility("default")))
@@ -41,56 +41,6 @@ static cudaError_t static_scratch(int device, float2 **out)
     return cudaSuccess;
 }
 
-__global__ void k_split_static(const double *__restrict__ x, float2 *__restrict__ out, int64_t n)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = split_double(x[i]);
-}
-
-// r = b - A x, one warp per star; x as (hi, lo) pairs, b split per row here.
-__global__ void __launch_bounds__(256) k_residual_static(SysView<float> S, const float2 *__restrict__ xhl,
-                                                         const double *__restrict__ b, float *__restrict__ r_out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float2 *__restrict__ xt = xhl + S.att0;
-    const float2 *__restrict__ xi = xhl + S.instr0;
-    const float2 xg = S.n_glob ? xhl[S.glob0] : make_float2(0.f, 0.f);
-    for (int64_t s = gw; s < S.n_stars; s += nw) {
-        const int64_t r0 = S.star_ptr[s], r1 = S.star_ptr[s + 1];
-        float2 xa[NASTRO];
-#pragma unroll
-        for (int j = 0; j < NASTRO; ++j) xa[j] = xhl[NASTRO * s + j];
-        for (int64_t r = r0 + lane; r < r1; r += 32) {
-            float a[NPAR];
-#pragma unroll
-            for (int j = 0; j < NPAR; ++j) a[j] = __ldcs(S.val + j * S.plane + r);
-            const int32_t k = __ldcs(S.knot + r);
-            int32_t ic[NINSTR];
-#pragma unroll
-            for (int j = 0; j < NINSTR; ++j) ic[j] = __ldcs(S.instr + j * S.plane + r);
-            float sh = 0.f, c = 0.f;
-#pragma unroll
-            for (int j = 0; j < NASTRO; ++j) acc_term(a[j], xa[j], sh, c);
-#pragma unroll
-            for (int ax = 0; ax < NAXES; ++ax) {
-                const float2 *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + k;
-#pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) acc_term(a[NASTRO + NPARAXIS * ax + j], xk[j], sh, c);
-            }
-#pragma unroll
-            for (int j = 0; j < NINSTR; ++j) acc_term(a[17 + j], xi[ic[j]], sh, c);
-            acc_term(a[23], xg, sh, c);
-            const float2 bb = split_double(__ldcs(b + r));
-            float t, e;
-            two_sum(bb.x, -sh, t, e);
-            const float lo = __fadd_rn(__fadd_rn(e, bb.y), -c);
-            r_out[r] = __fadd_rn(t, lo);
-        }
-    }
-}
-
 }  // namespace gsr
 
 using namespace gsr;
@@ -111,16 +61,9 @@ GSR_API gsr_status gsr_residual_static(gsr_ctx *c, const double *x, float *r, vo
     if ((e = static_scratch(c->device, &xhl)) != cudaSuccess) return cuda_fail(c, e, "static scratch address");
     if (c->n_rows == 0) return GSR_OK;
     const cudaStream_t s = (cudaStream_t)stream;
-    int64_t gsplit = (c->n_cols + 255) / 256;
-    gsplit = std::min<int64_t>(std::max<int64_t>(gsplit, 1), (int64_t)c->sm_count * 4);
-    k_split_static<<<(unsigned)gsplit, 256, 0, s>>>(x, xhl, c->n_cols);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual_static, 256, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t blocks = (int64_t)per_sm * c->sm_count;
-    blocks = std::min<int64_t>(blocks, (c->n_stars + 7) / 8);
-    blocks = std::max<int64_t>(blocks, 1);
-    k_residual_static<<<(unsigned)blocks, 256, 0, s>>>(view<float>(c), xhl, c->b, r);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual_static");
+    // the same kernels as gsr_residual, with b split inside the residual kernel and no partial sums
+    if ((e = split_launch(c, x, xhl, c->n_cols, s)) != cudaSuccess ||
+        (e = residual_launch(c, xhl, nullptr, c->b, r, nullptr, s, nullptr)) != cudaSuccess)
+        return cuda_fail(c, e, "residual_static");
     return GSR_OK;
 }

@@ -63,7 +63,10 @@ def test_aprod_vs_oracle(name, fp32):
     ctx.close()
 
 
-def test_aprod2_astro_reproducible_rest_close():
+def test_aprod2_repeat_runs_agree():
+    """aprod 2 adds per-star segments and per-knot runs with atomic adds, so the
+    order of additions (and the last bits) can change from run to run; repeated
+    runs agree to 1e-13 of the sum of |terms| in every unknown."""
     h = gsrgen.generate(CASES["c1"])
     s = oracle.from_host_system(h)
     ctx = context_for(h)
@@ -74,11 +77,9 @@ def test_aprod2_astro_reproducible_rest_close():
         z = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
         ctx.aprod2(u, z)
         outs.append(z.cpu().numpy())
-    a = 5 * s.n_stars
     scale = oracle.aprod2(abs_system(s), np.abs(u.cpu().numpy()), np.zeros(s.n_cols))
     for o in outs[1:]:
-        assert np.array_equal(o[:a], outs[0][:a])  # astro: one warp per star, no atomics
-        assert np.all(np.abs(o[a:] - outs[0][a:]) <= 1e-13 * scale[a:])  # reordered atomic sums
+        assert np.all(np.abs(o - outs[0]) <= 1e-13 * scale)
     ctx.close()
 
 
