@@ -93,12 +93,21 @@ def _load():
 
 
 def _extra_signatures(lib):
-    """Signatures of the warm-start reference routines (oracle_warm.c), when present."""
+    """Signatures of the warm-start reference routines (warm.c)."""
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-    if hasattr(lib, "oracle_astro_solve"):
-        lib.oracle_astro_solve.restype = ctypes.c_int
-        lib.oracle_astro_solve.argtypes = [ctypes.POINTER(_Sys), P, P, f64, P]
+    lib.oracle_bf16.restype = f64
+    lib.oracle_bf16.argtypes = [f64]
+    lib.oracle_conv_fwd.restype = None
+    lib.oracle_conv_fwd.argtypes = [P, i64, i64, i32, P, P, i32, i32, i32, P]
+    lib.oracle_conv_bwd.restype = None
+    lib.oracle_conv_bwd.argtypes = [P, P, i64, i64, i32, P, i32, i32, P, P, P]
+    lib.oracle_mse.restype = f64
+    lib.oracle_mse.argtypes = [P, P, i64, P]
+    lib.oracle_adam.restype = None
+    lib.oracle_adam.argtypes = [P, P, P, P, i64, f64, f64, f64, f64, i32]
+    lib.oracle_astro_solve.restype = i64
+    lib.oracle_astro_solve.argtypes = [ctypes.POINTER(_Sys), P, P]
 
 
 def _p(a: np.ndarray) -> int:
@@ -200,3 +209,108 @@ def lsqr(s: System, b: np.ndarray, itnlim: int, atol: float = 0.0, btol: float =
     if want_var:
         return x, info.as_dict(), var
     return x, info.as_dict()
+
+
+# ---------------------------------------------------------------- warm start (warm.c)
+def bf16(v: float) -> float:
+    """binary32 -> bfloat16 -> float, round to nearest even."""
+    return _load().oracle_bf16(float(v))
+
+
+def conv_fwd(inp: np.ndarray, W: np.ndarray, bias: np.ndarray, relu: bool, mirrored: bool = False) -> np.ndarray:
+    """One conv1d layer (kernel 5, zero padding 2). inp [nb, L, cin], W [cout, cin, 5], bias [cout]."""
+    inp = np.ascontiguousarray(inp, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    bias = np.ascontiguousarray(bias, dtype=np.float64)
+    nb, L, cin = inp.shape
+    cout = W.shape[0]
+    out = np.empty((nb, L, cout))
+    _load().oracle_conv_fwd(_p(inp), nb, L, cin, _p(W), _p(bias), cout, int(relu), int(mirrored), _p(out))
+    return out
+
+
+def conv_bwd(inp: np.ndarray, dout: np.ndarray, W: np.ndarray, mirrored: bool = False, want_din: bool = True):
+    """Gradients of one layer given dout (w.r.t. the pre-activation output): (din, dW, dbias)."""
+    inp = np.ascontiguousarray(inp, dtype=np.float64)
+    dout = np.ascontiguousarray(dout, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    nb, L, cin = inp.shape
+    cout = W.shape[0]
+    din = np.empty_like(inp) if want_din else None
+    dW = np.zeros_like(W)
+    db = np.zeros(cout)
+    _load().oracle_conv_bwd(_p(inp), _p(dout), nb, L, cin, _p(W), cout, int(mirrored), _p(din) if want_din else None,
+                            _p(dW), _p(db))
+    return din, dW, db
+
+
+def mse(y: np.ndarray, t: np.ndarray):
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.empty_like(y)
+    loss = _load().oracle_mse(_p(y), _p(t), y.size, _p(g))
+    return loss, g
+
+
+def adam(w, m, v, g, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):
+    """In-place Adam step on float64 arrays."""
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _load().oracle_adam(_p(w), _p(m), _p(v), _p(g), w.size, lr, b1, b2, eps, int(step))
+
+
+def astro_solve(s: System, b: np.ndarray, x: np.ndarray) -> int:
+    """Per-star 5x5 astrometric solve given the attitude part of x (in place). Returns failed stars."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+    return int(_load().oracle_astro_solve(ctypes.byref(s._s), _p(b), _p(x)))
+
+
+# The network: 6 conv1d layers, 64 channels, kernel 5: 6 -> 64 -> 64 -> 64 -> 64 -> 64 -> 3,
+# ReLU after the first five. Parameters are a list of (W [cout, cin, 5], bias [cout]).
+NET_CHANNELS = [6, 64, 64, 64, 64, 64, 3]
+
+
+def net_forward(params, x: np.ndarray, mirrored: bool = False):
+    """x [nb, L, 6] -> (y [nb, L, 3], activations: the input of every layer)."""
+    acts = [np.ascontiguousarray(x, dtype=np.float64)]
+    h = acts[0]
+    for i, (W, bias) in enumerate(params):
+        last = i == len(params) - 1
+        h = conv_fwd(h, W, bias, relu=not last, mirrored=mirrored)
+        if not last:
+            acts.append(h)
+    return h, acts
+
+
+def net_backward(params, acts, dy: np.ndarray, mirrored: bool = False):
+    """Gradients of all parameters given dLoss/dy; acts from net_forward."""
+    grads = [None] * len(params)
+    d = np.ascontiguousarray(dy, dtype=np.float64)
+    for i in range(len(params) - 1, -1, -1):
+        W, _ = params[i]
+        din, dW, db = conv_bwd(acts[i], d, W, mirrored=mirrored, want_din=i > 0)
+        grads[i] = (dW, db)
+        if i > 0:
+            d = din * (acts[i] > 0.0)  # ReLU of the previous layer
+    return grads
+
+
+def jacobi_features(s: System, b: np.ndarray):
+    """Attitude features of the warm start: per knot and axis the Jacobi estimate
+    (A^T b)_j / |A_:,j|^2, scaled by its root mean square, and the centred log of
+    |A_:,j|^2. Returns (features [n_dfa, 6], scale)."""
+    z = aprod2(s, b, np.zeros(s.n_cols))
+    p = precond(s)
+    a0, a1 = s.blocks()["att"]
+    colsq = 1.0 / (p[a0:a1] ** 2)
+    jac = z[a0:a1] / colsq
+    scale = float(np.sqrt(np.mean(jac ** 2))) or 1.0
+    lg = np.log(colsq)
+    lg = lg - lg.mean()
+    f = np.empty((s.n_dfa, 6))
+    for ax in range(3):
+        f[:, ax] = jac[ax * s.n_dfa:(ax + 1) * s.n_dfa] / scale
+        f[:, 3 + ax] = lg[ax * s.n_dfa:(ax + 1) * s.n_dfa]
+    return f, scale

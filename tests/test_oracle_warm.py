@@ -1,0 +1,172 @@
+"""Pins of the warm-start oracle (oracle/warm.c and its composition in oracle/__init__.py).
+
+* conv1d forward against a direct numpy evaluation of the definition;
+* conv1d / network gradients against central finite differences;
+* bfloat16 rounding against hand-computed ties and carries;
+* MSE and Adam against closed forms;
+* the per-star 5x5 astrometric solve against numpy least squares per star;
+* the Jacobi features against an explicit dense evaluation.
+"""
+import numpy as np
+import pytest
+
+import gsrgen
+import oracle
+from conftest import dense_matrix
+
+
+def _conv_numpy(x, W, b):
+    nb, L, cin = x.shape
+    cout = W.shape[0]
+    xp = np.zeros((nb, L + 4, cin))
+    xp[:, 2:L + 2] = x
+    out = np.zeros((nb, L, cout)) + b
+    for t in range(5):
+        out += np.einsum("bpc,oc->bpo", xp[:, t:t + L], W[:, :, t])
+    return out
+
+
+def test_conv_forward_definition():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((3, 37, 6))
+    W = rng.standard_normal((9, 6, 5))
+    b = rng.standard_normal(9)
+    np.testing.assert_allclose(oracle.conv_fwd(x, W, b, relu=False), _conv_numpy(x, W, b), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle.conv_fwd(x, W, b, relu=True), np.maximum(_conv_numpy(x, W, b), 0), atol=1e-13)
+
+
+def test_conv_backward_finite_differences():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 11, 4))
+    W = rng.standard_normal((5, 4, 5))
+    b = rng.standard_normal(5)
+    dout = rng.standard_normal((2, 11, 5))  # loss = sum(dout * conv(x))
+    din, dW, db = oracle.conv_bwd(x, dout, W)
+    h = 1e-6
+
+    def loss(x_, W_, b_):
+        return float(np.sum(dout * oracle.conv_fwd(x_, W_, b_, relu=False)))
+
+    for idx in [(0, 3, 1), (1, 0, 0), (1, 10, 3), (0, 5, 2)]:
+        e = np.zeros_like(x)
+        e[idx] = h
+        fd = (loss(x + e, W, b) - loss(x - e, W, b)) / (2 * h)
+        assert din[idx] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    for idx in [(0, 0, 0), (4, 3, 4), (2, 1, 2)]:
+        e = np.zeros_like(W)
+        e[idx] = h
+        fd = (loss(x, W + e, b) - loss(x, W - e, b)) / (2 * h)
+        assert dW[idx] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    np.testing.assert_allclose(db, dout.sum(axis=(0, 1)), rtol=1e-13)
+
+
+def _params(rng, chans=oracle.NET_CHANNELS):
+    return [(rng.standard_normal((co, ci, 5)) * np.sqrt(2.0 / (5 * ci)), rng.standard_normal(co) * 0.1)
+            for ci, co in zip(chans[:-1], chans[1:])]
+
+
+def test_network_gradients_finite_differences():
+    rng = np.random.default_rng(2)
+    chans = [6, 8, 8, 8, 8, 8, 3]
+    params = _params(rng, chans)
+    x = rng.standard_normal((2, 13, 6))
+    t = rng.standard_normal((2, 13, 3))
+
+    def loss_of(ps):
+        y, _ = oracle.net_forward(ps, x)
+        return oracle.mse(y, t)[0]
+
+    y, acts = oracle.net_forward(params, x)
+    loss, dy = oracle.mse(y, t)
+    grads = oracle.net_backward(params, acts, dy)
+    h = 1e-6
+    for layer, idx in [(0, (3, 2, 1)), (2, (1, 7, 4)), (5, (2, 0, 3)), (3, (5, 5, 0))]:
+        W, b = params[layer]
+        Wp, Wm = W.copy(), W.copy()
+        Wp[idx] += h
+        Wm[idx] -= h
+        pp = list(params)
+        pp[layer] = (Wp, b)
+        pm = list(params)
+        pm[layer] = (Wm, b)
+        fd = (loss_of(pp) - loss_of(pm)) / (2 * h)
+        assert grads[layer][0][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    W, b = params[4]
+    bp, bm = b.copy(), b.copy()
+    bp[3] += h
+    bm[3] -= h
+    pp, pm = list(params), list(params)
+    pp[4], pm[4] = (W, bp), (W, bm)
+    assert grads[4][1][3] == pytest.approx((loss_of(pp) - loss_of(pm)) / (2 * h), rel=1e-5, abs=1e-9)
+
+
+def test_bf16_rounding():
+    assert oracle.bf16(1.0) == 1.0
+    assert oracle.bf16(1 + 2 ** -8) == 1.0                  # tie: round to even
+    assert oracle.bf16(1 + 3 * 2 ** -8) == 1 + 2 ** -6      # tie: round to even (up)
+    assert oracle.bf16(1 + 2 ** -8 + 2 ** -20) == 1 + 2 ** -7
+    assert oracle.bf16(-3.0) == -3.0
+    assert oracle.bf16(0.0) == 0.0
+    assert oracle.bf16(2 - 2 ** -9) == 2.0                   # carry into the exponent
+    # the mirrored convolution uses exactly these roundings
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((1, 9, 3))
+    W = rng.standard_normal((2, 3, 5))
+    b = rng.standard_normal(2)
+    xr = np.vectorize(oracle.bf16)(x)
+    Wr = np.vectorize(oracle.bf16)(W)
+    np.testing.assert_allclose(oracle.conv_fwd(x, W, b, False, mirrored=True), _conv_numpy(xr, Wr, b), rtol=1e-13,
+                               atol=1e-13)
+
+
+def test_mse_and_adam_closed_forms():
+    y = np.array([1.0, 2.0, -1.0, 0.5])
+    t = np.array([0.0, 2.5, -1.0, 1.5])
+    loss, g = oracle.mse(y, t)
+    assert loss == pytest.approx(np.mean((y - t) ** 2))
+    np.testing.assert_allclose(g, 2 * (y - t) / 4)
+    w = np.array([1.0, -2.0, 0.5])
+    m = np.zeros(3)
+    v = np.zeros(3)
+    gr = np.array([0.3, -4.0, 1e-3])
+    lr, eps = 0.01, 1e-8
+    oracle.adam(w, m, v, gr, lr, eps=eps, step=1)
+    # first step: m_hat = g, v_hat = g^2, update = lr g / (|g| + eps)
+    np.testing.assert_allclose(w, np.array([1.0, -2.0, 0.5]) - lr * gr / (np.abs(gr) + eps), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * gr)
+    np.testing.assert_allclose(v, 0.001 * gr ** 2)
+
+
+def test_astro_solve_vs_lstsq_per_star():
+    cfg = gsrgen.make_cfg(11, 40, (6, 80), 30, 12)
+    h = gsrgen.generate(cfg)
+    s = oracle.from_host_system(h)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    x = np.zeros(s.n_cols)
+    a0, a1 = s.blocks()["att"]
+    x[a0:a1] = h.x_true[a0:a1]
+    assert oracle.astro_solve(s, b, x) == 0
+    D = dense_matrix(h.star_ptr, h.A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    r = b - D[:, a0:a1] @ h.x_true[a0:a1]
+    for st in range(cfg.n_stars):
+        r0, r1 = h.star_ptr[st], h.star_ptr[st + 1]
+        ref = np.linalg.lstsq(D[r0:r1, 5 * st:5 * st + 5], r[r0:r1], rcond=None)[0]
+        np.testing.assert_allclose(x[5 * st:5 * st + 5], ref, rtol=1e-8, atol=1e-10)
+    assert np.all(x[a0:a1] == h.x_true[a0:a1])  # attitude part untouched
+
+
+def test_jacobi_features_dense():
+    cfg = gsrgen.make_cfg(12, 30, 40, 10, 8)
+    h = gsrgen.generate(cfg)
+    s = oracle.from_host_system(h)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    f, scale = oracle.jacobi_features(s, b)
+    D = dense_matrix(h.star_ptr, h.A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    a0, a1 = s.blocks()["att"]
+    colsq = (D[:, a0:a1] ** 2).sum(axis=0)
+    jac = (D[:, a0:a1].T @ b) / colsq
+    np.testing.assert_allclose(scale, np.sqrt(np.mean(jac ** 2)), rtol=1e-12)
+    for ax in range(3):
+        np.testing.assert_allclose(f[:, ax] * scale, jac[ax * 10:(ax + 1) * 10], rtol=1e-11)
+        lg = np.log(colsq) - np.log(colsq).mean()
+        np.testing.assert_allclose(f[:, 3 + ax], lg[ax * 10:(ax + 1) * 10], rtol=1e-11, atol=1e-12)
