@@ -2,8 +2,10 @@
 // system into SoA device planes, aprod 1/2 on caller buffers, and the solve.
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstring>
 
+#include "../../include/gsr_warm.h"
 #include "tiles.cuh"
 
 #define GSR_API extern "C" __attribute__((visibility("default")))
@@ -314,6 +316,7 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     if (!c) return GSR_OK;
     cudaSetDevice(c->device);
     free_workspace(c);
+    if (c->warm_net) gsr_net_destroy(c->warm_net);
     cudaFree(c->tiles);
     cudaFree(c->atiles);
     cudaFree(c->first_star);
@@ -495,8 +498,10 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     if (!c->rhs_set) return fail(c, GSR_ESTATE, "b not loaded");
     if (prm.mode == GSR_MIXED && c->prec != GSR_FP32)
         return fail(c, GSR_EINVAL, "GSR_MIXED needs an FP32-stored context");
-    if (prm.warm != GSR_WARM_NONE) return fail(c, GSR_EINVAL, "warm start not available in this build");
     if (prm.mode == GSR_MIXED && se_out) return fail(c, GSR_EINVAL, "se_out is computed by GSR_PLAIN solves only");
+    if (prm.warm != GSR_WARM_NONE && x0) return fail(c, GSR_EINVAL, "x0 and a warm start are exclusive");
+    if (prm.warm == GSR_WARM_LEARNED && !prm.weights_path)
+        return fail(c, GSR_EINVAL, "GSR_WARM_LEARNED needs weights_path");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // run on the context's own stream (graph capture needs a non-legacy stream), after the caller's work
@@ -507,8 +512,45 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         const gsr_status rl = ensure_att_layout(c, c->own);
         if (rl != GSR_OK) return rl;
     }
-    const gsr_status rc = prm.mode == GSR_MIXED ? mixed_solve(c, &prm, x0, x_out, info, c->own)
-                                                : lsqr_solve(c, &prm, x0, x_out, se_out, info, c->own);
+    // warm start: x0 on the device from the features (and the network)
+    const double *x0_use = x0;
+    bool x0_dev = false;
+    double ms_warm = 0.0;
+    if (prm.warm != GSR_WARM_NONE) {
+        const auto tw = std::chrono::steady_clock::now();
+        gsr_status rw = ensure_workspace(c);
+        if (rw != GSR_OK) return rw;
+        if (!c->ws.x0w && (e = cudaMalloc(&c->ws.x0w, sizeof(double) * (size_t)c->n_cols)) != cudaSuccess)
+            return cuda_fail(c, e, "warm-start vector");
+        gsr_net *net = nullptr;
+        if (prm.warm == GSR_WARM_LEARNED) {
+            if (!c->warm_net || c->warm_path != prm.weights_path) {
+                if (c->warm_net) gsr_net_destroy(c->warm_net);
+                c->warm_net = nullptr;
+                c->warm_path.clear();
+                if ((rw = gsr_net_create(&c->warm_net, c->device)) != GSR_OK) return fail(c, rw, "network allocation");
+                if ((rw = gsr_net_load(c->warm_net, prm.weights_path)) != GSR_OK) {
+                    const std::string m = gsr_net_last_error(c->warm_net);
+                    gsr_net_destroy(c->warm_net);
+                    c->warm_net = nullptr;
+                    return fail(c, rw, m);
+                }
+                c->warm_path = prm.weights_path;
+            }
+            net = c->warm_net;
+        }
+        if ((rw = warm_start_dev(c, net, c->ws.x0w, c->own)) != GSR_OK) return rw;
+        if ((e = cudaStreamSynchronize(c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
+        x0_use = c->ws.x0w;
+        x0_dev = true;
+        ms_warm = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
+    }
+    const gsr_status rc = prm.mode == GSR_MIXED ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own)
+                                                : lsqr_solve(c, &prm, x0_use, x0_dev, x_out, se_out, info, c->own);
+    if (info) {
+        info->ms_warm = ms_warm;
+        info->ms_total += ms_warm;
+    }
     // the caller's stream continues after the solve's last kernel
     if (cudaEventRecord(c->ev, c->own) == cudaSuccess) cudaStreamWaitEvent((cudaStream_t)stream, c->ev, 0);
     cudaGetLastError();

@@ -12,6 +12,8 @@
 
 #include "../../include/gsr.h"
 
+struct gsr_net;  // the warm start's network (net.cu, include/gsr_warm.h)
+
 namespace gsr {
 
 constexpr int NPAR = 24;     // coefficients per observation row (Sec. 2)
@@ -80,6 +82,10 @@ struct Workspace {
     float2 *xhl = nullptr;      // n_cols: xo split into two binary32 parts
     float2 *bhl = nullptr;      // n_rows: b split into two binary32 parts
     double *blk = nullptr;      // 16: per-block sums of squares of the correction and of x
+    float *feats = nullptr;     // n_dfa x 6: warm-start features
+    float *netout = nullptr;    // n_dfa x 3: network output
+    double *wacc = nullptr;     // 4: feature sums [0..1], scale [2]
+    double *x0w = nullptr;      // n_cols: warm start vector
     std::vector<GraphCache> graphs;
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
@@ -108,6 +114,8 @@ struct gsr_ctx {
     std::vector<std::pair<int64_t, int64_t>> rows_set;  // merged [lo, hi) ranges of loaded rows
     int32_t *errw = nullptr;         // device error words for validation (4 int32)
     cudaStream_t own = nullptr;      // non-blocking stream the solve runs (and captures) on
+    struct gsr_net *warm_net = nullptr;  // network of GSR_WARM_LEARNED solves, loaded from warm_path
+    std::string warm_path;
     cudaEvent_t ev = nullptr;        // orders `own` after the caller's stream
     gsr::Workspace ws;
     std::string err;
@@ -153,8 +161,9 @@ int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s);
 
 // LSQR driver (lsqr.cu)
-gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,
-                      gsr_solve_info *info, cudaStream_t s);
+// x0_dev: x0 is device memory whatever prm->where says (the warm start's vector)
+gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
+                      double *se_out, gsr_solve_info *info, cudaStream_t s);
 gsr_status ensure_workspace(gsr_ctx *c);
 void free_workspace(gsr_ctx *c);
 void default_params(gsr_solve_params *p);
@@ -164,12 +173,14 @@ LsqrState initial_state(const gsr_solve_params *prm);
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
+// warm start (warm.cu)
+gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out);
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
-gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out,
+gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
                        gsr_solve_info *info, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers

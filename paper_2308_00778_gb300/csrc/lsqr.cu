@@ -374,7 +374,10 @@ oom:
 void free_workspace(gsr_ctx *c)
 {
     Workspace &ws = c->ws;
-    double *ptrs[] = {ws.u, ws.z, ws.v, ws.w, ws.x, ws.pv, ws.p, ws.var, ws.tmp, ws.part_u, ws.xo, ws.blk};
+    double *ptrs[] = {ws.u, ws.z, ws.v, ws.w, ws.x, ws.pv, ws.p, ws.var, ws.tmp, ws.part_u, ws.xo, ws.blk, ws.wacc,
+                      ws.x0w};
+    if (ws.feats) cudaFree(ws.feats);
+    if (ws.netout) cudaFree(ws.netout);
     for (double *p : ptrs)
         if (p) cudaFree(p);
     if (ws.u32) cudaFree(ws.u32);
@@ -551,8 +554,8 @@ void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_c
     info->ms_warm = 0.0;
 }
 
-gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out, double *se_out,
-                      gsr_solve_info *info, cudaStream_t s)
+gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
+                      double *se_out, gsr_solve_info *info, cudaStream_t s)
 {
     const auto t0 = std::chrono::steady_clock::now();
     gsr_status rc = ensure_workspace(c);
@@ -572,7 +575,7 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
     const double *x0d = nullptr;
     double *x0_buf = nullptr;
     if (x0) {
-        if (dev_io) {
+        if (dev_io || x0_dev) {
             x0d = x0;
         } else {
             if ((e = cudaMalloc(&x0_buf, nc * sizeof(double))) != cudaSuccess)

@@ -172,7 +172,7 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
     return GSR_OK;
 }
 
-gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, double *x_out,
+gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
                        gsr_solve_info *info, cudaStream_t s)
 {
     const auto t0 = std::chrono::steady_clock::now();
@@ -188,8 +188,8 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     if ((rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
     k_split<<<grow, kThreads, 0, s>>>(c->b, ws.bhl, nr);
     if (x0)
-        e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double), dev_io ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            s);
+        e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
+                            (dev_io || x0_dev) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     else
         e = cudaMemsetAsync(ws.xo, 0, nc * sizeof(double), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "mixed start");

@@ -1,0 +1,719 @@
+// net.cu -- the learned warm start's network: six 1D convolution layers over the
+// attitude knots (6 -> 64 -> 64 -> 64 -> 64 -> 64 -> 3 channels, kernel 5, zero
+// padding 2, ReLU after the first five), trained and evaluated on the GPU.
+//
+// Each convolution is an implicit GEMM on the BF16 tensor cores
+// (mma.sync.m16n8k16, FP32 accumulation):
+//   forward      out[p][co]   = sum_{t,ci} W[co][ci][t] in[p+t-2][ci]        M = positions, N = co, K = 5*Cin
+//   backward x   dIn[p][ci]   = sum_{t,co} W[co][ci][4-t] dOut[p+t-2][co]    the same kernel, flipped weights
+//   backward W   dW[co][t,ci] = sum_p dOut[p][co] in[p+t-2][ci]               M = co, N = 5*Cin, K = positions
+// Activations are position-major bf16 [B][L][C] with C padded to a multiple
+// of 16 (the first layer's 6 input channels and the last layer's 3 output
+// channels to 16). FP32 master weights are updated with Adam and copied to
+// two bf16 GEMM operands: Bf [Cout][5*Cin] (tap-major K) for the forward pass
+// and Bb [Cin][5*Cout] (flipped taps) for the backward-data pass.
+// Rounding points (mirrored by the oracle): weights and layer inputs in bf16
+// for the forward; the output gradients fed to both backward products in bf16.
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/gsr_warm.h"
+#include "gsr_internal.cuh"
+
+#define GSR_API extern "C" __attribute__((visibility("default")))
+
+namespace gsr {
+
+constexpr int NLAYER = 6;
+// channel counts at layer boundaries 0..6 (true, and padded to multiples of 16, the MMA's K step)
+__host__ __device__ constexpr int CH(int l) { return l == 0 ? 6 : (l == NLAYER ? 3 : 64); }
+__host__ __device__ constexpr int CHP(int l) { return (l == 0 || l == NLAYER) ? 16 : 64; }
+constexpr int KW = 5;                                          // kernel width
+
+__host__ __device__ constexpr int64_t layer_wsize(int l) { return (int64_t)CH(l + 1) * CH(l) * KW; }
+
+static int64_t total_params()
+{
+    int64_t n = 0;
+    for (int l = 0; l < NLAYER; ++l) n += layer_wsize(l) + CH(l + 1);
+    return n;
+}
+
+// ---------------------------------------------------------------- MMA helper
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// ---------------------------------------------------------------- convolution (forward / backward-data)
+enum { CONV_RELU = 0, CONV_LAST = 1, CONV_BWD = 2 };
+
+constexpr int CONV_POS = 64;  // positions per block (4 warps x 16)
+
+// in: bf16 [B][L][CIN]; Bm: bf16 [COUT][5*CIN]. MODE:
+//   CONV_RELU: out16 = bf16(relu(acc + bias))                     [B][L][COUT]
+//   CONV_LAST: out32 = acc + bias (fp32)                          [B][L][COUT]
+//   CONV_BWD : v = acc * (mask > 0): out32 = v, out16 = bf16(v)   [B][L][COUT]
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16 *__restrict__ in, int64_t L,
+                                              const __nv_bfloat16 *__restrict__ Bm, const float *__restrict__ bias,
+                                              const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ out16,
+                                              float *__restrict__ out32)
+{
+    constexpr int K = KW * CIN;
+    constexpr int IS = CIN + 8;  // padded row strides (bank-conflict-free fragment loads)
+    constexpr int BS = K + 8;
+    constexpr int NT = COUT / 8;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16 *s_in = reinterpret_cast<__nv_bfloat16 *>(conv_smem);  // (CONV_POS + 4) * IS
+    __nv_bfloat16 *s_b = s_in + (CONV_POS + 4) * IS;                       // COUT * BS
+    const int64_t b = blockIdx.y;
+    const int64_t p0 = (int64_t)blockIdx.x * CONV_POS;
+    const __nv_bfloat16 *inb = in + b * L * CIN;
+    // stage the input rows p0-2 .. p0+65 (zero outside [0, L)) and the weights
+    for (int i = threadIdx.x; i < (CONV_POS + 4) * CIN; i += blockDim.x) {
+        const int r = i / CIN, c = i % CIN;
+        const int64_t p = p0 - 2 + r;
+        s_in[r * IS + c] = (p >= 0 && p < L) ? inb[p * CIN + c] : __float2bfloat16_rn(0.f);
+    }
+    for (int i = threadIdx.x; i < COUT * K; i += blockDim.x) s_b[(i / K) * BS + (i % K)] = Bm[i];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int wr = warp * 16;  // first position (relative to p0) of this warp's 16 rows
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int t = 0; t < KW; ++t) {
+#pragma unroll
+        for (int c0 = 0; c0 < CIN; c0 += 16) {
+            // A: rows = positions wr..wr+15 at tap t (smem row wr + r + t), cols = channels c0..c0+15
+            const __nv_bfloat16 *ra = s_in + (wr + g + t) * IS + c0 + 2 * tq;
+            const __nv_bfloat16 *rb = s_in + (wr + g + 8 + t) * IS + c0 + 2 * tq;
+            uint32_t a[4];
+            a[0] = *reinterpret_cast<const uint32_t *>(ra);
+            a[1] = *reinterpret_cast<const uint32_t *>(rb);
+            a[2] = *reinterpret_cast<const uint32_t *>(ra + 8);
+            a[3] = *reinterpret_cast<const uint32_t *>(rb + 8);
+            const int k0 = t * CIN + c0;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const __nv_bfloat16 *bb = s_b + (n * 8 + g) * BS + k0 + 2 * tq;
+                uint32_t bf[2];
+                bf[0] = *reinterpret_cast<const uint32_t *>(bb);
+                bf[1] = *reinterpret_cast<const uint32_t *>(bb + 8);
+                mma_bf16(acc[n], a, bf);
+            }
+        }
+    }
+    // epilogue: C fragment (row g / g+8 = position, col 2tq / 2tq+1 = channel)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t p = p0 + wr + g + 8 * h;
+            if (p >= L) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int co = n * 8 + 2 * tq + e;
+                float v = acc[n][2 * h + e];
+                const int64_t o = (b * L + p) * COUT + co;
+                if (MODE == CONV_RELU) {
+                    v += bias[co];
+                    out16[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+                } else if (MODE == CONV_LAST) {
+                    out32[o] = v + bias[co];
+                } else {
+                    v = (__bfloat162float(mask[o]) > 0.f) ? v : 0.f;
+                    out32[o] = v;
+                    out16[o] = __float2bfloat16_rn(v);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- backward weights
+// dW[co][t*CIN + ci] += sum_p dout[p][co] * in[p+t-2][ci] over a block's positions.
+// Block: 4 warps; warp w covers output rows (co) 16*(w % MT) and a range of
+// n-tiles; gridDim.y splits the 5*CIN columns into chunks of NCH n-tiles.
+constexpr int WG_POS = 64;  // positions per chunk
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv_wgrad(const __nv_bfloat16 *__restrict__ in,
+                                                    const __nv_bfloat16 *__restrict__ dout, int64_t B, int64_t L,
+                                                    float *__restrict__ dW)
+{
+    constexpr int K = KW * CIN;          // columns of dW
+    constexpr int MP = COUT < 16 ? 16 : COUT;  // rows padded to the MMA's 16
+    constexpr int MT = MP / 16;          // m-tiles
+    constexpr int NCH = 10;              // n-tiles per grid.y chunk (80 columns)
+    constexpr int WPM = 4 / MT;          // warps sharing one m-tile
+    constexpr int NPW = (NCH + WPM - 1) / WPM;  // n-tiles per warp
+    constexpr int DS = MP + 8, IS = CIN + 8;
+    __shared__ __align__(16) __nv_bfloat16 s_d[WG_POS * DS];
+    __shared__ __align__(16) __nv_bfloat16 s_in[(WG_POS + 4) * IS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int mt = warp % MT;
+    const int nt0 = blockIdx.y * NCH + (warp / MT) * NPW;
+    float acc[NPW][4];
+#pragma unroll
+    for (int n = 0; n < NPW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const int64_t chunks_per_seq = (L + WG_POS - 1) / WG_POS;
+    const int64_t n_chunks = B * chunks_per_seq;
+    for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const int64_t b = ch / chunks_per_seq;
+        const int64_t p0 = (ch % chunks_per_seq) * WG_POS;
+        __syncthreads();
+        for (int i = threadIdx.x; i < WG_POS * MP; i += blockDim.x) {
+            const int r = i / MP, c = i % MP;
+            const int64_t p = p0 + r;
+            s_d[r * DS + c] =
+                (p < L && c < COUT) ? dout[(b * L + p) * COUT + c] : __float2bfloat16_rn(0.f);
+        }
+        for (int i = threadIdx.x; i < (WG_POS + 4) * CIN; i += blockDim.x) {
+            const int r = i / CIN, c = i % CIN;
+            const int64_t p = p0 - 2 + r;
+            s_in[r * IS + c] = (p >= 0 && p < L) ? in[(b * L + p) * CIN + c] : __float2bfloat16_rn(0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k0 = 0; k0 < WG_POS; k0 += 16) {
+            // A[m][k] = dout[k0 + k][16 mt + m] (m = co row, k = position)
+            uint32_t a[4];
+            const int m0 = 16 * mt;
+            a[0] = pack2(s_d[(k0 + 2 * tq) * DS + m0 + g], s_d[(k0 + 2 * tq + 1) * DS + m0 + g]);
+            a[1] = pack2(s_d[(k0 + 2 * tq) * DS + m0 + g + 8], s_d[(k0 + 2 * tq + 1) * DS + m0 + g + 8]);
+            a[2] = pack2(s_d[(k0 + 2 * tq + 8) * DS + m0 + g], s_d[(k0 + 2 * tq + 9) * DS + m0 + g]);
+            a[3] = pack2(s_d[(k0 + 2 * tq + 8) * DS + m0 + g + 8], s_d[(k0 + 2 * tq + 9) * DS + m0 + g + 8]);
+#pragma unroll
+            for (int n = 0; n < NPW; ++n) {
+                const int nt = nt0 + n;
+                if ((warp / MT) * NPW + n >= NCH || nt * 8 >= K) continue;
+                // B[k][j] = in[k0 + k + t - 2][ci] with column j = n*8 + g -> (t, ci)
+                const int col = nt * 8 + g;
+                const int t = col / CIN, ci = col % CIN;
+                uint32_t bf[2];
+                bf[0] = pack2(s_in[(k0 + 2 * tq + t) * IS + ci], s_in[(k0 + 2 * tq + 1 + t) * IS + ci]);
+                bf[1] = pack2(s_in[(k0 + 2 * tq + 8 + t) * IS + ci], s_in[(k0 + 2 * tq + 9 + t) * IS + ci]);
+                mma_bf16(acc[n], a, bf);
+            }
+        }
+    }
+    // flush: C rows = co (16 mt + g / + 8), cols = (nt*8 + 2tq + e)
+#pragma unroll
+    for (int n = 0; n < NPW; ++n) {
+        const int nt = nt0 + n;
+        if ((warp / MT) * NPW + n >= NCH || nt * 8 >= K) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = 16 * mt + g + 8 * h;
+            if (co >= COUT) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int col = nt * 8 + 2 * tq + e;
+                const float v = acc[n][2 * h + e];
+                if (v != 0.f) atomicAdd(dW + (int64_t)co * K + col, v);
+            }
+        }
+    }
+}
+
+// db[co] += sum over positions of the fp32 output gradient
+__global__ void k_bias_grad(const float *__restrict__ d32, int64_t n_pos, int cout, int cstride, float *__restrict__ db)
+{
+    extern __shared__ float sdb[];
+    for (int c = threadIdx.x; c < cout; c += blockDim.x) sdb[c] = 0.f;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pos * cout;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / cout;
+        const int c = (int)(i % cout);
+        atomicAdd(sdb + c, d32[p * cstride + c]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < cout; c += blockDim.x)
+        if (sdb[c] != 0.f) atomicAdd(db + c, sdb[c]);
+}
+
+// ---------------------------------------------------------------- input / output / loss
+// fp32 [n][6] -> bf16 [n][16] (zero padding)
+__global__ void k_pack_input(const float *__restrict__ x, int64_t n, __nv_bfloat16 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * CHP(0);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / CHP(0);
+        const int c = (int)(i % CHP(0));
+        out[i] = __float2bfloat16_rn(c < CH(0) ? x[p * CH(0) + c] : 0.f);
+    }
+}
+
+__global__ void k_unpack_output(const float *__restrict__ y8, int64_t n, float *__restrict__ y3)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * CH(NLAYER);
+         i += (int64_t)gridDim.x * blockDim.x)
+        y3[i] = y8[(i / CH(NLAYER)) * CHP(NLAYER) + i % CH(NLAYER)];
+}
+
+// MSE over the 3 true output channels: d = 2 (y - t) / N in fp32 and bf16 [n][8]; loss partial sums
+__global__ void k_mse(const float *__restrict__ y8, const float *__restrict__ t3, int64_t n,
+                      float *__restrict__ d32, __nv_bfloat16 *__restrict__ d16, double *__restrict__ loss)
+{
+    __shared__ double sm32[32];
+    const double inv = 1.0 / (double)(n * CH(NLAYER));
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * CHP(NLAYER);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / CHP(NLAYER);
+        const int c = (int)(i % CHP(NLAYER));
+        float d = 0.f;
+        if (c < CH(NLAYER)) {
+            const float e = y8[i] - t3[p * CH(NLAYER) + c];
+            s += (double)e * (double)e;
+            d = (float)(2.0 * (double)e * inv);
+        }
+        d32[i] = d;
+        d16[i] = __float2bfloat16_rn(d);
+    }
+    const double tot = block_sum(s, sm32);
+    if (threadIdx.x == 0) atomicAdd(loss, tot * inv);
+}
+
+// ---------------------------------------------------------------- Adam + operand refresh
+// Per true parameter (co, ci, t) of layer l: Adam on the fp32 master and
+// refresh of the two bf16 GEMM operands; bias entries follow the weights.
+__global__ void k_adam_layer(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                             float *__restrict__ bias, float *__restrict__ mb, float *__restrict__ vb,
+                             float *__restrict__ dW, float *__restrict__ db, int cin, int cout, int cinp, int coutp,
+                             float lr, float b1, float b2, float eps, float c1, float c2, int update,
+                             __nv_bfloat16 *__restrict__ Bf, __nv_bfloat16 *__restrict__ Bb)
+{
+    const int64_t nw = (int64_t)cout * cin * KW;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw + cout;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nw) {
+            const int co = (int)(i / (cin * KW));
+            const int ci = (int)((i / KW) % cin);
+            const int t = (int)(i % KW);
+            const int64_t gi = (int64_t)co * (KW * cinp) + t * cinp + ci;
+            float wv = w[i];
+            if (update) {
+                const float gr = dW[gi];
+                const float mv = b1 * m[i] + (1.f - b1) * gr;
+                const float vv = b2 * v[i] + (1.f - b2) * gr * gr;
+                m[i] = mv;
+                v[i] = vv;
+                wv = wv - lr * (mv / c1) / (sqrtf(vv / c2) + eps);
+                w[i] = wv;
+                dW[gi] = 0.f;
+            }
+            const __nv_bfloat16 h = __float2bfloat16_rn(wv);
+            Bf[gi] = h;
+            Bb[(int64_t)ci * (KW * coutp) + (KW - 1 - t) * coutp + co] = h;
+        } else {
+            const int co = (int)(i - nw);
+            if (update) {
+                const float gr = db[co];
+                const float mv = b1 * mb[co] + (1.f - b1) * gr;
+                const float vv = b2 * vb[co] + (1.f - b2) * gr * gr;
+                mb[co] = mv;
+                vb[co] = vv;
+                bias[co] = bias[co] - lr * (mv / c1) / (sqrtf(vv / c2) + eps);
+                db[co] = 0.f;
+            }
+        }
+    }
+}
+
+}  // namespace gsr
+
+using namespace gsr;
+
+// ---------------------------------------------------------------- the net object
+struct gsr_net {
+    int device = 0;
+    float *w[NLAYER] = {}, *b[NLAYER] = {}, *mw[NLAYER] = {}, *vw[NLAYER] = {}, *mb[NLAYER] = {}, *vb[NLAYER] = {};
+    float *dW[NLAYER] = {}, *db[NLAYER] = {};
+    __nv_bfloat16 *Bf[NLAYER] = {}, *Bb[NLAYER] = {};
+    // activations for a batch of up to cap_pos positions
+    int64_t cap_pos = 0;
+    __nv_bfloat16 *act[NLAYER] = {};  // input of layer l, [pos][CHP(l)]
+    float *y8 = nullptr;              // last layer output [pos][16] (3 used)
+    float *d32 = nullptr;             // output gradient fp32 [pos][64]
+    __nv_bfloat16 *d16a = nullptr, *d16b = nullptr;  // output gradients bf16 [pos][64] (ping-pong)
+    double *loss = nullptr;
+    int step = 0;
+    std::string err;
+};
+
+namespace gsr {
+
+static void net_free_acts(gsr_net *n)
+{
+    for (int l = 0; l < NLAYER; ++l) {
+        cudaFree(n->act[l]);
+        n->act[l] = nullptr;
+    }
+    cudaFree(n->y8);
+    cudaFree(n->d32);
+    cudaFree(n->d16a);
+    cudaFree(n->d16b);
+    n->y8 = n->d32 = nullptr;
+    n->d16a = n->d16b = nullptr;
+    n->cap_pos = 0;
+}
+
+static cudaError_t net_reserve(gsr_net *n, int64_t pos)
+{
+    if (pos <= n->cap_pos) return cudaSuccess;
+    net_free_acts(n);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l)
+        e = cudaMalloc(&n->act[l], sizeof(__nv_bfloat16) * (size_t)pos * CHP(l));
+    if (e == cudaSuccess) e = cudaMalloc(&n->y8, sizeof(float) * (size_t)pos * CHP(NLAYER));
+    if (e == cudaSuccess) e = cudaMalloc(&n->d32, sizeof(float) * (size_t)pos * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&n->d16a, sizeof(__nv_bfloat16) * (size_t)pos * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&n->d16b, sizeof(__nv_bfloat16) * (size_t)pos * 64);
+    if (e != cudaSuccess) {
+        net_free_acts(n);
+        return e;
+    }
+    n->cap_pos = pos;
+    return cudaSuccess;
+}
+
+static int grid_n(int64_t n, int threads = 256)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 4096));
+}
+
+static cudaError_t refresh_operands(gsr_net *n, bool update, float lr, cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = update ? 1.f - powf(b1, (float)n->step) : 1.f;
+    const float c2 = update ? 1.f - powf(b2, (float)n->step) : 1.f;
+    for (int l = 0; l < NLAYER; ++l) {
+        const int64_t cnt = layer_wsize(l) + CH(l + 1);
+        k_adam_layer<<<grid_n(cnt), 256, 0, s>>>(n->w[l], n->mw[l], n->vw[l], n->b[l], n->mb[l], n->vb[l], n->dW[l],
+                                                 n->db[l], CH(l), CH(l + 1), CHP(l), CHP(l + 1), lr, b1, b2, eps, c1,
+                                                 c2, update ? 1 : 0, n->Bf[l], n->Bb[l]);
+    }
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int MODE>
+static void conv_launch(dim3 grid, const __nv_bfloat16 *in, int64_t L, const __nv_bfloat16 *Bm, const float *bias,
+                        const __nv_bfloat16 *mask, __nv_bfloat16 *out16, float *out32, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(__nv_bfloat16) * ((CONV_POS + 4) * (CIN + 8) + COUT * (KW * CIN + 8));
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    k_conv<CIN, COUT, MODE><<<grid, 128, smem, s>>>(in, L, Bm, bias, mask, out16, out32);
+}
+
+// forward of the whole net on act[0] (already packed); fills act[1..5] and y8
+static cudaError_t net_forward_packed(gsr_net *n, int64_t B, int64_t L, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
+    conv_launch<16, 64, CONV_RELU>(grid, n->act[0], L, n->Bf[0], n->b[0], nullptr, n->act[1], nullptr, s);
+    for (int l = 1; l < NLAYER - 1; ++l)
+        conv_launch<64, 64, CONV_RELU>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, n->act[l + 1], nullptr, s);
+    conv_launch<64, 16, CONV_LAST>(grid, n->act[NLAYER - 1], L, n->Bf[NLAYER - 1], n->b[NLAYER - 1], nullptr,
+                                   nullptr, n->y8, s);
+    return cudaGetLastError();
+}
+
+cudaError_t net_forward_dev(gsr_net *n, const float *in, int64_t B, int64_t L, float *out, cudaStream_t s)
+{
+    cudaError_t e = net_reserve(n, B * L);
+    if (e != cudaSuccess) return e;
+    k_pack_input<<<grid_n(B * L * CHP(0)), 256, 0, s>>>(in, B * L, n->act[0]);
+    if ((e = net_forward_packed(n, B, L, s)) != cudaSuccess) return e;
+    k_unpack_output<<<grid_n(B * L * 3), 256, 0, s>>>(n->y8, B * L, out);
+    return cudaGetLastError();
+}
+
+// gradients of layer l from its output gradient (dcur bf16, d32 fp32): dW, db and,
+// for l > 0, the masked gradient of the previous layer's output into dnext / d32
+static void backward_layer(gsr_net *n, int l, const __nv_bfloat16 *dcur, __nv_bfloat16 *dnext, int64_t B, int64_t L,
+                           cudaStream_t s)
+{
+    const int64_t P = B * L;
+    const int cin = CHP(l), cout = CHP(l + 1);
+    const unsigned wg = (unsigned)std::min<int64_t>(std::max<int64_t>((P + WG_POS - 1) / WG_POS, 1), 1024);
+    const dim3 gw(wg, (unsigned)((KW * cin / 8 + 9) / 10));
+    if (l == 0)
+        k_conv_wgrad<16, 64><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+    else if (l == NLAYER - 1)
+        k_conv_wgrad<64, 16><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+    else
+        k_conv_wgrad<64, 64><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+    k_bias_grad<<<grid_n(P * CH(l + 1)), 256, sizeof(float) * CH(l + 1), s>>>(n->d32, P, CH(l + 1), cout, n->db[l]);
+    if (l > 0) {
+        const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
+        if (l == NLAYER - 1)
+            conv_launch<16, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, s);
+        else
+            conv_launch<64, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, s);
+    }
+}
+
+static cudaError_t net_train_dev(gsr_net *n, const float *in, const float *target, int64_t B, int64_t L, float lr,
+                                 double *loss_host, cudaStream_t s)
+{
+    cudaError_t e = net_reserve(n, B * L);
+    if (e != cudaSuccess) return e;
+    const int64_t P = B * L;
+    k_pack_input<<<grid_n(P * CHP(0)), 256, 0, s>>>(in, P, n->act[0]);
+    if ((e = net_forward_packed(n, B, L, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(n->loss, 0, sizeof(double), s)) != cudaSuccess) return e;
+    k_mse<<<grid_n(P * CHP(NLAYER)), 256, 0, s>>>(n->y8, target, P, n->d32, n->d16a, n->loss);
+    __nv_bfloat16 *dcur = n->d16a, *dnext = n->d16b;
+    for (int l = NLAYER - 1; l >= 0; --l) {
+        backward_layer(n, l, dcur, dnext, B, L, s);
+        if (l > 0) std::swap(dcur, dnext);
+    }
+    n->step += 1;
+    if ((e = refresh_operands(n, true, lr, s)) != cudaSuccess) return e;
+    if (loss_host) {
+        if ((e = cudaMemcpyAsync(loss_host, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+static gsr_status net_fail(gsr_net *n, gsr_status st, const std::string &m)
+{
+    if (n) n->err = m;
+    return st;
+}
+
+}  // namespace gsr
+
+// ---------------------------------------------------------------- C ABI
+GSR_API int64_t gsr_net_num_params(void) { return total_params(); }
+
+GSR_API const char *gsr_net_last_error(const gsr_net *n) { return n ? n->err.c_str() : "null net"; }
+
+GSR_API gsr_status gsr_net_destroy(gsr_net *n)
+{
+    if (!n) return GSR_OK;
+    cudaSetDevice(n->device);
+    net_free_acts(n);
+    for (int l = 0; l < NLAYER; ++l) {
+        float *fp[] = {n->w[l], n->b[l], n->mw[l], n->vw[l], n->mb[l], n->vb[l], n->dW[l], n->db[l]};
+        for (float *p : fp) cudaFree(p);
+        cudaFree(n->Bf[l]);
+        cudaFree(n->Bb[l]);
+    }
+    cudaFree(n->loss);
+    cudaGetLastError();
+    delete n;
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_create(gsr_net **out, int32_t device)
+{
+    if (!out) return GSR_EINVAL;
+    *out = nullptr;
+    gsr_net *n = new gsr_net();
+    n->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        const size_t ws = sizeof(float) * (size_t)layer_wsize(l), bs = sizeof(float) * CHP(l + 1);
+        const size_t gs = sizeof(float) * (size_t)CHP(l + 1) * KW * CHP(l);
+        const size_t os = sizeof(__nv_bfloat16) * (size_t)CHP(l + 1) * KW * CHP(l);
+        float **wp[] = {&n->w[l], &n->mw[l], &n->vw[l]};
+        for (float **p : wp)
+            if (e == cudaSuccess && (e = cudaMalloc(p, ws)) == cudaSuccess) e = cudaMemset(*p, 0, ws);
+        float **bp[] = {&n->b[l], &n->mb[l], &n->vb[l], &n->db[l]};
+        for (float **p : bp)
+            if (e == cudaSuccess && (e = cudaMalloc(p, bs)) == cudaSuccess) e = cudaMemset(*p, 0, bs);
+        if (e == cudaSuccess && (e = cudaMalloc(&n->dW[l], gs)) == cudaSuccess) e = cudaMemset(n->dW[l], 0, gs);
+        if (e == cudaSuccess && (e = cudaMalloc(&n->Bf[l], os)) == cudaSuccess) e = cudaMemset(n->Bf[l], 0, os);
+        if (e == cudaSuccess && (e = cudaMalloc(&n->Bb[l], os)) == cudaSuccess) e = cudaMemset(n->Bb[l], 0, os);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gsr_net_destroy(n);
+        return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
+    }
+    *out = n;
+    return GSR_OK;
+}
+
+// parameters: for each layer, W [cout][cin][5] then bias [cout] (fp32); resets Adam
+GSR_API gsr_status gsr_net_set_params(gsr_net *n, const float *params, int64_t count)
+{
+    if (!n || !params) return GSR_EINVAL;
+    if (count != total_params()) return net_fail(n, GSR_EINVAL, "parameter count mismatch");
+    cudaError_t e = cudaSetDevice(n->device);
+    int64_t off = 0;
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        const int64_t nw = layer_wsize(l), nb = CH(l + 1);
+        e = cudaMemcpy(n->w[l], params + off, sizeof(float) * nw, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(n->b[l], params + off + nw, sizeof(float) * nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(n->mw[l], 0, sizeof(float) * nw);
+        if (e == cudaSuccess) e = cudaMemset(n->vw[l], 0, sizeof(float) * nw);
+        if (e == cudaSuccess) e = cudaMemset(n->mb[l], 0, sizeof(float) * nb);
+        if (e == cudaSuccess) e = cudaMemset(n->vb[l], 0, sizeof(float) * nb);
+        off += nw + nb;
+    }
+    n->step = 0;
+    if (e == cudaSuccess) e = refresh_operands(n, false, 0.f, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, GSR_ECUDA, std::string("set_params: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_get_params(gsr_net *n, float *params, int64_t count)
+{
+    if (!n || !params) return GSR_EINVAL;
+    if (count != total_params()) return net_fail(n, GSR_EINVAL, "parameter count mismatch");
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int64_t off = 0;
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        const int64_t nw = layer_wsize(l), nb = CH(l + 1);
+        e = cudaMemcpy(params + off, n->w[l], sizeof(float) * nw, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(params + off + nw, n->b[l], sizeof(float) * nb, cudaMemcpyDeviceToHost);
+        off += nw + nb;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, GSR_ECUDA, std::string("get_params: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_forward(gsr_net *n, const float *in, int64_t batch, int64_t len, float *out, void *stream)
+{
+    if (!n || !in || !out || batch < 1 || len < 1) return GSR_EINVAL;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = net_forward_dev(n, in, batch, len, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA,
+                        std::string("forward: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_train_step(gsr_net *n, const float *in, const float *target, int64_t batch, int64_t len,
+                                      float lr, double *loss, void *stream)
+{
+    if (!n || !in || !target || batch < 1 || len < 1 || !(lr >= 0.f)) return GSR_EINVAL;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = net_train_dev(n, in, target, batch, len, lr, loss, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA,
+                        std::string("train_step: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+// gradients of the last train step are consumed by Adam; this returns the
+// gradients of one batch without updating (for checks): fp32, same layout as
+// the parameters. Adam state and step count are left unchanged.
+GSR_API gsr_status gsr_net_gradients(gsr_net *n, const float *in, const float *target, int64_t batch, int64_t len,
+                                     float *grads, int64_t count, double *loss, void *stream)
+{
+    if (!n || !in || !target || !grads || batch < 1 || len < 1) return GSR_EINVAL;
+    if (count != total_params()) return net_fail(n, GSR_EINVAL, "parameter count mismatch");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = net_reserve(n, batch * len);
+    const int64_t P = batch * len;
+    if (e == cudaSuccess) {
+        k_pack_input<<<grid_n(P * CHP(0)), 256, 0, s>>>(in, P, n->act[0]);
+        e = net_forward_packed(n, batch, len, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->loss, 0, sizeof(double), s);
+    if (e == cudaSuccess) {
+        k_mse<<<grid_n(P * CHP(NLAYER)), 256, 0, s>>>(n->y8, target, P, n->d32, n->d16a, n->loss);
+        __nv_bfloat16 *dcur = n->d16a, *dnext = n->d16b;
+        for (int l = NLAYER - 1; l >= 0 && e == cudaSuccess; --l) {
+            backward_layer(n, l, dcur, dnext, batch, len, s);
+            if (l > 0) std::swap(dcur, dnext);
+            e = cudaGetLastError();
+        }
+    }
+    // copy out (padded dW -> true layout on the host) and clear the accumulators
+    int64_t off = 0;
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        const int cin = CH(l), cout = CH(l + 1), cinp = CHP(l);
+        std::vector<float> dWp((size_t)CHP(l + 1) * KW * cinp), dbv((size_t)cout);
+        e = cudaMemcpyAsync(dWp.data(), n->dW[l], sizeof(float) * dWp.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dbv.data(), n->db[l], sizeof(float) * cout, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int t = 0; t < KW; ++t)
+                    grads[off + ((int64_t)co * cin + ci) * KW + t] = dWp[(size_t)co * KW * cinp + t * cinp + ci];
+        for (int co = 0; co < cout; ++co) grads[off + layer_wsize(l) + co] = dbv[(size_t)co];
+        off += layer_wsize(l) + cout;
+        e = cudaMemsetAsync(n->dW[l], 0, sizeof(float) * dWp.size(), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(n->db[l], 0, sizeof(float) * cout, s);
+    }
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, GSR_ECUDA, std::string("gradients: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_save(gsr_net *n, const char *path)
+{
+    if (!n || !path) return GSR_EINVAL;
+    std::vector<float> p((size_t)total_params());
+    gsr_status st = gsr_net_get_params(n, p.data(), (int64_t)p.size());
+    if (st != GSR_OK) return st;
+    FILE *f = fopen(path, "wb");
+    if (!f) return net_fail(n, GSR_EINVAL, std::string("cannot write ") + path);
+    const char magic[8] = {'G', 'S', 'R', 'N', 'E', 'T', '0', '1'};
+    const int64_t cnt = (int64_t)p.size();
+    const bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&cnt, sizeof(cnt), 1, f) == 1 &&
+                    fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    fclose(f);
+    return ok ? GSR_OK : net_fail(n, GSR_EINVAL, std::string("short write ") + path);
+}
+
+GSR_API gsr_status gsr_net_load(gsr_net *n, const char *path)
+{
+    if (!n || !path) return GSR_EINVAL;
+    FILE *f = fopen(path, "rb");
+    if (!f) return net_fail(n, GSR_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    int64_t cnt = 0;
+    std::vector<float> p((size_t)total_params());
+    const bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "GSRNET01", 8) == 0 &&
+                    fread(&cnt, sizeof(cnt), 1, f) == 1 && cnt == (int64_t)p.size() &&
+                    fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    fclose(f);
+    if (!ok) return net_fail(n, GSR_EINVAL, std::string("not a weights file of this network: ") + path);
+    return gsr_net_set_params(n, p.data(), cnt);
+}

@@ -100,6 +100,19 @@ def lib():
             "gsr_residual": (I32, [P, P, P, P]),
             "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
+            "gsr_net_num_params": (I64, []),
+            "gsr_net_create": (I32, [ctypes.POINTER(P), I32]),
+            "gsr_net_destroy": (I32, [P]),
+            "gsr_net_last_error": (ctypes.c_char_p, [P]),
+            "gsr_net_set_params": (I32, [P, P, I64]),
+            "gsr_net_get_params": (I32, [P, P, I64]),
+            "gsr_net_save": (I32, [P, ctypes.c_char_p]),
+            "gsr_net_load": (I32, [P, ctypes.c_char_p]),
+            "gsr_net_forward": (I32, [P, P, I64, I64, P, P]),
+            "gsr_net_train_step": (I32, [P, P, P, I64, I64, ctypes.c_float, P, P]),
+            "gsr_net_gradients": (I32, [P, P, P, I64, I64, P, I64, P, P]),
+            "gsr_warm_features": (I32, [P, P, P, P]),
+            "gsr_warm_start": (I32, [P, P, P, P]),
             "gsr_lsqr_solve": (I32, [P, ctypes.POINTER(SolveParams), P, P, P, ctypes.POINTER(SolveInfo), P]),
         }
         for name, (res, args) in sig.items():
@@ -183,6 +196,63 @@ def gsr_lsqr_solve(ctx, params: SolveParams, x0, x_out, se_out, info: SolveInfo,
                                 ctypes.byref(info), stream or None)
 
 
+def gsr_net_num_params() -> int:
+    return lib().gsr_net_num_params()
+
+
+def gsr_net_create(device=0):
+    h = ctypes.c_void_p()
+    st = lib().gsr_net_create(ctypes.byref(h), device)
+    return st, h.value
+
+
+def gsr_net_destroy(net):
+    return lib().gsr_net_destroy(net)
+
+
+def gsr_net_last_error(net) -> str:
+    r = lib().gsr_net_last_error(net)
+    return r.decode() if r else ""
+
+
+def gsr_net_set_params(net, params, count):
+    return lib().gsr_net_set_params(net, params or None, count)
+
+
+def gsr_net_get_params(net, params, count):
+    return lib().gsr_net_get_params(net, params or None, count)
+
+
+def gsr_net_save(net, path: str):
+    return lib().gsr_net_save(net, path.encode())
+
+
+def gsr_net_load(net, path: str):
+    return lib().gsr_net_load(net, path.encode())
+
+
+def gsr_net_forward(net, x, batch, length, out, stream=0):
+    return lib().gsr_net_forward(net, x or None, batch, length, out or None, stream or None)
+
+
+def gsr_net_train_step(net, x, target, batch, length, lr, loss_ptr, stream=0):
+    return lib().gsr_net_train_step(net, x or None, target or None, batch, length, lr, loss_ptr or None,
+                                    stream or None)
+
+
+def gsr_net_gradients(net, x, target, batch, length, grads, count, loss_ptr, stream=0):
+    return lib().gsr_net_gradients(net, x or None, target or None, batch, length, grads or None, count,
+                                   loss_ptr or None, stream or None)
+
+
+def gsr_warm_features(ctx, feats, scale_ptr, stream=0):
+    return lib().gsr_warm_features(ctx, feats or None, scale_ptr or None, stream or None)
+
+
+def gsr_warm_start(ctx, net, x0, stream=0):
+    return lib().gsr_warm_start(ctx, net or None, x0 or None, stream or None)
+
+
 # ---------------------------------------------------------------- convenience wrapper
 class GsrError(RuntimeError):
     def __init__(self, status, msg):
@@ -200,6 +270,73 @@ def _ptr(a) -> int:
 
 def _where(a) -> int:
     return GSR_DEVICE if hasattr(a, "is_cuda") and a.is_cuda else GSR_HOST
+
+
+class Net:
+    """Owns one gsr_net (the warm start's conv1d network)."""
+
+    def __init__(self, device=0):
+        st, h = gsr_net_create(device)
+        if st != 0:
+            raise GsrError(st, "gsr_net_create failed")
+        self.h = h
+        self.n_params = gsr_net_num_params()
+
+    def _check(self, st):
+        if st != 0:
+            raise GsrError(st, gsr_net_last_error(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            gsr_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        import numpy as np
+
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(gsr_net_set_params(self.h, p.ctypes.data, p.size))
+
+    def get_params(self):
+        import numpy as np
+
+        p = np.empty(self.n_params, dtype=np.float32)
+        self._check(gsr_net_get_params(self.h, p.ctypes.data, p.size))
+        return p
+
+    def save(self, path):
+        self._check(gsr_net_save(self.h, str(path)))
+
+    def load(self, path):
+        self._check(gsr_net_load(self.h, str(path)))
+
+    def forward(self, x, out, stream=0):
+        """x: CUDA float32 [batch, len, 6]; out: CUDA float32 [batch, len, 3]."""
+        b, n, _ = x.shape
+        self._check(gsr_net_forward(self.h, x.data_ptr(), b, n, out.data_ptr(), stream))
+
+    def train_step(self, x, target, lr, stream=0):
+        b, n, _ = x.shape
+        loss = ctypes.c_double()
+        self._check(gsr_net_train_step(self.h, x.data_ptr(), target.data_ptr(), b, n, lr, ctypes.addressof(loss),
+                                       stream))
+        return loss.value
+
+    def gradients(self, x, target, stream=0):
+        import numpy as np
+
+        b, n, _ = x.shape
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(gsr_net_gradients(self.h, x.data_ptr(), target.data_ptr(), b, n, g.ctypes.data, g.size,
+                                      ctypes.addressof(loss), stream))
+        return g, loss.value
 
 
 class Context:
@@ -257,6 +394,16 @@ class Context:
 
     def residual(self, x, r, stream=0):
         self._check(gsr_residual(self.h, _ptr(x), _ptr(r), stream))
+
+    def warm_features(self, feats, stream=0):
+        """feats: CUDA float32 [n_dfa, 6]; returns the scale."""
+        sc = ctypes.c_double()
+        self._check(gsr_warm_features(self.h, feats.data_ptr(), ctypes.addressof(sc), stream))
+        return sc.value
+
+    def warm_start(self, x0, net=None, stream=0):
+        """x0: CUDA float64 [n_cols] receives the start vector."""
+        self._check(gsr_warm_start(self.h, net.h if net is not None else 0, x0.data_ptr(), stream))
 
     def solve(self, x_out, x0=None, se_out=None, stream=0, **kw):
         p = gsr_default_params()

@@ -1,0 +1,86 @@
+"""The warm start on the GPU: features and per-star solves against the oracle;
+warm-started solves reach the same solution as cold solves."""
+import numpy as np
+import pytest
+import torch
+
+import gsrgen
+import oracle
+import paper_2308_00778_gb300 as g
+from gpu_util import block_errors, context_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(cfg, fp32):
+    h = gsrgen.generate(cfg, fp32=fp32)
+    s = oracle.from_host_system(h)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    ctx = context_for(h, fp32=fp32)
+    ctx.set_system(h.A32 if fp32 else h.A, h.knot, h.instr, b)
+    return h, s, b, ctx
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_features_vs_oracle(fp32):
+    cfg = gsrgen.make_cfg(81, 2000, (50, 150), 400, 60, att_kind=1)
+    h, s, b, ctx = _setup(cfg, fp32)
+    f = torch.zeros((cfg.n_dfa, 6), dtype=torch.float32, device="cuda")
+    scale = ctx.warm_features(f)
+    fr, sr = oracle.jacobi_features(s, b)
+    # binary32 storage: A^T b in binary32 products and partial sums
+    tol = 2e-4 if fp32 else 1e-6
+    assert scale == pytest.approx(sr, rel=tol)
+    got = f.cpu().numpy().astype(np.float64)
+    for c in range(6):
+        assert np.linalg.norm(got[:, c] - fr[:, c]) <= tol * np.linalg.norm(fr[:, c]) + 1e-6, c
+    ctx.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_astro_solve_vs_oracle(fp32):
+    cfg = gsrgen.make_cfg(82, 1500, (20, 120), 300, 40, att_kind=1)
+    h, s, b, ctx = _setup(cfg, fp32)
+    x0 = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    ctx.warm_start(x0)  # Jacobi attitude, per-star astrometric solve, zeros elsewhere
+    got = x0.cpu().numpy()
+    a0, a1 = s.blocks()["att"]
+    ref = np.zeros(s.n_cols)
+    ref[a0:a1] = got[a0:a1]
+    assert oracle.astro_solve(s, b, ref) == 0
+    # binary32 accumulation of the 5x5 normal equations: ~1e-6 relative per star
+    for st in range(cfg.n_stars):
+        r, gg = ref[5 * st:5 * st + 5], got[5 * st:5 * st + 5]
+        assert np.linalg.norm(gg - r) <= 1e-4 * np.linalg.norm(r) + 1e-9, st
+    assert not got[a1:].any()
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_warm_started_solves_reach_the_cold_solution(mode, tmp_path):
+    cfg = gsrgen.make_cfg(83, 4000, (100, 200), 500, 100, att_kind=1)
+    h, s, b, ctx = _setup(cfg, fp32=True)
+    kw = dict(damp=1e-6)
+    if mode == "mixed":
+        kw["mode"] = g.GSR_MIXED
+    x_cold = np.zeros(s.n_cols)
+    i_cold = ctx.solve(x_cold, itnlim=500, atol=1e-14, btol=1e-14, conlim=0.0, **kw)
+    x_j = np.zeros(s.n_cols)
+    i_j = ctx.solve(x_j, itnlim=500, atol=1e-14, btol=1e-14, conlim=0.0, warm=g.GSR_WARM_JACOBI, **kw)
+    # a learned start with random (untrained) weights is still a valid start
+    rng = np.random.default_rng(6)
+    net = g.Net()
+    net.set_params((rng.standard_normal(net.n_params) * 0.01).astype(np.float32))
+    net.save(tmp_path / "w.bin")
+    net.close()
+    x_l = np.zeros(s.n_cols)
+    i_l = ctx.solve(x_l, itnlim=500, atol=1e-14, btol=1e-14, conlim=0.0, warm=g.GSR_WARM_LEARNED,
+                    weights_path=str(tmp_path / "w.bin"), **kw)
+    for x, info in ((x_j, i_j), (x_l, i_l)):
+        for k, e in block_errors(x, x_cold, s).items():
+            assert e <= 1e-9, (mode, k, e, info)
+        assert info["ms_warm"] > 0.0
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(np.zeros(s.n_cols), warm=g.GSR_WARM_LEARNED, weights_path=str(tmp_path / "missing.bin"))
+    assert e.value.status == g.Status.EINVAL
+    ctx.close()
