@@ -80,9 +80,9 @@ gsr_status gsr_warm_features(gsr_ctx *ctx, float *feats, double *scale, void *st
 /*
  * gsr_warm_start -- the start vector x0 (n_cols binary64, device): attitude
  * part = scale * (features[:, 0:3] + net(features)) (net NULL: the Jacobi
- * estimate alone), astrometric part = per-star least squares of the rows'
- * residual after the attitude part, instrumental and global parts 0.
- * Synchronous.
+ * estimate alone); instrumental and global parts = their Jacobi estimates
+ * (A^T b)_j / |A_:,j|^2; astrometric part = per-star least squares (5x5) of
+ * the rows' residual after all the other parts. Synchronous.
  */
 gsr_status gsr_warm_start(gsr_ctx *ctx, gsr_net *net, double *x0, void *stream);
 

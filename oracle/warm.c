@@ -111,13 +111,14 @@ ORACLE_API void oracle_adam(double *w, double *m, double *v, const double *g, in
 }
 
 /*
- * Per-star astrometric solve: for each star s, with r_i = b_i - (attitude part
- * of row i) . x_att (instrumental and global parts of the start are 0),
+ * Per-star astrometric solve: for each star s, with r_i = b_i minus the
+ * attitude, instrumental and global parts of row i applied to x,
  *   G_s = sum_i a_i a_i^T + lambda_s I,   h_s = sum_i a_i r_i,   x_s = G_s^-1 h_s
  * over the star's rows (a_i = the 5 astrometric coefficients), with
  * lambda_s = 1e-12 * trace(sum a a^T) / 5 so that stars with fewer than five
  * observations still give a finite start. Solved by Cholesky.
- * x (n_cols): reads the attitude part, writes the astrometric part.
+ * x (n_cols): reads the attitude, instrumental and global parts, writes the
+ * astrometric part.
  * Returns the number of stars whose G was not positive definite (x_s = 0).
  */
 ORACLE_API int64_t oracle_astro_solve(const oracle_sys *s, const double *b, double *x)
@@ -128,10 +129,13 @@ ORACLE_API int64_t oracle_astro_solve(const oracle_sys *s, const double *b, doub
         double G[5][5] = {{0}}, h[5] = {0};
         for (int64_t i = s->star_ptr[star]; i < s->star_ptr[star + 1]; ++i) {
             const double *a = s->A + i * ORACLE_NPAR;
+            const int64_t instr0 = att0 + 3 * (int64_t)s->n_dfa, glob0 = instr0 + s->n_instr;
             double r = b[i];
             for (int ax = 0; ax < 3; ++ax)
                 for (int j = 0; j < 4; ++j)
                     r = r - a[5 + 4 * ax + j] * x[att0 + (int64_t)ax * s->n_dfa + s->knot[i] + j];
+            for (int j = 0; j < 6; ++j) r = r - a[17 + j] * x[instr0 + s->instr[i * 6 + j]];
+            if (s->n_glob) r = r - a[23] * x[glob0];
             for (int p = 0; p < 5; ++p) {
                 h[p] = h[p] + a[p] * r;
                 for (int q = 0; q < 5; ++q) G[p][q] = G[p][q] + a[p] * a[q];

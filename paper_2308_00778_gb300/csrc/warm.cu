@@ -63,6 +63,7 @@ __global__ void k_normalise_features(float *__restrict__ feats, int32_t n_dfa, c
 }
 
 // x0: attitude part = scale * (feats[:, 0:3] + net_out), everything else 0
+// (the instrumental and global parts are then set by k_rest_guess)
 __global__ void k_att_guess(const float *__restrict__ feats, const float *__restrict__ net_out,
                             const double *__restrict__ scale, int64_t att0, int32_t n_dfa, int64_t n_cols,
                             double *__restrict__ x0)
@@ -80,8 +81,18 @@ __global__ void k_att_guess(const float *__restrict__ feats, const float *__rest
     }
 }
 
-// Per-star 5x5 solve (one warp per star): with r_i = b_i - (attitude part of
-// row i) . x_att, accumulate G = sum a a^T and h = sum a r over the star's rows
+// x0 of the instrumental and global unknowns: their Jacobi estimates z_j p_j^2
+__global__ void k_rest_guess(const double *__restrict__ z, const double *__restrict__ p, int64_t instr0,
+                             int64_t n_cols, double *__restrict__ x0)
+{
+    for (int64_t j = instr0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols;
+         j += (int64_t)gridDim.x * blockDim.x)
+        x0[j] = z[j] * p[j] * p[j];
+}
+
+// Per-star 5x5 solve (one warp per star): with r_i = b_i minus the attitude,
+// instrumental and global parts of row i applied to x0, accumulate G = sum a a^T
+// and h = sum a r over the star's rows
 // (a = the 5 astrometric coefficients; binary32), add lambda = 1e-12 trace(G)/5
 // to the diagonal and solve G x = h by Cholesky in binary64 (x = 0 when G is
 // not positive definite).
@@ -111,6 +122,12 @@ __global__ void __launch_bounds__(256) k_astro_solve(SysView<VT> S, const double
                 for (int j = 0; j < NPARAXIS; ++j)
                     rr -= (float)reinterpret_cast<const VT *>(tb + (NASTRO + NPARAXIS * ax + j) * TL::VBLK)[i] *
                           (float)xt[(int64_t)ax * S.n_dfa + k + j];
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) {
+                const int32_t ic = reinterpret_cast<const int32_t *>(tb + NPAR * TL::VBLK + (1 + j) * TL::IBLK)[i];
+                rr -= (float)reinterpret_cast<const VT *>(tb + (17 + j) * TL::VBLK)[i] * (float)x0[S.instr0 + ic];
+            }
+            if (S.n_glob) rr -= (float)reinterpret_cast<const VT *>(tb + 23 * TL::VBLK)[i] * (float)x0[S.glob0];
             float a[5];
 #pragma unroll
             for (int p = 0; p < 5; ++p) a[p] = (float)reinterpret_cast<const VT *>(tb + p * TL::VBLK)[i];
@@ -179,8 +196,9 @@ static int grid_for(const gsr_ctx *c, int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->sm_count * 4));
 }
 
-// features of the loaded system into ws.feats; the device scale into ws.blk[8]
-gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s)
+// features of the loaded system into ws.feats, the device scale into ws.wacc[2];
+// keep_z leaves z = A^T b in ws.z (the caller clears it)
+gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s, bool keep_z)
 {
     gsr_status rc = ensure_workspace(c);
     if (rc != GSR_OK) return rc;
@@ -207,7 +225,7 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s)
     if ((e = cudaMemsetAsync(ws.wacc, 0, sizeof(double) * 4, s)) != cudaSuccess) return cuda_fail(c, e, "memset");
     k_att_features<<<grid_for(c, c->n_dfa), kThreads, 0, s>>>(ws.z, ws.p, att0, c->n_dfa, ws.feats, ws.wacc);
     k_normalise_features<<<grid_for(c, c->n_dfa), kThreads, 0, s>>>(ws.feats, c->n_dfa, ws.wacc, ws.wacc + 2);
-    if ((e = cudaMemsetAsync(ws.z, 0, sizeof(double) * (size_t)c->n_cols, s)) != cudaSuccess)
+    if (!keep_z && (e = cudaMemsetAsync(ws.z, 0, sizeof(double) * (size_t)c->n_cols, s)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "features");
     return GSR_OK;
@@ -216,14 +234,17 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s)
 // x0 (device) from the features and (optionally) the network
 gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s)
 {
-    gsr_status rc = warm_features_dev(c, s);
+    gsr_status rc = warm_features_dev(c, s, true);
     if (rc != GSR_OK) return rc;
     Workspace &ws = c->ws;
     if (net && (rc = gsr_net_forward(net, ws.feats, 1, c->n_dfa, ws.netout, s)) != GSR_OK)
         return fail(c, rc, std::string("warm start: ") + gsr_net_last_error(net));
-    const int64_t att0 = (int64_t)NASTRO * c->n_stars;
+    const int64_t att0 = (int64_t)NASTRO * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa;
     k_att_guess<<<grid_for(c, c->n_cols), kThreads, 0, s>>>(ws.feats, net ? ws.netout : nullptr, ws.wacc + 2, att0,
                                                             c->n_dfa, c->n_cols, x0);
+    k_rest_guess<<<grid_for(c, c->n_cols - instr0), kThreads, 0, s>>>(ws.z, ws.p, instr0, c->n_cols, x0);
+    cudaError_t ez = cudaMemsetAsync(ws.z, 0, sizeof(double) * (size_t)c->n_cols, s);
+    if (ez != cudaSuccess) return cuda_fail(c, ez, "memset");
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((c->n_stars + 7) / 8, (int64_t)c->sm_count * 8));
     if (c->prec == GSR_FP32)
         k_astro_solve<float><<<g, kThreads, 0, s>>>(view<float>(c), c->b, x0);
@@ -246,7 +267,7 @@ GSR_API gsr_status gsr_warm_features(gsr_ctx *c, float *feats, double *scale, vo
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     const cudaStream_t s = (cudaStream_t)stream;
-    gsr_status rc = warm_features_dev(c, s);
+    gsr_status rc = warm_features_dev(c, s, false);
     if (rc != GSR_OK) return rc;
     if ((e = cudaMemcpyAsync(feats, c->ws.feats, sizeof(float) * 6 * (size_t)c->n_dfa, cudaMemcpyDeviceToDevice, s)) !=
         cudaSuccess)
