@@ -232,37 +232,9 @@ def desc(w):
 
 # ---------------------------------------------------------------- our arm
 def _device_system(g, gsrgen, torch, cfg, fp32_store, round32, dev, sh, keep_host=False):
-    """Generate the system on the device, load it into a context, assemble b = A x_true + eps
-    with the library's aprod 1. Returns (ctx, b, host copies or None)."""
-    sp = gsrgen.star_ptr(cfg)
-    n = int(sp[-1])
-    nc = cfg.ncols()
-    spd = torch.tensor(sp, device=dev)
-    vdt = torch.float32 if fp32_store else torch.float64
-    vals = torch.empty(24 * n, dtype=vdt, device=dev)
-    knot = torch.empty(n, dtype=torch.int32, device=dev)
-    ins = torch.empty(6 * n, dtype=torch.int32, device=dev)
-    gsrgen.dev_rows(cfg, spd, sp, 0, cfg.n_stars, vals, n, knot, ins, stream=sh, round32=round32)
-    obs = cfg.obs_min if cfg.obs_min == cfg.obs_max else 0
-    ctx = g.Context(cfg.n_stars, obs_per_star=obs, star_ptr=None if obs else sp, n_dfa=cfg.n_dfa,
-                    n_instr=cfg.n_instr, n_glob=cfg.n_glob, fp32=fp32_store, device=dev.index or 0)
-    ctx.set_rows(0, n, vals, knot, ins, layout=g.GSR_SOA, plane_stride=n, stream=sh)
-    xt = torch.empty(nc, dtype=torch.float64, device=dev)
-    gsrgen.dev_xtrue(cfg, xt, stream=sh)
-    b = torch.empty(n, dtype=torch.float64, device=dev)
-    gsrgen.dev_noise(cfg, b, stream=sh)
-    ctx.aprod1(xt, b, stream=sh)  # b = A x_true + eps (binary64 arithmetic)
-    ctx.set_rhs(b, stream=sh)
-    torch.cuda.synchronize()
-    host = None
-    if keep_host:
-        host = {"A": vals.view(24, n).t().contiguous().cpu().pin_memory(),
-                "knot": knot.cpu().pin_memory(),
-                "instr": ins.view(6, n).t().contiguous().cpu().pin_memory(),
-                "b": b.cpu().pin_memory(), "star_ptr": sp}
-    del vals, ins, knot
-    torch.cuda.empty_cache()
-    return ctx, b, host
+    from paper_2308_00778_gb300.data import device_system
+
+    return device_system(cfg, fp32_store, round32, dev, stream=sh, keep_host=keep_host)
 
 
 def _time_solves(torch, ctx, x, kw, steps, warmup, stream, sh, clocks=None, nvtx=None):
