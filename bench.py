@@ -267,6 +267,44 @@ def _time_kernel(torch, fn, stream, reps=20):
     return e0.elapsed_time(e1) / reps
 
 
+def start_activity_record(torch, dev):
+    """A first, empty profiler session: the device's activity record (CUPTI) only sees kernels of the
+    library when it was attached before the library's first CUDA work."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+
+        with profile(activities=[ProfilerActivity.CUDA]):
+            torch.zeros(1, device=dev).add_(1)
+            torch.cuda.synchronize()
+    except Exception as e:
+        print(f"activity record unavailable: {e!r}", file=sys.stderr)
+
+
+def count_launches(torch, fn):
+    """Kernels the device ran during one call of fn, from torch.profiler's CUDA activity record."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+
+        fn()
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n = 0
+        kinds = {}
+        for ev in prof.events():
+            name = ev.name.lower()
+            kinds[str(ev.device_type)] = kinds.get(str(ev.device_type), 0) + 1
+            if "CUDA" in str(ev.device_type) and "memcpy" not in name and "memset" not in name:
+                n += 1
+        if not n:
+            print(f"launch count unavailable: profiler events by device {kinds}", file=sys.stderr)
+        return n or None
+    except Exception as e:  # the count is reported as unknown
+        print(f"launch count unavailable: {e!r}", file=sys.stderr)
+        return None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -283,6 +321,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
+    start_activity_record(torch, dev)
 
     w = gsrgen.workloads()[args.workload]
     cfg = w.cfg
@@ -303,13 +342,9 @@ def run_ours(args):
     xs = torch.zeros(nc, dtype=torch.float64, device=dev)
     ref_info = ctx64.solve(xs, itnlim=20000, atol=1e-15, btol=1e-15, damp=damp, conlim=0.0, stream=sh)
     x = torch.zeros(nc, dtype=torch.float64, device=dev)
+    learned = dict(warm=g.GSR_WARM_LEARNED, weights_path=g.WARM_WEIGHTS) if os.path.exists(g.WARM_WEIGHTS) else None
 
-    def err_plain(k):
-        ctx64.solve(x, itnlim=k, atol=0.0, btol=0.0, conlim=0.0, damp=damp, stream=sh)
-        torch.cuda.synchronize()
-        return max_block_err(x, xs, cfg)
-
-    def first_k(err, lo_k=2, cap=None):
+    def first_k(err, lo_k=1, cap=None):
         k = 8
         cap = cap or ref_info["itn"] + 40
         while err(k) > TOL and k < cap:
@@ -323,51 +358,77 @@ def run_ours(args):
                 lo = mid
         return hi
 
-    n9 = first_k(err_plain)
-    plain_kw = dict(itnlim=n9, atol=0.0, btol=0.0, conlim=0.0, damp=damp)
+    def plain_kw(k, warm=None):
+        return dict(itnlim=k, atol=0.0, btol=0.0, conlim=0.0, damp=damp, **(warm or {}))
 
-    def mixed_kw(k, m):
-        return dict(mode=g.GSR_MIXED, inner_itn=k, max_outer=m, refine_tol=-1.0, inner_tol=1e-30, atol=0.0,
-                    btol=0.0, conlim=0.0, damp=damp)
+    def mixed_kw(k, m, warm=None, k2=0):
+        return dict(mode=g.GSR_MIXED, inner_itn=k, inner_itn_next=k2, max_outer=m, refine_tol=-1.0,
+                    inner_tol=1e-30, atol=0.0, btol=0.0, conlim=0.0, damp=damp, **(warm or {}))
 
-    schedules = {}
-    for m in (2, 3):
-        def err_mixed(k, m=m):
-            ctx32.solve(x, stream=sh, **mixed_kw(k, m))
-            torch.cuda.synchronize()
-            return max_block_err(x, xs, cfg)
+    def min_k2(k1, m, warm, hi):
+        """Fewest inner iterations of the later refinement steps reaching TOL after k1 in the first (or None)."""
+        if err_of(ctx32, mixed_kw(k1, m, warm, hi)) > TOL:
+            return None
+        lo = 0
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if err_of(ctx32, mixed_kw(k1, m, warm, mid)) <= TOL:
+                hi = mid
+            else:
+                lo = mid
+        return hi
 
-        k = first_k(err_mixed, cap=n9 + 20)
-        if err_mixed(k) <= TOL:
-            schedules[m] = k
-    # quick timing of the candidate schedules, keep the fastest
-    best = None
-    for m, k in schedules.items():
-        ms_c, _ = _time_solves(torch, ctx32, x, mixed_kw(k, m), 2, 1, stream, sh)
-        if best is None or ms_c < best[0]:
-            best = (ms_c, m, k)
+    def err_of(ctx, kw):
+        ctx.solve(x, stream=sh, **kw)
+        torch.cuda.synchronize()
+        return max_block_err(x, xs, cfg)
 
-    # ---- timed region: plain binary64, then the mixed solver (headline)
+    # each solver: (context, keyword arguments, description) at the fewest iterations reaching 1e-9
+    legs = {}
+    n9 = first_k(lambda k: err_of(ctx64, plain_kw(k)))
+    legs["fp64_plain"] = (ctx64, plain_kw(n9), {"iterations": n9, "start": "x0 = 0"})
+    if learned:
+        nl = first_k(lambda k: err_of(ctx64, plain_kw(k, learned)))
+        legs["fp64_learned"] = (ctx64, plain_kw(nl, learned), {"iterations": nl, "start": "learned"})
+    for name, warm, outers in (("mixed", None, (2, 3)), ("mixed_learned", learned, (1, 2, 3))):
+        if name == "mixed_learned" and not learned:
+            continue
+        cands = []
+        for m in outers:
+            k = first_k(lambda k, m=m: err_of(ctx32, mixed_kw(k, m, warm)), cap=n9 + 20)
+            if err_of(ctx32, mixed_kw(k, m, warm)) > TOL:
+                continue
+            sched = {(k, k)}
+            if m > 1:  # a shorter inner limit for the steps after the first
+                for k1 in range(max(k - 1, 1), k + 3):
+                    k2 = min_k2(k1, m, warm, k + 2)
+                    if k2 is not None:
+                        sched.add((k1, k2))
+            for k1, k2 in sorted(sched, key=lambda q: q[0] + (m - 1) * q[1])[:3]:
+                ms_c, _ = _time_solves(torch, ctx32, x, mixed_kw(k1, m, warm, k2), 2, 1, stream, sh)
+                cands.append((ms_c, m, k1, k2))
+        if cands:
+            _, m, k1, k2 = min(cands)
+            legs[name] = (ctx32, mixed_kw(k1, m, warm, k2),
+                          {"outer": m, "inner_iterations": [k1] + [k2] * (m - 1),
+                           "start": "learned" if warm else "x0 = 0"})
+
+    # ---- timed region: every solver, the same K steps after W warm-up steps each
     if world > 1:
         dist.barrier()
-    ms_plain, _ = _time_solves(torch, ctx64, x, plain_kw, args.steps, args.warmup, stream, sh)
-    err_plain_final = max_block_err(x, xs, cfg)
-    ms_mixed, mixed_final, mixed_info = None, None, None
-    if best is not None:
-        with Clocks(local) as clk:
-            ms_mixed, mixed_info = _time_solves(torch, ctx32, x, mixed_kw(best[2], best[1]), args.steps, args.warmup,
-                                                stream, sh, nvtx="timed")
-        mixed_final = max_block_err(x, xs, cfg)
-    else:
-        with Clocks(local) as clk:
-            ms_plain, _ = _time_solves(torch, ctx64, x, plain_kw, args.steps, 0, stream, sh, nvtx="timed")
-    ms = ms_mixed if ms_mixed is not None and ms_mixed < ms_plain else ms_plain
+    solvers = {}
+    with Clocks(local) as clk:
+        for name, (ctx, kw, meta) in legs.items():
+            ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh, nvtx=f"timed:{name}")
+            solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
+                                 final_block_err=max_block_err(x, xs, cfg))
+    headline = min(solvers, key=lambda nm: solvers[nm]["s"])
+    ms = solvers[headline]["s"] * 1e3
     t_ms = torch.tensor([ms], device=dev)
     if world > 1:
         dist.barrier()
         dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
     ms = float(t_ms.item())
-    headline = "mixed" if ms_mixed is not None and ms_mixed <= ms_plain else "fp64_plain"
 
     # ---- per-kernel timing (same kernels, standalone launches, CUDA events on their stream)
     u64 = torch.randn(n, dtype=torch.float64, device=dev)
@@ -388,12 +449,18 @@ def run_ours(args):
         kern[name] = {"ms": kms, "GB/s": bpr * n / (kms * 1e-3) / 1e9, "bytes_per_row": bpr,
                       "TFLOP/s": FLOPS_PER_ROW * n / (kms * 1e-3) / 1e12}
     peaks = load_peaks()
-    if headline == "mixed":
-        m, k = best[1], best[2]
-        share = {"aprod1_f32": m * k * t["aprod1_f32"], "aprod2_f32": m * (k + 1) * t["aprod2_f32"],
-                 "residual_df": m * t["residual_df"]}
+    # launches of each hot kernel in one step of the headline solver (the dominant one is the roofline's)
+    hctx, hkw, hmeta = legs[headline]
+    warm_aprod2 = 1 if hkw.get("warm") else 0  # A^T b of the warm start (its column norms replace the solve's)
+    if hkw.get("mode") == g.GSR_MIXED:
+        m, its = hmeta["outer"], sum(hmeta["inner_iterations"])
+        n_res = m if hkw.get("warm") else m - 1  # the cold start's first residual is b itself
+        share = {"aprod1_f32": its * t["aprod1_f32"], "aprod2_f32": (its + m + 1 + warm_aprod2) * t["aprod2_f32"],
+                 "residual_df": n_res * t["residual_df"]}
     else:
-        share = {"aprod1_f64": n9 * t["aprod1_f64"], "aprod2_f64": (n9 + 2) * t["aprod2_f64"]}
+        k = hmeta["iterations"]
+        share = {"aprod1_f64": (k + (1 if hkw.get("warm") else 0)) * t["aprod1_f64"],
+                 "aprod2_f64": (k + 2 + warm_aprod2) * t["aprod2_f64"]}
     dom = max(share, key=share.get)
     if dom.endswith("f64"):
         fp64_peak = 1.25
@@ -405,22 +472,27 @@ def run_ours(args):
                 "unit": "GB/s", "frac": kern[dom]["GB/s"] / peaks["hbm_gbs"], "traffic": None,
                 "peak_src": peaks["src"]}
 
+    # ---- kernel launches of one headline step, counted from the device's activity record (CUPTI)
+    launches = count_launches(torch, lambda: hctx.solve(x, stream=sh, **hkw))
+
     # ---- end to end through the C ABI with host buffers (upload + solve + download every step)
     e2e = None
     if not args.no_e2e and host is not None:
+        f32 = hctx is ctx32
         xh = torch.zeros(nc, dtype=torch.float64).pin_memory()
         up = {k2: v for k2, v in host.items() if k2 != "star_ptr"}
+        if not f32:
+            up["A"] = up["A"].double().pin_memory()
         h2d = sum(v.numel() * v.element_size() for v in up.values())
         d2h = xh.numel() * 8
         sp = host["star_ptr"]
         obs = cfg.obs_min if cfg.obs_min == cfg.obs_max else 0
         ctx2 = g.Context(cfg.n_stars, obs_per_star=obs, star_ptr=None if obs else sp, n_dfa=cfg.n_dfa,
-                         n_instr=cfg.n_instr, n_glob=cfg.n_glob, fp32=True, device=local)
-        kw = mixed_kw(best[2], best[1]) if headline == "mixed" else plain_kw
+                         n_instr=cfg.n_instr, n_glob=cfg.n_glob, fp32=f32, device=local)
 
         def e2e_step():
             ctx2.set_system(up["A"], up["knot"], up["instr"], up["b"], stream=sh)
-            ctx2.solve(xh, stream=sh, **kw)
+            ctx2.solve(xh, stream=sh, **hkw)
 
         ms_e2e = _time_kernel(torch, e2e_step, stream, reps=args.steps)
         e2e = {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -439,24 +511,21 @@ def run_ours(args):
                          f"time extrapolated to the {n9} iterations that reach 1e-9; host has {cpu_count()} cores"}
 
     if rank == 0:
-        solvers = {"fp64_plain": {"s": ms_plain / 1e3, "iterations": n9, "final_block_err": err_plain_final}}
-        launches = {"fp64_plain": 6 * n9 + 9}
-        if ms_mixed is not None:
-            solvers["mixed"] = {"s": ms_mixed / 1e3, "outer": best[1], "inner_iterations": best[2],
-                                "final_block_err": mixed_final}
-            launches["mixed"] = best[1] * (6 * best[2] + 8) + 3
+        cold = solvers.get("fp64_plain", {}).get("s")
         line = {
             "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if headline == "mixed" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if headline.startswith("mixed") else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {desc(w)}; coefficients rounded to binary32",
                        "solver": headline, "reference": f"binary64 LSQR to atol=btol=1e-15 ({ref_info['itn']} itn)",
                        "tolerance": "1e-9 relative per block (astro, attitude, instrumental, global)",
+                       "warm_start_weights": os.path.relpath(g.WARM_WEIGHTS, ROOT) if learned else None,
                        "l2": "inputs larger than L2 (matrix >= 2.4 GB), no flush",
                        "parallelism": f"replicas x{world}"},
-            "solvers": solvers, "speedup_mixed_vs_fp64": (ms_plain / ms_mixed) if ms_mixed else None,
+            "solvers": solvers,
+            "speedup_vs_fp64_plain": {nm: cold / v["s"] for nm, v in solvers.items()} if cold else None,
             "kernels": kern, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches[headline] * args.steps,
+            "gpu_launches": launches * args.steps if launches is not None else None,
         }
         print(json.dumps(line), flush=True)
     ctx64.close()

@@ -201,6 +201,9 @@ typedef struct {
     double inner_tol;   /* MIXED: inner relative tolerance (0 = 1e-6)                    */
     double refine_tol;  /* MIXED: stop when every block's |dx|/|x| < refine_tol (0 = 1e-10) */
     int32_t max_outer;  /* MIXED: maximum refinement steps (0 = 20)                     */
+    int32_t inner_itn_next; /* MIXED: inner iteration limit of the refinement steps after
+                               the first (0 = inner_itn); the first step solves for the whole
+                               error of x0, the later ones only for its binary32 residue     */
 } gsr_solve_params;
 
 typedef struct {

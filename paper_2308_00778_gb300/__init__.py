@@ -5,6 +5,8 @@ binding only marshals arguments: every step of the path runs in the library's
 CUDA kernels. PyTorch tensors may be passed wherever the ABI takes a device
 pointer; their ``data_ptr()`` is forwarded unchanged.
 """
+import os as _os
+
 from .gsr import (  # noqa: F401
     GSR_AOS, GSR_DEVICE, GSR_FP32, GSR_FP64, GSR_HOST, GSR_MIXED, GSR_PLAIN, GSR_SOA, GSR_WARM_JACOBI,
     GSR_WARM_LEARNED, GSR_WARM_NONE, GsrError, SolveInfo, SolveParams, Status, gsr_aprod1, gsr_aprod1_f32, gsr_aprod2, gsr_aprod2_f32, gsr_residual, gsr_residual_static, gsr_create,
@@ -13,3 +15,7 @@ from .gsr import (  # noqa: F401
     gsr_net_gradients, gsr_net_get_params, gsr_net_last_error, gsr_net_load, gsr_net_num_params, gsr_net_save,
     gsr_net_set_params, gsr_net_train_step, gsr_warm_features, gsr_warm_start,
 )
+
+#: trained warm-start network shipped with the package (``python -m paper_2308_00778_gb300.train``
+#: wrote it; the .json beside it records the training run and its held-out evaluation)
+WARM_WEIGHTS = _os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "weights", "warmstart.bin")

@@ -33,6 +33,9 @@
 
 namespace gsr {
 
+// what an aprod 2 pass accumulates per column: sum a y, sum a^2, or both (into a second vector)
+enum { A2_PROD = 0, A2_SQUARE = 1, A2_BOTH = 2 };
+
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v)
 {
@@ -138,11 +141,13 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // crosses a star boundary moves its rows of the next star into a second
 // accumulator; rows of stars that begin and end inside one tile are added
 // directly).
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, bool SQUARE, bool LSQR>
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
-                                                     double *__restrict__ z, const LsqrState *__restrict__ st,
-                                                     int64_t tiles_per_warp)
+                                                     double *__restrict__ z, double *__restrict__ z2,
+                                                     const LsqrState *__restrict__ st, int64_t tiles_per_warp)
 {
+    constexpr bool SQUARE = MODE == A2_SQUARE;
+    constexpr bool BOTH = MODE == A2_BOTH;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -150,7 +155,8 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     __shared__ AT wred[8][NASTRO * 32];
     if (LSQR && st->done) return;
     AT *sm_ins = reinterpret_cast<AT *>(smem_raw);
-    const int32_t nsm = INSTR_SMEM ? S.n_instr : 0;
+    AT *sm_sq = sm_ins + S.n_instr;  // BOTH: the squares' accumulators follow the products'
+    const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * S.n_instr : S.n_instr) : 0;
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;
     __syncthreads();
 
@@ -160,10 +166,11 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     const int64_t t0 = gw * tiles_per_warp;
     const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
     double *__restrict__ zi = z + S.instr0;
-    AT gsum = (AT)0;
-    AT acc[NASTRO], acc2[NASTRO];
+    double *__restrict__ z2i = BOTH ? z2 + S.instr0 : nullptr;
+    AT gsum = (AT)0, gsq = (AT)0;
+    AT acc[NASTRO], acc2[NASTRO], sacc[NASTRO], sacc2[NASTRO];
 #pragma unroll
-    for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = (AT)0;
+    for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = sacc[j] = sacc2[j] = (AT)0;
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current run
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
@@ -195,13 +202,27 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                         atomicAdd(sm_ins + ic[j][i], av * yr[i]);
                     else
                         atomicAdd(zi + ic[j][i], (double)(av * yr[i]));
+                    if constexpr (BOTH) {
+                        if (INSTR_SMEM)
+                            atomicAdd(sm_sq + ic[j][i], av * av);
+                        else
+                            atomicAdd(z2i + ic[j][i], (double)(av * av));
+                    }
                 }
             }
             const AT gv = SQUARE ? ag[i] * ag[i] : ag[i];
             gsum = fma(gv, yr[i], gsum);
+            if constexpr (BOTH) gsq = fma(gv, in[i] ? gv : (AT)0, gsq);
         }
         // astrometric part: does the whole tile belong to star k?
         const int64_t tile_end = min((t + 1) * T, S.n_rows);  // one past the tile's last row
+        if constexpr (BOTH) {  // squares of padding rows (past n_rows) are masked here
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (!in[i])
+#pragma unroll
+                    for (int j = 0; j < NASTRO; ++j) a[j][i] = (AT)0;
+        }
         if (__ldg(S.star_ptr + k + 1) >= tile_end) {
 #pragma unroll
             for (int i = 0; i < R; ++i)
@@ -209,6 +230,7 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                 for (int j = 0; j < NASTRO; ++j) {
                     const AT av = SQUARE ? a[j][i] * a[j][i] : a[j][i];
                     acc[j] = fma(av, yr[i], acc[j]);
+                    if constexpr (BOTH) sacc[j] = fma(av, av, sacc[j]);
                 }
         } else {
             // the star of the tile's last row ends the next run
@@ -221,32 +243,47 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                 for (int j = 0; j < NASTRO; ++j) {
                     const AT av = SQUARE ? a[j][i] * a[j][i] : a[j][i];
                     const AT pv = av * yr[i];
-                    if (sr[i] == k)
+                    const AT qv = BOTH ? av * av : (AT)0;
+                    if (sr[i] == k) {
                         acc[j] += pv;
-                    else if (sr[i] == kn)
+                        if constexpr (BOTH) sacc[j] += qv;
+                    } else if (sr[i] == kn) {
                         acc2[j] += pv;
-                    else if (in[i])
+                        if constexpr (BOTH) sacc2[j] += qv;
+                    } else if (in[i]) {
                         atomicAdd(z + NASTRO * sr[i] + j, (double)pv);
+                        if constexpr (BOTH) atomicAdd(z2 + NASTRO * sr[i] + j, (double)qv);
+                    }
                 }
             }
             flush_astro_run(acc, k, wbuf, z);
+            if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2);
 #pragma unroll
             for (int j = 0; j < NASTRO; ++j) {
                 acc[j] = acc2[j];
                 acc2[j] = (AT)0;
+                sacc[j] = sacc2[j];
+                sacc2[j] = (AT)0;
             }
             k = kn;
         }
     }
-    if (t0 < t1) flush_astro_run(acc, k, wbuf, z);
+    if (t0 < t1) {
+        flush_astro_run(acc, k, wbuf, z);
+        if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2);
+    }
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
         const AT v = sm_ins[i];
-        if (v != (AT)0) atomicAdd(zi + i, (double)v);
+        if (v != (AT)0) atomicAdd(BOTH && i >= S.n_instr ? z2i + (i - S.n_instr) : zi + i, (double)v);
     }
     if (S.n_glob) {
         const double tot = block_sum((double)gsum, sm32);
         if (threadIdx.x == 0 && tot != 0.0) atomicAdd(z + S.glob0, tot);
+        if constexpr (BOTH) {
+            const double tq = block_sum((double)gsq, sm32);
+            if (threadIdx.x == 0 && tq != 0.0) atomicAdd(z2 + S.glob0, tq);
+        }
     }
 }
 
@@ -267,11 +304,13 @@ __device__ __forceinline__ void flush_att_run(AT (&acc)[NAXES * NPARAXIS], int32
 // aprod 2, attitude pass over the knot-ordered tiles: each warp owns the tiles
 // [w*tiles_per_warp, (w+1)*tiles_per_warp); runs of equal knot are summed in
 // registers and added once per run (one atomic add per column per run).
-template <typename VT, typename UT, typename AT, bool SQUARE, bool LSQR>
+template <typename VT, typename UT, typename AT, int MODE, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__restrict__ y,
-                                                    double *__restrict__ z, const LsqrState *__restrict__ st,
-                                                    int64_t tiles_per_warp)
+                                                    double *__restrict__ z, double *__restrict__ z2,
+                                                    const LsqrState *__restrict__ st, int64_t tiles_per_warp)
 {
+    constexpr bool SQUARE = MODE == A2_SQUARE;
+    constexpr bool BOTH = MODE == A2_BOTH;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     constexpr int NA = NAXES * NPARAXIS;
@@ -296,9 +335,12 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
     int32_t k = lo;
     int64_t next = S.knot_ptr[k + 1];
     double *__restrict__ zt = z + S.att0;
-    AT acc[NA];
+    double *__restrict__ z2t = BOTH ? z2 + S.att0 : nullptr;
+    AT acc[NA], sacc[BOTH ? NA : 1];
 #pragma unroll
     for (int j = 0; j < NA; ++j) acc[j] = (AT)0;
+#pragma unroll
+    for (int j = 0; j < (BOTH ? NA : 1); ++j) sacc[j] = (AT)0;
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.atiles + t * Tile<VT>::ABYTES;
         const int64_t q = t * T;
@@ -320,14 +362,25 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
             load_ints<R>(tb + NA * Tile<VT>::VBLK, 0, pr);
 #pragma unroll
             for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)y[pr[i]] : (AT)0;
+            if constexpr (BOTH) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    if (pl + i >= n)
+#pragma unroll
+                        for (int j = 0; j < NA; ++j) a[j][i] = (AT)0;
+            }
         }
         if (lastp < next) {  // every position of this tile is on knot k
 #pragma unroll
             for (int j = 0; j < NA; ++j)
 #pragma unroll
-                for (int i = 0; i < R; ++i) acc[j] = fma(a[j][i], yr[i], acc[j]);
+                for (int i = 0; i < R; ++i) {
+                    acc[j] = fma(a[j][i], yr[i], acc[j]);
+                    if constexpr (BOTH) sacc[j] = fma(a[j][i], a[j][i], sacc[j]);
+                }
         } else {  // the tile crosses knot boundaries: add its products position by position
             flush_att_run(acc, k, S.n_dfa, zt);
+            if constexpr (BOTH) flush_att_run(sacc, k, S.n_dfa, z2t);
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const int64_t p = pl + i;
@@ -336,9 +389,13 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
                     while (S.knot_ptr[kl + 1] <= p) ++kl;
 #pragma unroll
                     for (int j = 0; j < NA; ++j) {
+                        const int64_t col = (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS);
                         const AT pv = a[j][i] * yr[i];
-                        if (pv != (AT)0)
-                            atomicAdd(zt + (j / NPARAXIS) * S.n_dfa + kl + (j % NPARAXIS), (double)pv);
+                        if (pv != (AT)0) atomicAdd(zt + col, (double)pv);
+                        if constexpr (BOTH) {
+                            const AT qv = a[j][i] * a[j][i];
+                            if (qv != (AT)0) atomicAdd(z2t + col, (double)qv);
+                        }
                     }
                 }
             }
@@ -347,6 +404,7 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
         }
     }
     flush_att_run(acc, k, S.n_dfa, zt);
+    if constexpr (BOTH) flush_att_run(sacc, k, S.n_dfa, z2t);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -427,38 +485,40 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
     return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, typename UT, typename AT, bool INS, bool SQ, bool LS>
-static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, const LsqrState *st,
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS>
+static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                       cudaStream_t s)
 {
-    auto kern = k_aprod2_star<VT, UT, AT, INS, SQ, LS>;
-    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr : 0;
+    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS>;
+    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
     int64_t per = 0, blocks = 0;
     tile_ranges(c, kern, dyn, &per, &blocks);
-    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, st, per);
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per);
     return cudaGetLastError();
 }
 
-template <typename VT, typename UT, typename AT, bool SQ, bool LS>
-static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, const LsqrState *st, cudaStream_t s)
+template <typename VT, typename UT, typename AT, int MODE, bool LS>
+static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
+                            cudaStream_t s)
 {
     if (LS != (st != nullptr)) return cudaErrorInvalidValue;  // the LSQR variants read the solver state
-    if (!SQ && !y) return cudaErrorInvalidValue;
+    if (MODE != A2_SQUARE && !y) return cudaErrorInvalidValue;
+    if (MODE == A2_BOTH && !x2) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (sizeof(AT) * (size_t)c->n_instr <= kSmemBudget)
-        e = aprod2_star_launch<VT, UT, AT, true, SQ, LS>(c, y, x, st, s);
+    if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget)
+        e = aprod2_star_launch<VT, UT, AT, true, MODE, LS>(c, y, x, x2, st, s);
     else
-        e = aprod2_star_launch<VT, UT, AT, false, SQ, LS>(c, y, x, st, s);
+        e = aprod2_star_launch<VT, UT, AT, false, MODE, LS>(c, y, x, x2, st, s);
     if (e != cudaSuccess) return e;
     // attitude pass
-    auto kern = k_aprod2_att<VT, UT, AT, SQ, LS>;
+    auto kern = k_aprod2_att<VT, UT, AT, MODE, LS>;
     int64_t per = 0, blocks = 0;
     tile_ranges(c, kern, 0, &per, &blocks);
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, st, per);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per);
     return cudaGetLastError();
 }
 
@@ -467,18 +527,26 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
 {
     if (c->n_rows == 0) return cudaSuccess;
     if (inner32) {
-        if (square) return aprod2_t<float, float, float, true, false>(c, y, x, nullptr, s);
-        if (st) return aprod2_t<float, float, float, false, true>(c, y, x, st, s);
-        return aprod2_t<float, float, float, false, false>(c, y, x, nullptr, s);
+        if (square) return aprod2_t<float, float, float, A2_SQUARE, false>(c, y, x, nullptr, nullptr, s);
+        if (st) return aprod2_t<float, float, float, A2_PROD, true>(c, y, x, nullptr, st, s);
+        return aprod2_t<float, float, float, A2_PROD, false>(c, y, x, nullptr, nullptr, s);
     }
     if (c->prec == GSR_FP32) {
-        if (square) return aprod2_t<float, double, double, true, false>(c, y, x, nullptr, s);
-        if (st) return aprod2_t<float, double, double, false, true>(c, y, x, st, s);
-        return aprod2_t<float, double, double, false, false>(c, y, x, nullptr, s);
+        if (square) return aprod2_t<float, double, double, A2_SQUARE, false>(c, y, x, nullptr, nullptr, s);
+        if (st) return aprod2_t<float, double, double, A2_PROD, true>(c, y, x, nullptr, st, s);
+        return aprod2_t<float, double, double, A2_PROD, false>(c, y, x, nullptr, nullptr, s);
     }
-    if (square) return aprod2_t<double, double, double, true, false>(c, y, x, nullptr, s);
-    if (st) return aprod2_t<double, double, double, false, true>(c, y, x, st, s);
-    return aprod2_t<double, double, double, false, false>(c, y, x, nullptr, s);
+    if (square) return aprod2_t<double, double, double, A2_SQUARE, false>(c, y, x, nullptr, nullptr, s);
+    if (st) return aprod2_t<double, double, double, A2_PROD, true>(c, y, x, nullptr, st, s);
+    return aprod2_t<double, double, double, A2_PROD, false>(c, y, x, nullptr, nullptr, s);
+}
+
+cudaError_t launch_aprod2_both(const gsr_ctx *c, const void *y, double *x, double *sq, cudaStream_t s, bool inner32)
+{
+    if (c->n_rows == 0) return cudaSuccess;
+    if (inner32) return aprod2_t<float, float, float, A2_BOTH, false>(c, y, x, sq, nullptr, s);
+    if (c->prec == GSR_FP32) return aprod2_t<float, double, double, A2_BOTH, false>(c, y, x, sq, nullptr, s);
+    return aprod2_t<double, double, double, A2_BOTH, false>(c, y, x, sq, nullptr, s);
 }
 
 }  // namespace gsr

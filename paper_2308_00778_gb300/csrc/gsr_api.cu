@@ -492,7 +492,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         default_params(&prm);
     if (prm.itnlim < 0 || prm.damp < 0.0 || prm.atol < 0.0 || prm.btol < 0.0 || prm.conlim < 0.0 ||
         (prm.where != GSR_HOST && prm.where != GSR_DEVICE) || (prm.mode != GSR_PLAIN && prm.mode != GSR_MIXED) ||
-        prm.warm < GSR_WARM_NONE || prm.warm > GSR_WARM_LEARNED)
+        prm.warm < GSR_WARM_NONE || prm.warm > GSR_WARM_LEARNED || prm.inner_itn < 0 || prm.inner_itn_next < 0 ||
+        prm.max_outer < 0)
         return fail(c, GSR_EINVAL, "invalid solve parameters");
     if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
     if (!c->rhs_set) return fail(c, GSR_ESTATE, "b not loaded");
@@ -545,8 +546,13 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         x0_dev = true;
         ms_warm = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
     }
-    const gsr_status rc = prm.mode == GSR_MIXED ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own)
-                                                : lsqr_solve(c, &prm, x0_use, x0_dev, x_out, se_out, info, c->own);
+    // the warm start computed p with binary32 sums on binary32 storage and binary64 sums otherwise: the
+    // mixed solver (binary32 storage) and the plain solver on binary64 storage reuse it
+    const bool p_ready = prm.warm != GSR_WARM_NONE && prm.precond != 0 &&
+                         (prm.mode == GSR_MIXED || c->prec == GSR_FP64);
+    const gsr_status rc = prm.mode == GSR_MIXED
+                              ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own, p_ready)
+                              : lsqr_solve(c, &prm, x0_use, x0_dev, x_out, se_out, info, c->own, p_ready);
     if (info) {
         info->ms_warm = ms_warm;
         info->ms_total += ms_warm;

@@ -86,6 +86,7 @@ struct Workspace {
     float *netout = nullptr;    // n_dfa x 3: network output
     double *wacc = nullptr;     // 4: feature sums [0..1], scale [2]
     double *x0w = nullptr;      // n_cols: warm start vector
+    float *astro_n = nullptr;   // n_stars x 20: per-star normal equations of the warm start
     std::vector<GraphCache> graphs;
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
@@ -155,6 +156,8 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
                           cudaStream_t s, bool inner32 = false);
 cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool square, const LsqrState *st,
                           cudaStream_t s, bool inner32 = false);
+// one pass computing x += A^T y and sq += the column sums of squares (the warm start)
+cudaError_t launch_aprod2_both(const gsr_ctx *c, const void *y, double *x, double *sq, cudaStream_t s, bool inner32);
 int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 
 // knot-ordered attitude copy (layout.cu); built once per loaded system
@@ -162,13 +165,17 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s);
 
 // LSQR driver (lsqr.cu)
 // x0_dev: x0 is device memory whatever prm->where says (the warm start's vector)
+// p_ready: ws.p already holds this solve's column scaling (computed by the warm
+// start of the same call, with the same precision), so the pass is skipped
 gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                      double *se_out, gsr_solve_info *info, cudaStream_t s);
+                      double *se_out, gsr_solve_info *info, cudaStream_t s, bool p_ready = false);
 gsr_status ensure_workspace(gsr_ctx *c);
 void free_workspace(gsr_ctx *c);
 void default_params(gsr_solve_params *p);
 int col_grid(const gsr_ctx *c, int64_t n);
-gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false);
+// with y (and use): the same pass also adds A^T y to z (binary32 products when f32)
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false, const void *y = nullptr,
+                        double *z = nullptr);
 LsqrState initial_state(const gsr_solve_params *prm);
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
@@ -181,7 +188,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *b
                             double *part, cudaStream_t s, int *grid_out);
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                       gsr_solve_info *info, cudaStream_t s);
+                       gsr_solve_info *info, cudaStream_t s, bool p_ready = false);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v)

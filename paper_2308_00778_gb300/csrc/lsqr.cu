@@ -378,6 +378,7 @@ void free_workspace(gsr_ctx *c)
                       ws.x0w};
     if (ws.feats) cudaFree(ws.feats);
     if (ws.netout) cudaFree(ws.netout);
+    if (ws.astro_n) cudaFree(ws.astro_n);
     for (double *p : ptrs)
         if (p) cudaFree(p);
     if (ws.u32) cudaFree(ws.u32);
@@ -457,19 +458,23 @@ void default_params(gsr_solve_params *p)
     p->inner_tol = 0.0;
     p->refine_tol = 0.0;
     p->max_outer = 0;
+    p->inner_itn_next = 0;
 }
 
 // p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in
 // binary32 (binary32-stored systems; used by the mixed solver, whose
 // refinement does not depend on the exact scaling), otherwise binary64.
-gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32)
+gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32, const void *y, double *z)
 {
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols;
     cudaError_t e = cudaMemsetAsync(ws.tmp, 0, nc * sizeof(double), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-    if (use && (e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s, f32)) != cudaSuccess)
+    if (use && y) {
+        if ((e = launch_aprod2_both(c, y, z, ws.tmp, s, f32)) != cudaSuccess) return cuda_fail(c, e, "A^T y + norms");
+    } else if (use && (e = launch_aprod2(c, nullptr, ws.tmp, true, nullptr, s, f32)) != cudaSuccess) {
         return cuda_fail(c, e, "column norms");
+    }
     k_precond_finish<<<col_grid(c, nc), kColThreads, 0, s>>>(ws.tmp, ws.p, nc, use ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "preconditioner");
     return GSR_OK;
@@ -555,7 +560,7 @@ void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_c
 }
 
 gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                      double *se_out, gsr_solve_info *info, cudaStream_t s)
+                      double *se_out, gsr_solve_info *info, cudaStream_t s, bool p_ready)
 {
     const auto t0 = std::chrono::steady_clock::now();
     gsr_status rc = ensure_workspace(c);
@@ -569,7 +574,7 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
     cudaError_t e;
 
     // preconditioner p = 1/|A_:,j| (Alg. 1): one pass over A per solve
-    if ((rc = precond_pass(c, prm->precond != 0, s)) != GSR_OK) return rc;
+    if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s)) != GSR_OK) return rc;
 
     // x0: u = b - A x0 ; otherwise u = b
     const double *x0d = nullptr;

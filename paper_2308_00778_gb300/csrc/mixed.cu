@@ -105,6 +105,21 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
     }
 }
 
+// The residual of x = 0: r = b rounded to binary32 (what k_residual computes
+// for x = 0, without reading A); per-block sums of squares into part.
+__global__ void k_rhs32(const double *__restrict__ b, float *__restrict__ r, double *__restrict__ part, int64_t n)
+{
+    __shared__ double sm32[32];
+    float ssq = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)__ldcs(b + i);
+        r[i] = v;
+        ssq = fmaf(v, v, ssq);
+    }
+    const double tot = block_sum((double)ssq, sm32);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 // x += p * y (the inner solution, scaled back); per-block sums of squares of
 // the correction (blk[0..3]) and of the new x (blk[4..7]).
 __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, const double *__restrict__ y,
@@ -173,7 +188,7 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
 }
 
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                       gsr_solve_info *info, cudaStream_t s)
+                       gsr_solve_info *info, cudaStream_t s, bool p_ready)
 {
     const auto t0 = std::chrono::steady_clock::now();
     gsr_status rc = ensure_workspace(c);
@@ -185,7 +200,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     const bool dev_io = prm->where == GSR_DEVICE;
     cudaError_t e;
 
-    if ((rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
+    if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
     k_split<<<grow, kThreads, 0, s>>>(c->b, ws.bhl, nr);
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
@@ -195,7 +210,8 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     if (e != cudaSuccess) return cuda_fail(c, e, "mixed start");
 
     LsqrState init = initial_state(prm);
-    init.itnlim = prm->inner_itn > 0 ? prm->inner_itn : prm->itnlim;
+    const int32_t itn_first = prm->inner_itn > 0 ? prm->inner_itn : prm->itnlim;
+    const int32_t itn_next = prm->inner_itn_next > 0 ? prm->inner_itn_next : itn_first;
     init.atol = init.btol = prm->inner_tol > 0.0 ? prm->inner_tol : 1e-6;
     const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
     const double refine_tol = prm->refine_tol != 0.0 ? prm->refine_tol : 1e-10;
@@ -208,9 +224,15 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     int total_itn = 0, outer = 0;
     gsr_status status = GSR_OK;
     for (; outer < max_outer; ++outer) {
-        k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
-        if (nr > 0 && (e = residual_launch(c, ws.xhl, ws.bhl, nullptr, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
-            return cuda_fail(c, e, "residual");
+        init.itnlim = outer == 0 ? itn_first : itn_next;
+        if (outer == 0 && !x0) {
+            if (nr > 0) k_rhs32<<<gres, kThreads, 0, s>>>(c->b, ws.u32, ws.part_u, nr);
+        } else {
+            k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
+            if (nr > 0 &&
+                (e = residual_launch(c, ws.xhl, ws.bhl, nullptr, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
+                return cuda_fail(c, e, "residual");
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
         status = run_lsqr(c, init, true, false, nr > 0 ? gres : 0, prm->graph_k, prm->timeout_s, t0, s, &fin);
         total_itn += fin.itn;

@@ -17,6 +17,18 @@ __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ out, 
         out[i] = (float)a[i];
 }
 
+__global__ void k_neg_f32(const double *__restrict__ a, float *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = -(float)a[i];
+}
+
+__global__ void k_neg_f64(const double *__restrict__ a, double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = -a[i];
+}
+
 // Jacobi estimate and log column norm of the attitude columns; sums for the
 // normalisation (sum of squares of the estimate, sum of the logs) in acc[0..1].
 __global__ void k_att_features(const double *__restrict__ z, const double *__restrict__ p, int64_t att0, int32_t n_dfa,
@@ -90,110 +102,213 @@ __global__ void k_rest_guess(const double *__restrict__ z, const double *__restr
         x0[j] = z[j] * p[j] * p[j];
 }
 
-// Per-star 5x5 solve (one warp per star): with r_i = b_i minus the attitude,
-// instrumental and global parts of row i applied to x0, accumulate G = sum a a^T
-// and h = sum a r over the star's rows
-// (a = the 5 astrometric coefficients; binary32), add lambda = 1e-12 trace(G)/5
-// to the diagonal and solve G x = h by Cholesky in binary64 (x = 0 when G is
-// not positive definite).
-template <typename VT>
-__global__ void __launch_bounds__(256) k_astro_solve(SysView<VT> S, const double *__restrict__ b,
-                                                     double *__restrict__ x0)
+// Per-star 5x5 solve of the astrometric block. With r_i = b_i minus the
+// attitude, instrumental and global parts of row i applied to x0 (one aprod 1
+// pass with the astrometric part of x0 still zero), k_astro_normal
+// accumulates for every star G = sum a a^T (upper triangle, 15 values) and
+// h = sum a r (5 values) over the star's rows (a = the row's 5 astrometric
+// coefficients; binary32 products and sums) into N[star][20]; k_astro_chol
+// adds lambda = 1e-12 trace(G)/5 to the diagonal and solves G x = h by
+// Cholesky in binary64, one thread per star (x = 0 when G is not positive
+// definite).
+static constexpr int NNORM = 20;
+
+// Add a warp's per-lane partial sums of the 20 normal-equation values of star
+// k to N (through a per-warp shared buffer: lanes 0..19 each sum one value).
+// Warp-collective.
+__device__ __forceinline__ void flush_normal_run(float (&acc)[NNORM], int64_t k, float *__restrict__ wbuf,
+                                                 float *__restrict__ N)
 {
-    using TL = Tile<VT>;
     const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NNORM; ++j) {
+        wbuf[j * 32 + lane] = acc[j];
+        acc[j] = 0.f;
+    }
+    __syncwarp();
+    if (lane < NNORM) {
+        float t = 0.f;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
+        atomicAdd(N + NNORM * k + lane, t);
+    }
+    __syncwarp();
+}
+
+// the 20 products of one row: a_p a_q (p <= q), then a_p r
+__device__ __forceinline__ void normal_terms(const float (&a)[NASTRO], float r, float (&out)[NNORM])
+{
+    int q = 0;
+#pragma unroll
+    for (int p = 0; p < NASTRO; ++p)
+#pragma unroll
+        for (int c = p; c < NASTRO; ++c) out[q++] = a[p] * a[c];
+#pragma unroll
+    for (int p = 0; p < NASTRO; ++p) out[15 + p] = a[p] * r;
+}
+
+// this lane's R consecutive entries of a row vector as binary32 (0 past n_rows)
+template <typename RT, int R>
+__device__ __forceinline__ void load_rows(const RT *__restrict__ r, int64_t r0, int64_t n, float (&out)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; ++i) out[i] = r0 + i < n ? (float)__ldcs(r + r0 + i) : 0.f;
+}
+
+// Each warp owns a contiguous range of row tiles (as the star pass of aprod 2):
+// products of the current star accumulate per lane and are flushed once per
+// star; at a tile that crosses a star boundary the run of star k is flushed
+// first, then the tile's rows of the next star start the new run, and stars
+// that begin and end inside one tile are added directly. N must be zero on
+// entry; r holds the residual of the non-astrometric parts (n_rows entries).
+template <typename VT, typename RT>
+__global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *__restrict__ r,
+                                                      float *__restrict__ N, int64_t tiles_per_warp)
+{
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
+    __shared__ float wred[8][NNORM * 32];
+    const int lane = threadIdx.x & 31;
+    float *wbuf = wred[threadIdx.x >> 5];
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double *xt = x0 + S.att0;
-    for (int64_t s = gw; s < S.n_stars; s += nw) {
-        float G[15], h[5];
+    const int64_t t0 = gw * tiles_per_warp;
+    const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
+    float acc[NNORM];
 #pragma unroll
-        for (int q = 0; q < 15; ++q) G[q] = 0.f;
+    for (int j = 0; j < NNORM; ++j) acc[j] = 0.f;
+    int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
+        const int64_t r0 = t * T + lane * R;
+        float rv[R];
+        load_rows<RT, R>(r, r0, S.n_rows, rv);
+        float a[NASTRO][R];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) h[q] = 0.f;
-        for (int64_t r = S.star_ptr[s] + lane; r < S.star_ptr[s + 1]; r += 32) {
-            const uint8_t *tb = S.tiles + (r / TL::T) * TL::BYTES;
-            const int64_t i = r % TL::T;
-            const int32_t k = reinterpret_cast<const int32_t *>(tb + NPAR * TL::VBLK)[i];
-            float rr = (float)b[r];
+        for (int j = 0; j < NASTRO; ++j) load_vals<VT, float>(tb, j, a[j]);
 #pragma unroll
-            for (int ax = 0; ax < NAXES; ++ax)
+        for (int i = 0; i < R; ++i)
+            if (r0 + i >= S.n_rows)
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j)
-                    rr -= (float)reinterpret_cast<const VT *>(tb + (NASTRO + NPARAXIS * ax + j) * TL::VBLK)[i] *
-                          (float)xt[(int64_t)ax * S.n_dfa + k + j];
+                for (int j = 0; j < NASTRO; ++j) a[j][i] = 0.f;
+        const int64_t tile_end = min((t + 1) * T, S.n_rows);
+        if (__ldg(S.star_ptr + k + 1) >= tile_end) {  // the whole tile belongs to star k
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) {
-                const int32_t ic = reinterpret_cast<const int32_t *>(tb + NPAR * TL::VBLK + (1 + j) * TL::IBLK)[i];
-                rr -= (float)reinterpret_cast<const VT *>(tb + (17 + j) * TL::VBLK)[i] * (float)x0[S.instr0 + ic];
+            for (int i = 0; i < R; ++i) {
+                float ar[NASTRO], tr[NNORM];
+#pragma unroll
+                for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
+                normal_terms(ar, rv[i], tr);
+#pragma unroll
+                for (int j = 0; j < NNORM; ++j) acc[j] += tr[j];
             }
-            if (S.n_glob) rr -= (float)reinterpret_cast<const VT *>(tb + 23 * TL::VBLK)[i] * (float)x0[S.glob0];
-            float a[5];
+        } else {
+            const int64_t kn2 = star_of_row(S.star_ptr, S.first_star, t, tile_end - 1);
+            int64_t sr[R];
+            stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
 #pragma unroll
-            for (int p = 0; p < 5; ++p) a[p] = (float)reinterpret_cast<const VT *>(tb + p * TL::VBLK)[i];
-            int q = 0;
+            for (int i = 0; i < R; ++i)
+                if (sr[i] == k) {
+                    float ar[NASTRO], tr[NNORM];
 #pragma unroll
-            for (int p = 0; p < 5; ++p) {
-                h[p] = fmaf(a[p], rr, h[p]);
+                    for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
+                    normal_terms(ar, rv[i], tr);
 #pragma unroll
-                for (int c = p; c < 5; ++c) {
-                    G[q] = fmaf(a[p], a[c], G[q]);
-                    ++q;
+                    for (int j = 0; j < NNORM; ++j) acc[j] += tr[j];
                 }
+            flush_normal_run(acc, k, wbuf, N);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (sr[i] == k) continue;
+                float ar[NASTRO], tr[NNORM];
+#pragma unroll
+                for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
+                normal_terms(ar, rv[i], tr);
+                if (sr[i] == kn2) {
+#pragma unroll
+                    for (int j = 0; j < NNORM; ++j) acc[j] += tr[j];
+                } else if (r0 + i < S.n_rows) {
+#pragma unroll
+                    for (int j = 0; j < NNORM; ++j) atomicAdd(N + NNORM * sr[i] + j, tr[j]);
+                }
+            }
+            k = kn2;
+        }
+    }
+    if (t0 < t1) flush_normal_run(acc, k, wbuf, N);
+}
+
+__global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, double *__restrict__ x0)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_stars;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const float *n = N + NNORM * s;
+        double M[NASTRO][NASTRO], L[NASTRO][NASTRO], y[NASTRO], xs[NASTRO];
+        int q = 0;
+#pragma unroll
+        for (int p = 0; p < NASTRO; ++p)
+#pragma unroll
+            for (int c = p; c < NASTRO; ++c) {
+                M[p][c] = M[c][p] = (double)n[q];
+                ++q;
+            }
+        const double lam = 1e-12 * (M[0][0] + M[1][1] + M[2][2] + M[3][3] + M[4][4]) / 5.0;
+#pragma unroll
+        for (int p = 0; p < NASTRO; ++p) M[p][p] += lam;
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < NASTRO; ++j) {
+            double d = M[j][j];
+#pragma unroll
+            for (int k2 = 0; k2 < j; ++k2) d -= L[j][k2] * L[j][k2];
+            ok = ok && d > 0.0;
+            L[j][j] = sqrt(ok ? d : 1.0);
+#pragma unroll
+            for (int i2 = j + 1; i2 < NASTRO; ++i2) {
+                double v = M[i2][j];
+#pragma unroll
+                for (int k2 = 0; k2 < j; ++k2) v -= L[i2][k2] * L[j][k2];
+                L[i2][j] = v / L[j][j];
             }
         }
 #pragma unroll
-        for (int q = 0; q < 15; ++q)
+        for (int i2 = 0; i2 < NASTRO; ++i2) {
+            double v = (double)n[15 + i2];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) G[q] += __shfl_xor_sync(0xffffffffu, G[q], o);
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) h[q] += __shfl_xor_sync(0xffffffffu, h[q], o);
-        if (lane == 0) {
-            double M[5][5], L[5][5] = {{0}}, y[5], xs[5];
-            int q = 0;
-            for (int p = 0; p < 5; ++p)
-                for (int c = p; c < 5; ++c) M[p][c] = M[c][p] = (double)G[q++];
-            const double lam = 1e-12 * (M[0][0] + M[1][1] + M[2][2] + M[3][3] + M[4][4]) / 5.0;
-            bool ok = true;
-            for (int p = 0; p < 5; ++p) M[p][p] += lam;
-            for (int j = 0; j < 5 && ok; ++j) {
-                double d = M[j][j];
-                for (int k2 = 0; k2 < j; ++k2) d -= L[j][k2] * L[j][k2];
-                if (!(d > 0.0)) {
-                    ok = false;
-                    break;
-                }
-                L[j][j] = sqrt(d);
-                for (int i2 = j + 1; i2 < 5; ++i2) {
-                    double v = M[i2][j];
-                    for (int k2 = 0; k2 < j; ++k2) v -= L[i2][k2] * L[j][k2];
-                    L[i2][j] = v / L[j][j];
-                }
-            }
-            if (ok) {
-                for (int i2 = 0; i2 < 5; ++i2) {
-                    double v = (double)h[i2];
-                    for (int k2 = 0; k2 < i2; ++k2) v -= L[i2][k2] * y[k2];
-                    y[i2] = v / L[i2][i2];
-                }
-                for (int i2 = 4; i2 >= 0; --i2) {
-                    double v = y[i2];
-                    for (int k2 = i2 + 1; k2 < 5; ++k2) v -= L[k2][i2] * xs[k2];
-                    xs[i2] = v / L[i2][i2];
-                }
-            } else {
-                for (int i2 = 0; i2 < 5; ++i2) xs[i2] = 0.0;
-            }
-            for (int i2 = 0; i2 < 5; ++i2) x0[NASTRO * s + i2] = xs[i2];
+            for (int k2 = 0; k2 < i2; ++k2) v -= L[i2][k2] * y[k2];
+            y[i2] = v / L[i2][i2];
         }
+#pragma unroll
+        for (int i2 = NASTRO - 1; i2 >= 0; --i2) {
+            double v = y[i2];
+#pragma unroll
+            for (int k2 = i2 + 1; k2 < NASTRO; ++k2) v -= L[k2][i2] * xs[k2];
+            xs[i2] = v / L[i2][i2];
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < NASTRO; ++i2) x0[NASTRO * s + i2] = ok ? xs[i2] : 0.0;
     }
 }
 
 static int grid_for(const gsr_ctx *c, int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->sm_count * 4));
+}
+
+// k_astro_normal over contiguous tile ranges, one range per resident warp (at least 8 tiles each)
+template <typename VT, typename RT>
+static cudaError_t astro_normal_launch(const gsr_ctx *c, const RT *r, cudaStream_t s)
+{
+    auto kern = k_astro_normal<VT, RT>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t wpb = kThreads / 32;
+    const int64_t max_warps = (int64_t)per_sm * c->sm_count * wpb;
+    const int64_t per = std::max<int64_t>((c->n_tiles + max_warps - 1) / max_warps, 8);
+    const int64_t warps = (c->n_tiles + per - 1) / per;
+    const int64_t blocks = std::max<int64_t>((warps + wpb - 1) / wpb, 1);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), r, c->ws.astro_n, per);
+    return cudaGetLastError();
 }
 
 // features of the loaded system into ws.feats, the device scale into ws.wacc[2];
@@ -211,16 +326,12 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s, bool keep_z)
             (e = cudaMalloc(&ws.wacc, sizeof(double) * 4)) != cudaSuccess)
             return cuda_fail(c, e, "warm-start buffers");
     }
+    // p = 1/|A_:,j| and z = A^T b (z is zero between uses) in one pass over the rows; binary32
+    // products and sums for binary32 storage (b rounded to binary32 in ws.u32)
     const bool f32 = c->prec == GSR_FP32;
-    if ((rc = precond_pass(c, true, s, f32)) != GSR_OK) return rc;
-    // z = A^T b (z is zero between uses); binary32 products for binary32 storage
-    if (f32) {
-        k_to_f32<<<grid_for(c, c->n_rows), kThreads, 0, s>>>(c->b, ws.u32, c->n_rows);
-        e = launch_aprod2(c, ws.u32, ws.z, false, nullptr, s, true);
-    } else {
-        e = launch_aprod2(c, c->b, ws.z, false, nullptr, s, false);
-    }
-    if (e != cudaSuccess) return cuda_fail(c, e, "features: A^T b");
+    if (f32) k_to_f32<<<grid_for(c, c->n_rows), kThreads, 0, s>>>(c->b, ws.u32, c->n_rows);
+    if ((rc = precond_pass(c, true, s, f32, f32 ? (const void *)ws.u32 : (const void *)c->b, ws.z)) != GSR_OK)
+        return rc;
     const int64_t att0 = (int64_t)NASTRO * c->n_stars;
     if ((e = cudaMemsetAsync(ws.wacc, 0, sizeof(double) * 4, s)) != cudaSuccess) return cuda_fail(c, e, "memset");
     k_att_features<<<grid_for(c, c->n_dfa), kThreads, 0, s>>>(ws.z, ws.p, att0, c->n_dfa, ws.feats, ws.wacc);
@@ -245,11 +356,28 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s)
     k_rest_guess<<<grid_for(c, c->n_cols - instr0), kThreads, 0, s>>>(ws.z, ws.p, instr0, c->n_cols, x0);
     cudaError_t ez = cudaMemsetAsync(ws.z, 0, sizeof(double) * (size_t)c->n_cols, s);
     if (ez != cudaSuccess) return cuda_fail(c, ez, "memset");
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((c->n_stars + 7) / 8, (int64_t)c->sm_count * 8));
-    if (c->prec == GSR_FP32)
-        k_astro_solve<float><<<g, kThreads, 0, s>>>(view<float>(c), c->b, x0);
-    else
-        k_astro_solve<double><<<g, kThreads, 0, s>>>(view<double>(c), c->b, x0);
+    if (!ws.astro_n && (ez = cudaMalloc(&ws.astro_n, sizeof(float) * NNORM * (size_t)c->n_stars)) != cudaSuccess)
+        return cuda_fail(c, ez, "normal-equation buffer");
+    if ((ez = cudaMemsetAsync(ws.astro_n, 0, sizeof(float) * NNORM * (size_t)c->n_stars, s)) != cudaSuccess)
+        return cuda_fail(c, ez, "memset");
+    if (c->n_rows > 0) {
+        // r = b - A x0 with the astrometric part of x0 still zero: the residual of the other parts
+        const int64_t nc = c->n_cols;
+        if (c->prec == GSR_FP32) {
+            // ws.u32 still holds b rounded to binary32 (the features' pass only read it)
+            k_neg_f32<<<grid_for(c, nc), kThreads, 0, s>>>(x0, ws.pv32, nc);
+            if ((ez = launch_aprod1(c, ws.pv32, ws.u32, nullptr, nullptr, s, true)) == cudaSuccess)
+                ez = astro_normal_launch<float, float>(c, ws.u32, s);
+        } else {
+            k_neg_f64<<<grid_for(c, nc), kThreads, 0, s>>>(x0, ws.tmp, nc);
+            if ((ez = cudaMemcpyAsync(ws.u, c->b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyDeviceToDevice,
+                                      s)) == cudaSuccess &&
+                (ez = launch_aprod1(c, ws.tmp, ws.u, nullptr, nullptr, s, false)) == cudaSuccess)
+                ez = astro_normal_launch<double, double>(c, ws.u, s);
+        }
+        if (ez != cudaSuccess) return cuda_fail(c, ez, "warm start: normal equations");
+    }
+    k_astro_chol<<<grid_for(c, c->n_stars), kThreads, 0, s>>>(ws.astro_n, c->n_stars, x0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "warm start");
     return GSR_OK;

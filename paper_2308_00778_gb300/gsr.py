@@ -52,6 +52,7 @@ class SolveParams(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("refine_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
+        ("inner_itn_next", ctypes.c_int32),
     ]
 
 
@@ -407,7 +408,10 @@ class Context:
 
     def solve(self, x_out, x0=None, se_out=None, stream=0, **kw):
         p = gsr_default_params()
+        fields = {f for f, _ in SolveParams._fields_}
         for k, v in kw.items():
+            if k not in fields:
+                raise TypeError(f"unknown solve parameter {k!r}")
             if k == "weights_path" and isinstance(v, str):
                 v = v.encode()
             setattr(p, k, v)

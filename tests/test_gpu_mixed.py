@@ -64,6 +64,17 @@ def test_mixed_fixed_schedule_and_x0():
                      atol=0.0, btol=0.0, inner_tol=1e-30)
     assert info["outer_itn"] == 3 and info["itn"] == 36, info
     assert max(block_errors(x, xo, s).values()) <= 1e-9
+    # a shorter inner limit for the refinement steps after the first
+    xs = np.zeros(s.n_cols)
+    info = ctx.solve(xs, mode=g.GSR_MIXED, damp=w.damp, inner_itn=14, inner_itn_next=9, max_outer=3,
+                     refine_tol=-1.0, atol=0.0, btol=0.0, inner_tol=1e-30)
+    assert info["outer_itn"] == 3 and info["itn"] == 14 + 2 * 9, info
+    assert max(block_errors(xs, xo, s).values()) <= 1e-9
+    with pytest.raises(TypeError):
+        ctx.solve(xs, mode=g.GSR_MIXED, inner_iterations=3)  # misspelt parameter
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(xs, mode=g.GSR_MIXED, inner_itn_next=-1)
+    assert e.value.status == g.Status.EINVAL
     x1 = np.zeros(s.n_cols)
     info = ctx.solve(x1, x0=xo, mode=g.GSR_MIXED, damp=w.damp)
     assert info["outer_itn"] <= 2 and max(block_errors(x1, xo, s).values()) <= 1e-9, info
