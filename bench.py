@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-stars", type=int, default=0,
+                    help="profiling mode only: override the workload's number of stars (a smaller case for ncu)")
     ap.add_argument("--profile", default=None, choices=["f32", "f64"],
                     help="profiling mode for ncu: load the system with binary32 (f32) or binary64 (f64) storage "
                          "and launch each hot kernel --steps times inside an NVTX range 'prof'; prints timings")
@@ -419,7 +421,7 @@ def run_ours(args):
     solvers = {}
     with Clocks(local) as clk:
         for name, (ctx, kw, meta) in legs.items():
-            ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh, nvtx=f"timed:{name}")
+            ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh, nvtx=f"timed_{name}")
             solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
                                  final_block_err=max_block_err(x, xs, cfg))
     headline = min(solvers, key=lambda nm: solvers[nm]["s"])
@@ -548,6 +550,9 @@ def run_profile(args):
     sh = stream.cuda_stream
     w = gsrgen.workloads()[args.workload]
     cfg = w.cfg
+    if args.n_stars:
+        cfg = gsrgen.make_cfg(cfg.seed, args.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
+                              cfg.n_glob, cfg.att_kind, cfg.noise_sigma)
     f32 = args.profile == "f32"
     ctx, b, _ = _device_system(g, gsrgen, torch, cfg, f32, True, dev, sh)
     n, nc = ctx.n_rows, ctx.n_cols
