@@ -198,12 +198,22 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Deterministic sum of n partials by one warp (lane-strided, then a fixed tree).
+// Deterministic sum of n partials by one warp: each lane keeps eight independent
+// lane-strided sums (eight loads in flight instead of one dependent chain), then a
+// fixed tree. The order depends only on n.
 __device__ __forceinline__ double warp_sum_partials(const double *__restrict__ part, int n)
 {
-    double acc = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) acc += part[i];
-    return warp_sum(acc);
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int i = threadIdx.x & 31;
+    for (; i + 7 * 32 < n; i += 8 * 32) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += part[i + q * 32];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (i + q * 32 < n) acc[q] += part[i + q * 32];
+    const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    return warp_sum(s);
 }
 
 // Block-wide sum; every thread must call it; result valid in thread 0.
