@@ -51,6 +51,11 @@ BYTES = {
     "residual_df": 24 * 4 + 4 + 24 + 8 + 4,  # values, indices, b (two binary32), r write  = 136
 }
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
+# DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
+# binary32 kernels on the 2e7-row workload; a launch's traffic is this figure times its rows. The binary64
+# kernels are bound by the binary64 units and have no capture (None).
+TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": 136.1, "residual_df": 133.4, "aprod1_f64": None,
+                   "aprod2_f64": None}
 
 
 def parse_args():
@@ -470,9 +475,11 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": kern[dom]["TFLOP/s"] / fp64_peak, "traffic": None,
                 "peak_src": "nominal FP64 of the profiling recipe"}
     else:
+        tr = TRAFFIC_PER_ROW.get(dom)
         roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": kern[dom]["GB/s"] / peaks["hbm_gbs"], "traffic": None,
-                "peak_src": peaks["src"]}
+                "unit": "GB/s", "frac": kern[dom]["GB/s"] / peaks["hbm_gbs"],
+                "traffic": tr * n if tr else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "algorithmic": BYTES[dom] * n, "peak_src": peaks["src"]}
 
     # ---- kernel launches of one headline step, counted from the device's activity record (CUPTI)
     launches = count_launches(torch, lambda: hctx.solve(x, stream=sh, **hkw))
