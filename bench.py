@@ -54,7 +54,7 @@ FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
 # binary32 kernels on the 2e7-row workload; a launch's traffic is this figure times its rows. The binary64
 # kernels are bound by the binary64 units and have no capture (None).
-TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": 136.1, "residual_df": 133.4, "aprod1_f64": None,
+TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": None, "residual_df": 133.4, "aprod1_f64": None,
                    "aprod2_f64": None}
 
 
@@ -158,6 +158,15 @@ def max_block_err(x, ref, cfg):
             den = max(torch.linalg.vector_norm(ref[a:z]).item(), 1e-3)
             worst = max(worst, num / den)
     return worst
+
+
+def eq5_q(x, xr, se, cfg):
+    """The paper's consistency ratio (Sec. 6, Eq. 5) of a solution against the binary64 reference,
+    q = |x - x_ref| / sqrt(se^2 + se^2) with the reference's standard errors for both; max per section."""
+    import torch
+
+    q = (x - xr).abs() / (se * 2.0 ** 0.5).clamp_min(1e-300)
+    return {k: float(q[a:z].max()) for k, (a, z) in block_ranges(cfg).items() if z > a}
 
 
 def cpu_count():
@@ -347,7 +356,9 @@ def run_ours(args):
 
     # ---- reference solution x* (binary64, tight) and the schedules that first reach 1e-9 (untimed)
     xs = torch.zeros(nc, dtype=torch.float64, device=dev)
-    ref_info = ctx64.solve(xs, itnlim=20000, atol=1e-15, btol=1e-15, damp=damp, conlim=0.0, stream=sh)
+    se_ref = torch.zeros(nc, dtype=torch.float64, device=dev)
+    ref_info = ctx64.solve(xs, se_out=se_ref, itnlim=20000, atol=1e-15, btol=1e-15, damp=damp, conlim=0.0,
+                           stream=sh)
     x = torch.zeros(nc, dtype=torch.float64, device=dev)
     learned = dict(warm=g.GSR_WARM_LEARNED, weights_path=g.WARM_WEIGHTS) if os.path.exists(g.WARM_WEIGHTS) else None
 
@@ -428,7 +439,7 @@ def run_ours(args):
         for name, (ctx, kw, meta) in legs.items():
             ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh, nvtx=f"timed_{name}")
             solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
-                                 final_block_err=max_block_err(x, xs, cfg))
+                                 final_block_err=max_block_err(x, xs, cfg), eq5_q_max=eq5_q(x, xs, se_ref, cfg))
     headline = min(solvers, key=lambda nm: solvers[nm]["s"])
     ms = solvers[headline]["s"] * 1e3
     t_ms = torch.tensor([ms], device=dev)

@@ -46,7 +46,8 @@ __device__ __forceinline__ T warp_sum_t(T v)
 
 template <typename VT, typename XT, typename UT, typename AT, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
-                                                const LsqrState *__restrict__ st, double *__restrict__ part)
+                                                const LsqrState *__restrict__ st, double *__restrict__ part,
+                                                uint32_t *__restrict__ ymax)
 {
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     const XT *__restrict__ xi = x + S.instr0;
     const AT xg = S.n_glob ? (AT)__ldg(x + S.glob0) : (AT)0;
     AT ssq = (AT)0;
+    float amx = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
         const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
         const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
@@ -102,12 +104,19 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
                     yn = (AT)y[r] + v;
                 }
                 y[r] = (UT)yn;
+                if constexpr (LSQR && sizeof(AT) == 4) amx = fmaxf(amx, fabsf((float)yn));
             }
         }
     }
     if (LSQR) {
         const double t = block_sum((double)ssq, sm32);
         if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+    if constexpr (LSQR && sizeof(AT) == 4) {
+        if (ymax) {  // max |new y| of the block (binary32 bits of non-negative values order as integers)
+            const float m = block_max(amx, reinterpret_cast<float *>(sm32));
+            if (threadIdx.x == 0) atomicMax(ymax, __float_as_uint(m));
+        }
     }
 }
 
@@ -141,13 +150,28 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // crosses a star boundary moves its rows of the next star into a second
 // accumulator; rows of stars that begin and end inside one tile are added
 // directly).
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR>
+//
+// FX (binary32 products only): the instrumental sums are kept in block-private
+// 32-bit integers, fixed point with a power-of-two scale per column and
+// launch, added with the integer shared-memory atomics (the binary32 ones cost
+// several times more per add). Column j's contributions are bounded by
+// max|a_j| max|y| (fx_word), and its bits b_j are chosen per system so that no
+// block of this fixed partition can overflow it (the most contributions one
+// block adds to column j, times 2^b_j, stays below 2^31); each contribution is
+// rounded to 2^-b_j of its column's bound (b_j >= 20), at the level of
+// binary32 accumulation. The per-block integer sums convert exactly to binary64
+// and sum exactly there, so these columns of A^T y do not depend on the order
+// of the additions.
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
                                                      double *__restrict__ z, double *__restrict__ z2,
-                                                     const LsqrState *__restrict__ st, int64_t tiles_per_warp)
+                                                     const LsqrState *__restrict__ st, int64_t tiles_per_warp,
+                                                     const uint32_t *__restrict__ fx_word)
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
+    static_assert(!FX || (INSTR_SMEM && MODE == A2_PROD && sizeof(AT) == 4), "fixed point: binary32 products");
+    __shared__ int s_bad;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -157,7 +181,20 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     AT *sm_ins = reinterpret_cast<AT *>(smem_raw);
     AT *sm_sq = sm_ins + S.n_instr;  // BOTH: the squares' accumulators follow the products'
     const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * S.n_instr : S.n_instr) : 0;
-    for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;
+    for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;  // also integer zero
+    float *sm_scale = reinterpret_cast<float *>(smem_raw) + S.n_instr;  // FX: per-column scales
+    if (FX) {
+        const float ymax = __uint_as_float(fx_word[2 * S.n_instr]);
+        if (threadIdx.x == 0) s_bad = !(ymax < INFINITY);  // non-finite y: the sums are made NaN below
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+            // the largest power of two with max|a_j| * max|y| * scale <= 2^b_j - 1
+            const float bound = __uint_as_float(fx_word[i]) * ymax;
+            const float lim = (float)((1u << fx_word[S.n_instr + i]) - 1u);
+            float sc = 1.f;
+            if (bound > 0.f && bound < INFINITY) sc = ldexpf(1.f, min(ilogbf(lim / bound), 126));
+            sm_scale[i] = sc;
+        }
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -198,7 +235,10 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
             for (int j = 0; j < NINSTR; ++j) {
                 const AT av = SQUARE ? ai[j][i] * ai[j][i] : ai[j][i];
                 if (in[i]) {
-                    if (INSTR_SMEM)
+                    if (FX)
+                        atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
+                                  __float2int_rn(av * yr[i] * sm_scale[ic[j][i]]));
+                    else if (INSTR_SMEM)
                         atomicAdd(sm_ins + ic[j][i], av * yr[i]);
                     else
                         atomicAdd(zi + ic[j][i], (double)(av * yr[i]));
@@ -273,9 +313,17 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
         if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2);
     }
     __syncthreads();
-    for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
-        const AT v = sm_ins[i];
-        if (v != (AT)0) atomicAdd(BOTH && i >= S.n_instr ? z2i + (i - S.n_instr) : zi + i, (double)v);
+    if (FX) {
+        for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
+            const int q = reinterpret_cast<const int *>(sm_ins)[i];
+            if (q != 0) atomicAdd(zi + i, (double)q / (double)sm_scale[i]);  // a power of two: exact
+        }
+        if (s_bad && threadIdx.x == 0) atomicAdd(zi, (double)NAN);
+    } else {
+        for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
+            const AT v = sm_ins[i];
+            if (v != (AT)0) atomicAdd(BOTH && i >= S.n_instr ? z2i + (i - S.n_instr) : zi + i, (double)v);
+        }
     }
     if (S.n_glob) {
         const double tot = block_sum((double)gsum, sm32);
@@ -307,7 +355,8 @@ __device__ __forceinline__ void flush_att_run(AT (&acc)[NAXES * NPARAXIS], int32
 template <typename VT, typename UT, typename AT, int MODE, bool LSQR>
 __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__restrict__ y,
                                                     double *__restrict__ z, double *__restrict__ z2,
-                                                    const LsqrState *__restrict__ st, int64_t tiles_per_warp)
+                                                    const LsqrState *__restrict__ st, int64_t tiles_per_warp,
+                                                    uint32_t *__restrict__ ymax_reset)
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
@@ -315,6 +364,8 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
     constexpr int T = Tile<VT>::T;
     constexpr int NA = NAXES * NPARAXIS;
     if (LSQR && st->done) return;
+    // the star pass of this aprod 2 has finished: the max |y| word is free for the next one
+    if (ymax_reset && blockIdx.x == 0 && threadIdx.x == 0) *ymax_reset = 0u;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n = S.n_rows;
@@ -455,7 +506,9 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
             return cudaSuccess;
         }
         if (!x || !y) return cudaErrorInvalidValue;
-        kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part);
+        // the inner iteration's star pass reads max |u| (fixed-point instrumental sums)
+        uint32_t *ymax = (sizeof(AT) == 4 && st && c->fx_bits) ? c->fx_word + 2 * (size_t)c->n_instr : nullptr;
+        kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part, ymax);
         return cudaGetLastError();
     };
     if (st) return pick(k_aprod1<VT, XT, UT, AT, true>);
@@ -485,20 +538,36 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
     return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS>
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX = false>
 static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                       cudaStream_t s)
 {
-    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS>;
-    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) : 0;
+    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX>;
+    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH || FX ? 2 : 1) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
     int64_t per = 0, blocks = 0;
-    tile_ranges(c, kern, dyn, &per, &blocks);
-    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per);
+    if (FX) {  // the partition the overflow bound was computed for
+        per = c->fx_per;
+        blocks = c->fx_blocks;
+    } else {
+        tile_ranges(c, kern, dyn, &per, &blocks);
+    }
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per, c->fx_word);
     return cudaGetLastError();
+}
+
+// max |y| of a binary32 row vector into *ymax (binary32 bits; the word is zero on entry)
+__global__ void k_absmax(const float *__restrict__ y, int64_t n, uint32_t *__restrict__ ymax)
+{
+    __shared__ float sm32[32];
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__ldcs(y + i)));
+    m = block_max(m, sm32);
+    if (threadIdx.x == 0) atomicMax(ymax, __float_as_uint(m));
 }
 
 template <typename VT, typename UT, typename AT, int MODE, bool LS>
@@ -508,17 +577,30 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     if (LS != (st != nullptr)) return cudaErrorInvalidValue;  // the LSQR variants read the solver state
     if (MODE != A2_SQUARE && !y) return cudaErrorInvalidValue;
     if (MODE == A2_BOTH && !x2) return cudaErrorInvalidValue;
-    cudaError_t e;
-    if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget)
+    cudaError_t e = cudaSuccess;
+    constexpr bool F32 = sizeof(AT) == 4 && MODE == A2_PROD;
+    const bool fx = F32 && c->fx_bits > 0;
+    if (fx) {
+        // fixed-point instrumental sums: max |y| comes from the LSQR aprod 1 of the same iteration,
+        // else from a pass over y here
+        if (!LS) {
+            k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows,
+                                                                 c->fx_word + 2 * (size_t)c->n_instr);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if constexpr (F32) e = aprod2_star_launch<VT, UT, AT, true, MODE, LS, true>(c, y, x, x2, st, s);
+    } else if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget) {
         e = aprod2_star_launch<VT, UT, AT, true, MODE, LS>(c, y, x, x2, st, s);
-    else
+    } else {
         e = aprod2_star_launch<VT, UT, AT, false, MODE, LS>(c, y, x, x2, st, s);
+    }
     if (e != cudaSuccess) return e;
-    // attitude pass
+    // attitude pass (resets the max |y| word after a fixed-point star pass)
     auto kern = k_aprod2_att<VT, UT, AT, MODE, LS>;
     int64_t per = 0, blocks = 0;
     tile_ranges(c, kern, 0, &per, &blocks);
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per,
+                                               fx ? c->fx_word + 2 * (size_t)c->n_instr : nullptr);
     return cudaGetLastError();
 }
 

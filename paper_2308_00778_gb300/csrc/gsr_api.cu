@@ -324,6 +324,7 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->b);
     cudaFree(c->errw);
     cudaFree(c->knot_ptr);
+    cudaFree(c->fx_word);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->ev) cudaEventDestroy(c->ev);
     cudaGetLastError();

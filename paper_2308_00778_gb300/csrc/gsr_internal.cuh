@@ -91,6 +91,7 @@ struct Workspace {
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
     int32_t *flag_d = nullptr;  // device alias of flag_h
+    uint32_t *counter = nullptr;  // finished-block count of k_colA (zero between launches)
 };
 
 }  // namespace gsr
@@ -107,6 +108,13 @@ struct gsr_ctx {
     int32_t *first_star = nullptr;   // [n_tiles + 1] star of the first row of each tile
     int64_t *knot_ptr = nullptr;     // [n_dfa-2] first position of each knot
     bool att_valid = false;          // atiles / knot_ptr match the loaded rows
+    // fixed-point instrumental sums of the binary32 star pass (layout.cu): the fewest bits per
+    // contribution over the columns (0: binary32 shared atomics instead), the pass's fixed
+    // partition, and device words: [n_instr] max |coefficient| per column (binary32 bits),
+    // [n_instr] bits per column, max |y| of the current aprod 2 (binary32 bits), scratch
+    int32_t fx_bits = 0;
+    int64_t fx_per = 0, fx_blocks = 0;
+    uint32_t *fx_word = nullptr;
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -200,18 +208,19 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Deterministic sum of n partials by one warp: each lane keeps eight independent
 // lane-strided sums (eight loads in flight instead of one dependent chain), then a
-// fixed tree. The order depends only on n.
+// fixed tree. The order depends only on n. Loads bypass L1 (partials may come from
+// other blocks of the running kernel).
 __device__ __forceinline__ double warp_sum_partials(const double *__restrict__ part, int n)
 {
     double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int i = threadIdx.x & 31;
     for (; i + 7 * 32 < n; i += 8 * 32) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] += part[i + q * 32];
+        for (int q = 0; q < 8; ++q) acc[q] += __ldcg(part + i + q * 32);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        if (i + q * 32 < n) acc[q] += part[i + q * 32];
+        if (i + q * 32 < n) acc[q] += __ldcg(part + i + q * 32);
     const double s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     return warp_sum(s);
 }
@@ -229,6 +238,25 @@ __device__ __forceinline__ double block_sum(double v, double *sm32)
         const int nw = (blockDim.x + 31) >> 5;
         r = lane < nw ? sm32[lane] : 0.0;
         r = warp_sum(r);
+    }
+    return r;
+}
+
+// Block-wide maximum of non-negative values; every thread must call it; result valid in thread 0.
+__device__ __forceinline__ float block_max(float v, float *sm32)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm32[wid] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? sm32[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
     }
     return r;
 }

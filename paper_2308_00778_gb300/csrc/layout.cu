@@ -12,6 +12,8 @@
 // With it the attitude part of aprod 2 reduces runs of equal knot in registers
 // and adds each run once (aprod.cu). The sort is CUB's stable radix sort on
 // (knot, row) pairs; ties keep row order, so the layout is deterministic.
+// For binary32-stored systems the same step measures what the fixed-point
+// instrumental sums of the inner star pass need (k_instr_stats).
 #include <cub/device/device_radix_sort.cuh>
 
 #include "tiles.cuh"
@@ -69,6 +71,100 @@ __global__ void k_gather_att(const uint8_t *__restrict__ tiles, const int32_t *_
     }
 }
 
+// For the fixed-point instrumental sums of the binary32 star pass (aprod.cu),
+// per instrumental column j over the pass's partition (each warp a contiguous
+// range of `per` tiles, 8 warps a block): the largest number of contributions
+// one block adds to column j (kmax[j]) and the largest |coefficient| of column
+// j (amax[j], binary32 bits). Both arrays are zero on entry.
+__global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t per, uint32_t *__restrict__ kmax,
+                                                     uint32_t *__restrict__ amax)
+{
+    constexpr int R = Tile<float>::R;
+    constexpr int T = Tile<float>::T;
+    extern __shared__ uint32_t cnt[];  // [n_instr] counts, then [n_instr] max |a| bits
+    uint32_t *am = cnt + S.n_instr;
+    for (int32_t i = threadIdx.x; i < 2 * S.n_instr; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t t0 = gw * per, t1 = min(S.n_tiles, t0 + per);
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
+        const uint8_t *ti = tb + NPAR * Tile<float>::VBLK;
+        const int64_t r0 = t * T + lane * R;
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j) {
+            int32_t ic[R];
+            load_ints<R>(ti, 1 + j, ic);
+            float a[R];
+            load_vals<float, float>(tb, 17 + j, a);
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (r0 + i < S.n_rows) {
+                    atomicAdd(cnt + ic[i], 1u);
+                    atomicMax(am + ic[i], __float_as_uint(fabsf(a[i])));
+                }
+        }
+    }
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+        if (cnt[i]) atomicMax(kmax + i, cnt[i]);
+        if (am[i]) atomicMax(amax + i, am[i]);
+    }
+}
+
+// Per-column bits of the fixed-point sums (all 0: keep binary32 atomics):
+// bits_j = 31 - ceil(log2(kmax_j + 1)), so that no block can overflow column j;
+// the sums are used only when every column gets at least 20 bits.
+static gsr_status fixed_point_setup(gsr_ctx *c, cudaStream_t s)
+{
+    c->fx_bits = 0;
+    if (c->prec != GSR_FP32 || c->n_rows == 0) return GSR_OK;
+    const int32_t ni = c->n_instr;
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)ni;  // the stats kernel's and the star pass's
+    if (smem > 100 * 1024) return GSR_OK;
+    cudaError_t e = cudaSuccess;
+    // device words: [0, ni) max |a| per column, [ni, 2ni) bits per column, [2ni] max |y| of the
+    // current aprod 2, then [ni] scratch counts
+    if (!c->fx_word && (e = cudaMalloc(&c->fx_word, sizeof(uint32_t) * (3 * (size_t)ni + 1))) != cudaSuccess)
+        return cuda_fail(c, e, "fixed-point words");
+    uint32_t *kcnt = c->fx_word + 2 * ni + 1;
+    // the partition: two blocks of 8 warps per SM, contiguous ranges of at least 8 tiles per warp
+    const int64_t warps = (int64_t)c->sm_count * 2 * 8;
+    const int64_t per = std::max<int64_t>((c->n_tiles + warps - 1) / warps, 8);
+    const int64_t blocks = std::max<int64_t>(((c->n_tiles + per - 1) / per + 7) / 8, 1);
+    if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)ni + 1), s)) != cudaSuccess)
+        return cuda_fail(c, e, "memset");
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_instr_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return cuda_fail(c, e, "fixed-point statistics");
+    k_instr_stats<<<(unsigned)blocks, 256, smem, s>>>(view<float>(c), per, kcnt, c->fx_word);
+    std::vector<uint32_t> kmax((size_t)ni);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(kmax.data(), kcnt, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "fixed-point statistics");
+    std::vector<uint32_t> bits((size_t)ni);
+    int min_bits = 30;
+    for (int32_t j = 0; j < ni; ++j) {
+        int lg = 0;  // ceil(log2(kmax + 1))
+        while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax[(size_t)j] + 1) ++lg;
+        bits[(size_t)j] = (uint32_t)std::min(31 - lg, 30);
+        min_bits = std::min(min_bits, (int)bits[(size_t)j]);
+    }
+    if (min_bits < 20) return GSR_OK;
+    if ((e = cudaMemcpyAsync(c->fx_word + ni, bits.data(), sizeof(uint32_t) * (size_t)ni, cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "fixed-point setup");
+    c->fx_bits = min_bits;
+    c->fx_per = per;
+    c->fx_blocks = blocks;
+    return GSR_OK;
+}
+
 gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
 {
     if (c->att_valid) return GSR_OK;
@@ -119,6 +215,10 @@ done:
     cudaFree(perm);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "attitude layout");
+    {
+        const gsr_status rf = fixed_point_setup(c, s);
+        if (rf != GSR_OK) return rf;
+    }
     c->att_valid = true;
     return GSR_OK;
 }

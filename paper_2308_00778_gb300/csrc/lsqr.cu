@@ -70,116 +70,17 @@ __global__ void k_precond_finish(double *__restrict__ colsq, double *__restrict_
     }
 }
 
-// colA: beta from the aprod1 partials; vhat = p z / beta - beta v (first=1: no v term); z <- 0;
-// per-block sums of squares of vhat (alpha) and of w (for the condition estimate).
-__global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *__restrict__ z,
-                       const double *__restrict__ p, double *__restrict__ v, const double *__restrict__ w, int64_t n,
-                       LsqrState *__restrict__ st, double *__restrict__ part_v, double *__restrict__ part_w,
-                       int32_t first)
-{
-    __shared__ double sm32[32];
-    __shared__ double s_beta;
-    if (!first && st->done) return;
-    if (threadIdx.x < 32) {
-        const double ssq = warp_sum_partials(part_u, n_part_u);
-        if (threadIdx.x == 0) s_beta = sqrt(ssq);
-    }
-    __syncthreads();
-    const double beta = s_beta;
-    double sv = 0.0, sw = 0.0;
-    if (beta > 0.0 && isfinite(beta)) {
-        const double ib = 1.0 / beta;
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            const double zj = z[j];
-            z[j] = 0.0;
-            double vh = p[j] * zj * ib;
-            if (!first) vh = fma(-beta, v[j], vh);
-            v[j] = vh;
-            sv = fma(vh, vh, sv);
-            if (!first) {
-                const double wj = w[j];
-                sw = fma(wj, wj, sw);
-            }
-        }
-    } else {
-        // beta = 0 (b in the range of A already reached) or non-finite: leave v as alpha*v,
-        // so that colB restores it; the scalar kernel keeps alpha.
-        const double a = first ? 0.0 : st->alpha;
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            z[j] = 0.0;
-            const double vh = a * v[j];
-            v[j] = vh;
-            sv = fma(vh, vh, sv);
-            if (!first) {
-                const double wj = w[j];
-                sw = fma(wj, wj, sw);
-            }
-        }
-    }
-    const double tv = block_sum(sv, sm32);
-    const double tw = block_sum(sw, sm32);
-    if (threadIdx.x == 0) {
-        part_v[blockIdx.x] = tv;
-        part_w[blockIdx.x] = tw;
-        if (blockIdx.x == 0) st->beta = beta;
-    }
-}
-
-// The start of LSQR: beta_1 u_1 = b, alpha_1 v_1 = A~^T u_1, w_1 = v_1, x_0 = 0,
-// phibar_1 = beta_1, rhobar_1 = alpha_1 (one warp; thread 0 writes).
-__global__ void k_scalar_init(LsqrState *__restrict__ st, const double *__restrict__ part_v, int n_part,
-                              int32_t *__restrict__ flag)
-{
-    const double ssq = warp_sum_partials(part_v, n_part);
-    if (threadIdx.x != 0) return;
-    const double beta = st->beta;
-    const double alpha = sqrt(ssq);
-    st->alpha = alpha;
-    st->rhobar = alpha;
-    st->phibar = beta;
-    st->anorm = 0.0;
-    st->acond = 0.0;
-    st->ddnorm = 0.0;
-    st->res2 = 0.0;
-    st->xnorm = 0.0;
-    st->xxnorm = 0.0;
-    st->zeta = 0.0;
-    st->cs2 = -1.0;
-    st->sn2 = 0.0;
-    st->bnorm = beta;
-    st->rnorm = beta;
-    st->r1norm = beta;
-    st->r2norm = beta;
-    st->arnorm = alpha * beta;
-    st->itn = 0;
-    st->istop = 0;
-    st->numeric = !(isfinite(alpha) && isfinite(beta));
-    st->done = (st->arnorm == 0.0 || st->numeric || st->itnlim <= 0) ? 1 : 0;
-    st->colb_skip = 0;
-    st->inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
-    st->t1 = 0.0;
-    st->t2 = 0.0;
-    st->inv_rho = 0.0;
-    st->coef_u = beta > 0.0 ? -alpha / beta : 0.0;
-    *flag = st->done;
-}
-
-// One step of the recurrence. Thread 0 of one warp.
-__global__ void k_scalar(LsqrState *__restrict__ st, const double *__restrict__ part_v,
-                         const double *__restrict__ part_w, int n_part, int32_t *__restrict__ flag)
+// One step of the recurrence (beta of this iteration given), by the first warp
+// of the block that finishes k_colA last; thread 0 writes.
+__device__ void scalar_step(LsqrState *__restrict__ st, double beta, const double *__restrict__ part_v,
+                            const double *__restrict__ part_w, int n_part, int32_t *__restrict__ flag)
 {
     const double ssq_v = warp_sum_partials(part_v, n_part);
     const double ssq_w = warp_sum_partials(part_w, n_part);
     if (threadIdx.x != 0) return;
-    if (st->done) {
-        st->colb_skip = 1;
-        return;
-    }
     st->colb_skip = 0;
     const double damp = st->damp, dampsq = damp * damp;
-    const double beta = st->beta;
+    st->beta = beta;
     double alpha = st->alpha;
     double anorm = st->anorm;
     if (beta > 0.0) {
@@ -273,6 +174,121 @@ __global__ void k_scalar(LsqrState *__restrict__ st, const double *__restrict__ 
     }
 }
 
+// colA: beta from the aprod1 partials; vhat = p z / beta - beta v (first=1: no v term); z <- 0;
+// per-block sums of squares of vhat (alpha) and of w (for the condition estimate). In the
+// iterations (first=0) the block that finishes last also runs the scalar step (the grid's
+// partials are complete then): `counter` counts finished blocks and is reset by that block.
+__global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *__restrict__ z,
+                       const double *__restrict__ p, double *__restrict__ v, const double *__restrict__ w, int64_t n,
+                       LsqrState *__restrict__ st, double *__restrict__ part_v, double *__restrict__ part_w,
+                       int32_t first, uint32_t *__restrict__ counter, int32_t *__restrict__ flag)
+{
+    __shared__ double sm32[32];
+    __shared__ double s_beta, s_ib;
+    __shared__ int s_last;
+    if (!first && st->done) {  // stopped: the x / w update of this iteration is skipped as well
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->colb_skip = 1;
+        return;
+    }
+    if (threadIdx.x < 32) {
+        const double ssq = warp_sum_partials(part_u, n_part_u);
+        if (threadIdx.x == 0) {
+            s_beta = sqrt(ssq);
+            s_ib = 1.0 / s_beta;
+        }
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    double sv = 0.0, sw = 0.0;
+    if (beta > 0.0 && isfinite(beta)) {
+        const double ib = s_ib;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const double zj = z[j];
+            z[j] = 0.0;
+            double vh = p[j] * zj * ib;
+            if (!first) vh = fma(-beta, v[j], vh);
+            v[j] = vh;
+            sv = fma(vh, vh, sv);
+            if (!first) {
+                const double wj = w[j];
+                sw = fma(wj, wj, sw);
+            }
+        }
+    } else {
+        // beta = 0 (b in the range of A already reached) or non-finite: leave v as alpha*v,
+        // so that colB restores it; the scalar kernel keeps alpha.
+        const double a = first ? 0.0 : st->alpha;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            z[j] = 0.0;
+            const double vh = a * v[j];
+            v[j] = vh;
+            sv = fma(vh, vh, sv);
+            if (!first) {
+                const double wj = w[j];
+                sw = fma(wj, wj, sw);
+            }
+        }
+    }
+    const double tv = block_sum(sv, sm32);
+    const double tw = block_sum(sw, sm32);
+    if (threadIdx.x == 0) {
+        part_v[blockIdx.x] = tv;
+        part_w[blockIdx.x] = tw;
+        if (first && blockIdx.x == 0) st->beta = beta;
+        if (!first) {
+            __threadfence();  // the partials are visible before the count
+            s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        }
+    }
+    if (first) return;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < 32) scalar_step(st, beta, part_v, part_w, gridDim.x, flag);
+    if (threadIdx.x == 0) *counter = 0;
+}
+
+// The start of LSQR: beta_1 u_1 = b, alpha_1 v_1 = A~^T u_1, w_1 = v_1, x_0 = 0,
+// phibar_1 = beta_1, rhobar_1 = alpha_1 (one warp; thread 0 writes).
+__global__ void k_scalar_init(LsqrState *__restrict__ st, const double *__restrict__ part_v, int n_part,
+                              int32_t *__restrict__ flag)
+{
+    const double ssq = warp_sum_partials(part_v, n_part);
+    if (threadIdx.x != 0) return;
+    const double beta = st->beta;
+    const double alpha = sqrt(ssq);
+    st->alpha = alpha;
+    st->rhobar = alpha;
+    st->phibar = beta;
+    st->anorm = 0.0;
+    st->acond = 0.0;
+    st->ddnorm = 0.0;
+    st->res2 = 0.0;
+    st->xnorm = 0.0;
+    st->xxnorm = 0.0;
+    st->zeta = 0.0;
+    st->cs2 = -1.0;
+    st->sn2 = 0.0;
+    st->bnorm = beta;
+    st->rnorm = beta;
+    st->r1norm = beta;
+    st->r2norm = beta;
+    st->arnorm = alpha * beta;
+    st->itn = 0;
+    st->istop = 0;
+    st->numeric = !(isfinite(alpha) && isfinite(beta));
+    st->done = (st->arnorm == 0.0 || st->numeric || st->itnlim <= 0) ? 1 : 0;
+    st->colb_skip = 0;
+    st->inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    st->t1 = 0.0;
+    st->t2 = 0.0;
+    st->inv_rho = 0.0;
+    st->coef_u = beta > 0.0 ? -alpha / beta : 0.0;
+    *flag = st->done;
+}
+
 // colB (first=1: the start, w = v and x = 0)
 __global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, float *__restrict__ pv32,
                        const double *__restrict__ p, double *__restrict__ w, double *__restrict__ x,
@@ -351,6 +367,8 @@ gsr_status ensure_workspace(gsr_ctx *c)
     if ((e = cudaMalloc(&ws.st, sizeof(LsqrState))) != cudaSuccess) goto oom;
     if ((e = cudaHostAlloc(&ws.flag_h, sizeof(int32_t), cudaHostAllocMapped)) != cudaSuccess) goto oom;
     if ((e = cudaHostGetDevicePointer(&ws.flag_d, ws.flag_h, 0)) != cudaSuccess) goto oom;
+    if ((e = cudaMalloc(&ws.counter, sizeof(uint32_t))) != cudaSuccess) goto oom;
+    if ((e = cudaMemset(ws.counter, 0, sizeof(uint32_t))) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.z, 0, nc * sizeof(double))) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.part_u, 0, 3 * MAX_PARTIALS * sizeof(double))) != cudaSuccess) goto oom;
     if (c->prec == GSR_FP32) {
@@ -386,13 +404,15 @@ void free_workspace(gsr_ctx *c)
     if (ws.xhl) cudaFree(ws.xhl);
     if (ws.bhl) cudaFree(ws.bhl);
     if (ws.st) cudaFree(ws.st);
+    if (ws.counter) cudaFree(ws.counter);
     if (ws.flag_h) cudaFreeHost(ws.flag_h);
     for (auto &gc : ws.graphs)
         if (gc.exec) cudaGraphExecDestroy(gc.exec);
     ws = Workspace();
 }
 
-// The executable graph of `k` LSQR iterations (5 kernels each), captured on
+// The executable graph of `k` LSQR iterations (aprod 1, the two aprod 2 passes, colA
+// with the scalar step, colB: 5 kernels each), captured on
 // first use and cached on the context (kernel arguments are the context's
 // fixed buffers; the iteration state lives in device memory).
 static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner32, cudaStream_t s,
@@ -418,8 +438,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
         if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
         if ((e = launch_aprod2(c, u, ws.z, false, ws.st, s, inner32)) != cudaSuccess) break;
         k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gu, ws.z, ws.p, ws.v, ws.w, c->n_cols, ws.st, ws.part_v,
-                                          ws.part_w, 0);
-        k_scalar<<<1, 32, 0, s>>>(ws.st, ws.part_v, ws.part_w, gc, ws.flag_d);
+                                          ws.part_w, 0, ws.counter, ws.flag_d);
         k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr,
                                           c->n_cols, ws.st, 0);
         e = cudaGetLastError();
@@ -497,7 +516,8 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
         return cuda_fail(c, e, "state upload");
     void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
     if ((e = launch_aprod2(c, u, ws.z, false, nullptr, s, inner32)) != cudaSuccess) return cuda_fail(c, e, "start");
-    k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, n_part_u, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1);
+    k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, n_part_u, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1,
+                                      ws.counter, ws.flag_d);
     k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);
     k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, nc, ws.st, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "LSQR start");

@@ -102,6 +102,30 @@ def test_standard_errors_and_warm_start():
     ctx.close()
 
 
+def test_eq5_consistency_with_oracle():
+    """The paper's check of two solvers (Sec. 6, Eq. 5): for every unknown,
+    q = |x_gpu - x_oracle| / sqrt(se_gpu^2 + se_oracle^2) < 1, plus the
+    mean / standard deviation of the differences per section (Table 1)."""
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup(w.cfg)
+    x = np.zeros(s.n_cols)
+    se = np.zeros(s.n_cols)
+    ctx.solve(x, se_out=se, itnlim=w.itnlim, atol=w.atol, btol=w.btol, conlim=1e12, damp=w.damp)
+    xo, io, var = oracle.lsqr(s, b, w.itnlim, w.atol, w.btol, 1e12, w.damp, want_var=True)
+    se_o = np.sqrt(var) * abs(io["r1norm"]) / np.sqrt(s.n_rows - s.n_cols)
+    assert np.all(se > 0) and np.all(np.isfinite(se))
+    q = np.abs(x - xo) / np.sqrt(se ** 2 + se_o ** 2)
+    assert q.max() < 1.0
+    # both codes compute in binary64: the agreement is far inside one sigma
+    assert q.max() < 1e-3, q.max()
+    for name, (a, z) in s.blocks().items():
+        if z > a:
+            dx, ds = x[a:z] - xo[a:z], se[a:z] - se_o[a:z]
+            print(f"{name}: d_x {dx.mean():.2e} +- {dx.std():.2e}, d_sigma {ds.mean():.2e} +- {ds.std():.2e}, "
+                  f"q_max {q[a:z].max():.2e}")
+    ctx.close()
+
+
 def test_edge_cases():
     cfg = gsrgen.make_cfg(7, 20, 30, 12, 8)
     h, s, b, ctx = _setup(cfg)

@@ -138,3 +138,36 @@ def test_binary32_entry_points_need_fp32_context():
                      torch.zeros(ctx.n_rows, dtype=torch.float32, device="cuda"))
     assert e.value.status == g.Status.EINVAL
     ctx.close()
+
+
+def test_binary32_instrumental_sums_are_order_independent():
+    """The binary32 aprod 2 keeps the instrumental sums in 32-bit fixed point
+    per block (scaled per column by a power of two) and adds the blocks in
+    binary64, where those sums are exact: the instrumental entries of A^T y are
+    bitwise the same from run to run, and match the oracle within the rounding
+    of the fixed point (at most 2^-20 of the column's largest |a| max|y| per
+    contribution) plus the binary32 products."""
+    cfg = gsrgen.workloads()["c1"].cfg
+    h, s, b, ctx = _setup32(cfg)
+    rng = np.random.default_rng(21)
+    y = rng.standard_normal(s.n_rows).astype(np.float32)
+    yd = torch.tensor(y, device="cuda")
+    a0, a1 = s.blocks()["instr"]
+    outs = []
+    for _ in range(3):
+        z = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+        ctx.aprod2_f32(yd, z)
+        outs.append(z.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o[a0:a1], outs[0][a0:a1])
+    want = oracle.aprod2(s, y.astype(np.float64), np.zeros(s.n_cols))
+    ic = s.instr.reshape(-1, 6)
+    av = np.abs(s.A.reshape(-1, 24)[:, 17:23])
+    amax = np.zeros(s.n_instr)
+    np.maximum.at(amax, ic.ravel(), av.ravel())
+    count = np.bincount(ic.ravel(), minlength=s.n_instr)
+    bound = count * (2.0 ** -20 * amax * np.abs(y).max())
+    scale = oracle.aprod2(_abs_sys(s), np.abs(y).astype(np.float64), np.zeros(s.n_cols))
+    err = np.abs(outs[0][a0:a1] - want[a0:a1])
+    assert np.all(err <= bound + 2.0 ** -23 * scale[a0:a1]), (err / (bound + 1e-300)).max()
+    ctx.close()
