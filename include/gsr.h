@@ -96,9 +96,14 @@ gsr_status gsr_dims(const gsr_ctx *ctx, int64_t *n_rows, int64_t *n_cols);
  *               GSR_SOA 6 planes at instr_col + j*plane_stride.
  *   where       GSR_HOST or GSR_DEVICE (all three arrays).
  * FP64 values into an FP32 context are rounded to nearest; FP32 values into an
- * FP64 context are widened exactly. Indices are validated on the device before
- * anything is committed: GSR_EINVAL on an out-of-range index (the rows are
- * left unchanged), GSR_ENUMERIC on a NaN or Inf coefficient.
+ * FP64 context are widened exactly. GSR_EINVAL on an out-of-range index,
+ * GSR_ENUMERIC on a NaN or Inf coefficient. Device arrays, and host arrays in
+ * pageable memory, are validated before anything is committed (the rows are
+ * left unchanged on an error). GSR_AOS host arrays in pinned (page-locked,
+ * mapped) memory, values 16-byte and instr_col 8-byte aligned, are converted
+ * straight from host memory in one pass that also validates them: on an error
+ * the rows of the call are then not loaded (their previous content is lost and
+ * the calls that need every row return GSR_ESTATE until they are set again).
  * Synchronous: returns after the rows are in place.
  */
 gsr_status gsr_set_rows(gsr_ctx *ctx, int64_t row0, int64_t nrows, const void *values, int32_t values_fp32,
@@ -106,8 +111,9 @@ gsr_status gsr_set_rows(gsr_ctx *ctx, int64_t row0, int64_t nrows, const void *v
                         int32_t where, void *stream);
 
 /*
- * gsr_set_rhs -- load the known terms b (n_rows binary64; Eq. 1). Copied.
- * GSR_ENUMERIC if b holds a NaN or Inf. Synchronous.
+ * gsr_set_rhs -- load the known terms b (n_rows binary64; Eq. 1). Copied, then
+ * checked on the device: GSR_ENUMERIC if b holds a NaN or Inf, and b is then
+ * not loaded (a solve returns GSR_ESTATE until b is set again). Synchronous.
  */
 gsr_status gsr_set_rhs(gsr_ctx *ctx, const double *b, int32_t where, void *stream);
 

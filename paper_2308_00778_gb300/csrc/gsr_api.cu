@@ -48,6 +48,21 @@ static void mark_rows(gsr_ctx *c, int64_t lo, int64_t hi)
     v.swap(m);
 }
 
+// remove [lo, hi) from the loaded ranges (rows whose content is no longer valid)
+static void unmark_rows(gsr_ctx *c, int64_t lo, int64_t hi)
+{
+    std::vector<std::pair<int64_t, int64_t>> m;
+    for (auto &r : c->rows_set) {
+        if (r.second <= lo || r.first >= hi) {
+            m.push_back(r);
+            continue;
+        }
+        if (r.first < lo) m.emplace_back(r.first, lo);
+        if (r.second > hi) m.emplace_back(hi, r.second);
+    }
+    c->rows_set.swap(m);
+}
+
 // ---------------------------------------------------------------- conversion kernels
 // error words: [0] knot out of range, [1] instr out of range, [2] non-finite value
 template <typename ST>
@@ -94,6 +109,67 @@ __global__ void k_convert(const ST *__restrict__ vals, int32_t layout, int64_t v
         for (int j = 0; j < NINSTR; ++j)
             ti[(1 + j) * TL::T + i] = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
     }
+}
+
+// AoS rows [0, n) of the caller (any device-visible address: device memory or mapped
+// pinned host memory) -> rows [row0, row0 + n) of the tiles, validated in the same
+// pass (error words as k_validate). One block per output tile: the tile's rows are
+// read with 16-byte loads (8-byte for the instrumental columns) into shared memory,
+// then written plane by plane. vals must be 16-byte aligned, instr 8-byte aligned.
+template <typename ST, typename DT>
+__global__ void __launch_bounds__(256) k_convert_aos(const ST *__restrict__ vals, const int32_t *__restrict__ knot,
+                                                     const int32_t *__restrict__ instr, int64_t n, int64_t row0,
+                                                     int32_t n_glob, int32_t n_dfa, int32_t n_instr,
+                                                     uint8_t *__restrict__ tiles, int32_t *__restrict__ errw)
+{
+    using TL = Tile<DT>;
+    constexpr int T = TL::T;
+    __shared__ __align__(16) ST sv[T * NPAR];
+    __shared__ __align__(16) int32_t si[T * NINSTR];
+    __shared__ int32_t sk[T];
+    int32_t bk = 0, bi = 0, bv = 0;
+    const int64_t t_first = row0 / T, t_last = (row0 + n - 1) / T;
+    for (int64_t t = t_first + blockIdx.x; t <= t_last; t += gridDim.x) {
+        const int64_t o_lo = max(row0, t * T), o_hi = min(row0 + n, (t + 1) * T);
+        const int64_t r_lo = o_lo - row0;  // first input row
+        const int m = (int)(o_hi - o_lo), off = (int)(o_lo - t * T);
+        {
+            const int nv = m * NPAR * (int)sizeof(ST) / 16;
+            const int4 *src = reinterpret_cast<const int4 *>(vals + r_lo * NPAR);
+            int4 *dst = reinterpret_cast<int4 *>(sv + off * NPAR);
+            for (int q = threadIdx.x; q < nv; q += blockDim.x) dst[q] = src[q];
+            const int ni = m * NINSTR / 2;
+            const int2 *srci = reinterpret_cast<const int2 *>(instr + r_lo * NINSTR);
+            int2 *dsti = reinterpret_cast<int2 *>(si + off * NINSTR);
+            for (int q = threadIdx.x; q < ni; q += blockDim.x) dsti[q] = srci[q];
+            for (int q = threadIdx.x; q < m; q += blockDim.x) sk[off + q] = knot[r_lo + q];
+        }
+        __syncthreads();
+        uint8_t *tb = tiles + t * TL::BYTES;
+        for (int i = off + (int)threadIdx.x; i < off + m; i += blockDim.x) {
+#pragma unroll 4
+            for (int j = 0; j < NPAR; ++j) {
+                ST v = sv[i * NPAR + j];
+                bv |= !isfinite((double)v);
+                if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
+                reinterpret_cast<DT *>(tb + j * TL::VBLK)[i] = (DT)v;
+            }
+            int32_t *ti = reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK);
+            const int32_t k = sk[i];
+            bk |= (k < 0 || k > n_dfa - 4);
+            ti[i] = k;
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) {
+                const int32_t ic = si[i * NINSTR + j];
+                bi |= (ic < 0 || ic >= n_instr);
+                ti[(1 + j) * T + i] = ic;
+            }
+        }
+        __syncthreads();
+    }
+    if (__syncthreads_or(bk) && threadIdx.x == 0) atomicOr(errw + 0, 1);
+    if (__syncthreads_or(bi) && threadIdx.x == 0) atomicOr(errw + 1, 1);
+    if (__syncthreads_or(bv) && threadIdx.x == 0) atomicOr(errw + 2, 1);
 }
 
 __global__ void k_check_finite(const double *__restrict__ a, int64_t n, int32_t *__restrict__ errw)
@@ -143,10 +219,56 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
 // are staged whole, validated on the device and converted (nothing is written
 // on error). Otherwise they are validated on the host first, then staged and
 // converted chunk by chunk.
+// the device address of mapped pinned host memory (nullptr for pageable memory)
+static const void *mapped(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// AoS rows in mapped pinned host memory: converted straight from host memory in one pass (the
+// transfer is the bound), validated in the same pass; on an error the rows are marked not loaded.
+template <typename ST>
+static gsr_status set_rows_mapped(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, const int32_t *knot,
+                                  const int32_t *instr, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->errw, 0, 4 * sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(c->n_tiles, (int64_t)c->sm_count * 4));
+    if (c->prec == GSR_FP32)
+        k_convert_aos<ST, float><<<g, 256, 0, s>>>(vals, knot, instr, nrows, row0, c->n_glob, c->n_dfa, c->n_instr,
+                                                    (uint8_t *)c->tiles, c->errw);
+    else
+        k_convert_aos<ST, double><<<g, 256, 0, s>>>(vals, knot, instr, nrows, row0, c->n_glob, c->n_dfa, c->n_instr,
+                                                     (uint8_t *)c->tiles, c->errw);
+    int32_t hw[4];
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(c, e, "conversion");
+    if (hw[0] || hw[1] || hw[2]) {
+        unmark_rows(c, row0, row0 + nrows);
+        c->att_valid = false;
+        if (hw[0]) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4] (the rows are not loaded)");
+        if (hw[1]) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr) (the rows are not loaded)");
+        return fail(c, GSR_ENUMERIC, "non-finite coefficient (the rows are not loaded)");
+    }
+    return GSR_OK;
+}
+
 template <typename ST>
 static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, int32_t layout,
                                 int64_t vstride, const int32_t *knot, const int32_t *instr, cudaStream_t s)
 {
+    if (layout == GSR_AOS) {
+        const void *dv = mapped(vals), *dk = mapped(knot), *di = mapped(instr);
+        if (dv && dk && di && (uintptr_t)dv % 16 == 0 && (uintptr_t)di % 8 == 0)
+            return set_rows_mapped<ST>(c, row0, nrows, (const ST *)dv, (const int32_t *)dk, (const int32_t *)di, s);
+    }
     const size_t row_bytes = sizeof(ST) * NPAR + sizeof(int32_t) * (1 + NINSTR);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -385,25 +507,20 @@ GSR_API gsr_status gsr_set_rhs(gsr_ctx *c, const double *b, int32_t where, void 
         c->rhs_set = true;
         return GSR_OK;
     }
-    if (where == GSR_HOST) {
-        for (int64_t i = 0; i < c->n_rows; ++i)
-            if (!std::isfinite(b[i])) return fail(c, GSR_ENUMERIC, "non-finite b");
-        e = cudaMemcpyAsync(c->b, b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyHostToDevice, s);
-    } else {
-        int32_t hw[4];
-        e = cudaMemsetAsync(c->errw, 0, sizeof(hw), s);
-        if (e == cudaSuccess) {
-            k_check_finite<<<grid_for(c, c->n_rows), 256, 0, s>>>(b, c->n_rows, c->errw);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess && hw[2]) return fail(c, GSR_ENUMERIC, "non-finite b");
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c->b, b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyDeviceToDevice, s);
+    // copy, then check on the device (a NaN or Inf leaves b unloaded)
+    c->rhs_set = false;
+    int32_t hw[4];
+    e = cudaMemcpyAsync(c->b, b, sizeof(double) * (size_t)c->n_rows,
+                        where == GSR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->errw, 0, sizeof(hw), s);
+    if (e == cudaSuccess) {
+        k_check_finite<<<grid_for(c, c->n_rows), 256, 0, s>>>(c->b, c->n_rows, c->errw);
+        e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "b upload");
+    if (hw[2]) return fail(c, GSR_ENUMERIC, "non-finite b (b is not loaded)");
     c->rhs_set = true;
     return GSR_OK;
 }

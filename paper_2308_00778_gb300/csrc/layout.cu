@@ -51,23 +51,54 @@ __global__ void k_knot_ptr(const int32_t *__restrict__ sorted_knot, int64_t n, i
     }
 }
 
-// position p of the knot-ordered tiles <- the attitude coefficients of row perm[p]
+// the 12 attitude coefficients of every row as one contiguous record per row
+// (rows in star order, read plane by plane from the tiles: coalesced)
 template <typename VT>
-__global__ void k_gather_att(const uint8_t *__restrict__ tiles, const int32_t *__restrict__ perm, int64_t n,
+__global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t n, VT *__restrict__ rec)
+{
+    using TL = Tile<VT>;
+    constexpr int NA = NAXES * NPARAXIS;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t *src = tiles + (r / TL::T) * TL::BYTES;
+        const int64_t ri = r % TL::T;
+        VT v[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) v[j] = reinterpret_cast<const VT *>(src + (NASTRO + j) * TL::VBLK)[ri];
+        using V = typename Vec16<VT>::type;
+        constexpr int PER = 16 / (int)sizeof(VT);
+#pragma unroll
+        for (int q = 0; q < NA / PER; ++q) {
+            V w;
+            VT *wp = reinterpret_cast<VT *>(&w);
+#pragma unroll
+            for (int e = 0; e < PER; ++e) wp[e] = v[q * PER + e];
+            reinterpret_cast<V *>(rec + r * NA)[q] = w;
+        }
+    }
+}
+
+// position p of the knot-ordered tiles <- the attitude record of row perm[p]
+// (one contiguous 48- or 96-byte record per gathered row instead of 12 scattered words)
+template <typename VT>
+__global__ void k_gather_att(const VT *__restrict__ rec, const int32_t *__restrict__ perm, int64_t n,
                              uint8_t *__restrict__ atiles)
 {
     using TL = Tile<VT>;
+    constexpr int NA = NAXES * NPARAXIS;
+    using V = typename Vec16<VT>::type;
+    constexpr int PER = 16 / (int)sizeof(VT);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = perm[p];
-        const uint8_t *src = tiles + (r / TL::T) * TL::BYTES;
-        const int64_t ri = r % TL::T;
         uint8_t *dst = atiles + (p / TL::T) * TL::ABYTES;
         const int64_t pi = p % TL::T;
 #pragma unroll
-        for (int j = 0; j < NAXES * NPARAXIS; ++j)
-            reinterpret_cast<VT *>(dst + j * TL::VBLK)[pi] =
-                reinterpret_cast<const VT *>(src + (NASTRO + j) * TL::VBLK)[ri];
-        reinterpret_cast<int32_t *>(dst + NAXES * NPARAXIS * TL::VBLK)[pi] = (int32_t)r;
+        for (int q = 0; q < NA / PER; ++q) {
+            const V w = __ldg(reinterpret_cast<const V *>(rec + r * NA) + q);
+            const VT *wp = reinterpret_cast<const VT *>(&w);
+#pragma unroll
+            for (int e = 0; e < PER; ++e) reinterpret_cast<VT *>(dst + (q * PER + e) * TL::VBLK)[pi] = wp[e];
+        }
+        reinterpret_cast<int32_t *>(dst + NA * TL::VBLK)[pi] = (int32_t)r;
     }
 }
 
@@ -115,10 +146,13 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
 
 // Per-column bits of the fixed-point sums (all 0: keep binary32 atomics):
 // bits_j = 31 - ceil(log2(kmax_j + 1)), so that no block can overflow column j;
-// the sums are used only when every column gets at least 20 bits.
-static gsr_status fixed_point_setup(gsr_ctx *c, cudaStream_t s)
+// the sums are used only when every column gets at least 20 bits. Launches the
+// statistics and the copy of kmax into *kmax_h (asynchronous); the caller
+// synchronises s and calls fixed_point_finish.
+static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uint32_t> *kmax_h)
 {
     c->fx_bits = 0;
+    kmax_h->clear();
     if (c->prec != GSR_FP32 || c->n_rows == 0) return GSR_OK;
     const int32_t ni = c->n_instr;
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)ni;  // the stats kernel's and the star pass's
@@ -131,37 +165,40 @@ static gsr_status fixed_point_setup(gsr_ctx *c, cudaStream_t s)
     uint32_t *kcnt = c->fx_word + 2 * ni + 1;
     // the partition: two blocks of 8 warps per SM, contiguous ranges of at least 8 tiles per warp
     const int64_t warps = (int64_t)c->sm_count * 2 * 8;
-    const int64_t per = std::max<int64_t>((c->n_tiles + warps - 1) / warps, 8);
-    const int64_t blocks = std::max<int64_t>(((c->n_tiles + per - 1) / per + 7) / 8, 1);
+    c->fx_per = std::max<int64_t>((c->n_tiles + warps - 1) / warps, 8);
+    c->fx_blocks = std::max<int64_t>(((c->n_tiles + c->fx_per - 1) / c->fx_per + 7) / 8, 1);
     if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)ni + 1), s)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_instr_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
-    k_instr_stats<<<(unsigned)blocks, 256, smem, s>>>(view<float>(c), per, kcnt, c->fx_word);
-    std::vector<uint32_t> kmax((size_t)ni);
+    k_instr_stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word);
+    kmax_h->resize((size_t)ni);
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(kmax.data(), kcnt, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
-    std::vector<uint32_t> bits((size_t)ni);
+    return GSR_OK;
+}
+
+static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vector<uint32_t> &kmax)
+{
+    if (kmax.empty()) return GSR_OK;
+    std::vector<uint32_t> bits(kmax.size());
     int min_bits = 30;
-    for (int32_t j = 0; j < ni; ++j) {
+    for (size_t j = 0; j < kmax.size(); ++j) {
         int lg = 0;  // ceil(log2(kmax + 1))
-        while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax[(size_t)j] + 1) ++lg;
-        bits[(size_t)j] = (uint32_t)std::min(31 - lg, 30);
-        min_bits = std::min(min_bits, (int)bits[(size_t)j]);
+        while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax[j] + 1) ++lg;
+        bits[j] = (uint32_t)std::min(31 - lg, 30);
+        min_bits = std::min(min_bits, (int)bits[j]);
     }
     if (min_bits < 20) return GSR_OK;
-    if ((e = cudaMemcpyAsync(c->fx_word + ni, bits.data(), sizeof(uint32_t) * (size_t)ni, cudaMemcpyHostToDevice,
-                             s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return cuda_fail(c, e, "fixed-point setup");
+    // pageable source: the call returns once the bytes are staged, the kernels that read them follow on s
+    const cudaError_t e = cudaMemcpyAsync(c->fx_word + kmax.size(), bits.data(), sizeof(uint32_t) * bits.size(),
+                                          cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fixed-point setup");
     c->fx_bits = min_bits;
-    c->fx_per = per;
-    c->fx_blocks = blocks;
     return GSR_OK;
 }
 
@@ -179,16 +216,19 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
         return GSR_OK;
     }
     int32_t *keys_in = nullptr, *keys_out = nullptr, *vals_in = nullptr, *perm = nullptr;
-    void *tmp = nullptr;
+    void *tmp = nullptr, *rec = nullptr;
     size_t tmp_bytes = 0;
     const int bits = 32 - __builtin_clz((unsigned)(nk > 1 ? nk : 1));
     const bool f32 = c->prec == GSR_FP32;
     const uint8_t *tiles = (const uint8_t *)c->tiles;
     int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 8);
-    if ((e = cudaMalloc(&keys_in, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&keys_out, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&vals_in, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
-    if ((e = cudaMalloc(&perm, sizeof(int32_t) * (size_t)n)) != cudaSuccess) goto done;
+    std::vector<uint32_t> kmax_h;
+    gsr_status rf = GSR_OK;
+    // scratch from the stream-ordered allocator: no device-wide synchronisation on free
+    if ((e = cudaMallocAsync(&keys_in, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocAsync(&keys_out, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocAsync(&vals_in, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocAsync(&perm, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
     if (f32)
         k_extract_knots<float><<<g, 256, 0, s>>>(tiles, n, keys_in);
     else
@@ -197,28 +237,38 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
         goto done;
-    if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) goto done;
+    if ((e = cudaMallocAsync(&tmp, tmp_bytes, s)) != cudaSuccess) goto done;
     if ((e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
         goto done;
     k_knot_ptr<<<(nk + 256) / 256, 256, 0, s>>>(keys_out, n, nk, c->knot_ptr);
-    if (f32)
-        k_gather_att<float><<<g, 256, 0, s>>>(tiles, perm, n, (uint8_t *)c->atiles);
-    else
-        k_gather_att<double><<<g, 256, 0, s>>>(tiles, perm, n, (uint8_t *)c->atiles);
-    if ((e = cudaGetLastError()) != cudaSuccess) goto done;
-    e = cudaStreamSynchronize(s);
-done:
-    cudaFree(keys_in);
-    cudaFree(keys_out);
-    cudaFree(vals_in);
-    cudaFree(perm);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return cuda_fail(c, e, "attitude layout");
-    {
-        const gsr_status rf = fixed_point_setup(c, s);
-        if (rf != GSR_OK) return rf;
+    // the attitude records in star order, then gathered by the permutation
+    if ((e = cudaMallocAsync(&rec, (f32 ? sizeof(float) : sizeof(double)) * NAXES * NPARAXIS * (size_t)n, s)) !=
+        cudaSuccess)
+        goto done;
+    if (f32) {
+        k_att_rows<float><<<g, 256, 0, s>>>(tiles, n, (float *)rec);
+        k_gather_att<float><<<g, 256, 0, s>>>((const float *)rec, perm, n, (uint8_t *)c->atiles);
+    } else {
+        k_att_rows<double><<<g, 256, 0, s>>>(tiles, n, (double *)rec);
+        k_gather_att<double><<<g, 256, 0, s>>>((const double *)rec, perm, n, (uint8_t *)c->atiles);
     }
+    if ((e = cudaGetLastError()) != cudaSuccess) goto done;
+    rf = fixed_point_launch(c, s, &kmax_h);
+done:
+    if (keys_in) cudaFreeAsync(keys_in, s);
+    if (keys_out) cudaFreeAsync(keys_out, s);
+    if (vals_in) cudaFreeAsync(vals_in, s);
+    if (perm) cudaFreeAsync(perm, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (rec) cudaFreeAsync(rec, s);
+    {
+        const cudaError_t es = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = es;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "attitude layout");
+    if (rf != GSR_OK) return rf;
+    if ((rf = fixed_point_finish(c, s, kmax_h)) != GSR_OK) return rf;
     c->att_valid = true;
     return GSR_OK;
 }

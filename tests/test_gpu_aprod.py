@@ -161,4 +161,63 @@ def test_validation_rejects_bad_rows(where):
     with pytest.raises(g.GsrError) as e:
         ctx.solve(np.zeros(ctx.n_cols))
     assert e.value.status == g.Status.ESTATE
+    # a good b, then a bad one: the bad one is not kept either
+    ctx.set_rhs(np.ones(ctx.n_rows))
+    with pytest.raises(g.GsrError) as e:
+        ctx.set_rhs(b)
+    assert e.value.status == g.Status.ENUMERIC
+    with pytest.raises(g.GsrError) as e:
+        ctx.solve(np.zeros(ctx.n_cols))
+    assert e.value.status == g.Status.ESTATE
+    ctx.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_pinned_host_rows_convert_in_one_pass(fp32):
+    """AoS rows in pinned host memory are converted straight from host memory
+    (one pass that also validates): the result equals the device-input load,
+    and on a bad index or value the rows of the call are not loaded."""
+    cfg = CASES["ragged_many"]
+    h = gsrgen.generate(cfg, fp32=fp32)
+    s = oracle.from_host_system(h)
+    A = torch.tensor(h.A32 if fp32 else h.A).pin_memory()
+    knot = torch.tensor(h.knot).pin_memory()
+    instr = torch.tensor(h.instr).pin_memory()
+    ref = context_for(h, fp32=fp32)
+    ref.set_system(A.cuda(), knot.cuda(), instr.cuda())
+    ctx = context_for(h, fp32=fp32)
+    ctx.set_system(A, knot, instr)
+    u = torch.randn(s.n_rows, dtype=torch.float64, device="cuda")
+    z1 = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    z2 = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    ref.aprod2(u, z1)
+    ctx.aprod2(u, z2)
+    scale = oracle.aprod2(abs_system(s), np.abs(u.cpu().numpy()), np.zeros(s.n_cols))
+    assert np.all(np.abs(z1.cpu().numpy() - z2.cpu().numpy()) <= 1e-13 * scale)
+    x = torch.randn(s.n_cols, dtype=torch.float64, device="cuda")
+    y1 = torch.zeros(s.n_rows, dtype=torch.float64, device="cuda")
+    y2 = torch.zeros(s.n_rows, dtype=torch.float64, device="cuda")
+    ref.aprod1(x, y1)
+    ctx.aprod1(x, y2)
+    assert torch.equal(y1, y2)
+    # rows 100.. of a second load carry a bad instrumental column: those rows are not loaded
+    bad = instr.clone().pin_memory()
+    bad[150, 3] = cfg.n_instr
+    n2 = s.n_rows - 100
+    with pytest.raises(g.GsrError) as e:
+        ctx.set_rows(100, n2, A[100:], knot[100:], bad[100:])
+    assert e.value.status == g.Status.EINVAL
+    with pytest.raises(g.GsrError) as e:
+        ctx.aprod1(x, y2)
+    assert e.value.status == g.Status.ESTATE
+    badA = A.clone().pin_memory()
+    badA[7, 2] = float("nan")
+    with pytest.raises(g.GsrError) as e:
+        ctx.set_rows(0, s.n_rows, badA, knot, instr)
+    assert e.value.status == g.Status.ENUMERIC
+    ctx.set_rows(0, s.n_rows, A, knot, instr)
+    y2.zero_()
+    ctx.aprod1(x, y2)
+    assert torch.equal(y1, y2)
+    ref.close()
     ctx.close()
