@@ -448,6 +448,10 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->knot_ptr);
     cudaFree(c->fx_word);
     if (c->own) cudaStreamDestroy(c->own);
+    if (c->pool) {
+        cudaDeviceSynchronize();
+        cudaMemPoolDestroy(c->pool);
+    }
     if (c->ev) cudaEventDestroy(c->ev);
     cudaGetLastError();
     delete c;

@@ -126,6 +126,7 @@ struct gsr_ctx {
     struct gsr_net *warm_net = nullptr;  // network of GSR_WARM_LEARNED solves, loaded from warm_path
     std::string warm_path;
     cudaEvent_t ev = nullptr;        // orders `own` after the caller's stream
+    cudaMemPool_t pool = nullptr;    // stream-ordered scratch of the layout build, kept between builds
     gsr::Workspace ws;
     std::string err;
 };

@@ -224,11 +224,22 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 8);
     std::vector<uint32_t> kmax_h;
     gsr_status rf = GSR_OK;
-    // scratch from the stream-ordered allocator: no device-wide synchronisation on free
-    if ((e = cudaMallocAsync(&keys_in, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
-    if ((e = cudaMallocAsync(&keys_out, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
-    if ((e = cudaMallocAsync(&vals_in, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
-    if ((e = cudaMallocAsync(&perm, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) goto done;
+    // scratch from the context's stream-ordered pool, which keeps its memory between builds (a
+    // reloaded system rebuilds the layout without new device allocations or a device-wide sync)
+    if (!c->pool) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = c->device;
+        if ((e = cudaMemPoolCreate(&c->pool, &props)) != cudaSuccess) return cuda_fail(c, e, "memory pool");
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+            return cuda_fail(c, e, "memory pool");
+    }
+    if ((e = cudaMallocFromPoolAsync(&keys_in, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocFromPoolAsync(&keys_out, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocFromPoolAsync(&vals_in, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocFromPoolAsync(&perm, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
     if (f32)
         k_extract_knots<float><<<g, 256, 0, s>>>(tiles, n, keys_in);
     else
@@ -237,14 +248,14 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
         goto done;
-    if ((e = cudaMallocAsync(&tmp, tmp_bytes, s)) != cudaSuccess) goto done;
+    if ((e = cudaMallocFromPoolAsync(&tmp, tmp_bytes, c->pool, s)) != cudaSuccess) goto done;
     if ((e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
         goto done;
     k_knot_ptr<<<(nk + 256) / 256, 256, 0, s>>>(keys_out, n, nk, c->knot_ptr);
     // the attitude records in star order, then gathered by the permutation
-    if ((e = cudaMallocAsync(&rec, (f32 ? sizeof(float) : sizeof(double)) * NAXES * NPARAXIS * (size_t)n, s)) !=
-        cudaSuccess)
+    if ((e = cudaMallocFromPoolAsync(&rec, (f32 ? sizeof(float) : sizeof(double)) * NAXES * NPARAXIS * (size_t)n,
+                                     c->pool, s)) != cudaSuccess)
         goto done;
     if (f32) {
         k_att_rows<float><<<g, 256, 0, s>>>(tiles, n, (float *)rec);
