@@ -113,9 +113,9 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
         if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
     if constexpr (LSQR && sizeof(AT) == 4) {
-        if (ymax) {  // max |new y| of the block (binary32 bits of non-negative values order as integers)
-            const float m = block_max(amx, reinterpret_cast<float *>(sm32));
-            if (threadIdx.x == 0) atomicMax(ymax, __float_as_uint(m));
+        if (ymax) {  // max |new y| of the warp (binary32 bits of non-negative values order as integers)
+            const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(amx));
+            if ((threadIdx.x & 31) == 0 && m) atomicMax(ymax, m);
         }
     }
 }
