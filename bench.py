@@ -230,7 +230,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {desc(w)}", "solver": "CPU oracle LSQR (FP64, 1 thread)"},
+            "config": {"workload": f"{args.workload}: {desc(w)}; coefficients rounded to binary32",
+                       "solver": "CPU oracle LSQR (binary64, 1 thread) from x0 = 0",
+                       "tolerance": "1e-9 relative per block (astro, attitude, instrumental, global)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle LSQR, 1 and 3 iterations on the full system, extrapolated to "
                                        f"{n9} iterations ({note})"},
