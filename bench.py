@@ -54,7 +54,7 @@ FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
 # binary32 kernels on the 2e7-row workload; a launch's traffic is this figure times its rows. The binary64
 # kernels are bound by the binary64 units and have no capture (None).
-TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": None, "residual_df": 133.4, "aprod1_f64": None,
+TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": 140.2, "residual_df": 133.4, "aprod1_f64": None,
                    "aprod2_f64": None}
 
 
