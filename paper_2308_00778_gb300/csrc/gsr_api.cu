@@ -638,6 +638,7 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     // warm start: x0 on the device from the features (and the network)
     const double *x0_use = x0;
     bool x0_dev = false;
+    int r0_parts = 0;  // mixed solve from a warm start on binary32 storage: the start's residual is ready
     double ms_warm = 0.0;
     if (prm.warm != GSR_WARM_NONE) {
         const auto tw = std::chrono::steady_clock::now();
@@ -662,7 +663,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
             }
             net = c->warm_net;
         }
-        if ((rw = warm_start_dev(c, net, c->ws.x0w, c->own)) != GSR_OK) return rw;
+        if ((rw = warm_start_dev(c, net, c->ws.x0w, c->own, prm.mode == GSR_MIXED ? &r0_parts : nullptr)) != GSR_OK)
+            return rw;
         if ((e = cudaStreamSynchronize(c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
         x0_use = c->ws.x0w;
         x0_dev = true;
@@ -673,7 +675,7 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     const bool p_ready = prm.warm != GSR_WARM_NONE && prm.precond != 0 &&
                          (prm.mode == GSR_MIXED || c->prec == GSR_FP64);
     const gsr_status rc = prm.mode == GSR_MIXED
-                              ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own, p_ready)
+                              ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own, p_ready, r0_parts)
                               : lsqr_solve(c, &prm, x0_use, x0_dev, x_out, se_out, info, c->own, p_ready);
     if (info) {
         info->ms_warm = ms_warm;

@@ -190,14 +190,18 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
 // warm start (warm.cu)
-gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s);
+// r0_parts (may be null): for binary32 storage the residual of x0 is also left in ws.u32, in
+// binary32, with its per-block sums of squares in ws.part_u (*r0_parts partials; 0 when not)
+gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, int *r0_parts);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out);
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
+// r0_parts > 0: ws.u32 / ws.part_u already hold the residual of x0 (from the warm start) for the
+// first refinement step
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                       gsr_solve_info *info, cudaStream_t s, bool p_ready = false);
+                       gsr_solve_info *info, cudaStream_t s, bool p_ready = false, int r0_parts = 0);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ double warp_sum(double v)

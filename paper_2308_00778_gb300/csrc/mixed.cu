@@ -188,7 +188,7 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
 }
 
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,
-                       gsr_solve_info *info, cudaStream_t s, bool p_ready)
+                       gsr_solve_info *info, cudaStream_t s, bool p_ready, int r0_parts)
 {
     const auto t0 = std::chrono::steady_clock::now();
     gsr_status rc = ensure_workspace(c);
@@ -225,7 +225,10 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     gsr_status status = GSR_OK;
     for (; outer < max_outer; ++outer) {
         init.itnlim = outer == 0 ? itn_first : itn_next;
-        if (outer == 0 && !x0) {
+        int n_part = gres;
+        if (outer == 0 && r0_parts > 0) {
+            n_part = r0_parts;  // the warm start left the residual of x0 (binary32) in ws.u32
+        } else if (outer == 0 && !x0) {
             if (nr > 0) k_rhs32<<<gres, kThreads, 0, s>>>(c->b, ws.u32, ws.part_u, nr);
         } else {
             k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
@@ -234,7 +237,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
                 return cuda_fail(c, e, "residual");
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
-        status = run_lsqr(c, init, true, false, nr > 0 ? gres : 0, prm->graph_k, prm->timeout_s, t0, s, &fin);
+        status = run_lsqr(c, init, true, false, nr > 0 ? n_part : 0, prm->graph_k, prm->timeout_s, t0, s, &fin);
         total_itn += fin.itn;
         if (status != GSR_OK && status != GSR_ETIMEOUT) return status;
         double hb[8];

@@ -237,6 +237,43 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
     if (t0 < t1) flush_normal_run(acc, k, wbuf, N);
 }
 
+// r -= (astrometric part of the rows) x0, in binary32, over the row tiles in
+// grid-stride order; per-block sums of squares of the new r into part. With r
+// the residual of the other parts of x0 this gives the residual of the whole
+// warm start, for the first refinement step of the mixed solver.
+__global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const double *__restrict__ x0,
+                                                        float *__restrict__ r, double *__restrict__ part)
+{
+    constexpr int R = Tile<float>::R;
+    constexpr int T = Tile<float>::T;
+    __shared__ double sm32[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float ssq = 0.f;
+    for (int64_t t = gw; t < S.n_tiles; t += nw) {
+        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
+        float a[NASTRO][R];
+#pragma unroll
+        for (int j = 0; j < NASTRO; ++j) load_vals<float, float>(tb, j, a[j]);
+        const int64_t r0 = t * T + lane * R;
+        int64_t sr[R];
+        stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (r0 + i >= S.n_rows) continue;
+            const double *xa = x0 + NASTRO * sr[i];
+            float v = r[r0 + i];
+#pragma unroll
+            for (int j = 0; j < NASTRO; ++j) v = fmaf(-a[j][i], (float)__ldg(xa + j), v);
+            r[r0 + i] = v;
+            ssq = fmaf(v, v, ssq);
+        }
+    }
+    const double tot = block_sum((double)ssq, sm32);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
 __global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, double *__restrict__ x0)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_stars;
@@ -343,8 +380,9 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s, bool keep_z)
 }
 
 // x0 (device) from the features and (optionally) the network
-gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s)
+gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, int *r0_parts)
 {
+    if (r0_parts) *r0_parts = 0;
     gsr_status rc = warm_features_dev(c, s, true);
     if (rc != GSR_OK) return rc;
     Workspace &ws = c->ws;
@@ -378,6 +416,13 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s)
         if (ez != cudaSuccess) return cuda_fail(c, ez, "warm start: normal equations");
     }
     k_astro_chol<<<grid_for(c, c->n_stars), kThreads, 0, s>>>(ws.astro_n, c->n_stars, x0);
+    if (r0_parts && c->prec == GSR_FP32 && c->n_rows > 0) {
+        // ws.u32 holds the residual of the non-astrometric parts: complete it (binary32) into the
+        // residual of x0, with its per-block sums of squares in ws.part_u
+        const int g = (int)std::min<int64_t>(std::max<int64_t>((c->n_tiles + 7) / 8, 1), (int64_t)c->sm_count * 4);
+        k_astro_residual<<<g, kThreads, 0, s>>>(view<float>(c), x0, ws.u32, ws.part_u);
+        *r0_parts = g;
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "warm start");
     return GSR_OK;
@@ -416,7 +461,7 @@ GSR_API gsr_status gsr_warm_start(gsr_ctx *c, gsr_net *net, double *x0, void *st
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     const cudaStream_t s = (cudaStream_t)stream;
-    gsr_status rc = warm_start_dev(c, net, x0, s);
+    gsr_status rc = warm_start_dev(c, net, x0, s, nullptr);
     if (rc != GSR_OK) return rc;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "warm start");
     return GSR_OK;
