@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
-    static_assert(!FX || (INSTR_SMEM && MODE == A2_PROD && sizeof(AT) == 4), "fixed point: binary32 products");
+    static_assert(!FX || (INSTR_SMEM && (MODE == A2_PROD || MODE == A2_BOTH) && sizeof(AT) == 4),
+                  "fixed point: binary32 products (and squares)");
     __shared__ int s_bad;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
@@ -182,17 +183,27 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     AT *sm_sq = sm_ins + S.n_instr;  // BOTH: the squares' accumulators follow the products'
     const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * S.n_instr : S.n_instr) : 0;
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;  // also integer zero
-    float *sm_scale = reinterpret_cast<float *>(smem_raw) + S.n_instr;  // FX: per-column scales
+    // FX: per-column scales after the accumulators (BOTH: products', then squares')
+    float *sm_scale = reinterpret_cast<float *>(smem_raw) + nsm;
+    float *sm_qscale = sm_scale + S.n_instr;
     if (FX) {
         const float ymax = __uint_as_float(fx_word[2 * S.n_instr]);
         if (threadIdx.x == 0) s_bad = !(ymax < INFINITY);  // non-finite y: the sums are made NaN below
         for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
-            // the largest power of two with max|a_j| * max|y| * scale <= 2^b_j - 1
-            const float bound = __uint_as_float(fx_word[i]) * ymax;
+            // the largest power of two with bound * scale <= 2^b_j - 1, bound = max|a_j| max|y|
+            // for the products and max|a_j|^2 for the squares
+            const float am = __uint_as_float(fx_word[i]);
             const float lim = (float)((1u << fx_word[S.n_instr + i]) - 1u);
+            const float bound = am * ymax;
             float sc = 1.f;
             if (bound > 0.f && bound < INFINITY) sc = ldexpf(1.f, min(ilogbf(lim / bound), 126));
             sm_scale[i] = sc;
+            if (BOTH) {
+                const float qb = am * am;
+                float qs = 1.f;
+                if (qb > 0.f && qb < INFINITY) qs = ldexpf(1.f, min(ilogbf(lim / qb), 126));
+                sm_qscale[i] = qs;
+            }
         }
     }
     __syncthreads();
@@ -243,7 +254,10 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                     else
                         atomicAdd(zi + ic[j][i], (double)(av * yr[i]));
                     if constexpr (BOTH) {
-                        if (INSTR_SMEM)
+                        if (FX)
+                            atomicAdd(reinterpret_cast<int *>(sm_sq) + ic[j][i],
+                                      __float2int_rn(av * av * sm_qscale[ic[j][i]]));
+                        else if (INSTR_SMEM)
                             atomicAdd(sm_sq + ic[j][i], av * av);
                         else
                             atomicAdd(z2i + ic[j][i], (double)(av * av));
@@ -316,7 +330,11 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     if (FX) {
         for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
             const int q = reinterpret_cast<const int *>(sm_ins)[i];
-            if (q != 0) atomicAdd(zi + i, (double)q / (double)sm_scale[i]);  // a power of two: exact
+            if (q == 0) continue;
+            if (BOTH && i >= S.n_instr)  // a power of two: exact
+                atomicAdd(z2i + (i - S.n_instr), (double)q / (double)sm_qscale[i - S.n_instr]);
+            else
+                atomicAdd(zi + i, (double)q / (double)sm_scale[i]);
         }
         if (s_bad && threadIdx.x == 0) atomicAdd(zi, (double)NAN);
     } else {
@@ -543,7 +561,7 @@ static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x
                                       cudaStream_t s)
 {
     auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX>;
-    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH || FX ? 2 : 1) : 0;
+    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX ? 2 : 1)) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -578,8 +596,10 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     if (MODE != A2_SQUARE && !y) return cudaErrorInvalidValue;
     if (MODE == A2_BOTH && !x2) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    constexpr bool F32 = sizeof(AT) == 4 && MODE == A2_PROD;
-    const bool fx = F32 && c->fx_bits > 0;
+    constexpr bool F32 = sizeof(AT) == 4 && (MODE == A2_PROD || MODE == A2_BOTH);
+    // the combined pass needs twice the shared words; it keeps binary32 atomics when they do not fit
+    const bool fx = F32 && c->fx_bits > 0 &&
+                    (MODE == A2_PROD || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
     if (fx) {
         // fixed-point instrumental sums: max |y| comes from the LSQR aprod 1 of the same iteration,
         // else from a pass over y here
