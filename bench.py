@@ -298,6 +298,24 @@ def start_activity_record(torch, dev):
         print(f"activity record unavailable: {e!r}", file=sys.stderr)
 
 
+def replica_cfg(gsrgen, cfg, rank, world):
+    """Rank r of an N-rank run solves its own replica of the workload: the same shape, seed + 1000 r
+    (the solve has no cross-GPU step on one system, so ranks share nothing but the timing)."""
+    if world <= 1:
+        return cfg
+    return gsrgen.make_cfg(cfg.seed + 1000 * rank, cfg.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
+                           cfg.n_glob, cfg.att_kind, cfg.noise_sigma)
+
+
+def max_over_ranks(torch, dist, value, world, device):
+    """The largest value over the ranks (the slowest replica's time), after a barrier."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def count_launches(torch, fn):
     """Kernels the device ran during one call of fn, from torch.profiler's CUDA activity record."""
     try:
@@ -342,10 +360,7 @@ def run_ours(args):
     start_activity_record(torch, dev)
 
     w = gsrgen.workloads()[args.workload]
-    cfg = w.cfg
-    if world > 1:
-        cfg = gsrgen.make_cfg(cfg.seed + 1000 * rank, cfg.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
-                              cfg.n_glob, cfg.att_kind, cfg.noise_sigma)
+    cfg = replica_cfg(gsrgen, w.cfg, rank, world)
     nc = cfg.ncols()
     damp = w.damp
 
@@ -443,12 +458,7 @@ def run_ours(args):
             solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
                                  final_block_err=max_block_err(x, xs, cfg), eq5_q_max=eq5_q(x, xs, se_ref, cfg))
     headline = min(solvers, key=lambda nm: solvers[nm]["s"])
-    ms = solvers[headline]["s"] * 1e3
-    t_ms = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
-    ms = float(t_ms.item())
+    ms = max_over_ranks(torch, dist, solvers[headline]["s"] * 1e3, world, dev)
 
     # ---- per-kernel timing (same kernels, standalone launches, CUDA events on their stream)
     u64 = torch.randn(n, dtype=torch.float64, device=dev)

@@ -66,3 +66,26 @@ def test_errors_without_gpu_are_status_codes():
     assert g.gsr_destroy(0) == g.Status.OK
     p = g.gsr_default_params()
     assert p.itnlim == 2000 and p.atol == 1e-12 and p.precond == 1 and p.mode == g.GSR_PLAIN
+
+
+def test_shipped_weights_match_the_network(libgsr):
+    """The trained warm-start network shipped with the package holds exactly the
+    parameters of the library's network (header, count, finite values), in the
+    layout the trainer writes (per layer W[cout][cin][5] then bias[cout])."""
+    import json
+
+    import numpy as np
+
+    import paper_2308_00778_gb300 as g
+    from paper_2308_00778_gb300 import train
+
+    raw = open(g.WARM_WEIGHTS, "rb").read()
+    assert raw[:8] == b"GSRNET01"
+    cnt = int(np.frombuffer(raw[8:16], dtype=np.int64)[0])
+    vals = np.frombuffer(raw[16:], dtype=np.float32)
+    libgsr.gsr_net_num_params.restype = ctypes.c_int64
+    n = libgsr.gsr_net_num_params()
+    assert cnt == n == vals.size == train.init_params(0).size
+    assert np.all(np.isfinite(vals))
+    meta = json.load(open(g.WARM_WEIGHTS[:-4] + ".json"))
+    assert meta["mean_iterations"]["learned"] < meta["mean_iterations"]["cold"]
