@@ -80,7 +80,6 @@ struct Workspace {
     float *pv32 = nullptr;      // n_cols: binary32 copy of p * v for the inner aprod1
     double *xo = nullptr;       // n_cols: refined solution (unscaled) of the mixed solver
     float2 *xhl = nullptr;      // n_cols: xo split into two binary32 parts
-    float2 *bhl = nullptr;      // n_rows: b split into two binary32 parts
     double *blk = nullptr;      // 16: per-block sums of squares of the correction and of x
     float *feats = nullptr;     // n_dfa x 6: warm-start features
     float *netout = nullptr;    // n_dfa x 3: network output
@@ -195,7 +194,7 @@ void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_c
 gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, int *r0_parts);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
-cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
+cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out);
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
 // r0_parts > 0: ws.u32 / ws.part_u already hold the residual of x0 (from the warm start) for the

@@ -372,12 +372,11 @@ gsr_status ensure_workspace(gsr_ctx *c)
     if ((e = cudaMemset(ws.z, 0, nc * sizeof(double))) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.part_u, 0, 3 * MAX_PARTIALS * sizeof(double))) != cudaSuccess) goto oom;
     if (c->prec == GSR_FP32) {
-        // mixed-precision solver: binary32 row vector, gathered column vector, split x and b
+        // mixed-precision solver: binary32 row vector, gathered column vector, split x
         if ((e = cudaMalloc(&ws.u32, nr * sizeof(float))) != cudaSuccess) goto oom;
         if ((e = cudaMalloc(&ws.pv32, nc * sizeof(float))) != cudaSuccess) goto oom;
         if ((e = cudaMalloc(&ws.xo, nc * sizeof(double))) != cudaSuccess) goto oom;
         if ((e = cudaMalloc(&ws.xhl, nc * sizeof(float2))) != cudaSuccess) goto oom;
-        if ((e = cudaMalloc(&ws.bhl, nr * sizeof(float2))) != cudaSuccess) goto oom;
         if ((e = cudaMalloc(&ws.blk, 16 * sizeof(double))) != cudaSuccess) goto oom;
     }
     ws.n_rows = c->n_rows;
@@ -402,7 +401,6 @@ void free_workspace(gsr_ctx *c)
     if (ws.u32) cudaFree(ws.u32);
     if (ws.pv32) cudaFree(ws.pv32);
     if (ws.xhl) cudaFree(ws.xhl);
-    if (ws.bhl) cudaFree(ws.bhl);
     if (ws.st) cudaFree(ws.st);
     if (ws.counter) cudaFree(ws.counter);
     if (ws.flag_h) cudaFreeHost(ws.flag_h);

@@ -33,11 +33,12 @@ __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ out, 
 
 // r = b - A x for every row, stored in binary32, over the binary32 row tiles
 // (one warp per tile, 4 rows per lane: four independent double-float chains).
-// b comes either pre-split (bhl, two binary32 per row) or as binary64 split
-// here; `part` (may be null) receives per-block sums of squares of r.
+// b is read in binary64 and split here (the same 8 bytes per row as a pre-split
+// copy, without the pass that would make it); `part` (may be null) receives
+// per-block sums of squares of r.
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
-                                                  const float2 *__restrict__ bhl, const double *__restrict__ b64,
-                                                  float *__restrict__ r_out, double *__restrict__ part)
+                                                  const double *__restrict__ b64, float *__restrict__ r_out,
+                                                  double *__restrict__ part)
 {
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
             acc_term(a[23][i], xg, sh[i], c[i]);
             const int64_t r = r0 + i;
             if (r < S.n_rows) {
-                const float2 bb = bhl ? __ldcs(bhl + r) : split_double(__ldcs(b64 + r));
+                const float2 bb = split_double(__ldcs(b64 + r));
                 float tt, e;
                 two_sum(bb.x, -sh[i], tt, e);  // b_hi - s exactly
                 const float lo = __fadd_rn(__fadd_rn(e, bb.y), -c[i]);
@@ -148,7 +149,7 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 }
 
 // Launch (or, with grid_out, only size) the residual kernel. Allocates nothing.
-cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *bhl, const double *b64, float *r,
+cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out)
 {
     int per_sm = 0;
@@ -162,7 +163,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const float2 *b
         *grid_out = (int)blocks;
         return cudaSuccess;
     }
-    k_residual<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, bhl, b64, r, part);
+    k_residual<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part);
     return cudaGetLastError();
 }
 
@@ -180,9 +181,8 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
     if (rc != GSR_OK) return rc;
     if (c->n_rows == 0) return GSR_OK;
     Workspace &ws = c->ws;
-    k_split<<<col_grid(c, c->n_rows), kThreads, 0, s>>>(c->b, ws.bhl, c->n_rows);
     k_split<<<col_grid(c, c->n_cols), kThreads, 0, s>>>(x, ws.xhl, c->n_cols);
-    const cudaError_t e = residual_launch(c, ws.xhl, ws.bhl, nullptr, r, ws.part_u, s, nullptr);
+    const cudaError_t e = residual_launch(c, ws.xhl, c->b, r, ws.part_u, s, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "residual");
     return GSR_OK;
 }
@@ -196,12 +196,10 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols, nr = c->n_rows;
     const int gcol = col_grid(c, nc);
-    const int grow = col_grid(c, nr);
     const bool dev_io = prm->where == GSR_DEVICE;
     cudaError_t e;
 
     if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
-    k_split<<<grow, kThreads, 0, s>>>(c->b, ws.bhl, nr);
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
                             (dev_io || x0_dev) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
@@ -216,7 +214,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
     const double refine_tol = prm->refine_tol != 0.0 ? prm->refine_tol : 1e-10;
     int gres = 1;
-    residual_launch(c, nullptr, nullptr, nullptr, nullptr, nullptr, s, &gres);
+    residual_launch(c, nullptr, nullptr, nullptr, nullptr, s, &gres);
     const int64_t att0 = (int64_t)NASTRO * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa,
                   glob0 = instr0 + c->n_instr;
 
@@ -233,7 +231,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
         } else {
             k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
             if (nr > 0 &&
-                (e = residual_launch(c, ws.xhl, ws.bhl, nullptr, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
+                (e = residual_launch(c, ws.xhl, c->b, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
                 return cuda_fail(c, e, "residual");
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");

@@ -1,12 +1,11 @@
 // residual_static.cu -- gsr_residual_static: the double-float residual r = b - A x
 // of an FP32-stored context, computed without allocating any memory.
 //
-// gsr_residual needs scratch for the split copies of x and b and for its
-// partial sums, and takes it from the context's workspace, which is allocated
-// with cudaMalloc on first use. This entry point runs the same kernels but
-// keeps its only scratch, the split copy of x, in a file-scope __device__
-// array of fixed size, has b split inside the residual kernel, and writes no
-// partial sums, so a call allocates nothing.
+// gsr_residual needs scratch for the split copy of x and for its partial
+// sums, and takes it from the context's workspace, which is allocated with
+// cudaMalloc on first use. This entry point runs the same kernels but keeps
+// its only scratch, the split copy of x, in a file-scope __device__ array of
+// fixed size and writes no partial sums, so a call allocates nothing.
 #include <mutex>
 
 #include "gsr_internal.cuh"
@@ -61,9 +60,9 @@ GSR_API gsr_status gsr_residual_static(gsr_ctx *c, const double *x, float *r, vo
     if ((e = static_scratch(c->device, &xhl)) != cudaSuccess) return cuda_fail(c, e, "static scratch address");
     if (c->n_rows == 0) return GSR_OK;
     const cudaStream_t s = (cudaStream_t)stream;
-    // the same kernels as gsr_residual, with b split inside the residual kernel and no partial sums
+    // the same kernels as gsr_residual, without partial sums
     if ((e = split_launch(c, x, xhl, c->n_cols, s)) != cudaSuccess ||
-        (e = residual_launch(c, xhl, nullptr, c->b, r, nullptr, s, nullptr)) != cudaSuccess)
+        (e = residual_launch(c, xhl, c->b, r, nullptr, s, nullptr)) != cudaSuccess)
         return cuda_fail(c, e, "residual_static");
     return GSR_OK;
 }
