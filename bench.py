@@ -42,19 +42,20 @@ sys.path.insert(0, ROOT)
 METRIC = "LSQR s-to-1e-9 (FP64 vs FP32+refine+learned x0), aprod1/2 HBM GB/s, 1 GB300"
 TOL = 1e-9
 
-# algorithmic bytes per row (int32 indices; star_ptr and column vectors amortised)
+# algorithmic bytes per row (int32 knot, 16-bit instrumental columns as stored for n_instr <= 65536;
+# star_ptr and column vectors amortised)
 BYTES = {
-    "aprod1_f64": 24 * 8 + 4 + 24 + 16,   # values, knot, 6 instr, y read + write          = 236
-    "aprod2_f64": 24 * 8 + 4 + 24 + 8,    # values, knot, 6 instr, y read                  = 228
-    "aprod1_f32": 24 * 4 + 4 + 24 + 8,    # binary32 values, y (binary32) read + write     = 132
-    "aprod2_f32": 24 * 4 + 4 + 24 + 4,    # binary32 values, y (binary32) read             = 128
-    "residual_df": 24 * 4 + 4 + 24 + 8 + 4,  # values, indices, b (two binary32), r write  = 136
+    "aprod1_f64": 24 * 8 + 4 + 12 + 16,   # values, knot, 6 instr, y read + write          = 224
+    "aprod2_f64": 24 * 8 + 4 + 12 + 8,    # values, knot, 6 instr, y read                  = 216
+    "aprod1_f32": 24 * 4 + 4 + 12 + 8,    # binary32 values, y (binary32) read + write     = 120
+    "aprod2_f32": 24 * 4 + 4 + 12 + 4,    # binary32 values, y (binary32) read             = 116
+    "residual_df": 24 * 4 + 4 + 12 + 8 + 4,  # values, indices, b (binary64), r write      = 124
 }
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
 # binary32 kernels on the 2e7-row workload; a launch's traffic is this figure times its rows. The binary64
 # kernels are bound by the binary64 units and have no capture (None).
-TRAFFIC_PER_ROW = {"aprod1_f32": 129.3, "aprod2_f32": 140.2, "residual_df": 133.4, "aprod1_f64": None,
+TRAFFIC_PER_ROW = {"aprod1_f32": None, "aprod2_f32": None, "residual_df": None, "aprod1_f64": None,
                    "aprod2_f64": None}
 
 
@@ -475,7 +476,7 @@ def run_ours(args):
     }
     kern = {}
     for name, kms in t.items():
-        bpr = BYTES[name]
+        bpr = BYTES[name] + (12 if cfg.n_instr > 65536 else 0)  # 32-bit instrumental planes
         kern[name] = {"ms": kms, "GB/s": bpr * n / (kms * 1e-3) / 1e9, "bytes_per_row": bpr,
                       "TFLOP/s": FLOPS_PER_ROW * n / (kms * 1e-3) / 1e12}
     peaks = load_peaks()
@@ -502,7 +503,7 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": kern[dom]["GB/s"] / peaks["hbm_gbs"],
                 "traffic": tr * n if tr else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "algorithmic": BYTES[dom] * n, "peak_src": peaks["src"]}
+                "algorithmic": kern[dom]["bytes_per_row"] * n, "peak_src": peaks["src"]}
 
     # ---- kernel launches of one headline step, counted from the device's activity record (CUPTI)
     launches = count_launches(torch, lambda: hctx.solve(x, stream=sh, **hkw))

@@ -66,13 +66,13 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     AT ssq = (AT)0;
     float amx = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
-        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
         AT a[NPAR][R];
 #pragma unroll
         for (int j = 0; j < NPAR; ++j) load_vals<VT, AT>(tb, j, a[j]);
@@ -221,11 +221,10 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = sacc[j] = sacc2[j] = (AT)0;
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current run
     for (int64_t t = t0; t < t1; ++t) {
-        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
-        const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
         AT a[NASTRO][R], ai[NINSTR][R], ag[R];
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) load_vals<VT, AT>(tb, j, a[j]);

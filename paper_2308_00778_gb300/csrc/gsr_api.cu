@@ -92,22 +92,21 @@ __global__ void k_validate(const ST *__restrict__ vals, int32_t layout, int64_t 
 template <typename ST, typename DT>
 __global__ void k_convert(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
                           const int32_t *__restrict__ instr, int64_t n, int32_t n_glob, uint8_t *__restrict__ tiles,
-                          int64_t row0)
+                          int64_t tile_bytes, int32_t iw16, int64_t row0)
 {
     using TL = Tile<DT>;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = row0 + r;
-        uint8_t *tb = tiles + (o / TL::T) * TL::BYTES;
+        uint8_t *tb = tiles + (o / TL::T) * tile_bytes;
         const int64_t i = o % TL::T;
         for (int j = 0; j < NPAR; ++j) {
             ST v = layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r];
             if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
             reinterpret_cast<DT *>(tb + j * TL::VBLK)[i] = (DT)v;
         }
-        int32_t *ti = reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK);
-        ti[i] = knot[r];
+        reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK)[i] = knot[r];
         for (int j = 0; j < NINSTR; ++j)
-            ti[(1 + j) * TL::T + i] = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+            store_instr<DT>(tb, iw16, j, (int)i, layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r]);
     }
 }
 
@@ -120,7 +119,8 @@ template <typename ST, typename DT>
 __global__ void __launch_bounds__(256) k_convert_aos(const ST *__restrict__ vals, const int32_t *__restrict__ knot,
                                                      const int32_t *__restrict__ instr, int64_t n, int64_t row0,
                                                      int32_t n_glob, int32_t n_dfa, int32_t n_instr,
-                                                     uint8_t *__restrict__ tiles, int32_t *__restrict__ errw)
+                                                     uint8_t *__restrict__ tiles, int64_t tile_bytes, int32_t iw16,
+                                                     int32_t *__restrict__ errw)
 {
     using TL = Tile<DT>;
     constexpr int T = TL::T;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_convert_aos(const ST *__restrict__ vals
             for (int q = threadIdx.x; q < m; q += blockDim.x) sk[off + q] = knot[r_lo + q];
         }
         __syncthreads();
-        uint8_t *tb = tiles + t * TL::BYTES;
+        uint8_t *tb = tiles + t * tile_bytes;
         for (int i = off + (int)threadIdx.x; i < off + m; i += blockDim.x) {
 #pragma unroll 4
             for (int j = 0; j < NPAR; ++j) {
@@ -154,15 +154,14 @@ __global__ void __launch_bounds__(256) k_convert_aos(const ST *__restrict__ vals
                 if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
                 reinterpret_cast<DT *>(tb + j * TL::VBLK)[i] = (DT)v;
             }
-            int32_t *ti = reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK);
             const int32_t k = sk[i];
             bk |= (k < 0 || k > n_dfa - 4);
-            ti[i] = k;
+            reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK)[i] = k;
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
                 const int32_t ic = si[i * NINSTR + j];
                 bi |= (ic < 0 || ic >= n_instr);
-                ti[(1 + j) * T + i] = ic;
+                store_instr<DT>(tb, iw16, j, i, ic);
             }
         }
         __syncthreads();
@@ -206,10 +205,10 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
     if (hw[2]) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
     if (c->prec == GSR_FP32)
         k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
-                                                (uint8_t *)c->tiles, row0);
+                                                (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
     else
         k_convert<ST, double><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
-                                                 (uint8_t *)c->tiles, row0);
+                                                 (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(c, e, "conversion");
     return GSR_OK;
@@ -241,10 +240,10 @@ static gsr_status set_rows_mapped(gsr_ctx *c, int64_t row0, int64_t nrows, const
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(c->n_tiles, (int64_t)c->sm_count * 4));
     if (c->prec == GSR_FP32)
         k_convert_aos<ST, float><<<g, 256, 0, s>>>(vals, knot, instr, nrows, row0, c->n_glob, c->n_dfa, c->n_instr,
-                                                    (uint8_t *)c->tiles, c->errw);
+                                                    (uint8_t *)c->tiles, c->tile_bytes, c->iw16, c->errw);
     else
         k_convert_aos<ST, double><<<g, 256, 0, s>>>(vals, knot, instr, nrows, row0, c->n_glob, c->n_dfa, c->n_instr,
-                                                     (uint8_t *)c->tiles, c->errw);
+                                                     (uint8_t *)c->tiles, c->tile_bytes, c->iw16, c->errw);
     int32_t hw[4];
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -380,7 +379,11 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
         c->max_obs = std::max<int64_t>(c->max_obs, c->star_ptr_h[s + 1] - c->star_ptr_h[s]);
     c->n_cols = (int64_t)NASTRO * n_stars + (int64_t)NAXES * n_dfa + n_instr + n_glob;
     const int64_t rows_per_tile = value_precision == GSR_FP32 ? Tile<float>::T : Tile<double>::T;
-    const int64_t tile_bytes = value_precision == GSR_FP32 ? Tile<float>::BYTES : Tile<double>::BYTES;
+    // instrumental columns in 16-bit planes whenever they fit (12 bytes less per row to stream)
+    c->iw16 = n_instr <= 65536 ? 1 : 0;
+    const int64_t tile_bytes =
+        value_precision == GSR_FP32 ? Tile<float>::bytes(c->iw16 != 0) : Tile<double>::bytes(c->iw16 != 0);
+    c->tile_bytes = tile_bytes;
     const int64_t atile_bytes = value_precision == GSR_FP32 ? Tile<float>::ABYTES : Tile<double>::ABYTES;
     c->n_tiles = (c->n_rows + rows_per_tile - 1) / rows_per_tile;
     // first star of each tile (host), star of the last row at index n_tiles

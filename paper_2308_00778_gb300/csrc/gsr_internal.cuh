@@ -39,6 +39,8 @@ struct SysView {
     int64_t n_stars, n_rows;
     int32_t n_dfa, n_instr, n_glob;
     int64_t att0, instr0, glob0;  // first column of each section
+    int64_t tile_bytes;           // bytes of one star-ordered tile record (tiles.cuh)
+    int32_t iw16;                 // instrumental columns stored as 16-bit (1) or 32-bit (0) integers
 };
 
 // LSQR scalars shared between the kernels of one solve (one instance in device
@@ -102,6 +104,8 @@ struct gsr_ctx {
     int64_t n_stars = 0, n_rows = 0, n_cols = 0;
     int32_t n_dfa = 0, n_instr = 0, n_glob = 0;
     int64_t n_tiles = 0;             // row tiles (tiles.cuh); rows per tile depend on the precision
+    int64_t tile_bytes = 0;          // bytes of one tile record
+    int32_t iw16 = 0;                // instrumental columns in 16-bit planes (n_instr <= 65536)
     void *tiles = nullptr;           // star-ordered tile records
     void *atiles = nullptr;          // knot-ordered attitude tile records
     int32_t *first_star = nullptr;   // [n_tiles + 1] star of the first row of each tile
@@ -155,6 +159,8 @@ SysView<VT> view(const gsr_ctx *c)
     s.att0 = (int64_t)NASTRO * c->n_stars;
     s.instr0 = s.att0 + (int64_t)NAXES * c->n_dfa;
     s.glob0 = s.instr0 + c->n_instr;
+    s.tile_bytes = c->tile_bytes;
+    s.iw16 = c->iw16;
     return s;
 }
 

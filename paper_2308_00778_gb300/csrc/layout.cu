@@ -28,11 +28,12 @@ __global__ void k_iota(int32_t *__restrict__ a, int64_t n)
 
 // knot of every row, read from the tiles
 template <typename VT>
-__global__ void k_extract_knots(const uint8_t *__restrict__ tiles, int64_t n, int32_t *__restrict__ keys)
+__global__ void k_extract_knots(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int64_t n,
+                                int32_t *__restrict__ keys)
 {
     using TL = Tile<VT>;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        keys[r] = reinterpret_cast<const int32_t *>(tiles + (r / TL::T) * TL::BYTES + NPAR * TL::VBLK)[r % TL::T];
+        keys[r] = reinterpret_cast<const int32_t *>(tiles + (r / TL::T) * tile_bytes + NPAR * TL::VBLK)[r % TL::T];
 }
 
 // knot_ptr[k] = first i with sorted_knot[i] >= k (lower bound), k = 0..nk
@@ -54,12 +55,12 @@ __global__ void k_knot_ptr(const int32_t *__restrict__ sorted_knot, int64_t n, i
 // the 12 attitude coefficients of every row as one contiguous record per row
 // (rows in star order, read plane by plane from the tiles: coalesced)
 template <typename VT>
-__global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t n, VT *__restrict__ rec)
+__global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int64_t n, VT *__restrict__ rec)
 {
     using TL = Tile<VT>;
     constexpr int NA = NAXES * NPARAXIS;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t *src = tiles + (r / TL::T) * TL::BYTES;
+        const uint8_t *src = tiles + (r / TL::T) * tile_bytes;
         const int64_t ri = r % TL::T;
         VT v[NA];
 #pragma unroll
@@ -120,13 +121,12 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t t0 = gw * per, t1 = min(S.n_tiles, t0 + per);
     for (int64_t t = t0; t < t1; ++t) {
-        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
-        const uint8_t *ti = tb + NPAR * Tile<float>::VBLK;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         const int64_t r0 = t * T + lane * R;
 #pragma unroll
         for (int j = 0; j < NINSTR; ++j) {
             int32_t ic[R];
-            load_ints<R>(ti, 1 + j, ic);
+            load_instr<float>(tb, S.iw16, j, ic);
             float a[R];
             load_vals<float, float>(tb, 17 + j, a);
 #pragma unroll
@@ -241,9 +241,9 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     if ((e = cudaMallocFromPoolAsync(&vals_in, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
     if ((e = cudaMallocFromPoolAsync(&perm, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
     if (f32)
-        k_extract_knots<float><<<g, 256, 0, s>>>(tiles, n, keys_in);
+        k_extract_knots<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, keys_in);
     else
-        k_extract_knots<double><<<g, 256, 0, s>>>(tiles, n, keys_in);
+        k_extract_knots<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, keys_in);
     k_iota<<<g, 256, 0, s>>>(vals_in, n);
     if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
@@ -258,10 +258,10 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
                                      c->pool, s)) != cudaSuccess)
         goto done;
     if (f32) {
-        k_att_rows<float><<<g, 256, 0, s>>>(tiles, n, (float *)rec);
+        k_att_rows<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, (float *)rec);
         k_gather_att<float><<<g, 256, 0, s>>>((const float *)rec, perm, n, (uint8_t *)c->atiles);
     } else {
-        k_att_rows<double><<<g, 256, 0, s>>>(tiles, n, (double *)rec);
+        k_att_rows<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, (double *)rec);
         k_gather_att<double><<<g, 256, 0, s>>>((const double *)rec, perm, n, (uint8_t *)c->atiles);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto done;

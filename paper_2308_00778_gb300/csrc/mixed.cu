@@ -51,13 +51,13 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
     const float2 xg = S.n_glob ? xhl[S.glob0] : make_float2(0.f, 0.f);
     float ssq = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
-        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         const uint8_t *ti = tb + NPAR * Tile<float>::VBLK;
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_ints<R>(ti, 1 + j, ic[j]);
+        for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
         float a[NPAR][R];
 #pragma unroll
         for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);

@@ -5,7 +5,8 @@
 // record of 31 planes:
 //   24 value planes   (T values each = 512 bytes)   slots: 0-4 astro, 5-16 attitude, 17-22 instr, 23 global
 //    1 knot plane     (T int32)
-//    6 instr planes   (T int32, instrumental index in [0, n_instr))
+//    6 instr planes   (T instrumental indices in [0, n_instr): 16-bit when n_instr <= 65536,
+//                      else 32-bit; SysView::iw16 says which, SysView::tile_bytes the record size)
 // Lane l of a warp owns rows [l*R, l*R + R) of a tile and reads each value plane
 // with one 16-byte load, so a warp reads a tile as one contiguous block and
 // warps working on consecutive tiles stream consecutive memory (measured:
@@ -26,8 +27,9 @@ struct Tile {
     static constexpr int T = 32 * R;                                  // rows per tile
     static constexpr int64_t VBLK = (int64_t)T * sizeof(VT);          // 512 bytes
     static constexpr int64_t IBLK = (int64_t)T * sizeof(int32_t);     // int32 plane
-    static constexpr int64_t BYTES = NPAR * VBLK + (1 + NINSTR) * IBLK;
     static constexpr int64_t ABYTES = NAXES * NPARAXIS * VBLK + IBLK;  // knot-ordered attitude tile
+    // bytes of a star-ordered tile record with 16- or 32-bit instrumental planes
+    static constexpr int64_t bytes(bool iw16) { return NPAR * VBLK + IBLK + NINSTR * T * (iw16 ? 2 : 4); }
 };
 
 template <typename VT>
@@ -81,6 +83,45 @@ __device__ __forceinline__ void load_ints(const uint8_t *__restrict__ ints, int 
         out[0] = v.x;
         out[1] = v.y;
     }
+}
+
+// instrumental-column plane j (0..5) of the tile record at tb, this lane's R entries
+template <typename VT>
+__device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, bool iw16, int j,
+                                           int32_t (&out)[Tile<VT>::R])
+{
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
+    const int lane = threadIdx.x & 31;
+    const uint8_t *p = tb + NPAR * Tile<VT>::VBLK + Tile<VT>::IBLK;  // the first instrumental plane
+    if (iw16) {
+        p += (int64_t)j * T * 2;
+        if constexpr (R == 4) {
+            const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p) + lane);
+            out[0] = (int32_t)(v.x & 0xffffu);
+            out[1] = (int32_t)(v.x >> 16);
+            out[2] = (int32_t)(v.y & 0xffffu);
+            out[3] = (int32_t)(v.y >> 16);
+        } else {
+            const uint32_t v = __ldcs(reinterpret_cast<const uint32_t *>(p) + lane);
+            out[0] = (int32_t)(v & 0xffffu);
+            out[1] = (int32_t)(v >> 16);
+        }
+    } else {
+        load_ints<R>(p + (int64_t)j * T * 4, 0, out);
+    }
+}
+
+// write instrumental index v of row i (0..T-1) into plane j of the tile record at tb
+template <typename VT>
+__device__ __forceinline__ void store_instr(uint8_t *__restrict__ tb, bool iw16, int j, int i, int32_t v)
+{
+    constexpr int T = Tile<VT>::T;
+    uint8_t *p = tb + NPAR * Tile<VT>::VBLK + Tile<VT>::IBLK;
+    if (iw16)
+        reinterpret_cast<uint16_t *>(p + (int64_t)j * T * 2)[i] = (uint16_t)v;
+    else
+        reinterpret_cast<int32_t *>(p + (int64_t)j * T * 4)[i] = v;
 }
 
 // The star of row r of tile t: the largest s in [first_star[t], first_star[t+1]]

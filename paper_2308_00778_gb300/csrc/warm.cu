@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
     for (int j = 0; j < NNORM; ++j) acc[j] = 0.f;
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;
     for (int64_t t = t0; t < t1; ++t) {
-        const uint8_t *tb = S.tiles + t * Tile<VT>::BYTES;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         const int64_t r0 = t * T + lane * R;
         float rv[R];
         load_rows<RT, R>(r, r0, S.n_rows, rv);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float ssq = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
-        const uint8_t *tb = S.tiles + t * Tile<float>::BYTES;
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
         float a[NASTRO][R];
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) load_vals<float, float>(tb, j, a[j]);

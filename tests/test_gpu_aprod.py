@@ -25,6 +25,7 @@ CASES = {
     "ragged_many": gsrgen.make_cfg(31, 3000, (1, 300), 250, 40),
     "wide_att_global": gsrgen.make_cfg(33, 400, 100, 20000, 15000),   # accumulators too big for shared memory
     "wide_att_instr_smem": gsrgen.make_cfg(34, 400, 100, 6000, 2000),  # attitude global, instr shared
+    "instr_32bit": gsrgen.make_cfg(35, 2000, 100, 100, 70000),  # n_instr > 65536: 32-bit instrumental planes
 }
 
 
