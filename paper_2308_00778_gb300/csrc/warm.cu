@@ -259,15 +259,28 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+        const bool full = r0 + R <= S.n_rows;  // all of this lane's rows exist: one 16-byte access
+        float v[R];
+        if (full) {
+            const float4 q = *reinterpret_cast<const float4 *>(r + r0);
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) v[i] = r0 + i < S.n_rows ? r[r0 + i] : 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            if (r0 + i >= S.n_rows) continue;
             const double *xa = x0 + NASTRO * sr[i];
-            float v = r[r0 + i];
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) v = fmaf(-a[j][i], (float)__ldg(xa + j), v);
-            r[r0 + i] = v;
-            ssq = fmaf(v, v, ssq);
+            for (int j = 0; j < NASTRO; ++j) v[i] = fmaf(-a[j][i], (float)__ldg(xa + j), v[i]);
+            if (r0 + i < S.n_rows) ssq = fmaf(v[i], v[i], ssq);
+        }
+        if (full) {
+            *reinterpret_cast<float4 *>(r + r0) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (r0 + i < S.n_rows) r[r0 + i] = v[i];
         }
     }
     const double tot = block_sum((double)ssq, sm32);
