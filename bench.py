@@ -52,11 +52,12 @@ BYTES = {
     "residual_df": 24 * 4 + 4 + 12 + 8 + 4,  # values, indices, b (binary64), r write      = 124
 }
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
-# DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
-# binary32 kernels on the 2e7-row workload; a launch's traffic is this figure times its rows. The binary64
-# kernels are bound by the binary64 units and have no capture (None).
-TRAFFIC_PER_ROW = {"aprod1_f32": None, "aprod2_f32": None, "residual_df": None, "aprod1_f64": None,
-                   "aprod2_f64": None}
+# DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu on the
+# 2e7-row workload (one-pass capture of the standalone launches the benchmark times); a launch's traffic is
+# this figure times its rows. aprod2_f32 is the max pass, the star pass and the attitude pass together.
+TRAFFIC_WORKLOAD = "c2"
+TRAFFIC_PER_ROW = {"aprod1_f32": 117.3, "aprod2_f32": 128.2, "residual_df": 121.4, "aprod1_f64": 221.4,
+                   "aprod2_f64": 275.2}
 
 
 def parse_args():
@@ -474,11 +475,13 @@ def run_ours(args):
         "aprod2_f32": _time_kernel(torch, lambda: ctx32.aprod2_f32(u32, z, stream=sh), stream),
         "residual_df": _time_kernel(torch, lambda: ctx32.residual(xs, r32, stream=sh), stream),
     }
+    traffic = TRAFFIC_PER_ROW if args.workload == TRAFFIC_WORKLOAD else {}
     kern = {}
     for name, kms in t.items():
         bpr = BYTES[name] + (12 if cfg.n_instr > 65536 else 0)  # 32-bit instrumental planes
         kern[name] = {"ms": kms, "GB/s": bpr * n / (kms * 1e-3) / 1e9, "bytes_per_row": bpr,
-                      "TFLOP/s": FLOPS_PER_ROW * n / (kms * 1e-3) / 1e12}
+                      "TFLOP/s": FLOPS_PER_ROW * n / (kms * 1e-3) / 1e12,
+                      "ncu_dram_bytes_per_row": traffic.get(name)}
     peaks = load_peaks()
     # launches of each hot kernel in one step of the headline solver (the dominant one is the roofline's)
     hctx, hkw, hmeta = legs[headline]
@@ -496,10 +499,11 @@ def run_ours(args):
     if dom.endswith("f64"):
         fp64_peak = 1.25
         roof = {"kernel": dom, "bound": "alu", "achieved": kern[dom]["TFLOP/s"], "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": kern[dom]["TFLOP/s"] / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": kern[dom]["TFLOP/s"] / fp64_peak,
+                "traffic": traffic[dom] * n if traffic.get(dom) else None,
                 "peak_src": "nominal FP64 of the profiling recipe"}
     else:
-        tr = TRAFFIC_PER_ROW.get(dom)
+        tr = traffic.get(dom)
         roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": kern[dom]["GB/s"] / peaks["hbm_gbs"],
                 "traffic": tr * n if tr else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
