@@ -9,7 +9,9 @@ bit-identical output.
 
 Row model (paper Sec. 2): 24 coefficients per observation (5 astrometric,
 3 axes x 4 attitude knots, 6 instrumental, 1 global), rows grouped by star,
-observation times sorted within a star.
+observation times sorted within a star. Section variants (0..5 astrometric
+and 0..6 instrumental coefficients per row, 0..5 globals) give compact rows of
+n_astro + 12 + n_ipr + n_glob coefficients (``Cfg.npar``).
 """
 from __future__ import annotations
 
@@ -35,19 +37,35 @@ class Cfg(ctypes.Structure):
         ("n_glob", ctypes.c_int32),
         ("att_kind", ctypes.c_int32),
         ("noise_sigma", ctypes.c_double),
+        ("n_astro", ctypes.c_int32),
+        ("n_ipr", ctypes.c_int32),
     ]
 
     def ncols(self) -> int:
-        return 5 * self.n_stars + 3 * self.n_dfa + self.n_instr + self.n_glob
+        return self.n_astro * self.n_stars + 3 * self.n_dfa + self.n_instr + self.n_glob
+
+    @property
+    def standard(self) -> bool:
+        """The paper's standard sections (5 astrometric, 6 instrumental per row, at most 1 global)."""
+        return self.n_astro == 5 and self.n_ipr == 6 and self.n_glob <= 1
+
+    @property
+    def npar(self) -> int:
+        """Coefficients per generated row: 24 for the standard sections, else the compact row."""
+        return 24 if self.standard else self.n_astro + 12 + self.n_ipr + self.n_glob
 
     def describe(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-def make_cfg(seed, n_stars, obs, n_dfa, n_instr, n_glob=1, att_kind=0, noise_sigma=1e-3) -> Cfg:
-    """obs is an int (fixed observations per star) or a (min, max) pair."""
+def make_cfg(seed, n_stars, obs, n_dfa, n_instr, n_glob=1, att_kind=0, noise_sigma=1e-3, n_astro=5,
+             n_ipr=6) -> Cfg:
+    """obs is an int (fixed observations per star) or a (min, max) pair. n_astro (0..5), n_ipr (0..6,
+    at most n_instr) and n_glob (0..5) choose the sections of a row."""
     lo, hi = (obs, obs) if isinstance(obs, int) else obs
-    return Cfg(seed, n_stars, lo, hi, n_dfa, n_instr, n_glob, att_kind, noise_sigma)
+    if not (0 <= n_astro <= 5 and 0 <= n_ipr <= min(6, n_instr) and 0 <= n_glob <= 5):
+        raise ValueError("sections: n_astro in [0, 5], n_ipr in [0, min(6, n_instr)], n_glob in [0, 5]")
+    return Cfg(seed, n_stars, lo, hi, n_dfa, n_instr, n_glob, att_kind, noise_sigma, n_astro, n_ipr)
 
 
 @dataclass(frozen=True)
@@ -133,16 +151,16 @@ def star_ptr(cfg: Cfg) -> np.ndarray:
 
 
 def rows(cfg: Cfg, sp: np.ndarray, s0: int, s1: int, fp32: bool = False, want32: bool = False):
-    """Rows of stars [s0, s1): (A_d as float64 n x 24, knot, instr n x 6[, A_d as float32]).
+    """Rows of stars [s0, s1): (A_d as float64 n x npar, knot, instr n x n_ipr[, A_d as float32]).
 
     With fp32 the float64 values are the binary32-rounded coefficients widened
     back (exactly what an FP32-stored system holds)."""
     lib = _load_host()
     n = int(sp[s1] - sp[s0])
-    A = np.empty((n, 24), dtype=np.float64)
-    A32 = np.empty((n, 24), dtype=np.float32) if want32 else None
+    A = np.empty((n, cfg.npar), dtype=np.float64)
+    A32 = np.empty((n, cfg.npar), dtype=np.float32) if want32 else None
     knot = np.empty(n, dtype=np.int32)
-    instr = np.empty((n, 6), dtype=np.int32)
+    instr = np.empty((n, cfg.n_ipr), dtype=np.int32)
     if n > 0:
         lib.gsrgen_host_rows(ctypes.byref(cfg), _ptr(sp), s0, s1, 1 if fp32 else 0, _ptr(A),
                              _ptr(A32) if want32 else None, _ptr(knot), _ptr(instr))
@@ -175,7 +193,7 @@ class HostSystem:
 
     cfg: Cfg
     star_ptr: np.ndarray
-    A: np.ndarray       # n x 24 float64 (binary32-rounded values when fp32)
+    A: np.ndarray       # n x npar float64 (binary32-rounded values when fp32)
     knot: np.ndarray
     instr: np.ndarray
     x_true: np.ndarray

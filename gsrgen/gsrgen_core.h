@@ -15,6 +15,16 @@
  * each star sorted, so the attitude knot of a row is nondecreasing within a
  * star.
  *
+ * Section variants (Sec. 2 allows 0..5 astrometric and 0..6 instrumental
+ * coefficients per row, and a global section of several unknowns or none):
+ * n_astro, n_ipr (instrumental coefficients per row) and n_glob. The paper's
+ * standard sections (5, 6, n_glob <= 1) keep the 24-slot row (slot 23 zero
+ * without a global); any other choice gives the compact row of
+ * n_astro + 12 + n_ipr + n_glob coefficients [astro | attitude | instr | glob].
+ * A coefficient present in both draws the same number: compact position j
+ * maps to the standard slot it stands for, and globals past the first draw
+ * from a tag of their own.
+ *
  * Random source: the SplitMix64 output function (Steele, Lea & Flood, "Fast
  * splittable pseudorandom number generators", OOPSLA 2014) applied to a
  * counter, keyed by (seed, tag). Each draw is a pure function of
@@ -45,6 +55,7 @@
 #define GSRGEN_NATT 12
 #define GSRGEN_NINSTR 6
 #define GSRGEN_MAX_OBS 4096
+#define GSRGEN_MAX_GLOB 5
 
 /* draw tags: one independent stream per kind of quantity */
 enum {
@@ -54,7 +65,8 @@ enum {
     GSRGEN_TAG_VAL = 4,   /* coefficients                    idx = row*24+slot  */
     GSRGEN_TAG_XTRUE = 5, /* planted solution                idx = column       */
     GSRGEN_TAG_SIN = 6,   /* attitude sinusoid parameters    idx = axis*8+m     */
-    GSRGEN_TAG_NOISE = 7  /* observation noise               idx = row          */
+    GSRGEN_TAG_NOISE = 7, /* observation noise               idx = row          */
+    GSRGEN_TAG_GLOB = 8   /* global coefficients 2..         idx = row*8+g-1    */
 };
 
 typedef struct {
@@ -66,6 +78,8 @@ typedef struct {
     int32_t n_glob;           /* global columns, 0 or 1                        */
     int32_t att_kind;         /* planted attitude: 0 = N(0,1), 1 = 8 sinusoids */
     double noise_sigma;       /* standard deviation of the observation noise   */
+    int32_t n_astro;          /* astrometric coefficients per row, 0..5        */
+    int32_t n_ipr;            /* instrumental coefficients per row, 0..6       */
 } gsrgen_cfg;
 
 GSRGEN_FN uint64_t gsrgen_mix64(uint64_t z)
@@ -219,7 +233,19 @@ GSRGEN_FN double gsrgen_normal_at(uint64_t seed, uint32_t tag, uint64_t idx)
 
 GSRGEN_FN int64_t gsrgen_ncols(const gsrgen_cfg *c)
 {
-    return 5LL * c->n_stars + 3LL * c->n_dfa + c->n_instr + c->n_glob;
+    return (int64_t)c->n_astro * c->n_stars + 3LL * c->n_dfa + c->n_instr + c->n_glob;
+}
+
+/* the paper's standard sections: 24-slot rows */
+GSRGEN_FN int32_t gsrgen_standard(const gsrgen_cfg *c)
+{
+    return c->n_astro == GSRGEN_NASTRO && c->n_ipr == GSRGEN_NINSTR && c->n_glob <= 1;
+}
+
+/* coefficients per generated row */
+GSRGEN_FN int32_t gsrgen_npar(const gsrgen_cfg *c)
+{
+    return gsrgen_standard(c) ? GSRGEN_NPAR : c->n_astro + GSRGEN_NATT + c->n_ipr + c->n_glob;
 }
 
 GSRGEN_FN int32_t gsrgen_obs_of_star(const gsrgen_cfg *c, int64_t star)
@@ -235,11 +261,13 @@ GSRGEN_FN int32_t gsrgen_knot_raw(const gsrgen_cfg *c, int64_t row)
     return gsrgen_below(gsrgen_bits(c->seed, GSRGEN_TAG_TIME, (uint64_t)row, 0), c->n_dfa - 3);
 }
 
-/* 6 distinct instrumental columns of a row in [0, n_instr), in draw order */
+/* n_ipr distinct instrumental columns of a row in [0, n_instr), in draw order
+ * (a prefix of the same draws for every n_ipr) */
 GSRGEN_FN void gsrgen_instr_row(const gsrgen_cfg *c, int64_t row, int32_t out[6])
 {
+    const int32_t want = c->n_ipr;
     int32_t got = 0;
-    for (int32_t a = 0; a < 64 && got < 6; ++a) {
+    for (int32_t a = 0; a < 64 && got < want; ++a) {
         int32_t v = gsrgen_below(gsrgen_bits(c->seed, GSRGEN_TAG_INSTR, (uint64_t)row * 64ULL + (uint64_t)a, 0),
                                  c->n_instr);
         int32_t dup = 0;
@@ -247,15 +275,29 @@ GSRGEN_FN void gsrgen_instr_row(const gsrgen_cfg *c, int64_t row, int32_t out[6]
         if (!dup) out[got++] = v;
     }
     /* deterministic completion in the (astronomically rare) case of 64 collisions */
-    for (int32_t v = 0; got < 6; ++v) {
+    for (int32_t v = 0; got < want; ++v) {
         int32_t dup = 0;
         for (int32_t k = 0; k < got; ++k) dup |= (out[k] == v);
         if (!dup) out[got++] = v;
     }
 }
 
-GSRGEN_FN double gsrgen_value(const gsrgen_cfg *c, int64_t row, int32_t slot)
+/* coefficient j (0 <= j < gsrgen_npar) of a row */
+GSRGEN_FN double gsrgen_value(const gsrgen_cfg *c, int64_t row, int32_t j)
 {
+    int32_t slot = j; /* the standard slot it stands for */
+    if (!gsrgen_standard(c)) {
+        const int32_t na = c->n_astro, ni = c->n_ipr;
+        if (j < na) slot = j;
+        else if (j < na + GSRGEN_NATT) slot = GSRGEN_NASTRO + (j - na);
+        else if (j < na + GSRGEN_NATT + ni) slot = GSRGEN_NASTRO + GSRGEN_NATT + (j - na - GSRGEN_NATT);
+        else {
+            const int32_t g = j - (na + GSRGEN_NATT + ni);
+            if (g > 0)
+                return gsrgen_normal_at(c->seed, GSRGEN_TAG_GLOB, (uint64_t)row * 8ULL + (uint64_t)(g - 1));
+            slot = GSRGEN_NPAR - 1;
+        }
+    }
     if (slot == GSRGEN_NPAR - 1 && c->n_glob == 0) return 0.0;
     return gsrgen_normal_at(c->seed, GSRGEN_TAG_VAL, (uint64_t)row * GSRGEN_NPAR + (uint64_t)slot);
 }
@@ -265,10 +307,10 @@ GSRGEN_FN double gsrgen_noise(const gsrgen_cfg *c, int64_t row)
     return c->noise_sigma * gsrgen_normal_at(c->seed, GSRGEN_TAG_NOISE, (uint64_t)row);
 }
 
-/* planted solution, column layout [astro 5*n_stars | att axis0 | axis1 | axis2 | instr | glob] */
+/* planted solution, column layout [astro n_astro*n_stars | att axis0 | axis1 | axis2 | instr | glob] */
 GSRGEN_FN double gsrgen_xtrue(const gsrgen_cfg *c, int64_t col)
 {
-    int64_t att0 = 5LL * c->n_stars;
+    int64_t att0 = (int64_t)c->n_astro * c->n_stars;
     int64_t att1 = att0 + 3LL * c->n_dfa;
     if (c->att_kind == 1 && col >= att0 && col < att1) {
         int64_t a = col - att0;

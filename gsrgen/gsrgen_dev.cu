@@ -7,8 +7,8 @@
  * compiled with -fmad=false, so every value is bit-identical to the host's.
  *
  * Row arrays are written as SoA planes: plane j of the values starts at
- * vals + j*plane_stride (24 planes), plane j of the instrumental columns at
- * instr + j*plane_stride (6 planes). Row r of the chunk is at offset
+ * vals + j*plane_stride (gsrgen_npar planes: 24 for the standard sections),
+ * plane j of the instrumental columns at instr + j*plane_stride (n_ipr planes). Row r of the chunk is at offset
  * r - star_ptr[s0] within each plane.
  */
 #include "gsrgen_core.h"
@@ -40,7 +40,7 @@ __global__ void gsrgen_knots_kernel(gsrgen_cfg c, const int64_t *__restrict__ st
     }
 }
 
-/* one thread per row: instrumental columns and the 24 coefficients */
+/* one thread per row: instrumental columns and the coefficients */
 template <typename VT>
 __global__ void gsrgen_rows_kernel(gsrgen_cfg c, int64_t row0, int64_t nrow, int64_t plane_stride, int32_t round32,
                                    VT *__restrict__ vals, int32_t *__restrict__ instr)
@@ -50,8 +50,9 @@ __global__ void gsrgen_rows_kernel(gsrgen_cfg c, int64_t row0, int64_t nrow, int
     const int64_t r = row0 + o;
     int32_t ic[6];
     gsrgen_instr_row(&c, r, ic);
-    for (int j = 0; j < 6; ++j) instr[(int64_t)j * plane_stride + o] = ic[j];
-    for (int j = 0; j < GSRGEN_NPAR; ++j) {
+    for (int j = 0; j < c.n_ipr; ++j) instr[(int64_t)j * plane_stride + o] = ic[j];
+    const int np = gsrgen_npar(&c);
+    for (int j = 0; j < np; ++j) {
         double v = gsrgen_value(&c, r, j);
         if (round32) v = (double)(float)v;
         vals[(int64_t)j * plane_stride + o] = (VT)v;

@@ -45,17 +45,19 @@ static void sort_i32(int32_t *a, int32_t n)
 
 /*
  * Rows of stars [s0, s1). Output arrays are indexed from row star_ptr[s0]:
- *   vals64 : AoS, 24 coefficients per row as doubles; with round32 != 0 each
+ *   vals64 : AoS, gsrgen_npar coefficients per row as doubles (24 for the
+ *            standard sections); with round32 != 0 each
  *            value is first rounded to binary32 (what an FP32-stored system
  *            holds), widened back exactly. May be NULL.
  *   vals32 : AoS, the same coefficients rounded to binary32. May be NULL.
  *   knot   : first attitude knot of the row, nondecreasing within a star
- *   instr  : 6 instrumental columns per row
+ *   instr  : n_ipr instrumental columns per row
  */
 GSRGEN_API void gsrgen_host_rows(const gsrgen_cfg *c, const int64_t *star_ptr, int64_t s0, int64_t s1,
                                  int32_t round32, double *vals64, float *vals32, int32_t *knot, int32_t *instr)
 {
     const int64_t base = star_ptr[s0];
+    const int32_t np = gsrgen_npar(c), ni = c->n_ipr;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t s = s0; s < s1; ++s) {
         const int64_t r0 = star_ptr[s], r1 = star_ptr[s + 1];
@@ -64,11 +66,13 @@ GSRGEN_API void gsrgen_host_rows(const gsrgen_cfg *c, const int64_t *star_ptr, i
         sort_i32(kn, (int32_t)(r1 - r0));
         for (int64_t r = r0; r < r1; ++r) {
             const int64_t o = r - base;
-            gsrgen_instr_row(c, r, instr + o * 6);
-            for (int32_t j = 0; j < GSRGEN_NPAR; ++j) {
+            int32_t ic[6];
+            gsrgen_instr_row(c, r, ic);
+            for (int32_t j = 0; j < ni; ++j) instr[o * ni + j] = ic[j];
+            for (int32_t j = 0; j < np; ++j) {
                 double v = gsrgen_value(c, r, j);
-                if (vals64) vals64[o * GSRGEN_NPAR + j] = round32 ? (double)(float)v : v;
-                if (vals32) vals32[o * GSRGEN_NPAR + j] = (float)v;
+                if (vals64) vals64[o * np + j] = round32 ? (double)(float)v : v;
+                if (vals32) vals32[o * np + j] = (float)v;
             }
         }
     }

@@ -28,6 +28,9 @@ class _Sys(ctypes.Structure):
         ("A", ctypes.c_void_p),
         ("knot", ctypes.c_void_p),
         ("instr", ctypes.c_void_p),
+        ("n_astro", ctypes.c_int32),
+        ("n_ipr", ctypes.c_int32),
+        ("npar", ctypes.c_int32),
     ]
 
 
@@ -117,7 +120,11 @@ def _p(a: np.ndarray) -> int:
 
 @dataclass
 class System:
-    """A system in the paper's storage: A_d (n x 24), knot (M_i's attitude part), instr (I_c)."""
+    """A system in the paper's storage: A_d (n x npar), knot (M_i's attitude part), instr (I_c, n x n_ipr).
+
+    Sections (Sec. 2): n_astro astrometric (0..5), 12 attitude, n_ipr instrumental (0..6) and n_glob
+    global (0..5) coefficients per row. The standard sections (5, 6, n_glob <= 1) use the paper's
+    24-slot row; other choices the compact row of n_astro + 12 + n_ipr + n_glob."""
 
     star_ptr: np.ndarray
     A: np.ndarray
@@ -126,14 +133,19 @@ class System:
     n_dfa: int
     n_instr: int
     n_glob: int
+    n_astro: int = 5
+    n_ipr: int = 6
 
     def __post_init__(self):
         self.star_ptr = np.ascontiguousarray(self.star_ptr, dtype=np.int64)
         self.A = np.ascontiguousarray(self.A, dtype=np.float64)
         self.knot = np.ascontiguousarray(self.knot, dtype=np.int32)
-        self.instr = np.ascontiguousarray(self.instr, dtype=np.int32)
+        self.instr = np.ascontiguousarray(self.instr, dtype=np.int32).reshape(len(self.knot), self.n_ipr)
+        std = self.n_astro == 5 and self.n_ipr == 6 and self.n_glob <= 1
+        self.npar = 24 if std else self.n_astro + 12 + self.n_ipr + self.n_glob
+        assert self.A.shape == (len(self.knot), self.npar), (self.A.shape, self.npar)
         self._s = _Sys(int(self.star_ptr[-1]), len(self.star_ptr) - 1, _p(self.star_ptr), self.n_dfa, self.n_instr,
-                       self.n_glob, _p(self.A), _p(self.knot), _p(self.instr))
+                       self.n_glob, _p(self.A), _p(self.knot), _p(self.instr), self.n_astro, self.n_ipr, self.npar)
 
     @property
     def n_rows(self) -> int:
@@ -145,18 +157,19 @@ class System:
 
     @property
     def n_cols(self) -> int:
-        return 5 * self.n_stars + 3 * self.n_dfa + self.n_instr + self.n_glob
+        return self.n_astro * self.n_stars + 3 * self.n_dfa + self.n_instr + self.n_glob
 
     def blocks(self) -> dict:
         """Column ranges of the four sections of x (Sec. 2)."""
-        a = 5 * self.n_stars
+        a = self.n_astro * self.n_stars
         t = a + 3 * self.n_dfa
         i = t + self.n_instr
         return {"astro": (0, a), "att": (a, t), "instr": (t, i), "glob": (i, i + self.n_glob)}
 
 
 def from_host_system(hs) -> System:
-    return System(hs.star_ptr, hs.A, hs.knot, hs.instr, hs.cfg.n_dfa, hs.cfg.n_instr, hs.cfg.n_glob)
+    c = hs.cfg
+    return System(hs.star_ptr, hs.A, hs.knot, hs.instr, c.n_dfa, c.n_instr, c.n_glob, c.n_astro, c.n_ipr)
 
 
 def aprod1(s: System, x: np.ndarray, y: np.ndarray) -> np.ndarray:
@@ -261,7 +274,7 @@ def adam(w, m, v, g, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):
 
 
 def astro_solve(s: System, b: np.ndarray, x: np.ndarray) -> int:
-    """Per-star 5x5 astrometric solve given the attitude part of x (in place). Returns failed stars."""
+    """Per-star n_astro x n_astro astrometric solve given the other parts of x (in place). Returns failed stars."""
     b = np.ascontiguousarray(b, dtype=np.float64)
     assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
     return int(_load().oracle_astro_solve(ctypes.byref(s._s), _p(b), _p(x)))

@@ -4,7 +4,7 @@
  * TEST INFRASTRUCTURE (see oracle.h): loaded only by the tests, the smoke
  * check and the benchmark's CPU baseline. Shares no code with the GPU path.
  *
- * Column layout of x (Sec. 2): [astro 5*n_stars | attitude axis 0, 1, 2
+ * Column layout of x (Sec. 2): [astro n_astro*n_stars | attitude axis 0, 1, 2
  * (n_dfa each) | instrumental n_instr | global n_glob].
  */
 #include "oracle.h"
@@ -15,37 +15,38 @@
 
 #define ORACLE_API __attribute__((visibility("default")))
 
-enum { N_ASTRO = 5, N_AXES = 3, N_PAR_AXIS = 4, N_INSTR = 6 };
+enum { N_AXES = 3, N_PAR_AXIS = 4 };
 
 ORACLE_API int64_t oracle_ncols(const oracle_sys *s)
 {
-    return (int64_t)N_ASTRO * s->n_stars + (int64_t)N_AXES * s->n_dfa + s->n_instr + s->n_glob;
+    return (int64_t)s->n_astro * s->n_stars + (int64_t)N_AXES * s->n_dfa + s->n_instr + s->n_glob;
 }
 
 /*
  * aprod 1, Eq. 2: y += A x. The row loop of Alg. 2 (OpenMP column): one sum
  * per observation over its astrometric, attitude, instrumental and global
- * sections, then added to y[i]. The astrometric offset of a row is 5 * (its
- * star); the attitude offset of axis a is a*n_dfa + knot[i]; the
- * instrumental map F(i,j) is the stored column instr[i*6+j].
+ * sections, then added to y[i]. The astrometric offset of a row is n_astro *
+ * (its star); the attitude offset of axis a is a*n_dfa + knot[i]; the
+ * instrumental map F(i,j) is the stored column instr[i*n_ipr+j].
  */
 static void aprod1_impl(const oracle_sys *s, const double *x, double *y)
 {
-    const int64_t att0 = (int64_t)N_ASTRO * s->n_stars;
+    const int na = s->n_astro, ni = s->n_ipr;
+    const int64_t att0 = (int64_t)na * s->n_stars;
     const int64_t instr0 = att0 + (int64_t)N_AXES * s->n_dfa;
     const int64_t glob0 = instr0 + s->n_instr;
     for (int64_t star = 0; star < s->n_stars; ++star) {
-        const int64_t offset_astro = (int64_t)N_ASTRO * star;
+        const int64_t offset_astro = (int64_t)na * star;
         for (int64_t i = s->star_ptr[star]; i < s->star_ptr[star + 1]; ++i) {
-            const double *a = s->A + i * ORACLE_NPAR;
+            const double *a = s->A + i * s->npar;
             double sum = 0.0;
             int k = 0;
-            for (int j = 0; j < N_ASTRO; ++j, ++k) sum = sum + a[k] * x[offset_astro + j];
+            for (int j = 0; j < na; ++j, ++k) sum = sum + a[k] * x[offset_astro + j];
             for (int ax = 0; ax < N_AXES; ++ax) {
                 const int64_t k2 = att0 + (int64_t)ax * s->n_dfa + s->knot[i];
                 for (int j2 = 0; j2 < N_PAR_AXIS; ++j2, ++k) sum = sum + a[k] * x[k2 + j2];
             }
-            for (int j = 0; j < N_INSTR; ++j, ++k) sum = sum + a[k] * x[instr0 + s->instr[i * N_INSTR + j]];
+            for (int j = 0; j < ni; ++j, ++k) sum = sum + a[k] * x[instr0 + s->instr[i * ni + j]];
             for (int j = 0; j < s->n_glob; ++j) sum = sum + a[k + j] * x[glob0 + j];
             y[i] = y[i] + sum;
         }
@@ -58,22 +59,23 @@ static void aprod1_impl(const oracle_sys *s, const double *x, double *y)
  */
 static void aprod2_impl(const oracle_sys *s, const double *y, double *x)
 {
-    const int64_t att0 = (int64_t)N_ASTRO * s->n_stars;
+    const int na = s->n_astro, ni = s->n_ipr;
+    const int64_t att0 = (int64_t)na * s->n_stars;
     const int64_t instr0 = att0 + (int64_t)N_AXES * s->n_dfa;
     const int64_t glob0 = instr0 + s->n_instr;
     for (int64_t star = 0; star < s->n_stars; ++star) {
-        const int64_t offset_astro = (int64_t)N_ASTRO * star;
+        const int64_t offset_astro = (int64_t)na * star;
         for (int64_t i = s->star_ptr[star]; i < s->star_ptr[star + 1]; ++i) {
-            const double *a = s->A + i * ORACLE_NPAR;
+            const double *a = s->A + i * s->npar;
             const double yi = y[i];
             int k = 0;
-            for (int j = 0; j < N_ASTRO; ++j, ++k) x[offset_astro + j] = x[offset_astro + j] + a[k] * yi;
+            for (int j = 0; j < na; ++j, ++k) x[offset_astro + j] = x[offset_astro + j] + a[k] * yi;
             for (int ax = 0; ax < N_AXES; ++ax) {
                 const int64_t k2 = att0 + (int64_t)ax * s->n_dfa + s->knot[i];
                 for (int j2 = 0; j2 < N_PAR_AXIS; ++j2, ++k) x[k2 + j2] = x[k2 + j2] + a[k] * yi;
             }
-            for (int j = 0; j < N_INSTR; ++j, ++k) {
-                const int64_t c = instr0 + s->instr[i * N_INSTR + j];
+            for (int j = 0; j < ni; ++j, ++k) {
+                const int64_t c = instr0 + s->instr[i * ni + j];
                 x[c] = x[c] + a[k] * yi;
             }
             for (int j = 0; j < s->n_glob; ++j) x[glob0 + j] = x[glob0 + j] + a[k + j] * yi;
@@ -122,9 +124,10 @@ ORACLE_API void oracle_precond(const oracle_sys *s, double *p)
 {
     const int64_t nc = oracle_ncols(s);
     oracle_sys sq = *s;
-    double *A2 = (double *)malloc(sizeof(double) * (size_t)(s->n_rows * ORACLE_NPAR));
+    const int64_t nv = s->n_rows * s->npar;
+    double *A2 = (double *)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
     double *ones = (double *)malloc(sizeof(double) * (size_t)(s->n_rows > 0 ? s->n_rows : 1));
-    for (int64_t i = 0; i < s->n_rows * ORACLE_NPAR; ++i) A2[i] = s->A[i] * s->A[i];
+    for (int64_t i = 0; i < nv; ++i) A2[i] = s->A[i] * s->A[i];
     for (int64_t i = 0; i < s->n_rows; ++i) ones[i] = 1.0;
     sq.A = A2;
     for (int64_t j = 0; j < nc; ++j) p[j] = 0.0;
@@ -137,21 +140,23 @@ ORACLE_API void oracle_precond(const oracle_sys *s, double *p)
 /* "Normalization of A by p" (Alg. 1): every coefficient times p of its column */
 ORACLE_API void oracle_scale_columns(const oracle_sys *s, const double *p, double *A_out)
 {
-    const int64_t att0 = (int64_t)N_ASTRO * s->n_stars;
+    const int na = s->n_astro, ni = s->n_ipr;
+    const int64_t att0 = (int64_t)na * s->n_stars;
     const int64_t instr0 = att0 + (int64_t)N_AXES * s->n_dfa;
     const int64_t glob0 = instr0 + s->n_instr;
     for (int64_t star = 0; star < s->n_stars; ++star) {
         for (int64_t i = s->star_ptr[star]; i < s->star_ptr[star + 1]; ++i) {
-            const double *a = s->A + i * ORACLE_NPAR;
-            double *o = A_out + i * ORACLE_NPAR;
+            const double *a = s->A + i * s->npar;
+            double *o = A_out + i * s->npar;
             int k = 0;
-            for (int j = 0; j < N_ASTRO; ++j, ++k) o[k] = a[k] * p[N_ASTRO * star + j];
+            for (int j = 0; j < na; ++j, ++k) o[k] = a[k] * p[(int64_t)na * star + j];
             for (int ax = 0; ax < N_AXES; ++ax) {
                 const int64_t k2 = att0 + (int64_t)ax * s->n_dfa + s->knot[i];
                 for (int j2 = 0; j2 < N_PAR_AXIS; ++j2, ++k) o[k] = a[k] * p[k2 + j2];
             }
-            for (int j = 0; j < N_INSTR; ++j, ++k) o[k] = a[k] * p[instr0 + s->instr[i * N_INSTR + j]];
-            o[k] = (s->n_glob > 0) ? a[k] * p[glob0] : 0.0;
+            for (int j = 0; j < ni; ++j, ++k) o[k] = a[k] * p[instr0 + s->instr[i * ni + j]];
+            for (int j = 0; j < s->n_glob; ++j, ++k) o[k] = a[k] * p[glob0 + j];
+            for (; k < s->npar; ++k) o[k] = 0.0; /* the standard row's unused global slot */
         }
     }
 }
@@ -178,7 +183,7 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
 {
     const int64_t m = s->n_rows, n = oracle_ncols(s);
     double *p = (double *)malloc(sizeof(double) * (size_t)n);
-    double *At = (double *)malloc(sizeof(double) * (size_t)(m * ORACLE_NPAR > 0 ? m * ORACLE_NPAR : 1));
+    double *At = (double *)malloc(sizeof(double) * (size_t)(m * s->npar > 0 ? m * s->npar : 1));
     double *u = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     double *v = (double *)malloc(sizeof(double) * (size_t)n);
     double *w = (double *)malloc(sizeof(double) * (size_t)n);

@@ -8,16 +8,21 @@
  *
  * Every routine is single-threaded, uses binary64 with round-to-nearest and no
  * FMA contraction (built with -ffp-contract=off), and follows the paper's data
- * layout: the dense-per-row coefficient matrix A_d (Sec. 2) holds 24 values
- * per row, row-major (row i, slot j at A[i*24 + j]); slots [0,5) astrometric,
- * [5,17) attitude (3 axes x 4 knots), [17,23) instrumental, [23] global.
+ * layout: the dense-per-row coefficient matrix A_d (Sec. 2) holds npar values
+ * per row, row-major (row i, slot j at A[i*npar + j]), section by section:
+ * n_astro astrometric, 12 attitude (3 axes x 4 knots), n_ipr instrumental,
+ * n_glob global. The paper's standard row is npar = 24: slots [0,5)
+ * astrometric, [5,17) attitude, [17,23) instrumental, [23] global (ignored
+ * when n_glob = 0). Sec. 2 allows 0 <= n_astro <= 5 and 0 <= n_ipr <= 6
+ * coefficients per row; other section choices use the compact row,
+ * npar = n_astro + 12 + n_ipr + n_glob.
  */
 #ifndef GSR_ORACLE_H
 #define GSR_ORACLE_H
 
 #include <stdint.h>
 
-#define ORACLE_NPAR 24
+#define ORACLE_NPAR 24 /* the paper's standard row */
 
 typedef struct {
     int64_t n_rows;
@@ -25,10 +30,13 @@ typedef struct {
     const int64_t *star_ptr; /* [n_stars+1], rows of star s are [star_ptr[s], star_ptr[s+1]) */
     int32_t n_dfa;           /* attitude degrees of freedom per axis                       */
     int32_t n_instr;         /* instrumental unknowns                                        */
-    int32_t n_glob;          /* global unknowns, 0 or 1                                      */
-    const double *A;         /* A_d, n_rows x 24, row-major                                  */
+    int32_t n_glob;          /* global unknowns (and global coefficients per row), 0..5      */
+    const double *A;         /* A_d, n_rows x npar, row-major                                */
     const int32_t *knot;     /* first attitude knot of each row (same for the 3 axes)        */
-    const int32_t *instr;    /* n_rows x 6 instrumental column indices in [0, n_instr)       */
+    const int32_t *instr;    /* n_rows x n_ipr instrumental column indices in [0, n_instr)   */
+    int32_t n_astro;         /* astrometric unknowns per star = coefficients per row, 0..5   */
+    int32_t n_ipr;           /* instrumental coefficients per row, 0..6                      */
+    int32_t npar;            /* coefficients per row of A: 24, or n_astro+12+n_ipr+n_glob     */
 } oracle_sys;
 
 typedef struct {

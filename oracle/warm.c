@@ -6,7 +6,7 @@
  *
  * The warm start is not part of the paper; it follows the benchmark spec:
  * attitude features from the Jacobi estimate, a six-layer 1D convolutional
- * network over the attitude knots, and per-star 5x5 least-squares solves for
+ * network over the attitude knots, and per-star 5x5 (n_astro x n_astro) least-squares solves for
  * the astrometric block. Activations are stored position-major: a[b][p][c]
  * (sequence b, position p, channel c). A convolution layer with kernel 5 and
  * zero padding 2 computes
@@ -114,44 +114,49 @@ ORACLE_API void oracle_adam(double *w, double *m, double *v, const double *g, in
  * Per-star astrometric solve: for each star s, with r_i = b_i minus the
  * attitude, instrumental and global parts of row i applied to x,
  *   G_s = sum_i a_i a_i^T + lambda_s I,   h_s = sum_i a_i r_i,   x_s = G_s^-1 h_s
- * over the star's rows (a_i = the 5 astrometric coefficients), with
- * lambda_s = 1e-12 * trace(sum a a^T) / 5 so that stars with fewer than five
- * observations still give a finite start. Solved by Cholesky.
+ * over the star's rows (a_i = the n_astro astrometric coefficients, five for
+ * the standard row), with lambda_s = 1e-12 * trace(sum a a^T) / n_astro so
+ * that stars with fewer observations than unknowns still give a finite start.
+ * Solved by Cholesky. Nothing to solve without an astrometric section.
  * x (n_cols): reads the attitude, instrumental and global parts, writes the
  * astrometric part.
  * Returns the number of stars whose G was not positive definite (x_s = 0).
  */
 ORACLE_API int64_t oracle_astro_solve(const oracle_sys *s, const double *b, double *x)
 {
-    const int64_t att0 = 5 * s->n_stars;
+    const int na = s->n_astro, ni = s->n_ipr;
+    const int64_t att0 = (int64_t)na * s->n_stars;
+    const int64_t instr0 = att0 + 3 * (int64_t)s->n_dfa, glob0 = instr0 + s->n_instr;
     int64_t bad = 0;
+    if (na == 0) return 0;
     for (int64_t star = 0; star < s->n_stars; ++star) {
         double G[5][5] = {{0}}, h[5] = {0};
         for (int64_t i = s->star_ptr[star]; i < s->star_ptr[star + 1]; ++i) {
-            const double *a = s->A + i * ORACLE_NPAR;
-            const int64_t instr0 = att0 + 3 * (int64_t)s->n_dfa, glob0 = instr0 + s->n_instr;
+            const double *a = s->A + i * s->npar;
             double r = b[i];
             for (int ax = 0; ax < 3; ++ax)
                 for (int j = 0; j < 4; ++j)
-                    r = r - a[5 + 4 * ax + j] * x[att0 + (int64_t)ax * s->n_dfa + s->knot[i] + j];
-            for (int j = 0; j < 6; ++j) r = r - a[17 + j] * x[instr0 + s->instr[i * 6 + j]];
-            if (s->n_glob) r = r - a[23] * x[glob0];
-            for (int p = 0; p < 5; ++p) {
+                    r = r - a[na + 4 * ax + j] * x[att0 + (int64_t)ax * s->n_dfa + s->knot[i] + j];
+            for (int j = 0; j < ni; ++j) r = r - a[na + 12 + j] * x[instr0 + s->instr[i * ni + j]];
+            for (int j = 0; j < s->n_glob; ++j) r = r - a[na + 12 + ni + j] * x[glob0 + j];
+            for (int p = 0; p < na; ++p) {
                 h[p] = h[p] + a[p] * r;
-                for (int q = 0; q < 5; ++q) G[p][q] = G[p][q] + a[p] * a[q];
+                for (int q = 0; q < na; ++q) G[p][q] = G[p][q] + a[p] * a[q];
             }
         }
-        const double lam = 1e-12 * (G[0][0] + G[1][1] + G[2][2] + G[3][3] + G[4][4]) / 5.0;
-        for (int p = 0; p < 5; ++p) G[p][p] = G[p][p] + lam;
+        double tr = 0.0;
+        for (int p = 0; p < na; ++p) tr = tr + G[p][p];
+        const double lam = 1e-12 * tr / (double)na;
+        for (int p = 0; p < na; ++p) G[p][p] = G[p][p] + lam;
         /* Cholesky G = L L^T */
         double Lm[5][5] = {{0}};
         int ok = 1;
-        for (int j = 0; j < 5 && ok; ++j) {
+        for (int j = 0; j < na && ok; ++j) {
             double d = G[j][j];
             for (int k = 0; k < j; ++k) d = d - Lm[j][k] * Lm[j][k];
             if (!(d > 0.0)) { ok = 0; break; }
             Lm[j][j] = sqrt(d);
-            for (int i = j + 1; i < 5; ++i) {
+            for (int i = j + 1; i < na; ++i) {
                 double v = G[i][j];
                 for (int k = 0; k < j; ++k) v = v - Lm[i][k] * Lm[j][k];
                 Lm[i][j] = v / Lm[j][j];
@@ -159,21 +164,21 @@ ORACLE_API int64_t oracle_astro_solve(const oracle_sys *s, const double *b, doub
         }
         double y[5], xs[5];
         if (ok) {
-            for (int i = 0; i < 5; ++i) {
+            for (int i = 0; i < na; ++i) {
                 double v = h[i];
                 for (int k = 0; k < i; ++k) v = v - Lm[i][k] * y[k];
                 y[i] = v / Lm[i][i];
             }
-            for (int i = 4; i >= 0; --i) {
+            for (int i = na - 1; i >= 0; --i) {
                 double v = y[i];
-                for (int k = i + 1; k < 5; ++k) v = v - Lm[k][i] * xs[k];
+                for (int k = i + 1; k < na; ++k) v = v - Lm[k][i] * xs[k];
                 xs[i] = v / Lm[i][i];
             }
         } else {
-            for (int i = 0; i < 5; ++i) xs[i] = 0.0;
+            for (int i = 0; i < na; ++i) xs[i] = 0.0;
             ++bad;
         }
-        for (int i = 0; i < 5; ++i) x[5 * star + i] = xs[i];
+        for (int i = 0; i < na; ++i) x[(int64_t)na * star + i] = xs[i];
     }
     return bad;
 }

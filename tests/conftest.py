@@ -31,27 +31,35 @@ def _host_libs():
     yield
 
 
-def dense_matrix(star_ptr, A, knot, instr, n_dfa, n_instr, n_glob):
+def dense_matrix(star_ptr, A, knot, instr, n_dfa, n_instr, n_glob, n_astro=5, n_ipr=6):
     """Explicit dense A (tiny systems only), placed entry by entry from the
-    paper's storage: astro 5*star, attitude axis*n_dfa + knot + j, instr, glob."""
+    paper's storage (Sec. 2): a row holds n_astro astrometric coefficients
+    (columns n_astro*star + j), 3 x 4 attitude coefficients (columns
+    n_astro*n_stars + axis*n_dfa + knot + j), n_ipr instrumental ones (their
+    stored columns) and n_glob global ones, in that order along the row."""
     import numpy as np
 
     n_stars = len(star_ptr) - 1
     n = int(star_ptr[-1])
-    c = 5 * n_stars + 3 * n_dfa + n_instr + n_glob
-    a0 = 5 * n_stars
+    c = n_astro * n_stars + 3 * n_dfa + n_instr + n_glob
+    a0 = n_astro * n_stars
     i0 = a0 + 3 * n_dfa
     g0 = i0 + n_instr
     D = np.zeros((n, c))
     for s in range(n_stars):
         for r in range(star_ptr[s], star_ptr[s + 1]):
-            for j in range(5):
-                D[r, 5 * s + j] += A[r, j]
+            k = 0
+            for j in range(n_astro):
+                D[r, n_astro * s + j] += A[r, k]
+                k += 1
             for ax in range(3):
                 for j in range(4):
-                    D[r, a0 + ax * n_dfa + knot[r] + j] += A[r, 5 + 4 * ax + j]
-            for j in range(6):
-                D[r, i0 + instr[r, j]] += A[r, 17 + j]
+                    D[r, a0 + ax * n_dfa + knot[r] + j] += A[r, k]
+                    k += 1
+            for j in range(n_ipr):
+                D[r, i0 + instr[r, j]] += A[r, k]
+                k += 1
             for j in range(n_glob):
-                D[r, g0 + j] += A[r, 23 + j]
+                D[r, g0 + j] += A[r, k]
+                k += 1
     return D

@@ -70,3 +70,28 @@ def test_sinusoid_attitude_is_smooth():
     att = x[50:50 + 3000]
     # sum of 8 sinusoids of <= 10 cycles per 1000 knots: neighbouring knots differ little
     assert np.abs(np.diff(att)).max() < 0.2 and att.std() > 0.2
+
+
+def test_section_variants_share_the_standard_draws():
+    """Compact rows of a section variant hold the same draws as the standard slots they stand for
+    (Sec. 2: 0..5 astrometric, 12 attitude, 0..6 instrumental, the global section); the instrumental
+    columns are a prefix of the standard row's; globals past the first have draws of their own."""
+    std = gsrgen.make_cfg(13, 9, (3, 17), 11, 8)
+    h = gsrgen.generate(std)
+    for na, ni, ng in [(3, 4, 2), (0, 6, 1), (5, 0, 0), (2, 1, 5), (5, 6, 3)]:
+        cfg = gsrgen.make_cfg(13, 9, (3, 17), 11, 8, n_glob=ng, n_astro=na, n_ipr=ni)
+        v = gsrgen.generate(cfg)
+        assert v.A.shape == (h.n_rows, na + 12 + ni + ng) and v.instr.shape == (h.n_rows, ni)
+        assert np.array_equal(v.star_ptr, h.star_ptr) and np.array_equal(v.knot, h.knot)
+        assert np.array_equal(v.A[:, :na], h.A[:, :na])
+        assert np.array_equal(v.A[:, na:na + 12], h.A[:, 5:17])
+        assert np.array_equal(v.A[:, na + 12:na + 12 + ni], h.A[:, 17:17 + ni])
+        assert np.array_equal(v.instr, h.instr[:, :ni])
+        g = v.A[:, na + 12 + ni:]
+        if ng:
+            assert np.array_equal(g[:, 0], h.A[:, 23])
+            assert all(len(set(r.tolist())) == ng for r in g)  # distinct draws
+        assert v.x_true.shape == (cfg.ncols(),) and cfg.ncols() == na * 9 + 33 + 8 + ng
+    # a section variant with fewer instrumental unknowns than the standard row's six
+    small = gsrgen.generate(gsrgen.make_cfg(2, 6, 10, 9, 3, n_ipr=3, n_glob=0))
+    assert all(sorted(r.tolist()) == [0, 1, 2] for r in small.instr)

@@ -27,7 +27,7 @@ def _sys(cfg, fp32=False):
 
 def _dense(h):
     c = h.cfg
-    return dense_matrix(h.star_ptr, h.A, h.knot, h.instr, c.n_dfa, c.n_instr, c.n_glob)
+    return dense_matrix(h.star_ptr, h.A, h.knot, h.instr, c.n_dfa, c.n_instr, c.n_glob, c.n_astro, c.n_ipr)
 
 
 CASES = [
@@ -35,9 +35,18 @@ CASES = [
     gsrgen.make_cfg(21, 13, (1, 37), 9, 6, n_glob=0),  # ragged stars, no global column, n_instr = 6
     gsrgen.make_cfg(22, 4, (3, 5), 4, 7),          # minimal attitude: n_dfa = 4, one knot position
 ]
+# section variants (Sec. 2: 0..5 astrometric and 0..6 instrumental coefficients per row; several
+# global unknowns or none): compact rows of n_astro + 12 + n_ipr + n_glob coefficients
+VARIANTS = [
+    gsrgen.make_cfg(31, 17, (2, 29), 10, 9, n_glob=2, n_astro=3, n_ipr=4),
+    gsrgen.make_cfg(32, 11, 20, 8, 5, n_glob=5, n_astro=2, n_ipr=1),
+    gsrgen.make_cfg(33, 9, (4, 25), 7, 6, n_glob=0, n_astro=0, n_ipr=6),   # no astrometric section
+    gsrgen.make_cfg(34, 14, (1, 30), 9, 0, n_glob=1, n_astro=5, n_ipr=0),  # no instrumental section
+    gsrgen.make_cfg(35, 12, 18, 6, 8, n_glob=3, n_astro=5, n_ipr=6),       # the standard row plus 2 globals
+]
 
 
-@pytest.mark.parametrize("cfg", CASES)
+@pytest.mark.parametrize("cfg", CASES + VARIANTS)
 def test_aprod_vs_dense(cfg):
     h, s = _sys(cfg)
     D = _dense(h)
@@ -61,6 +70,22 @@ def test_adjoint_identity_c1():
     Aty = oracle.aprod2(s, y, np.zeros(s.n_cols))
     # scale: sum |A_ij x_j y_i|
     absA = oracle.System(s.star_ptr, np.abs(s.A), s.knot, s.instr, s.n_dfa, s.n_instr, s.n_glob)
+    scale = float(np.abs(y) @ oracle.aprod1(absA, np.abs(x), np.zeros(s.n_rows)))
+    assert abs(math.fsum(Ax * y) - math.fsum(x * Aty)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("sections", [(3, 4, 2), (0, 2, 5), (5, 0, 0)])
+def test_adjoint_identity_section_variants(sections):
+    na, ni, ng = sections
+    c = gsrgen.workloads()["c1"].cfg
+    h, s = _sys(gsrgen.make_cfg(c.seed, c.n_stars, (c.obs_min, c.obs_max), c.n_dfa, c.n_instr, n_glob=ng,
+                                n_astro=na, n_ipr=ni))
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(s.n_cols)
+    y = rng.standard_normal(s.n_rows)
+    Ax = oracle.aprod1(s, x, np.zeros(s.n_rows))
+    Aty = oracle.aprod2(s, y, np.zeros(s.n_cols))
+    absA = oracle.System(s.star_ptr, np.abs(s.A), s.knot, s.instr, s.n_dfa, s.n_instr, s.n_glob, na, ni)
     scale = float(np.abs(y) @ oracle.aprod1(absA, np.abs(x), np.zeros(s.n_rows)))
     assert abs(math.fsum(Ax * y) - math.fsum(x * Aty)) <= 1e-13 * scale
 
@@ -112,6 +137,18 @@ def test_lsqr_vs_dense_lstsq(damp, precond):
     assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("cfg", VARIANTS)
+def test_lsqr_section_variants_vs_lstsq(cfg):
+    h, s = _sys(cfg)
+    D = _dense(h)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    x, info = oracle.lsqr(s, b, itnlim=5000, atol=1e-15, btol=1e-15, damp=1e-6)
+    ref = _lstsq_solution(D, b, 1e-6)
+    assert info["istop"] in (1, 2, 4, 5)
+    assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert s.n_cols == D.shape[1] and s.blocks()["glob"][1] == s.n_cols
+
+
 def test_lsqr_ragged_vs_lstsq():
     h, s = _sys(gsrgen.make_cfg(21, 13, (6, 37), 9, 6, n_glob=0))
     D = _dense(h)
@@ -121,8 +158,10 @@ def test_lsqr_ragged_vs_lstsq():
     assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-def test_lsqr_planted_recovery():
-    cfg = gsrgen.make_cfg(8, 40, 40, 20, 10, noise_sigma=0.0)
+@pytest.mark.parametrize("sections", [(5, 6, 1), (2, 3, 4)])
+def test_lsqr_planted_recovery(sections):
+    na, ni, ng = sections
+    cfg = gsrgen.make_cfg(8, 40, 40, 20, 10, noise_sigma=0.0, n_astro=na, n_ipr=ni, n_glob=ng)
     h, s = _sys(cfg)
     b = oracle.rhs(s, h.x_true, h.eps)
     x, info = oracle.lsqr(s, b, itnlim=2000, atol=1e-15, btol=1e-15, damp=0.0)

@@ -27,6 +27,13 @@ MUTANTS = {
     "w update sign": ("const double t2 = -theta / rho;", "const double t2 = theta / rho;"),
     "preconditioner not inverted": ("p[j] = (p[j] > 0.0) ? 1.0 / sqrt(p[j]) : 1.0;",
                                     "p[j] = (p[j] > 0.0) ? sqrt(p[j]) : 1.0;"),
+    # section variants: mistakes invisible on the standard 24-coefficient row
+    "astrometric stride fixed at five": ("const int64_t offset_astro = (int64_t)na * star;",
+                                         "const int64_t offset_astro = (int64_t)5 * star;"),
+    "instrumental row stride fixed at six": ("sum = sum + a[k] * x[instr0 + s->instr[i * ni + j]];",
+                                             "sum = sum + a[k] * x[instr0 + s->instr[i * 6 + j]];"),
+    "second global reads the first": ("x[glob0 + j] = x[glob0 + j] + a[k + j] * yi;",
+                                      "x[glob0 + j] = x[glob0 + j] + a[k] * yi;"),
 }
 
 

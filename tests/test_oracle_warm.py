@@ -4,7 +4,8 @@
 * conv1d / network gradients against central finite differences;
 * bfloat16 rounding against hand-computed ties and carries;
 * MSE and Adam against closed forms;
-* the per-star 5x5 astrometric solve against numpy least squares per star;
+* the per-star 5x5 astrometric solve (n_astro x n_astro for section variants)
+  against numpy least squares per star;
 * the Jacobi features against an explicit dense evaluation.
 """
 import numpy as np
@@ -137,8 +138,10 @@ def test_mse_and_adam_closed_forms():
     np.testing.assert_allclose(v, 0.001 * gr ** 2)
 
 
-def test_astro_solve_vs_lstsq_per_star():
-    cfg = gsrgen.make_cfg(11, 40, (6, 80), 30, 12)
+@pytest.mark.parametrize("sections", [(5, 6, 1), (3, 4, 2), (1, 0, 5)])
+def test_astro_solve_vs_lstsq_per_star(sections):
+    na, ni, ng = sections
+    cfg = gsrgen.make_cfg(11, 40, (6, 80), 30, 12, n_astro=na, n_ipr=ni, n_glob=ng)
     h = gsrgen.generate(cfg)
     s = oracle.from_host_system(h)
     b = oracle.rhs(s, h.x_true, h.eps)
@@ -147,12 +150,12 @@ def test_astro_solve_vs_lstsq_per_star():
     x[a0:] = h.x_true[a0:] + 0.1  # some non-astrometric start
     rest = x[a0:].copy()
     assert oracle.astro_solve(s, b, x) == 0
-    D = dense_matrix(h.star_ptr, h.A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    D = dense_matrix(h.star_ptr, h.A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob, na, ni)
     r = b - D[:, a0:] @ rest
     for st in range(cfg.n_stars):
         r0, r1 = h.star_ptr[st], h.star_ptr[st + 1]
-        ref = np.linalg.lstsq(D[r0:r1, 5 * st:5 * st + 5], r[r0:r1], rcond=None)[0]
-        np.testing.assert_allclose(x[5 * st:5 * st + 5], ref, rtol=1e-8, atol=1e-10)
+        ref = np.linalg.lstsq(D[r0:r1, na * st:na * st + na], r[r0:r1], rcond=None)[0]
+        np.testing.assert_allclose(x[na * st:na * st + na], ref, rtol=1e-8, atol=1e-10)
     assert np.all(x[a0:] == rest)  # non-astrometric parts untouched
 
 
