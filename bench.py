@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sections", action="store_true",
+                    help="skip the section-variant measurement (c2-shaped systems with other row sections)")
     ap.add_argument("--n-stars", type=int, default=0,
                     help="profiling mode only: override the workload's number of stars (a smaller case for ncu)")
     ap.add_argument("--profile", default=None, choices=["f32", "f64"],
@@ -144,7 +146,7 @@ class Clocks:
 
 # ---------------------------------------------------------------- helpers
 def block_ranges(cfg):
-    a = 5 * cfg.n_stars
+    a = cfg.n_astro * cfg.n_stars
     t = a + 3 * cfg.n_dfa
     i = t + cfg.n_instr
     return {"astro": (0, a), "att": (a, t), "instr": (t, i), "glob": (i, i + cfg.n_glob)}
@@ -245,9 +247,57 @@ def run_reference(args):
 
 def desc(w):
     c = w.cfg
+    sec = "" if c.standard else f", sections {c.n_astro} astro / 12 att / {c.n_ipr} instr / {c.n_glob} glob per row"
     return (f"{c.n_stars} stars x {c.obs_min} obs = {c.n_stars * c.obs_min} rows, {c.n_dfa} knots/axis, "
             f"{c.n_instr} instr, {c.n_glob} glob, seed {c.seed}, {'FP32' if w.fp32 else 'FP64'} values, "
-            f"damp {w.damp}")
+            f"damp {w.damp}{sec}")
+
+
+def variant_bytes(cfg, kernel):
+    """Algorithmic bytes per row of a binary32 kernel for the sections of cfg: the row's values, the knot,
+    its instrumental columns (16-bit planes up to 65536 unknowns) and the row vector."""
+    vals = 4 * (cfg.n_astro + 12 + cfg.n_ipr + cfg.n_glob)
+    idx = 4 + cfg.n_ipr * (2 if cfg.n_instr <= 65536 else 4)
+    return vals + idx + {"aprod1_f32": 8, "aprod2_f32": 4, "residual_df": 12}[kernel]
+
+
+def measure_sections(torch, g, gsrgen, dev, stream, sh, peaks, names=("c2g5", "c2a2")):
+    """Section variants (Sec. 2, Sec. 4.2) at the benchmark's scale: the binary32 kernels against the HBM
+    roofline, and one mixed-precision solve from the learned start with the library's default refinement
+    (refine_tol 1e-10) against a tight binary64-arithmetic solve of the same stored values."""
+    from paper_2308_00778_gb300.data import device_system
+
+    out = {}
+    for name in names:
+        w = gsrgen.workloads()[name]
+        cfg = w.cfg
+        ctx, b, _ = device_system(cfg, True, True, dev, stream=sh)
+        n, nc = ctx.n_rows, ctx.n_cols
+        xs = torch.zeros(nc, dtype=torch.float64, device=dev)
+        ctx.solve(xs, itnlim=20000, atol=1e-15, btol=1e-15, damp=w.damp, conlim=0.0, stream=sh)
+        x32 = xs.float()
+        u32 = torch.randn(n, dtype=torch.float32, device=dev)
+        z = torch.zeros(nc, dtype=torch.float64, device=dev)
+        r32 = torch.empty(n, dtype=torch.float32, device=dev)
+        t = {"aprod1_f32": _time_kernel(torch, lambda: ctx.aprod1_f32(x32, u32, stream=sh), stream),
+             "aprod2_f32": _time_kernel(torch, lambda: ctx.aprod2_f32(u32, z, stream=sh), stream),
+             "residual_df": _time_kernel(torch, lambda: ctx.residual(xs, r32, stream=sh), stream)}
+        kern = {}
+        for k, ms in t.items():
+            bpr = variant_bytes(cfg, k)
+            gbs = bpr * n / (ms * 1e-3) / 1e9
+            kern[k] = {"ms": ms, "GB/s": gbs, "bytes_per_row": bpr, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+        x = torch.zeros(nc, dtype=torch.float64, device=dev)
+        kw = dict(mode=g.GSR_MIXED, damp=w.damp, warm=g.GSR_WARM_LEARNED, weights_path=g.WARM_WEIGHTS)
+        ms_solve, info = _time_solves(torch, ctx, x, kw, 3, 1, stream, sh)
+        out[name] = {"workload": desc(w), "coefficients_per_row": cfg.npar, "kernels": kern,
+                     "mixed_learned_default": {"s": ms_solve / 1e3, "outer": info["outer_itn"],
+                                               "inner_iterations": info["itn"],
+                                               "max_block_err": max_block_err(x, xs, cfg)}}
+        ctx.close()
+        del xs, x32, u32, z, r32, x, b
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -306,7 +356,7 @@ def replica_cfg(gsrgen, cfg, rank, world):
     if world <= 1:
         return cfg
     return gsrgen.make_cfg(cfg.seed + 1000 * rank, cfg.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
-                           cfg.n_glob, cfg.att_kind, cfg.noise_sigma)
+                           cfg.n_glob, cfg.att_kind, cfg.noise_sigma, n_astro=cfg.n_astro, n_ipr=cfg.n_ipr)
 
 
 def max_over_ranks(torch, dist, value, world, device):
@@ -547,6 +597,11 @@ def run_ours(args):
                "sample": f"oracle LSQR (1 thread) for 1 and 3 iterations on the full system, setup + per-iteration "
                          f"time extrapolated to the {n9} iterations that reach 1e-9; host has {cpu_count()} cores"}
 
+    # ---- section variants (rank 0, N = 1): kernels and a default mixed solve on c2-shaped variants
+    sections = None
+    if rank == 0 and world == 1 and not args.no_sections:
+        sections = measure_sections(torch, g, gsrgen, dev, stream, sh, peaks)
+
     if rank == 0:
         cold = solvers.get("fp64_plain", {}).get("s")
         line = {
@@ -562,6 +617,7 @@ def run_ours(args):
             "solvers": solvers,
             "speedup_vs_fp64_plain": {nm: cold / v["s"] for nm, v in solvers.items()} if cold else None,
             "kernels": kern, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "sections": sections,
             "gpu_launches": launches * args.steps if launches is not None else None,
         }
         print(json.dumps(line), flush=True)
@@ -587,7 +643,7 @@ def run_profile(args):
     cfg = w.cfg
     if args.n_stars:
         cfg = gsrgen.make_cfg(cfg.seed, args.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
-                              cfg.n_glob, cfg.att_kind, cfg.noise_sigma)
+                              cfg.n_glob, cfg.att_kind, cfg.noise_sigma, n_astro=cfg.n_astro, n_ipr=cfg.n_ipr)
     f32 = args.profile == "f32"
     ctx, b, _ = _device_system(g, gsrgen, torch, cfg, f32, True, dev, sh)
     n, nc = ctx.n_rows, ctx.n_cols

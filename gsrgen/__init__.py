@@ -91,6 +91,8 @@ def workloads() -> dict:
     c3   : 1M stars x 200 obs (2e8 rows), 30,000 knots/axis, 10,000 instr, FP32 values, seed 2
     c4   : 50k stars x 200 obs (1e7 rows), 2,000 knots/axis, 500 instr, sinusoid attitude (seed per system)
     c5   : 2M stars x 250 obs (5e8 rows), 60,000 knots/axis, 20,000 instr, sinusoid attitude, FP32 values, seed 5
+    c2g5 : c2 with five global unknowns (the five-global systems of Sec. 4.2): 28 coefficients per row
+    c2a2 : c2 with 2 astrometric and 3 instrumental coefficients per row and no global: 17 per row
     """
     return {
         "tiny": Workload("tiny", make_cfg(7, 20, 30, 12, 8), False, 1e-6, 1e-12, 1e-12, 400),
@@ -100,6 +102,10 @@ def workloads() -> dict:
         "c3": Workload("c3", make_cfg(2, 1_000_000, 200, 30000, 10000), True, 1e-6, 1e-12, 1e-12, 2000),
         "c4": Workload("c4", make_cfg(100, 50_000, 200, 2000, 500, att_kind=1), False, 1e-6, 1e-12, 1e-12, 2000),
         "c5": Workload("c5", make_cfg(5, 2_000_000, 250, 60000, 20000, att_kind=1), True, 1e-6, 1e-12, 1e-12, 2000),
+        "c2g5": Workload("c2g5", make_cfg(1, 100_000, 200, 3000, 1000, n_glob=5, att_kind=1), False, 1e-6, 1e-12,
+                         1e-12, 2000),
+        "c2a2": Workload("c2a2", make_cfg(1, 100_000, 200, 3000, 1000, n_glob=0, att_kind=1, n_astro=2, n_ipr=3),
+                         False, 1e-6, 1e-12, 1e-12, 2000),
     }
 
 

@@ -51,6 +51,7 @@ enum { GSR_HOST = 0, GSR_DEVICE = 1 }; /* where a caller pointer lives          
 enum { GSR_AOS = 0, GSR_SOA = 1 };     /* layout of caller coefficient arrays     */
 enum { GSR_PLAIN = 0, GSR_MIXED = 1 }; /* solver mode                             */
 enum { GSR_WARM_NONE = 0, GSR_WARM_JACOBI = 1, GSR_WARM_LEARNED = 2 };
+#define GSR_MAX_GLOB 5 /* global unknowns of a section variant (gsr_create_sections) */
 
 /*
  * gsr_create -- size a context for one system and allocate its device memory.
@@ -71,6 +72,36 @@ enum { GSR_WARM_NONE = 0, GSR_WARM_JACOBI = 1, GSR_WARM_LEARNED = 2 };
 gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr, int32_t n_dfa,
                       int32_t n_instr, int32_t n_glob, int32_t value_precision, int32_t device);
 
+/*
+ * gsr_create_sections -- gsr_create for any choice of the sections of a row.
+ * Sec. 2 allows 0 to 5 astrometric and 0 to 6 instrumental coefficients per
+ * row beside the 12 attitude ones, and a global section or none; Sec. 4.2
+ * runs systems with one and with five global unknowns.
+ *   n_astro   astrometric unknowns per star = coefficients per row, 0..5.
+ *   n_instr   instrumental unknowns (>= n_ipr; may be 0 when n_ipr = 0).
+ *   n_ipr     instrumental coefficients per row, 0..6 (distinct columns per row
+ *             are not required).
+ *   n_glob    global unknowns = global coefficients per row, 0..GSR_MAX_GLOB.
+ *   Other arguments as gsr_create.
+ * Unknowns: [astro n_astro*n_stars | attitude 3*n_dfa | instr n_instr | glob n_glob].
+ * Rows passed to gsr_set_rows / gsr_set_system then hold
+ * n_astro + 12 + n_ipr + n_glob coefficients in that order (the compact row;
+ * 23 or 24 for the standard sections 5, 6 and 0 or 1 global) and n_ipr
+ * instrumental columns. The context stores only the planes present: a
+ * variant streams (n_astro + 12 + n_ipr + n_glob) values per row, the
+ * standard sections run the same kernels as gsr_create. Errors as gsr_create.
+ */
+gsr_status gsr_create_sections(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
+                               int32_t n_astro, int32_t n_dfa, int32_t n_instr, int32_t n_ipr, int32_t n_glob,
+                               int32_t value_precision, int32_t device);
+
+/*
+ * gsr_sections -- the context's sections: astrometric, instrumental and global
+ * coefficients per row, and coefficients per row of the caller's arrays
+ * (any pointer may be NULL).
+ */
+gsr_status gsr_sections(const gsr_ctx *ctx, int32_t *n_astro, int32_t *n_ipr, int32_t *n_glob, int32_t *row_width);
+
 /* gsr_destroy -- free everything the context owns. NULL is accepted. */
 gsr_status gsr_destroy(gsr_ctx *ctx);
 
@@ -90,10 +121,16 @@ gsr_status gsr_dims(const gsr_ctx *ctx, int64_t *n_rows, int64_t *n_cols);
  *               GSR_SOA: 24 planes, plane j at values + j*plane_stride elements.
  *               Slots [0,5) astro, [5,17) attitude axis-major (4 knots each),
  *               [17,23) instrumental, 23 global (ignored when n_glob = 0).
+ *               A gsr_create_sections context takes W = n_astro + 12 + n_ipr +
+ *               n_glob coefficients per row (rows of W, or W planes), in the
+ *               order astro, attitude, instrumental, global.
  *   att_knot    nrows first attitude knots, each in [0, n_dfa-4]; slot
- *               5+4a+k of a row multiplies unknown 5*n_stars + a*n_dfa + knot + k.
+ *               5+4a+k of a row multiplies unknown 5*n_stars + a*n_dfa + knot + k
+ *               (n_astro+4a+k and n_astro*n_stars + a*n_dfa + knot + k for a
+ *               gsr_create_sections context).
  *   instr_col   instrumental columns in [0, n_instr): GSR_AOS nrows x 6 row-major,
- *               GSR_SOA 6 planes at instr_col + j*plane_stride.
+ *               GSR_SOA 6 planes at instr_col + j*plane_stride (n_ipr per row for
+ *               a gsr_create_sections context; may be NULL when n_ipr = 0).
  *   where       GSR_HOST or GSR_DEVICE (all three arrays).
  * FP64 values into an FP32 context are rounded to nearest; FP32 values into an
  * FP64 context are widened exactly. GSR_EINVAL on an out-of-range index,
@@ -204,7 +241,8 @@ typedef struct {
     int32_t graph_k;    /* LSQR iterations per CUDA-graph launch (0 = automatic)        */
     int32_t where;      /* GSR_HOST / GSR_DEVICE: x0, x_out and se_out                  */
     int32_t inner_itn;  /* MIXED: iterations per inner FP32 solve (0 = automatic)       */
-    double inner_tol;   /* MIXED: inner relative tolerance (0 = 1e-6)                    */
+    double inner_tol;   /* MIXED: an inner solve stops when its |A~^T r| estimate is below
+                           inner_tol times its value at the start of that solve (0 = 1e-6) */
     double refine_tol;  /* MIXED: stop when every block's |dx|/|x| < refine_tol (0 = 1e-10) */
     int32_t max_outer;  /* MIXED: maximum refinement steps (0 = 20)                     */
     int32_t inner_itn_next; /* MIXED: inner iteration limit of the refinement steps after

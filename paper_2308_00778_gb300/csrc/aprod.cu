@@ -44,13 +44,15 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-template <typename VT, typename XT, typename UT, typename AT, bool LSQR>
+template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool SV = false>
 __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
                                                 uint32_t *__restrict__ ymax)
 {
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
+    constexpr int MG = Sec<SV>::MAXG;
+    const Sec<SV> G(S);
     __shared__ double sm32[32];
     AT coef = (AT)1;
     if (LSQR) {
@@ -62,38 +64,55 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const XT *__restrict__ xt = x + S.att0;
     const XT *__restrict__ xi = x + S.instr0;
-    const AT xg = S.n_glob ? (AT)__ldg(x + S.glob0) : (AT)0;
+    AT xg[MG];
+#pragma unroll
+    for (int q = 0; q < MG; ++q) xg[q] = q < S.n_glob ? (AT)__ldg(x + S.glob0 + q) : (AT)0;
     AT ssq = (AT)0;
     float amx = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
-        const uint8_t *ti = tb + NPAR * Tile<VT>::VBLK;
+        const uint8_t *ti = tb + (int64_t)G.npl * Tile<VT>::VBLK;
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
-        AT a[NPAR][R];
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_instr<VT>(tb, G.npl, S.iw16, j, ic[j]);
+        AT a[A_GLOB + MG][R];
 #pragma unroll
-        for (int j = 0; j < NPAR; ++j) load_vals<VT, AT>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j)
+            if (j < G.na) load_vals<VT, AT>(tb, j, a[j]);
+#pragma unroll
+        for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<VT, AT>(tb, G.p_att + j, a[A_ATT + j]);
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_vals<VT, AT>(tb, G.p_ins + j, a[A_INS + j]);
+#pragma unroll
+        for (int q = 0; q < MG; ++q)
+            if (!SV || q < G.ng) load_vals<VT, AT>(tb, G.p_glob + q, a[A_GLOB + q]);
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const XT *__restrict__ xa = x + NASTRO * sr[i];
-            AT v = a[0][i] * (AT)__ldg(xa);
+            const XT *__restrict__ xa = x + (int64_t)G.na * sr[i];
+            AT v = (AT)0;
+            if (G.na > 0) v = a[0][i] * (AT)__ldg(xa);
 #pragma unroll
-            for (int j = 1; j < NASTRO; ++j) v = fma(a[j][i], (AT)__ldg(xa + j), v);
+            for (int j = 1; j < NASTRO; ++j)
+                if (j < G.na) v = fma(a[j][i], (AT)__ldg(xa + j), v);
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
                 const XT *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + kn[i];
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) v = fma(a[NASTRO + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
+                for (int j = 0; j < NPARAXIS; ++j) v = fma(a[A_ATT + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
             }
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j) v = fma(a[17 + j][i], (AT)__ldg(xi + ic[j][i]), v);
-            v = fma(a[23][i], xg, v);
+            for (int j = 0; j < NINSTR; ++j)
+                if (j < G.ni) v = fma(a[A_INS + j][i], (AT)__ldg(xi + ic[j][i]), v);
+#pragma unroll
+            for (int q = 0; q < MG; ++q)
+                if (!SV || q < G.ng) v = fma(a[A_GLOB + q][i], xg[q], v);
             const int64_t r = r0 + i;
             if (r < S.n_rows) {
                 AT yn;
@@ -120,13 +139,14 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     }
 }
 
-// Add a warp's per-lane partial sums of the 5 astrometric columns of star k:
-// the 32 x 5 partials go through a per-warp shared-memory buffer and lanes
-// 0..4 each sum one column (31 adds per column instead of a 5-step shuffle
-// tree per value on every lane). Warp-collective.
+// Add a warp's per-lane partial sums of the na (5 in the standard row)
+// astrometric columns of star k: the 32 x 5 partials go through a per-warp
+// shared-memory buffer and lanes 0..na-1 each sum one column (31 adds per
+// column instead of a 5-step shuffle tree per value on every lane).
+// Warp-collective.
 template <typename AT>
 __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT *__restrict__ wbuf,
-                                                double *__restrict__ z)
+                                                double *__restrict__ z, int na = NASTRO)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -135,11 +155,11 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
         acc[j] = (AT)0;
     }
     __syncwarp();
-    if (lane < NASTRO) {
+    if (lane < na) {
         AT t = (AT)0;
 #pragma unroll 8
         for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
-        atomicAdd(z + NASTRO * k + lane, (double)t);
+        atomicAdd(z + (int64_t)na * k + lane, (double)t);
     }
     __syncwarp();
 }
@@ -162,7 +182,8 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // binary32 accumulation. The per-block integer sums convert exactly to binary64
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false,
+          bool SV = false>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
                                                      double *__restrict__ z, double *__restrict__ z2,
                                                      const LsqrState *__restrict__ st, int64_t tiles_per_warp,
@@ -170,6 +191,8 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
+    constexpr int MG = Sec<SV>::MAXG;
+    const Sec<SV> G(S);
     static_assert(!FX || (INSTR_SMEM && (MODE == A2_PROD || MODE == A2_BOTH) && sizeof(AT) == 4),
                   "fixed point: binary32 products (and squares)");
     __shared__ int s_bad;
@@ -215,7 +238,9 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
     double *__restrict__ zi = z + S.instr0;
     double *__restrict__ z2i = BOTH ? z2 + S.instr0 : nullptr;
-    AT gsum = (AT)0, gsq = (AT)0;
+    AT gsum[MG], gsq[MG];
+#pragma unroll
+    for (int q = 0; q < MG; ++q) gsum[q] = gsq[q] = (AT)0;
     AT acc[NASTRO], acc2[NASTRO], sacc[NASTRO], sacc2[NASTRO];
 #pragma unroll
     for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = sacc[j] = sacc2[j] = (AT)0;
@@ -224,13 +249,30 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
-        AT a[NASTRO][R], ai[NINSTR][R], ag[R];
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_instr<VT>(tb, G.npl, S.iw16, j, ic[j]);
+        AT a[NASTRO][R], ai[NINSTR][R], ag[MG][R];
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) load_vals<VT, AT>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j) {
+            if (j < G.na) {
+                load_vals<VT, AT>(tb, j, a[j]);
+            } else {  // a section variant's missing astrometric slots add zeros (flushed to no column)
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_vals<VT, AT>(tb, 17 + j, ai[j]);
-        load_vals<VT, AT>(tb, 23, ag);
+                for (int i = 0; i < R; ++i) a[j][i] = (AT)0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_vals<VT, AT>(tb, G.p_ins + j, ai[j]);
+#pragma unroll
+        for (int q = 0; q < MG; ++q) {
+            if (!SV || q < G.ng) {
+                load_vals<VT, AT>(tb, G.p_glob + q, ag[q]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) ag[q][i] = (AT)0;
+            }
+        }
         const int64_t r0 = t * T + lane * R;
         bool in[R];
         AT yr[R];
@@ -243,6 +285,7 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
         for (int i = 0; i < R; ++i) {
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
+                if (j >= G.ni) continue;
                 const AT av = SQUARE ? ai[j][i] * ai[j][i] : ai[j][i];
                 if (in[i]) {
                     if (FX)
@@ -263,9 +306,12 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                     }
                 }
             }
-            const AT gv = SQUARE ? ag[i] * ag[i] : ag[i];
-            gsum = fma(gv, yr[i], gsum);
-            if constexpr (BOTH) gsq = fma(gv, in[i] ? gv : (AT)0, gsq);
+#pragma unroll
+            for (int q = 0; q < MG; ++q) {
+                const AT gv = SQUARE ? ag[q][i] * ag[q][i] : ag[q][i];
+                gsum[q] = fma(gv, yr[i], gsum[q]);
+                if constexpr (BOTH) gsq[q] = fma(gv, in[i] ? gv : (AT)0, gsq[q]);
+            }
         }
         // astrometric part: does the whole tile belong to star k?
         const int64_t tile_end = min((t + 1) * T, S.n_rows);  // one past the tile's last row
@@ -303,14 +349,14 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
                     } else if (sr[i] == kn) {
                         acc2[j] += pv;
                         if constexpr (BOTH) sacc2[j] += qv;
-                    } else if (in[i]) {
-                        atomicAdd(z + NASTRO * sr[i] + j, (double)pv);
-                        if constexpr (BOTH) atomicAdd(z2 + NASTRO * sr[i] + j, (double)qv);
+                    } else if (in[i] && j < G.na) {
+                        atomicAdd(z + (int64_t)G.na * sr[i] + j, (double)pv);
+                        if constexpr (BOTH) atomicAdd(z2 + (int64_t)G.na * sr[i] + j, (double)qv);
                     }
                 }
             }
-            flush_astro_run(acc, k, wbuf, z);
-            if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2);
+            flush_astro_run(acc, k, wbuf, z, G.na);
+            if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2, G.na);
 #pragma unroll
             for (int j = 0; j < NASTRO; ++j) {
                 acc[j] = acc2[j];
@@ -322,8 +368,8 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
         }
     }
     if (t0 < t1) {
-        flush_astro_run(acc, k, wbuf, z);
-        if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2);
+        flush_astro_run(acc, k, wbuf, z, G.na);
+        if constexpr (BOTH) flush_astro_run(sacc, k, wbuf, z2, G.na);
     }
     __syncthreads();
     if (FX) {
@@ -342,12 +388,15 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
             if (v != (AT)0) atomicAdd(BOTH && i >= S.n_instr ? z2i + (i - S.n_instr) : zi + i, (double)v);
         }
     }
-    if (S.n_glob) {
-        const double tot = block_sum((double)gsum, sm32);
-        if (threadIdx.x == 0 && tot != 0.0) atomicAdd(z + S.glob0, tot);
-        if constexpr (BOTH) {
-            const double tq = block_sum((double)gsq, sm32);
-            if (threadIdx.x == 0 && tq != 0.0) atomicAdd(z2 + S.glob0, tq);
+#pragma unroll
+    for (int q = 0; q < MG; ++q) {
+        if (q < S.n_glob) {  // the same for every thread of the block
+            const double tot = block_sum((double)gsum[q], sm32);
+            if (threadIdx.x == 0 && tot != 0.0) atomicAdd(z + S.glob0 + q, tot);
+            if constexpr (BOTH) {
+                const double tq = block_sum((double)gsq[q], sm32);
+                if (threadIdx.x == 0 && tq != 0.0) atomicAdd(z2 + S.glob0 + q, tq);
+            }
         }
     }
 }
@@ -528,6 +577,10 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
         kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part, ymax);
         return cudaGetLastError();
     };
+    if (c->sv) {  // a section variant (run-time section geometry)
+        if (st) return pick(k_aprod1<VT, XT, UT, AT, true, true>);
+        return pick(k_aprod1<VT, XT, UT, AT, false, true>);
+    }
     if (st) return pick(k_aprod1<VT, XT, UT, AT, true>);
     return pick(k_aprod1<VT, XT, UT, AT, false>);
 }
@@ -555,11 +608,11 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
     return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX = false>
-static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
-                                      cudaStream_t s)
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX, bool SV>
+static cudaError_t aprod2_star_launch_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
+                                        cudaStream_t s)
 {
-    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX>;
+    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX, SV>;
     const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX ? 2 : 1)) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -574,6 +627,14 @@ static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x
     }
     kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per, c->fx_word);
     return cudaGetLastError();
+}
+
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX = false>
+static cudaError_t aprod2_star_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
+                                      cudaStream_t s)
+{
+    if (c->sv) return aprod2_star_launch_t<VT, UT, AT, INS, MODE, LS, FX, true>(c, y, x, x2, st, s);
+    return aprod2_star_launch_t<VT, UT, AT, INS, MODE, LS, FX, false>(c, y, x, x2, st, s);
 }
 
 // max |y| of a binary32 row vector into *ymax (binary32 bits; the word is zero on entry)

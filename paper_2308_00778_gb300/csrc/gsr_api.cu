@@ -64,22 +64,24 @@ static void unmark_rows(gsr_ctx *c, int64_t lo, int64_t hi)
 }
 
 // ---------------------------------------------------------------- conversion kernels
+// Caller rows: in_w coefficients and ni instrumental columns per row (24 and 6
+// for the paper's standard row; the compact row of a section variant).
 // error words: [0] knot out of range, [1] instr out of range, [2] non-finite value
 template <typename ST>
 __global__ void k_validate(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
                            const int32_t *__restrict__ instr, int64_t n, int32_t n_dfa, int32_t n_instr,
-                           int32_t *__restrict__ errw)
+                           int32_t in_w, int32_t ni, int32_t *__restrict__ errw)
 {
     int32_t bk = 0, bi = 0, bv = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = knot[r];
         bk |= (k < 0 || k > n_dfa - 4);
-        for (int j = 0; j < NINSTR; ++j) {
-            const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+        for (int j = 0; j < ni; ++j) {
+            const int32_t ic = layout == GSR_AOS ? instr[r * ni + j] : instr[j * vstride + r];
             bi |= (ic < 0 || ic >= n_instr);
         }
-        for (int j = 0; j < NPAR; ++j) {
-            const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
+        for (int j = 0; j < in_w; ++j) {
+            const double v = (double)(layout == GSR_AOS ? vals[r * in_w + j] : vals[j * vstride + r]);
             bv |= !isfinite(v);
         }
     }
@@ -88,31 +90,33 @@ __global__ void k_validate(const ST *__restrict__ vals, int32_t layout, int64_t 
     if (bv) atomicOr(errw + 2, 1);
 }
 
-// rows [0, n) of the caller's arrays -> rows [row0, row0 + n) of the tiled layout (tiles.cuh)
+// rows [0, n) of the caller's arrays -> rows [row0, row0 + n) of the tiled layout (tiles.cuh):
+// value plane j < npl takes coefficient j of the row when j < in_used, else zero (the
+// standard row's global slot without a global)
 template <typename ST, typename DT>
 __global__ void k_convert(const ST *__restrict__ vals, int32_t layout, int64_t vstride, const int32_t *__restrict__ knot,
-                          const int32_t *__restrict__ instr, int64_t n, int32_t n_glob, uint8_t *__restrict__ tiles,
-                          int64_t tile_bytes, int32_t iw16, int64_t row0)
+                          const int32_t *__restrict__ instr, int64_t n, int32_t in_w, int32_t in_used, int32_t npl,
+                          int32_t ni, uint8_t *__restrict__ tiles, int64_t tile_bytes, int32_t iw16, int64_t row0)
 {
     using TL = Tile<DT>;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = row0 + r;
         uint8_t *tb = tiles + (o / TL::T) * tile_bytes;
         const int64_t i = o % TL::T;
-        for (int j = 0; j < NPAR; ++j) {
-            ST v = layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r];
-            if (j == NPAR - 1 && n_glob == 0) v = (ST)0;
+        for (int j = 0; j < npl; ++j) {
+            ST v = (ST)0;
+            if (j < in_used) v = layout == GSR_AOS ? vals[r * in_w + j] : vals[j * vstride + r];
             reinterpret_cast<DT *>(tb + j * TL::VBLK)[i] = (DT)v;
         }
-        reinterpret_cast<int32_t *>(tb + NPAR * TL::VBLK)[i] = knot[r];
-        for (int j = 0; j < NINSTR; ++j)
-            store_instr<DT>(tb, iw16, j, (int)i, layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r]);
+        reinterpret_cast<int32_t *>(tb + npl * TL::VBLK)[i] = knot[r];
+        for (int j = 0; j < ni; ++j)
+            store_instr<DT>(tb, npl, iw16, j, (int)i, layout == GSR_AOS ? instr[r * ni + j] : instr[j * vstride + r]);
     }
 }
 
 // AoS rows [0, n) of the caller (any device-visible address: device memory or mapped
 // pinned host memory) -> rows [row0, row0 + n) of the tiles, validated in the same
-// pass (error words as k_validate). One block per output tile: the tile's rows are
+// pass (error words as k_validate). The paper's standard 24-coefficient rows only. One block per output tile: the tile's rows are
 // read with 16-byte loads (8-byte for the instrumental columns) into shared memory,
 // then written plane by plane. vals must be 16-byte aligned, instr 8-byte aligned.
 template <typename ST, typename DT>
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(256) k_convert_aos(const ST *__restrict__ vals
             for (int j = 0; j < NINSTR; ++j) {
                 const int32_t ic = si[i * NINSTR + j];
                 bi |= (ic < 0 || ic >= n_instr);
-                store_instr<DT>(tb, iw16, j, i, ic);
+                store_instr<DT>(tb, NPAR, iw16, j, i, ic);
             }
         }
         __syncthreads();
@@ -195,7 +199,8 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->errw, 0, 4 * sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
     const int g = grid_for(c, nrows);
-    k_validate<ST><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_dfa, c->n_instr, c->errw);
+    k_validate<ST><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_dfa, c->n_instr, c->in_w,
+                                     c->n_ipr, c->errw);
     int32_t hw[4];
     if ((e = cudaMemcpyAsync(hw, c->errw, sizeof(hw), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -203,12 +208,15 @@ static gsr_status set_rows_device(gsr_ctx *c, int64_t row0, int64_t nrows, const
     if (hw[0]) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
     if (hw[1]) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
     if (hw[2]) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
+    // coefficients copied from the row: all of a compact row; the standard row's global slot only
+    // with a global
+    const int32_t in_used = c->sv ? c->in_w : std::min(c->in_w, A_GLOB + c->n_glob);
     if (c->prec == GSR_FP32)
-        k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
-                                                (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
+        k_convert<ST, float><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->in_w, in_used, c->npl,
+                                                c->n_ipr, (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
     else
-        k_convert<ST, double><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->n_glob,
-                                                 (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
+        k_convert<ST, double><<<g, 256, 0, s>>>(vals, layout, vstride, knot, instr, nrows, c->in_w, in_used, c->npl,
+                                                 c->n_ipr, (uint8_t *)c->tiles, c->tile_bytes, c->iw16, row0);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(c, e, "conversion");
     return GSR_OK;
@@ -263,12 +271,13 @@ template <typename ST>
 static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const ST *vals, int32_t layout,
                                 int64_t vstride, const int32_t *knot, const int32_t *instr, cudaStream_t s)
 {
-    if (layout == GSR_AOS) {
+    if (layout == GSR_AOS && !c->sv && c->in_w == NPAR) {  // the standard row: the single-pass path
         const void *dv = mapped(vals), *dk = mapped(knot), *di = mapped(instr);
         if (dv && dk && di && (uintptr_t)dv % 16 == 0 && (uintptr_t)di % 8 == 0)
             return set_rows_mapped<ST>(c, row0, nrows, (const ST *)dv, (const int32_t *)dk, (const int32_t *)di, s);
     }
-    const size_t row_bytes = sizeof(ST) * NPAR + sizeof(int32_t) * (1 + NINSTR);
+    const int32_t W = c->in_w, NI = c->n_ipr;  // coefficients and instrumental columns per caller row
+    const size_t row_bytes = sizeof(ST) * W + sizeof(int32_t) * (1 + NI);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const bool whole = (size_t)nrows * row_bytes <= free_b / 4;
@@ -276,12 +285,12 @@ static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const S
         for (int64_t r = 0; r < nrows; ++r) {
             if (knot[r] < 0 || knot[r] > c->n_dfa - 4)
                 return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4]");
-            for (int j = 0; j < NINSTR; ++j) {
-                const int32_t ic = layout == GSR_AOS ? instr[r * NINSTR + j] : instr[j * vstride + r];
+            for (int j = 0; j < NI; ++j) {
+                const int32_t ic = layout == GSR_AOS ? instr[r * NI + j] : instr[j * vstride + r];
                 if (ic < 0 || ic >= c->n_instr) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr)");
             }
-            for (int j = 0; j < NPAR; ++j) {
-                const double v = (double)(layout == GSR_AOS ? vals[r * NPAR + j] : vals[j * vstride + r]);
+            for (int j = 0; j < W; ++j) {
+                const double v = (double)(layout == GSR_AOS ? vals[r * W + j] : vals[j * vstride + r]);
                 if (!std::isfinite(v)) return fail(c, GSR_ENUMERIC, "non-finite coefficient");
             }
         }
@@ -290,9 +299,10 @@ static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const S
     ST *dv = nullptr;
     int32_t *dk = nullptr, *di = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&dv, sizeof(ST) * NPAR * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess ||
+    if ((e = cudaMalloc(&dv, sizeof(ST) * W * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess ||
         (e = cudaMalloc(&dk, sizeof(int32_t) * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess ||
-        (e = cudaMalloc(&di, sizeof(int32_t) * NINSTR * (size_t)std::max<int64_t>(chunk, 1))) != cudaSuccess) {
+        (e = cudaMalloc(&di, sizeof(int32_t) * std::max(NI, 1) * (size_t)std::max<int64_t>(chunk, 1))) !=
+            cudaSuccess) {
         cudaFree(dv);
         cudaFree(dk);
         cudaFree(di);
@@ -302,15 +312,15 @@ static gsr_status set_rows_host(gsr_ctx *c, int64_t row0, int64_t nrows, const S
     for (int64_t r = 0; r < nrows && rc == GSR_OK; r += chunk) {
         const int64_t m = std::min(chunk, nrows - r);
         if (layout == GSR_AOS) {
-            e = cudaMemcpyAsync(dv, vals + r * NPAR, sizeof(ST) * NPAR * m, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(di, instr + r * NINSTR, sizeof(int32_t) * NINSTR * m, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(dv, vals + r * W, sizeof(ST) * W * m, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && NI > 0)
+                e = cudaMemcpyAsync(di, instr + r * NI, sizeof(int32_t) * NI * m, cudaMemcpyHostToDevice, s);
         } else {
-            e = cudaMemcpy2DAsync(dv, sizeof(ST) * m, vals + r, sizeof(ST) * vstride, sizeof(ST) * m, NPAR,
+            e = cudaMemcpy2DAsync(dv, sizeof(ST) * m, vals + r, sizeof(ST) * vstride, sizeof(ST) * m, W,
                                   cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && NI > 0)
                 e = cudaMemcpy2DAsync(di, sizeof(int32_t) * m, instr + r, sizeof(int32_t) * vstride,
-                                      sizeof(int32_t) * m, NINSTR, cudaMemcpyHostToDevice, s);
+                                      sizeof(int32_t) * m, NI, cudaMemcpyHostToDevice, s);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(dk, knot + r, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
@@ -342,12 +352,16 @@ GSR_API void gsr_default_params(gsr_solve_params *p)
     if (p) default_params(p);
 }
 
-GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
-                              int32_t n_dfa, int32_t n_instr, int32_t n_glob, int32_t value_precision, int32_t device)
+// one context: sections (n_astro, n_ipr, n_glob), the caller's row width in_w and whether the
+// tiles use the compact layout of a section variant (sv)
+static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
+                             int32_t n_astro, int32_t n_dfa, int32_t n_instr, int32_t n_ipr, int32_t n_glob,
+                             int32_t in_w, bool sv, int32_t value_precision, int32_t device)
 {
     if (!out) return GSR_EINVAL;
     *out = nullptr;
-    if (n_stars < 1 || n_dfa < 4 || n_instr < NINSTR || (n_glob != 0 && n_glob != 1) ||
+    if (n_stars < 1 || n_dfa < 4 || n_instr < n_ipr || n_ipr < 0 || n_ipr > NINSTR || n_astro < 0 ||
+        n_astro > NASTRO || n_glob < 0 || n_glob > NGLOB_MAX ||
         (value_precision != GSR_FP64 && value_precision != GSR_FP32) || obs_per_star < 0 ||
         (obs_per_star == 0) != (star_ptr != nullptr))
         return GSR_EINVAL;
@@ -358,6 +372,11 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
     c->n_dfa = n_dfa;
     c->n_instr = n_instr;
     c->n_glob = n_glob;
+    c->n_astro = n_astro;
+    c->n_ipr = n_ipr;
+    c->sv = sv;
+    c->npl = sv ? n_astro + NAXES * NPARAXIS + n_ipr + n_glob : NPAR;
+    c->in_w = in_w;
     c->star_ptr_h.resize((size_t)n_stars + 1);
     if (star_ptr) {
         if (star_ptr[0] != 0) {
@@ -377,12 +396,12 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
     c->n_rows = c->star_ptr_h[n_stars];
     for (int64_t s = 0; s < n_stars; ++s)
         c->max_obs = std::max<int64_t>(c->max_obs, c->star_ptr_h[s + 1] - c->star_ptr_h[s]);
-    c->n_cols = (int64_t)NASTRO * n_stars + (int64_t)NAXES * n_dfa + n_instr + n_glob;
+    c->n_cols = (int64_t)n_astro * n_stars + (int64_t)NAXES * n_dfa + n_instr + n_glob;
     const int64_t rows_per_tile = value_precision == GSR_FP32 ? Tile<float>::T : Tile<double>::T;
     // instrumental columns in 16-bit planes whenever they fit (12 bytes less per row to stream)
     c->iw16 = n_instr <= 65536 ? 1 : 0;
-    const int64_t tile_bytes =
-        value_precision == GSR_FP32 ? Tile<float>::bytes(c->iw16 != 0) : Tile<double>::bytes(c->iw16 != 0);
+    const int64_t tile_bytes = value_precision == GSR_FP32 ? Tile<float>::bytes(c->npl, n_ipr, c->iw16 != 0)
+                                                           : Tile<double>::bytes(c->npl, n_ipr, c->iw16 != 0);
     c->tile_bytes = tile_bytes;
     const int64_t atile_bytes = value_precision == GSR_FP32 ? Tile<float>::ABYTES : Tile<double>::ABYTES;
     c->n_tiles = (c->n_rows + rows_per_tile - 1) / rows_per_tile;
@@ -436,6 +455,39 @@ GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_st
     return GSR_OK;
 }
 
+GSR_API gsr_status gsr_create(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
+                              int32_t n_dfa, int32_t n_instr, int32_t n_glob, int32_t value_precision, int32_t device)
+{
+    if (out) *out = nullptr;
+    if (n_glob != 0 && n_glob != 1) return GSR_EINVAL;
+    return create_ctx(out, n_stars, obs_per_star, star_ptr, NASTRO, n_dfa, n_instr, NINSTR, n_glob, NPAR, false,
+                      value_precision, device);
+}
+
+GSR_API gsr_status gsr_create_sections(gsr_ctx **out, int64_t n_stars, int32_t obs_per_star, const int64_t *star_ptr,
+                                       int32_t n_astro, int32_t n_dfa, int32_t n_instr, int32_t n_ipr, int32_t n_glob,
+                                       int32_t value_precision, int32_t device)
+{
+    if (out) *out = nullptr;
+    if (n_astro < 0 || n_astro > NASTRO || n_ipr < 0 || n_ipr > NINSTR || n_glob < 0 || n_glob > NGLOB_MAX)
+        return GSR_EINVAL;
+    // the standard sections keep the standard tiles and kernels; the caller's rows are compact
+    const bool sv = !(n_astro == NASTRO && n_ipr == NINSTR && n_glob <= 1);
+    return create_ctx(out, n_stars, obs_per_star, star_ptr, n_astro, n_dfa, n_instr, n_ipr, n_glob,
+                      n_astro + NAXES * NPARAXIS + n_ipr + n_glob, sv, value_precision, device);
+}
+
+GSR_API gsr_status gsr_sections(const gsr_ctx *c, int32_t *n_astro, int32_t *n_ipr, int32_t *n_glob,
+                                int32_t *row_width)
+{
+    if (!c) return GSR_EINVAL;
+    if (n_astro) *n_astro = c->n_astro;
+    if (n_ipr) *n_ipr = c->n_ipr;
+    if (n_glob) *n_glob = c->n_glob;
+    if (row_width) *row_width = c->in_w;
+    return GSR_OK;
+}
+
 GSR_API gsr_status gsr_destroy(gsr_ctx *c)
 {
     if (!c) return GSR_OK;
@@ -479,7 +531,7 @@ GSR_API gsr_status gsr_set_rows(gsr_ctx *c, int64_t row0, int64_t nrows, const v
     if (where != GSR_HOST && where != GSR_DEVICE) return fail(c, GSR_EINVAL, "where must be GSR_HOST or GSR_DEVICE");
     if (values_fp32 != 0 && values_fp32 != 1) return fail(c, GSR_EINVAL, "values_fp32 must be 0 or 1");
     if (nrows == 0) return GSR_OK;
-    if (!values || !att_knot || !instr_col) return fail(c, GSR_EINVAL, "null array");
+    if (!values || !att_knot || (!instr_col && c->n_ipr > 0)) return fail(c, GSR_EINVAL, "null array");
     if (layout == GSR_SOA && plane_stride < nrows) return fail(c, GSR_EINVAL, "plane_stride < nrows");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");

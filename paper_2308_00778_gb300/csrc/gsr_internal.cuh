@@ -21,6 +21,9 @@ constexpr int NASTRO = 5;    // astrometric unknowns per star
 constexpr int NAXES = 3;     // attitude axes
 constexpr int NPARAXIS = 4;  // attitude B-spline knots per axis touched by a row
 constexpr int NINSTR = 6;    // instrumental coefficients per row
+constexpr int NGLOB_MAX = GSR_MAX_GLOB;  // global unknowns of a section variant
+// register slots of a row's coefficients in the kernels, by section (the standard row's slots)
+constexpr int A_ATT = NASTRO, A_INS = NASTRO + NAXES * NPARAXIS, A_GLOB = NPAR - 1;
 constexpr int MAX_PARTIALS = 4096;  // per-block partial sums kept for the norms
 
 // ---------------------------------------------------------------- device views
@@ -28,6 +31,9 @@ constexpr int MAX_PARTIALS = 4096;  // per-block partial sums kept for the norms
 // star-ordered tile records, `atiles` the knot-ordered attitude tiles
 // (layout.cu). Rows of star s are [star_ptr[s], star_ptr[s+1]); first_star[t]
 // is the star of the first row of tile t (first_star[n_tiles] = last star).
+// The section geometry (na, ni, n_glob, planes) is the standard row's
+// (5, 6, 0|1; planes 5, 17, 23 of 24) unless the context holds a section
+// variant (Sec. 2: 0..5 astrometric, 0..6 instrumental, 0..NGLOB_MAX globals).
 template <typename VT>
 struct SysView {
     const uint8_t *__restrict__ tiles;
@@ -41,6 +47,9 @@ struct SysView {
     int64_t att0, instr0, glob0;  // first column of each section
     int64_t tile_bytes;           // bytes of one star-ordered tile record (tiles.cuh)
     int32_t iw16;                 // instrumental columns stored as 16-bit (1) or 32-bit (0) integers
+    int32_t na, ni;               // astrometric / instrumental coefficients per row
+    int32_t npl;                  // value planes per tile record
+    int32_t p_att, p_ins, p_glob; // plane of the first attitude / instrumental / global coefficient
 };
 
 // LSQR scalars shared between the kernels of one solve (one instance in device
@@ -51,6 +60,9 @@ struct LsqrState {
     double anorm, acond, ddnorm, res2, xnorm, xxnorm, zeta, cs2, sn2;
     double bnorm, rnorm, r1norm, r2norm, arnorm;
     double damp, atol, btol, ctol;
+    // relative gradient test of the mixed solver's inner solves: stop (istop 2) once the
+    // |A~^T r| estimate is below artol times its value at the start, arnorm0 (0: off)
+    double artol, arnorm0;
     double coef_u;     // aprod1: u_next = A pv + coef_u * u   (= -alpha/beta)
     double inv_alpha;  // colB: v = vhat * inv_alpha
     double t1, t2;     // colB: x += t1 w, w = v + t2 w
@@ -103,6 +115,13 @@ struct gsr_ctx {
     int sm_count = 0;
     int64_t n_stars = 0, n_rows = 0, n_cols = 0;
     int32_t n_dfa = 0, n_instr = 0, n_glob = 0;
+    // sections of a row (Sec. 2): astrometric and instrumental coefficients per row; sv marks a
+    // section variant (anything but 5 and 6 with at most one global), stored in compact tiles of
+    // npl = n_astro + 12 + n_ipr + n_glob value planes and run by the kernels' variant instances;
+    // the standard row keeps 24 planes (plane 23 zero without a global). in_w: coefficients per
+    // row of the caller's arrays (24 for gsr_create, the compact count for gsr_create_sections).
+    int32_t n_astro = gsr::NASTRO, n_ipr = gsr::NINSTR, npl = gsr::NPAR, in_w = gsr::NPAR;
+    bool sv = false;
     int64_t n_tiles = 0;             // row tiles (tiles.cuh); rows per tile depend on the precision
     int64_t tile_bytes = 0;          // bytes of one tile record
     int32_t iw16 = 0;                // instrumental columns in 16-bit planes (n_instr <= 65536)
@@ -156,11 +175,17 @@ SysView<VT> view(const gsr_ctx *c)
     s.n_dfa = c->n_dfa;
     s.n_instr = c->n_instr;
     s.n_glob = c->n_glob;
-    s.att0 = (int64_t)NASTRO * c->n_stars;
+    s.att0 = (int64_t)c->n_astro * c->n_stars;
     s.instr0 = s.att0 + (int64_t)NAXES * c->n_dfa;
     s.glob0 = s.instr0 + c->n_instr;
     s.tile_bytes = c->tile_bytes;
     s.iw16 = c->iw16;
+    s.na = c->n_astro;
+    s.ni = c->n_ipr;
+    s.npl = c->npl;
+    s.p_att = c->sv ? c->n_astro : A_ATT;
+    s.p_ins = s.p_att + NAXES * NPARAXIS;
+    s.p_glob = c->sv ? s.p_ins + c->n_ipr : A_GLOB;
     return s;
 }
 

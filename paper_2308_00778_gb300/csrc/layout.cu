@@ -6,7 +6,7 @@
 // add. This file builds, once per loaded system, a second copy of the 12
 // attitude coefficients with the rows ordered by knot, in tiles of T positions
 // (tiles.cuh; 13 planes per tile):
-//   plane j < 12 : coefficient 5+j of row perm[p] at position p
+//   plane j < 12 : attitude coefficient j of row perm[p] at position p
 //   plane 12     : perm[p], the row of position p (int32)
 //   knot_ptr[k]  : first position of knot k (k = 0..n_dfa-3), knot_ptr[n_dfa-3] = n
 // With it the attitude part of aprod 2 reduces runs of equal knot in registers
@@ -26,14 +26,14 @@ __global__ void k_iota(int32_t *__restrict__ a, int64_t n)
         a[i] = (int32_t)i;
 }
 
-// knot of every row, read from the tiles
+// knot of every row, read from the tiles (npl value planes precede the knot plane)
 template <typename VT>
-__global__ void k_extract_knots(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int64_t n,
+__global__ void k_extract_knots(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int32_t npl, int64_t n,
                                 int32_t *__restrict__ keys)
 {
     using TL = Tile<VT>;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        keys[r] = reinterpret_cast<const int32_t *>(tiles + (r / TL::T) * tile_bytes + NPAR * TL::VBLK)[r % TL::T];
+        keys[r] = reinterpret_cast<const int32_t *>(tiles + (r / TL::T) * tile_bytes + npl * TL::VBLK)[r % TL::T];
 }
 
 // knot_ptr[k] = first i with sorted_knot[i] >= k (lower bound), k = 0..nk
@@ -52,10 +52,12 @@ __global__ void k_knot_ptr(const int32_t *__restrict__ sorted_knot, int64_t n, i
     }
 }
 
-// the 12 attitude coefficients of every row as one contiguous record per row
-// (rows in star order, read plane by plane from the tiles: coalesced)
+// the 12 attitude coefficients of every row (planes p_att..p_att+11) as one
+// contiguous record per row (rows in star order, read plane by plane from the
+// tiles: coalesced)
 template <typename VT>
-__global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int64_t n, VT *__restrict__ rec)
+__global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t tile_bytes, int32_t p_att, int64_t n,
+                           VT *__restrict__ rec)
 {
     using TL = Tile<VT>;
     constexpr int NA = NAXES * NPARAXIS;
@@ -64,7 +66,7 @@ __global__ void k_att_rows(const uint8_t *__restrict__ tiles, int64_t tile_bytes
         const int64_t ri = r % TL::T;
         VT v[NA];
 #pragma unroll
-        for (int j = 0; j < NA; ++j) v[j] = reinterpret_cast<const VT *>(src + (NASTRO + j) * TL::VBLK)[ri];
+        for (int j = 0; j < NA; ++j) v[j] = reinterpret_cast<const VT *>(src + (p_att + j) * TL::VBLK)[ri];
         using V = typename Vec16<VT>::type;
         constexpr int PER = 16 / (int)sizeof(VT);
 #pragma unroll
@@ -108,9 +110,11 @@ __global__ void k_gather_att(const VT *__restrict__ rec, const int32_t *__restri
 // range of `per` tiles, 8 warps a block): the largest number of contributions
 // one block adds to column j (kmax[j]) and the largest |coefficient| of column
 // j (amax[j], binary32 bits). Both arrays are zero on entry.
+template <bool SV>
 __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t per, uint32_t *__restrict__ kmax,
                                                      uint32_t *__restrict__ amax)
 {
+    const Sec<SV> G(S);
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
     extern __shared__ uint32_t cnt[];  // [n_instr] counts, then [n_instr] max |a| bits
@@ -125,10 +129,11 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
         const int64_t r0 = t * T + lane * R;
 #pragma unroll
         for (int j = 0; j < NINSTR; ++j) {
+            if (j >= G.ni) break;
             int32_t ic[R];
-            load_instr<float>(tb, S.iw16, j, ic);
+            load_instr<float>(tb, G.npl, S.iw16, j, ic);
             float a[R];
-            load_vals<float, float>(tb, 17 + j, a);
+            load_vals<float, float>(tb, G.p_ins + j, a);
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (r0 + i < S.n_rows) {
@@ -153,7 +158,7 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
 {
     c->fx_bits = 0;
     kmax_h->clear();
-    if (c->prec != GSR_FP32 || c->n_rows == 0) return GSR_OK;
+    if (c->prec != GSR_FP32 || c->n_rows == 0 || c->n_ipr == 0 || c->n_instr == 0) return GSR_OK;
     const int32_t ni = c->n_instr;
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)ni;  // the stats kernel's and the star pass's
     if (smem > 100 * 1024) return GSR_OK;
@@ -169,11 +174,11 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
     c->fx_blocks = std::max<int64_t>(((c->n_tiles + c->fx_per - 1) / c->fx_per + 7) / 8, 1);
     if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)ni + 1), s)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
+    auto stats = c->sv ? k_instr_stats<true> : k_instr_stats<false>;
     if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_instr_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+        (e = cudaFuncSetAttribute(stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
-    k_instr_stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word);
+    stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word);
     kmax_h->resize((size_t)ni);
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToHost, s)) !=
@@ -241,9 +246,9 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     if ((e = cudaMallocFromPoolAsync(&vals_in, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
     if ((e = cudaMallocFromPoolAsync(&perm, sizeof(int32_t) * (size_t)n, c->pool, s)) != cudaSuccess) goto done;
     if (f32)
-        k_extract_knots<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, keys_in);
+        k_extract_knots<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, c->npl, n, keys_in);
     else
-        k_extract_knots<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, keys_in);
+        k_extract_knots<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, c->npl, n, keys_in);
     k_iota<<<g, 256, 0, s>>>(vals_in, n);
     if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, keys_out, vals_in, perm, n, 0, bits, s)) !=
         cudaSuccess)
@@ -258,10 +263,10 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
                                      c->pool, s)) != cudaSuccess)
         goto done;
     if (f32) {
-        k_att_rows<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, (float *)rec);
+        k_att_rows<float><<<g, 256, 0, s>>>(tiles, c->tile_bytes, view<float>(c).p_att, n, (float *)rec);
         k_gather_att<float><<<g, 256, 0, s>>>((const float *)rec, perm, n, (uint8_t *)c->atiles);
     } else {
-        k_att_rows<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, n, (double *)rec);
+        k_att_rows<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, view<double>(c).p_att, n, (double *)rec);
         k_gather_att<double><<<g, 256, 0, s>>>((const double *)rec, perm, n, (uint8_t *)c->atiles);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) goto done;

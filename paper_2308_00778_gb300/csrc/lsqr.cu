@@ -150,6 +150,7 @@ __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_
     if (1.0 + tt1 <= 1.0) istop = 4;
     if (test3 <= st->ctol) istop = 3;
     if (test2 <= st->atol) istop = 2;
+    if (arnorm <= st->artol * st->arnorm0) istop = 2;
     if (test1 <= rtol) istop = 1;
     const bool bad = !(isfinite(alpha) && isfinite(rho) && isfinite(phi) && isfinite(theta) && isfinite(rnorm));
     // store
@@ -282,6 +283,7 @@ __global__ void k_scalar_init(LsqrState *__restrict__ st, const double *__restri
     st->r1norm = beta;
     st->r2norm = beta;
     st->arnorm = alpha * beta;
+    st->arnorm0 = alpha * beta;
     st->itn = 0;
     st->istop = 0;
     st->numeric = !(isfinite(alpha) && isfinite(beta));

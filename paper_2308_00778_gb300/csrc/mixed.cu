@@ -36,31 +36,46 @@ __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ out, 
 // b is read in binary64 and split here (the same 8 bytes per row as a pre-split
 // copy, without the pass that would make it); `part` (may be null) receives
 // per-block sums of squares of r.
+template <bool SV = false>
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
                                                   const double *__restrict__ b64, float *__restrict__ r_out,
                                                   double *__restrict__ part)
 {
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
+    constexpr int MG = Sec<SV>::MAXG;
+    const Sec<SV> G(S);
     __shared__ double sm32[32];
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float2 *__restrict__ xt = xhl + S.att0;
     const float2 *__restrict__ xi = xhl + S.instr0;
-    const float2 xg = S.n_glob ? xhl[S.glob0] : make_float2(0.f, 0.f);
+    float2 xg[MG];
+#pragma unroll
+    for (int q = 0; q < MG; ++q) xg[q] = q < S.n_glob ? xhl[S.glob0 + q] : make_float2(0.f, 0.f);
     float ssq = 0.f;
     for (int64_t t = gw; t < S.n_tiles; t += nw) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
-        const uint8_t *ti = tb + NPAR * Tile<float>::VBLK;
+        const uint8_t *ti = tb + (int64_t)G.npl * Tile<float>::VBLK;
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
-        float a[NPAR][R];
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_instr<float>(tb, G.npl, S.iw16, j, ic[j]);
+        float a[A_GLOB + MG][R];
 #pragma unroll
-        for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j)
+            if (j < G.na) load_vals<float, float>(tb, j, a[j]);
+#pragma unroll
+        for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<float, float>(tb, G.p_att + j, a[A_ATT + j]);
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni) load_vals<float, float>(tb, G.p_ins + j, a[A_INS + j]);
+#pragma unroll
+        for (int q = 0; q < MG; ++q)
+            if (!SV || q < G.ng) load_vals<float, float>(tb, G.p_glob + q, a[A_GLOB + q]);
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
@@ -72,22 +87,26 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
         }
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j)
+            if (j < G.na)
 #pragma unroll
-            for (int i = 0; i < R; ++i) acc_term(a[j][i], xhl[NASTRO * sr[i] + j], sh[i], c[i]);
+                for (int i = 0; i < R; ++i) acc_term(a[j][i], xhl[(int64_t)G.na * sr[i] + j], sh[i], c[i]);
 #pragma unroll
         for (int ax = 0; ax < NAXES; ++ax)
 #pragma unroll
             for (int j = 0; j < NPARAXIS; ++j)
 #pragma unroll
                 for (int i = 0; i < R; ++i)
-                    acc_term(a[NASTRO + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
+                    acc_term(a[A_ATT + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
 #pragma unroll
         for (int j = 0; j < NINSTR; ++j)
+            if (j < G.ni)
 #pragma unroll
-            for (int i = 0; i < R; ++i) acc_term(a[17 + j][i], xi[ic[j][i]], sh[i], c[i]);
+                for (int i = 0; i < R; ++i) acc_term(a[A_INS + j][i], xi[ic[j][i]], sh[i], c[i]);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            acc_term(a[23][i], xg, sh[i], c[i]);
+#pragma unroll
+            for (int q = 0; q < MG; ++q)
+                if (!SV || q < G.ng) acc_term(a[A_GLOB + q][i], xg[q], sh[i], c[i]);
             const int64_t r = r0 + i;
             if (r < S.n_rows) {
                 const float2 bb = split_double(__ldcs(b64 + r));
@@ -152,8 +171,10 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out)
 {
+    // a section variant runs the run-time-geometry instance
+    auto kern = c->sv ? k_residual<true> : k_residual<false>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * c->sm_count;
     blocks = std::min<int64_t>(blocks, (c->n_tiles + (kThreads / 32) - 1) / (kThreads / 32));
@@ -163,7 +184,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b
         *grid_out = (int)blocks;
         return cudaSuccess;
     }
-    k_residual<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part);
     return cudaGetLastError();
 }
 
@@ -210,12 +231,17 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     LsqrState init = initial_state(prm);
     const int32_t itn_first = prm->inner_itn > 0 ? prm->inner_itn : prm->itnlim;
     const int32_t itn_next = prm->inner_itn_next > 0 ? prm->inner_itn_next : itn_first;
-    init.atol = init.btol = prm->inner_tol > 0.0 ? prm->inner_tol : 1e-6;
+    // inner stop: the correction problem's gradient |A~^T r| reduced by inner_tol from its start. The
+    // Paige-Saunders tests 1 and 2 compare with |r|, which is mostly the part of b no correction can
+    // fit; on noisy systems they stop the inner solves after one to three iterations and the
+    // refinement crawls
+    init.atol = init.btol = 0.0;
+    init.artol = prm->inner_tol > 0.0 ? prm->inner_tol : 1e-6;
     const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
     const double refine_tol = prm->refine_tol != 0.0 ? prm->refine_tol : 1e-10;
     int gres = 1;
     residual_launch(c, nullptr, nullptr, nullptr, nullptr, s, &gres);
-    const int64_t att0 = (int64_t)NASTRO * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa,
+    const int64_t att0 = (int64_t)c->n_astro * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa,
                   glob0 = instr0 + c->n_instr;
 
     LsqrState fin = LsqrState();

@@ -7,6 +7,9 @@
 //    1 knot plane     (T int32)
 //    6 instr planes   (T instrumental indices in [0, n_instr): 16-bit when n_instr <= 65536,
 //                      else 32-bit; SysView::iw16 says which, SysView::tile_bytes the record size)
+// A section variant (Sec. 2: n_astro 0..5, n_ipr 0..6, n_glob 0..NGLOB_MAX)
+// stores only its planes: n_astro + 12 + n_ipr + n_glob value planes in that
+// order, the knot plane, n_ipr instrumental planes (Sec<true> below).
 // Lane l of a warp owns rows [l*R, l*R + R) of a tile and reads each value plane
 // with one 16-byte load, so a warp reads a tile as one contiguous block and
 // warps working on consecutive tiles stream consecutive memory (measured:
@@ -29,7 +32,30 @@ struct Tile {
     static constexpr int64_t IBLK = (int64_t)T * sizeof(int32_t);     // int32 plane
     static constexpr int64_t ABYTES = NAXES * NPARAXIS * VBLK + IBLK;  // knot-ordered attitude tile
     // bytes of a star-ordered tile record with 16- or 32-bit instrumental planes
-    static constexpr int64_t bytes(bool iw16) { return NPAR * VBLK + IBLK + NINSTR * T * (iw16 ? 2 : 4); }
+    static constexpr int64_t bytes(bool iw16) { return bytes(NPAR, NINSTR, iw16); }
+    // ... with npl value planes and ni instrumental planes (a section variant)
+    static constexpr int64_t bytes(int npl, int ni, bool iw16)
+    {
+        return npl * VBLK + IBLK + (int64_t)ni * T * (iw16 ? 2 : 4);
+    }
+};
+
+// Section geometry of a tile record. SV = false: the paper's standard row,
+// compile-time constants (the code every standard system runs). SV = true: a
+// section variant, read from the view at run time; MAXG register slots hold
+// its global coefficients. Kernels keep a row's coefficients in register slots
+// of the standard row (A_ATT, A_INS, A_GLOB) and load them from planes
+// p_att / p_ins / p_glob.
+template <bool SV>
+struct Sec {
+    static constexpr int MAXG = SV ? NGLOB_MAX : 1;
+    int na, ni, ng, p_att, p_ins, p_glob, npl;
+    template <typename VT>
+    __device__ __forceinline__ explicit Sec(const SysView<VT> &S)
+        : na(SV ? S.na : NASTRO), ni(SV ? S.ni : NINSTR), ng(S.n_glob), p_att(SV ? S.p_att : A_ATT),
+          p_ins(SV ? S.p_ins : A_INS), p_glob(SV ? S.p_glob : A_GLOB), npl(SV ? S.npl : NPAR)
+    {
+    }
 };
 
 template <typename VT>
@@ -85,15 +111,15 @@ __device__ __forceinline__ void load_ints(const uint8_t *__restrict__ ints, int 
     }
 }
 
-// instrumental-column plane j (0..5) of the tile record at tb, this lane's R entries
+// instrumental-column plane j (0..5) of the tile record at tb (npl value planes), this lane's R entries
 template <typename VT>
-__device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, bool iw16, int j,
+__device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, int npl, bool iw16, int j,
                                            int32_t (&out)[Tile<VT>::R])
 {
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     const int lane = threadIdx.x & 31;
-    const uint8_t *p = tb + NPAR * Tile<VT>::VBLK + Tile<VT>::IBLK;  // the first instrumental plane
+    const uint8_t *p = tb + (int64_t)npl * Tile<VT>::VBLK + Tile<VT>::IBLK;  // the first instrumental plane
     if (iw16) {
         p += (int64_t)j * T * 2;
         if constexpr (R == 4) {
@@ -112,12 +138,20 @@ __device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, bool 
     }
 }
 
-// write instrumental index v of row i (0..T-1) into plane j of the tile record at tb
+// the same for the standard row's 24 value planes
 template <typename VT>
-__device__ __forceinline__ void store_instr(uint8_t *__restrict__ tb, bool iw16, int j, int i, int32_t v)
+__device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, bool iw16, int j,
+                                           int32_t (&out)[Tile<VT>::R])
+{
+    load_instr<VT>(tb, NPAR, iw16, j, out);
+}
+
+// write instrumental index v of row i (0..T-1) into plane j of the tile record at tb (npl value planes)
+template <typename VT>
+__device__ __forceinline__ void store_instr(uint8_t *__restrict__ tb, int npl, bool iw16, int j, int i, int32_t v)
 {
     constexpr int T = Tile<VT>::T;
-    uint8_t *p = tb + NPAR * Tile<VT>::VBLK + Tile<VT>::IBLK;
+    uint8_t *p = tb + (int64_t)npl * Tile<VT>::VBLK + Tile<VT>::IBLK;
     if (iw16)
         reinterpret_cast<uint16_t *>(p + (int64_t)j * T * 2)[i] = (uint16_t)v;
     else

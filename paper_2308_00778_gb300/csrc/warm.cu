@@ -161,10 +161,15 @@ __device__ __forceinline__ void load_rows(const RT *__restrict__ r, int64_t r0, 
 // first, then the tile's rows of the next star start the new run, and stars
 // that begin and end inside one tile are added directly. N must be zero on
 // entry; r holds the residual of the non-astrometric parts (n_rows entries).
-template <typename VT, typename RT>
+//
+// A section variant with n_astro < 5 keeps the 20-value layout: its missing
+// astrometric coefficients are zero, so their rows and columns of G and
+// entries of h stay zero (k_astro_chol solves only the leading n_astro).
+template <typename VT, typename RT, bool SV = false>
 __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *__restrict__ r,
                                                       float *__restrict__ N, int64_t tiles_per_warp)
 {
+    const int na = SV ? S.na : NASTRO;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     __shared__ float wred[8][NNORM * 32];
@@ -184,7 +189,14 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
         load_rows<RT, R>(r, r0, S.n_rows, rv);
         float a[NASTRO][R];
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) load_vals<VT, float>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j) {
+            if (j < na) {
+                load_vals<VT, float>(tb, j, a[j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) a[j][i] = 0.f;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < R; ++i)
             if (r0 + i >= S.n_rows)
@@ -241,9 +253,11 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
 // grid-stride order; per-block sums of squares of the new r into part. With r
 // the residual of the other parts of x0 this gives the residual of the whole
 // warm start, for the first refinement step of the mixed solver.
+template <bool SV = false>
 __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const double *__restrict__ x0,
                                                         float *__restrict__ r, double *__restrict__ part)
 {
+    const int na = SV ? S.na : NASTRO;
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
     __shared__ double sm32[32];
@@ -255,7 +269,8 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         float a[NASTRO][R];
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) load_vals<float, float>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j)
+            if (j < na) load_vals<float, float>(tb, j, a[j]);
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
@@ -270,9 +285,10 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
         }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const double *xa = x0 + NASTRO * sr[i];
+            const double *xa = x0 + (int64_t)na * sr[i];
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j) v[i] = fmaf(-a[j][i], (float)__ldg(xa + j), v[i]);
+            for (int j = 0; j < NASTRO; ++j)
+                if (j < na) v[i] = fmaf(-a[j][i], (float)__ldg(xa + j), v[i]);
             if (r0 + i < S.n_rows) ssq = fmaf(v[i], v[i], ssq);
         }
         if (full) {
@@ -287,7 +303,9 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, double *__restrict__ x0)
+// na: astrometric unknowns per star (5 in the standard row); a section variant's
+// trailing rows and columns (zero in N) get a unit diagonal and give x = 0
+__global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, double *__restrict__ x0, int na)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_stars;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -301,9 +319,12 @@ __global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, doubl
                 M[p][c] = M[c][p] = (double)n[q];
                 ++q;
             }
-        const double lam = 1e-12 * (M[0][0] + M[1][1] + M[2][2] + M[3][3] + M[4][4]) / 5.0;
+        double tr = 0.0;
 #pragma unroll
-        for (int p = 0; p < NASTRO; ++p) M[p][p] += lam;
+        for (int p = 0; p < NASTRO; ++p) tr += p < na ? M[p][p] : 0.0;
+        const double lam = 1e-12 * tr / (double)na;
+#pragma unroll
+        for (int p = 0; p < NASTRO; ++p) M[p][p] = p < na ? M[p][p] + lam : 1.0;
         bool ok = true;
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) {
@@ -335,7 +356,8 @@ __global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, doubl
             xs[i2] = v / L[i2][i2];
         }
 #pragma unroll
-        for (int i2 = 0; i2 < NASTRO; ++i2) x0[NASTRO * s + i2] = ok ? xs[i2] : 0.0;
+        for (int i2 = 0; i2 < NASTRO; ++i2)
+            if (i2 < na) x0[(int64_t)na * s + i2] = ok ? xs[i2] : 0.0;
     }
 }
 
@@ -348,7 +370,7 @@ static int grid_for(const gsr_ctx *c, int64_t n)
 template <typename VT, typename RT>
 static cudaError_t astro_normal_launch(const gsr_ctx *c, const RT *r, cudaStream_t s)
 {
-    auto kern = k_astro_normal<VT, RT>;
+    auto kern = c->sv ? k_astro_normal<VT, RT, true> : k_astro_normal<VT, RT, false>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -382,7 +404,7 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s, bool keep_z)
     if (f32) k_to_f32<<<grid_for(c, c->n_rows), kThreads, 0, s>>>(c->b, ws.u32, c->n_rows);
     if ((rc = precond_pass(c, true, s, f32, f32 ? (const void *)ws.u32 : (const void *)c->b, ws.z)) != GSR_OK)
         return rc;
-    const int64_t att0 = (int64_t)NASTRO * c->n_stars;
+    const int64_t att0 = (int64_t)c->n_astro * c->n_stars;
     if ((e = cudaMemsetAsync(ws.wacc, 0, sizeof(double) * 4, s)) != cudaSuccess) return cuda_fail(c, e, "memset");
     k_att_features<<<grid_for(c, c->n_dfa), kThreads, 0, s>>>(ws.z, ws.p, att0, c->n_dfa, ws.feats, ws.wacc);
     k_normalise_features<<<grid_for(c, c->n_dfa), kThreads, 0, s>>>(ws.feats, c->n_dfa, ws.wacc, ws.wacc + 2);
@@ -401,7 +423,7 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
     Workspace &ws = c->ws;
     if (net && (rc = gsr_net_forward(net, ws.feats, 1, c->n_dfa, ws.netout, s)) != GSR_OK)
         return fail(c, rc, std::string("warm start: ") + gsr_net_last_error(net));
-    const int64_t att0 = (int64_t)NASTRO * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa;
+    const int64_t att0 = (int64_t)c->n_astro * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa;
     k_att_guess<<<grid_for(c, c->n_cols), kThreads, 0, s>>>(ws.feats, net ? ws.netout : nullptr, ws.wacc + 2, att0,
                                                             c->n_dfa, c->n_cols, x0);
     k_rest_guess<<<grid_for(c, c->n_cols - instr0), kThreads, 0, s>>>(ws.z, ws.p, instr0, c->n_cols, x0);
@@ -411,7 +433,7 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
         return cuda_fail(c, ez, "normal-equation buffer");
     if ((ez = cudaMemsetAsync(ws.astro_n, 0, sizeof(float) * NNORM * (size_t)c->n_stars, s)) != cudaSuccess)
         return cuda_fail(c, ez, "memset");
-    if (c->n_rows > 0) {
+    if (c->n_rows > 0 && c->n_astro > 0) {
         // r = b - A x0 with the astrometric part of x0 still zero: the residual of the other parts
         const int64_t nc = c->n_cols;
         if (c->prec == GSR_FP32) {
@@ -428,12 +450,16 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
         }
         if (ez != cudaSuccess) return cuda_fail(c, ez, "warm start: normal equations");
     }
-    k_astro_chol<<<grid_for(c, c->n_stars), kThreads, 0, s>>>(ws.astro_n, c->n_stars, x0);
-    if (r0_parts && c->prec == GSR_FP32 && c->n_rows > 0) {
+    if (c->n_astro > 0)
+        k_astro_chol<<<grid_for(c, c->n_stars), kThreads, 0, s>>>(ws.astro_n, c->n_stars, x0, c->n_astro);
+    if (r0_parts && c->prec == GSR_FP32 && c->n_rows > 0 && c->n_astro > 0) {
         // ws.u32 holds the residual of the non-astrometric parts: complete it (binary32) into the
         // residual of x0, with its per-block sums of squares in ws.part_u
         const int g = (int)std::min<int64_t>(std::max<int64_t>((c->n_tiles + 7) / 8, 1), (int64_t)c->sm_count * 4);
-        k_astro_residual<<<g, kThreads, 0, s>>>(view<float>(c), x0, ws.u32, ws.part_u);
+        if (c->sv)
+            k_astro_residual<true><<<g, kThreads, 0, s>>>(view<float>(c), x0, ws.u32, ws.part_u);
+        else
+            k_astro_residual<false><<<g, kThreads, 0, s>>>(view<float>(c), x0, ws.u32, ws.part_u);
         *r0_parts = g;
     }
     const cudaError_t e = cudaGetLastError();

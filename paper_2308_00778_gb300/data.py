@@ -20,9 +20,9 @@ def load_rows(ctx, cfg, round32: bool, device, stream=0):
     n = int(sp[-1])
     spd = torch.tensor(sp, device=device)
     vdt = torch.float32 if ctx_fp32(ctx) else torch.float64
-    vals = torch.empty(24 * n, dtype=vdt, device=device)
+    vals = torch.empty(cfg.npar * n, dtype=vdt, device=device)
     knot = torch.empty(n, dtype=torch.int32, device=device)
-    ins = torch.empty(6 * n, dtype=torch.int32, device=device)
+    ins = torch.empty(max(cfg.n_ipr, 1) * n, dtype=torch.int32, device=device)
     gsrgen.dev_rows(cfg, spd, sp, 0, cfg.n_stars, vals, n, knot, ins, stream=stream, round32=round32)
     ctx.set_rows(0, n, vals, knot, ins, layout=g.GSR_SOA, plane_stride=n, stream=stream)
     return vals, knot, ins, sp
@@ -36,7 +36,8 @@ def new_context(cfg, fp32_store: bool, device_index: int = 0):
     sp = gsrgen.star_ptr(cfg)
     obs = cfg.obs_min if cfg.obs_min == cfg.obs_max else 0
     ctx = g.Context(cfg.n_stars, obs_per_star=obs, star_ptr=None if obs else sp, n_dfa=cfg.n_dfa,
-                    n_instr=cfg.n_instr, n_glob=cfg.n_glob, fp32=fp32_store, device=device_index)
+                    n_instr=cfg.n_instr, n_glob=cfg.n_glob, fp32=fp32_store, device=device_index,
+                    n_astro=cfg.n_astro, n_ipr=cfg.n_ipr)
     ctx.fp32 = fp32_store
     return ctx
 
@@ -62,9 +63,9 @@ def device_system(cfg, fp32_store: bool, round32: bool, device, stream=0, keep_h
     host = None
     if keep_host:
         n = ctx.n_rows
-        host = {"A": vals.view(24, n).t().contiguous().cpu().pin_memory(),
+        host = {"A": vals.view(cfg.npar, n).t().contiguous().cpu().pin_memory(),
                 "knot": knot.cpu().pin_memory(),
-                "instr": ins.view(6, n).t().contiguous().cpu().pin_memory(),
+                "instr": ins[:cfg.n_ipr * n].view(cfg.n_ipr, n).t().contiguous().cpu().pin_memory(),
                 "b": b.cpu().pin_memory(), "star_ptr": sp}
     del vals, ins, knot
     return ctx, b, host

@@ -88,6 +88,8 @@ def lib():
         P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         sig = {
             "gsr_create": (I32, [ctypes.POINTER(P), I64, I32, P, I32, I32, I32, I32, I32]),
+            "gsr_create_sections": (I32, [ctypes.POINTER(P), I64, I32, P, I32, I32, I32, I32, I32, I32, I32]),
+            "gsr_sections": (I32, [P, P, P, P, P]),
             "gsr_destroy": (I32, [P]),
             "gsr_last_error": (ctypes.c_char_p, [P]),
             "gsr_dims": (I32, [P, P, P]),
@@ -131,6 +133,22 @@ def gsr_create(n_stars, obs_per_star, star_ptr, n_dfa, n_instr, n_glob, value_pr
     st = lib().gsr_create(ctypes.byref(h), n_stars, obs_per_star, star_ptr or None, n_dfa, n_instr, n_glob,
                           value_precision, device)
     return st, h.value
+
+
+def gsr_create_sections(n_stars, obs_per_star, star_ptr, n_astro, n_dfa, n_instr, n_ipr, n_glob, value_precision,
+                        device):
+    """Returns (status, ctx handle). star_ptr: host pointer (int) or 0."""
+    h = ctypes.c_void_p()
+    st = lib().gsr_create_sections(ctypes.byref(h), n_stars, obs_per_star, star_ptr or None, n_astro, n_dfa, n_instr,
+                                   n_ipr, n_glob, value_precision, device)
+    return st, h.value
+
+
+def gsr_sections(ctx):
+    """Returns (status, n_astro, n_ipr, n_glob, row_width)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    st = lib().gsr_sections(ctx, *[ctypes.byref(q) for q in v])
+    return (st, *[q.value for q in v])
 
 
 def gsr_destroy(ctx):
@@ -341,18 +359,28 @@ class Net:
 
 
 class Context:
-    """Owns one gsr_ctx. Arrays may be numpy arrays (host) or torch tensors (host or CUDA)."""
+    """Owns one gsr_ctx. Arrays may be numpy arrays (host) or torch tensors (host or CUDA).
 
-    def __init__(self, n_stars, obs_per_star=0, star_ptr=None, n_dfa=4, n_instr=6, n_glob=1, fp32=False, device=0):
+    The paper's standard sections (n_astro = 5, n_ipr = 6, n_glob 0 or 1) create the context with
+    gsr_create (rows of 24 coefficients); any other choice with gsr_create_sections (compact rows of
+    n_astro + 12 + n_ipr + n_glob coefficients and n_ipr instrumental columns)."""
+
+    def __init__(self, n_stars, obs_per_star=0, star_ptr=None, n_dfa=4, n_instr=6, n_glob=1, fp32=False, device=0,
+                 n_astro=5, n_ipr=6):
         import numpy as np
 
         self._sp = None if star_ptr is None else np.ascontiguousarray(star_ptr, dtype=np.int64)
-        st, h = gsr_create(n_stars, obs_per_star, _ptr(self._sp), n_dfa, n_instr, n_glob,
-                           GSR_FP32 if fp32 else GSR_FP64, device)
+        prec = GSR_FP32 if fp32 else GSR_FP64
+        if n_astro == 5 and n_ipr == 6 and n_glob in (0, 1):
+            st, h = gsr_create(n_stars, obs_per_star, _ptr(self._sp), n_dfa, n_instr, n_glob, prec, device)
+        else:
+            st, h = gsr_create_sections(n_stars, obs_per_star, _ptr(self._sp), n_astro, n_dfa, n_instr, n_ipr,
+                                        n_glob, prec, device)
         if st != 0:
             raise GsrError(st, "gsr_create failed")
         self.h = h
         _, self.n_rows, self.n_cols = gsr_dims(h)
+        _, self.n_astro, self.n_ipr, self.n_glob, self.row_width = gsr_sections(h)
 
     def _check(self, st):
         if st != 0:

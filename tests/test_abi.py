@@ -61,6 +61,17 @@ def test_errors_without_gpu_are_status_codes():
     assert L.gsr_create(ctypes.byref(h), 1, 1, None, 4, 6, 1, 7, 0) == g.Status.EINVAL  # precision
     assert L.gsr_create(ctypes.byref(h), 1, 0, None, 4, 6, 1, 0, 0) == g.Status.EINVAL  # no grouping
     assert h.value is None
+    # section variants (Sec. 2): 0..5 astrometric, 0..6 instrumental per row (<= n_instr), 0..5 globals
+    cs = L.gsr_create_sections
+    assert cs(ctypes.byref(h), 1, 1, None, 6, 4, 6, 6, 1, 0, 0) == g.Status.EINVAL   # n_astro > 5
+    assert cs(ctypes.byref(h), 1, 1, None, -1, 4, 6, 6, 1, 0, 0) == g.Status.EINVAL  # n_astro < 0
+    assert cs(ctypes.byref(h), 1, 1, None, 5, 4, 6, 7, 1, 0, 0) == g.Status.EINVAL   # n_ipr > 6
+    assert cs(ctypes.byref(h), 1, 1, None, 5, 4, 3, 4, 1, 0, 0) == g.Status.EINVAL   # n_instr < n_ipr
+    assert cs(ctypes.byref(h), 1, 1, None, 5, 4, 6, 6, 6, 0, 0) == g.Status.EINVAL   # n_glob > GSR_MAX_GLOB
+    assert cs(ctypes.byref(h), 1, 1, None, 5, 3, 6, 6, 1, 0, 0) == g.Status.EINVAL   # n_dfa < 4
+    assert cs(None, 1, 1, None, 5, 4, 6, 6, 1, 0, 0) == g.Status.EINVAL
+    assert h.value is None
+    assert g.gsr_sections(0)[0] == g.Status.EINVAL
     assert g.gsr_aprod1(0, 0, 0) == g.Status.EINVAL
     assert g.gsr_lsqr_solve(0, g.gsr_default_params(), 0, 0, 0, g.SolveInfo()) == g.Status.EINVAL
     assert g.gsr_destroy(0) == g.Status.OK
