@@ -75,32 +75,47 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
-#pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_instr<VT>(tb, G.npl, S.iw16, j, ic[j]);
         AT a[A_GLOB + MG][R];
+        if constexpr (SV) {
+            // run-time sections: every load is unconditional (absent slots read an attitude plane or
+            // the knot plane, always present in the record) and what an absent slot gathers is
+            // masked to zero, so the loads schedule together as in the standard instance
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j)
-            if (j < G.na) load_vals<VT, AT>(tb, j, a[j]);
+            for (int j = 0; j < NINSTR; ++j) load_instr_or_knot<VT>(tb, G.npl, G.ni, S.iw16, j, ic[j]);
 #pragma unroll
-        for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<VT, AT>(tb, G.p_att + j, a[A_ATT + j]);
+            for (int j = 0; j < NASTRO; ++j) load_vals<VT, AT>(tb, j < G.na ? j : G.p_att, a[j]);
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_vals<VT, AT>(tb, G.p_ins + j, a[A_INS + j]);
+            for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<VT, AT>(tb, G.p_att + j, a[A_ATT + j]);
 #pragma unroll
-        for (int q = 0; q < MG; ++q)
-            if (!SV || q < G.ng) load_vals<VT, AT>(tb, G.p_glob + q, a[A_GLOB + q]);
+            for (int j = 0; j < NINSTR; ++j) load_vals<VT, AT>(tb, j < G.ni ? G.p_ins + j : G.p_att, a[A_INS + j]);
+#pragma unroll
+            for (int q = 0; q < MG; ++q) load_vals<VT, AT>(tb, q < G.ng ? G.p_glob + q : G.p_att, a[A_GLOB + q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
+#pragma unroll
+            for (int j = 0; j < A_GLOB + MG; ++j) load_vals<VT, AT>(tb, j, a[j]);
+        }
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const XT *__restrict__ xa = x + (int64_t)G.na * sr[i];
-            AT v = (AT)0;
-            if (G.na > 0) v = a[0][i] * (AT)__ldg(xa);
+            AT v;
+            if constexpr (SV) {
+                const XT *__restrict__ xa = x + (int64_t)G.na * sr[i];
+                v = (AT)0;
 #pragma unroll
-            for (int j = 1; j < NASTRO; ++j)
-                if (j < G.na) v = fma(a[j][i], (AT)__ldg(xa + j), v);
+                for (int j = 0; j < NASTRO; ++j) {
+                    const AT xv = (AT)__ldg(j < G.na ? xa + j : x);
+                    v = fma(a[j][i], j < G.na ? xv : (AT)0, v);
+                }
+            } else {
+                const XT *__restrict__ xa = x + NASTRO * sr[i];
+                v = a[0][i] * (AT)__ldg(xa);
+#pragma unroll
+                for (int j = 1; j < NASTRO; ++j) v = fma(a[j][i], (AT)__ldg(xa + j), v);
+            }
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
                 const XT *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + kn[i];
@@ -108,11 +123,16 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
                 for (int j = 0; j < NPARAXIS; ++j) v = fma(a[A_ATT + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
             }
 #pragma unroll
-            for (int j = 0; j < NINSTR; ++j)
-                if (j < G.ni) v = fma(a[A_INS + j][i], (AT)__ldg(xi + ic[j][i]), v);
+            for (int j = 0; j < NINSTR; ++j) {
+                if constexpr (SV) {
+                    const AT xv = (AT)__ldg(j < G.ni ? xi + ic[j][i] : x);
+                    v = fma(a[A_INS + j][i], j < G.ni ? xv : (AT)0, v);
+                } else {
+                    v = fma(a[A_INS + j][i], (AT)__ldg(xi + ic[j][i]), v);
+                }
+            }
 #pragma unroll
-            for (int q = 0; q < MG; ++q)
-                if (!SV || q < G.ng) v = fma(a[A_GLOB + q][i], xg[q], v);
+            for (int q = 0; q < MG; ++q) v = fma(a[A_GLOB + q][i], xg[q], v);  // xg[q] = 0 past n_glob
             const int64_t r = r0 + i;
             if (r < S.n_rows) {
                 AT yn;
@@ -182,12 +202,11 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // binary32 accumulation. The per-block integer sums convert exactly to binary64
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false,
-          bool SV = false>
-__global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y,
-                                                     double *__restrict__ z, double *__restrict__ z2,
-                                                     const LsqrState *__restrict__ st, int64_t tiles_per_warp,
-                                                     const uint32_t *__restrict__ fx_word)
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV>
+__device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
+                                                 double *__restrict__ z, double *__restrict__ z2,
+                                                 const LsqrState *__restrict__ st, int64_t tiles_per_warp,
+                                                 const uint32_t *__restrict__ fx_word)
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
@@ -248,30 +267,35 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         int32_t ic[NINSTR][R];
-#pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_instr<VT>(tb, G.npl, S.iw16, j, ic[j]);
         AT a[NASTRO][R], ai[NINSTR][R], ag[MG][R];
+        if constexpr (SV) {
+            // run-time sections: unconditional loads (absent slots read an attitude plane or the knot
+            // plane) so that they schedule together; absent astrometric and global slots are zeroed
+            // after the load, absent instrumental slots add nothing (their atomics are skipped)
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j) {
-            if (j < G.na) {
-                load_vals<VT, AT>(tb, j, a[j]);
-            } else {  // a section variant's missing astrometric slots add zeros (flushed to no column)
+            for (int j = 0; j < NINSTR; ++j) load_instr_or_knot<VT>(tb, G.npl, G.ni, S.iw16, j, ic[j]);
 #pragma unroll
-                for (int i = 0; i < R; ++i) a[j][i] = (AT)0;
+            for (int j = 0; j < NASTRO; ++j) {
+                load_vals<VT, AT>(tb, j < G.na ? j : G.p_att, a[j]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) a[j][i] = j < G.na ? a[j][i] : (AT)0;
             }
-        }
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_vals<VT, AT>(tb, G.p_ins + j, ai[j]);
+            for (int j = 0; j < NINSTR; ++j) load_vals<VT, AT>(tb, j < G.ni ? G.p_ins + j : G.p_att, ai[j]);
 #pragma unroll
-        for (int q = 0; q < MG; ++q) {
-            if (!SV || q < G.ng) {
-                load_vals<VT, AT>(tb, G.p_glob + q, ag[q]);
-            } else {
+            for (int q = 0; q < MG; ++q) {
+                load_vals<VT, AT>(tb, q < G.ng ? G.p_glob + q : G.p_att, ag[q]);
 #pragma unroll
-                for (int i = 0; i < R; ++i) ag[q][i] = (AT)0;
+                for (int i = 0; i < R; ++i) ag[q][i] = q < G.ng ? ag[q][i] : (AT)0;
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) load_instr<VT>(tb, S.iw16, j, ic[j]);
+#pragma unroll
+            for (int j = 0; j < NASTRO; ++j) load_vals<VT, AT>(tb, j, a[j]);
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) load_vals<VT, AT>(tb, A_INS + j, ai[j]);
+            load_vals<VT, AT>(tb, A_GLOB, ag[0]);
         }
         const int64_t r0 = t * T + lane * R;
         bool in[R];
@@ -285,8 +309,33 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
         for (int i = 0; i < R; ++i) {
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
-                if (j >= G.ni) continue;
                 const AT av = SQUARE ? ai[j][i] * ai[j][i] : ai[j][i];
+                if constexpr (SV) {
+                    // every contribution is formed from a valid column (an absent slot's index, read
+                    // from the knot plane, is replaced by 0) and only the atomic is predicated, so the
+                    // scale loads and products of the row overlap as in the standard instance
+                    const bool on = j < G.ni && in[i];
+                    const int32_t cj = j < G.ni ? ic[j][i] : 0;
+                    if (FX) {
+                        const int qv = __float2int_rn(av * yr[i] * sm_scale[cj]);
+                        if (on) atomicAdd(reinterpret_cast<int *>(sm_ins) + cj, qv);
+                    } else if (INSTR_SMEM) {
+                        if (on) atomicAdd(sm_ins + cj, av * yr[i]);
+                    } else {
+                        if (on) atomicAdd(zi + cj, (double)(av * yr[i]));
+                    }
+                    if constexpr (BOTH) {
+                        if (FX) {
+                            const int qq = __float2int_rn(av * av * sm_qscale[cj]);
+                            if (on) atomicAdd(reinterpret_cast<int *>(sm_sq) + cj, qq);
+                        } else if (INSTR_SMEM) {
+                            if (on) atomicAdd(sm_sq + cj, av * av);
+                        } else {
+                            if (on) atomicAdd(z2i + cj, (double)(av * av));
+                        }
+                    }
+                    continue;
+                }
                 if (in[i]) {
                     if (FX)
                         atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
@@ -399,6 +448,25 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
             }
         }
     }
+}
+
+// The standard row's instance, and a section variant's (run-time geometry) with
+// its registers capped for two resident blocks per SM, as the standard one has.
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
+__global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y, double *__restrict__ z,
+                                                     double *__restrict__ z2, const LsqrState *__restrict__ st,
+                                                     int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word)
+{
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false>(S, y, z, z2, st, tiles_per_warp, fx_word);
+}
+
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
+__global__ void __launch_bounds__(256, 2) k_aprod2_star_sv(SysView<VT> S, const UT *__restrict__ y,
+                                                           double *__restrict__ z, double *__restrict__ z2,
+                                                           const LsqrState *__restrict__ st, int64_t tiles_per_warp,
+                                                           const uint32_t *__restrict__ fx_word)
+{
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, true>(S, y, z, z2, st, tiles_per_warp, fx_word);
 }
 
 // Add a warp's run sums of the 12 attitude columns of knot k (warp-collective).
@@ -612,7 +680,7 @@ template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bo
 static cudaError_t aprod2_star_launch_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                         cudaStream_t s)
 {
-    auto kern = k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX, SV>;
+    auto kern = SV ? k_aprod2_star_sv<VT, UT, AT, INS, MODE, LS, FX> : k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX>;
     const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX ? 2 : 1)) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

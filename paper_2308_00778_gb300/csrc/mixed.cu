@@ -61,21 +61,28 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
         int32_t kn[R];
         load_ints<R>(ti, 0, kn);
         int32_t ic[NINSTR][R];
-#pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_instr<float>(tb, G.npl, S.iw16, j, ic[j]);
         float a[A_GLOB + MG][R];
+        if constexpr (SV) {
+            // run-time sections: unconditional loads (absent slots read an attitude plane or the
+            // knot plane) and masked gathers, as in aprod 1
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j)
-            if (j < G.na) load_vals<float, float>(tb, j, a[j]);
+            for (int j = 0; j < NINSTR; ++j) load_instr_or_knot<float>(tb, G.npl, G.ni, S.iw16, j, ic[j]);
 #pragma unroll
-        for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<float, float>(tb, G.p_att + j, a[A_ATT + j]);
+            for (int j = 0; j < NASTRO; ++j) load_vals<float, float>(tb, j < G.na ? j : G.p_att, a[j]);
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni) load_vals<float, float>(tb, G.p_ins + j, a[A_INS + j]);
+            for (int j = 0; j < NAXES * NPARAXIS; ++j) load_vals<float, float>(tb, G.p_att + j, a[A_ATT + j]);
 #pragma unroll
-        for (int q = 0; q < MG; ++q)
-            if (!SV || q < G.ng) load_vals<float, float>(tb, G.p_glob + q, a[A_GLOB + q]);
+            for (int j = 0; j < NINSTR; ++j)
+                load_vals<float, float>(tb, j < G.ni ? G.p_ins + j : G.p_att, a[A_INS + j]);
+#pragma unroll
+            for (int q = 0; q < MG; ++q)
+                load_vals<float, float>(tb, q < G.ng ? G.p_glob + q : G.p_att, a[A_GLOB + q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
+#pragma unroll
+            for (int j = 0; j < A_GLOB + MG; ++j) load_vals<float, float>(tb, j, a[j]);
+        }
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
@@ -85,11 +92,18 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
             sh[i] = 0.f;
             c[i] = 0.f;
         }
+        const float2 zero2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j)
-            if (j < G.na)
 #pragma unroll
-                for (int i = 0; i < R; ++i) acc_term(a[j][i], xhl[(int64_t)G.na * sr[i] + j], sh[i], c[i]);
+            for (int i = 0; i < R; ++i) {
+                if constexpr (SV) {
+                    const float2 xv = xhl[j < G.na ? (int64_t)G.na * sr[i] + j : 0];
+                    acc_term(a[j][i], j < G.na ? xv : zero2, sh[i], c[i]);
+                } else {
+                    acc_term(a[j][i], xhl[NASTRO * sr[i] + j], sh[i], c[i]);
+                }
+            }
 #pragma unroll
         for (int ax = 0; ax < NAXES; ++ax)
 #pragma unroll
@@ -99,14 +113,19 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
                     acc_term(a[A_ATT + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
 #pragma unroll
         for (int j = 0; j < NINSTR; ++j)
-            if (j < G.ni)
 #pragma unroll
-                for (int i = 0; i < R; ++i) acc_term(a[A_INS + j][i], xi[ic[j][i]], sh[i], c[i]);
+            for (int i = 0; i < R; ++i) {
+                if constexpr (SV) {
+                    const float2 xv = xhl[j < G.ni ? S.instr0 + ic[j][i] : 0];
+                    acc_term(a[A_INS + j][i], j < G.ni ? xv : zero2, sh[i], c[i]);
+                } else {
+                    acc_term(a[A_INS + j][i], xi[ic[j][i]], sh[i], c[i]);
+                }
+            }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
 #pragma unroll
-            for (int q = 0; q < MG; ++q)
-                if (!SV || q < G.ng) acc_term(a[A_GLOB + q][i], xg[q], sh[i], c[i]);
+            for (int q = 0; q < MG; ++q) acc_term(a[A_GLOB + q][i], xg[q], sh[i], c[i]);  // xg[q] = 0 past n_glob
             const int64_t r = r0 + i;
             if (r < S.n_rows) {
                 const float2 bb = split_double(__ldcs(b64 + r));

@@ -138,6 +138,36 @@ __device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, int n
     }
 }
 
+// For the run-time geometry of a section variant: instrumental plane j when j < ni, else a
+// same-width read of the record's knot plane (always present), so that the load is
+// unconditional and can be scheduled with the others; the caller masks what an absent plane
+// would gather.
+template <typename VT>
+__device__ __forceinline__ void load_instr_or_knot(const uint8_t *__restrict__ tb, int npl, int ni, bool iw16, int j,
+                                                   int32_t (&out)[Tile<VT>::R])
+{
+    constexpr int R = Tile<VT>::R;
+    constexpr int T = Tile<VT>::T;
+    const int lane = threadIdx.x & 31;
+    const uint8_t *knot = tb + (int64_t)npl * Tile<VT>::VBLK;
+    const uint8_t *p = j < ni ? knot + Tile<VT>::IBLK + (int64_t)j * T * (iw16 ? 2 : 4) : knot;
+    if (iw16) {
+        if constexpr (R == 4) {
+            const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p) + lane);
+            out[0] = (int32_t)(v.x & 0xffffu);
+            out[1] = (int32_t)(v.x >> 16);
+            out[2] = (int32_t)(v.y & 0xffffu);
+            out[3] = (int32_t)(v.y >> 16);
+        } else {
+            const uint32_t v = __ldcs(reinterpret_cast<const uint32_t *>(p) + lane);
+            out[0] = (int32_t)(v & 0xffffu);
+            out[1] = (int32_t)(v >> 16);
+        }
+    } else {
+        load_ints<R>(p, 0, out);
+    }
+}
+
 // the same for the standard row's 24 value planes
 template <typename VT>
 __device__ __forceinline__ void load_instr(const uint8_t *__restrict__ tb, bool iw16, int j,

@@ -190,12 +190,10 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
         float a[NASTRO][R];
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) {
-            if (j < na) {
-                load_vals<VT, float>(tb, j, a[j]);
-            } else {
+            // a variant's absent slots read an attitude plane (always present), zeroed after the load
+            load_vals<VT, float>(tb, j < na ? j : (SV ? S.p_att : A_ATT), a[j]);
 #pragma unroll
-                for (int i = 0; i < R; ++i) a[j][i] = 0.f;
-            }
+            for (int i = 0; i < R; ++i) a[j][i] = j < na ? a[j][i] : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < R; ++i)
@@ -269,8 +267,7 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         float a[NASTRO][R];
 #pragma unroll
-        for (int j = 0; j < NASTRO; ++j)
-            if (j < na) load_vals<float, float>(tb, j, a[j]);
+        for (int j = 0; j < NASTRO; ++j) load_vals<float, float>(tb, j < na ? j : (SV ? S.p_att : A_ATT), a[j]);
         const int64_t r0 = t * T + lane * R;
         int64_t sr[R];
         stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
@@ -287,8 +284,10 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
         for (int i = 0; i < R; ++i) {
             const double *xa = x0 + (int64_t)na * sr[i];
 #pragma unroll
-            for (int j = 0; j < NASTRO; ++j)
-                if (j < na) v[i] = fmaf(-a[j][i], (float)__ldg(xa + j), v[i]);
+            for (int j = 0; j < NASTRO; ++j) {  // a variant's absent slots gather x0[0], masked to zero
+                const float xv = (float)__ldg(j < na ? xa + j : x0);
+                v[i] = fmaf(-a[j][i], j < na ? xv : 0.f, v[i]);
+            }
             if (r0 + i < S.n_rows) ssq = fmaf(v[i], v[i], ssq);
         }
         if (full) {
