@@ -202,18 +202,19 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // binary32 accumulation. The per-block integer sums convert exactly to binary64
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV>
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV,
+          bool ATT = false>
 __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
                                                  double *__restrict__ z, double *__restrict__ z2,
                                                  const LsqrState *__restrict__ st, int64_t tiles_per_warp,
-                                                 const uint32_t *__restrict__ fx_word)
+                                                 const uint32_t *__restrict__ fx_word, int32_t fxs)
 {
     constexpr bool SQUARE = MODE == A2_SQUARE;
     constexpr bool BOTH = MODE == A2_BOTH;
     constexpr int MG = Sec<SV>::MAXG;
     const Sec<SV> G(S);
-    static_assert(!FX || (INSTR_SMEM && (MODE == A2_PROD || MODE == A2_BOTH) && sizeof(AT) == 4),
-                  "fixed point: binary32 products (and squares)");
+    static_assert(!FX || (INSTR_SMEM && sizeof(AT) == 4), "fixed point: binary32 products and squares");
+    static_assert(!ATT || (FX && !SV), "attitude columns: fixed point, standard row");
     __shared__ int s_bad;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
@@ -221,22 +222,38 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     __shared__ double sm32[32];
     __shared__ AT wred[8][NASTRO * 32];
     if (LSQR && st->done) return;
+    // block-private columns: the instrumental ones, then (ATT) the attitude ones at n_instr + a*n_dfa + k
+    const int32_t ncol = ATT ? S.n_instr + NAXES * S.n_dfa : S.n_instr;
     AT *sm_ins = reinterpret_cast<AT *>(smem_raw);
-    AT *sm_sq = sm_ins + S.n_instr;  // BOTH: the squares' accumulators follow the products'
-    const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * S.n_instr : S.n_instr) : 0;
+    AT *sm_sq = sm_ins + ncol;  // BOTH: the squares' accumulators follow the products'
+    const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * ncol : ncol) : 0;
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;  // also integer zero
-    // FX: per-column scales after the accumulators (BOTH: products', then squares')
+    // FX: per-column scales of the instrumental columns after the accumulators (BOTH: products', then
+    // squares'); fx_word holds fxs columns of max |a| and of bits, then max |y|. The attitude columns
+    // share one scale (their bounds differ little): from their largest |a| and fewest bits, the two
+    // words at 3 fxs + 1 and 3 fxs + 2 (one shared-memory read less per product).
+    __shared__ float s_att_sc, s_att_qsc;
     float *sm_scale = reinterpret_cast<float *>(smem_raw) + nsm;
     float *sm_qscale = sm_scale + S.n_instr;
     if (FX) {
-        const float ymax = __uint_as_float(fx_word[2 * S.n_instr]);
+        const float ymax = SQUARE ? 1.f : __uint_as_float(fx_word[2 * fxs]);
         if (threadIdx.x == 0) s_bad = !(ymax < INFINITY);  // non-finite y: the sums are made NaN below
+        if (ATT && threadIdx.x == 0) {
+            const float am = __uint_as_float(fx_word[3 * fxs + 1]);
+            const float lim = (float)((1u << fx_word[3 * fxs + 2]) - 1u);
+            const float bound = SQUARE ? am * am : am * ymax;
+            float sc = 1.f, qs = 1.f;
+            if (bound > 0.f && bound < INFINITY) sc = ldexpf(1.f, min(ilogbf(lim / bound), 126));
+            if (am * am > 0.f && am * am < INFINITY) qs = ldexpf(1.f, min(ilogbf(lim / (am * am)), 126));
+            s_att_sc = sc;
+            s_att_qsc = qs;
+        }
         for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
             // the largest power of two with bound * scale <= 2^b_j - 1, bound = max|a_j| max|y|
-            // for the products and max|a_j|^2 for the squares
+            // for the products and max|a_j|^2 for the squares (and for the squares' pass)
             const float am = __uint_as_float(fx_word[i]);
-            const float lim = (float)((1u << fx_word[S.n_instr + i]) - 1u);
-            const float bound = am * ymax;
+            const float lim = (float)((1u << fx_word[fxs + i]) - 1u);
+            const float bound = SQUARE ? am * am : am * ymax;
             float sc = 1.f;
             if (bound > 0.f && bound < INFINITY) sc = ldexpf(1.f, min(ilogbf(lim / bound), 126));
             sm_scale[i] = sc;
@@ -415,6 +432,34 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
             }
             k = kn;
         }
+        if constexpr (ATT) {
+            // the 12 attitude products of each row into the block-private fixed-point columns
+            // (after the rest of the tile: fewer registers live than with all planes loaded at once)
+            int32_t knot[R];
+            load_ints<R>(tb + NPAR * Tile<VT>::VBLK, 0, knot);
+            int *acc_a = reinterpret_cast<int *>(sm_ins) + S.n_instr;
+            int *accq_a = reinterpret_cast<int *>(sm_ins) + ncol + S.n_instr;
+            const float sc_a = s_att_sc, qsc_a = s_att_qsc;
+#pragma unroll
+            for (int ax = 0; ax < NAXES; ++ax) {
+                AT at[NPARAXIS][R];
+#pragma unroll
+                for (int j = 0; j < NPARAXIS; ++j) load_vals<VT, AT>(tb, A_ATT + NPARAXIS * ax + j, at[j]);
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+#pragma unroll
+                    for (int j = 0; j < NPARAXIS; ++j) {
+                        const int32_t col = ax * S.n_dfa + knot[i] + j;
+                        const AT av = SQUARE ? at[j][i] * at[j][i] : at[j][i];
+                        const int qv = __float2int_rn(av * yr[i] * sc_a);
+                        if (in[i]) atomicAdd(acc_a + col, qv);
+                        if constexpr (BOTH) {
+                            const int qq = __float2int_rn(av * av * qsc_a);
+                            if (in[i]) atomicAdd(accq_a + col, qq);
+                        }
+                    }
+            }
+        }
     }
     if (t0 < t1) {
         flush_astro_run(acc, k, wbuf, z, G.na);
@@ -425,12 +470,15 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
         for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
             const int q = reinterpret_cast<const int *>(sm_ins)[i];
             if (q == 0) continue;
-            if (BOTH && i >= S.n_instr)  // a power of two: exact
-                atomicAdd(z2i + (i - S.n_instr), (double)q / (double)sm_qscale[i - S.n_instr]);
-            else
-                atomicAdd(zi + i, (double)q / (double)sm_scale[i]);
+            const bool sq = BOTH && i >= ncol;
+            const int32_t col = sq ? i - ncol : i;
+            // column col of the block-private space: instrumental, or (ATT) attitude
+            const bool ins = col < S.n_instr;
+            const int64_t dst = ins ? S.instr0 + col : S.att0 + (col - S.n_instr);
+            const float sc = ins ? (sq ? sm_qscale[col] : sm_scale[col]) : (sq ? s_att_qsc : s_att_sc);
+            atomicAdd((sq ? z2 : z) + dst, (double)q / (double)sc);  // the scale is a power of two: exact
         }
-        if (s_bad && threadIdx.x == 0) atomicAdd(zi, (double)NAN);
+        if (s_bad && threadIdx.x == 0) atomicAdd(S.n_instr ? zi : z + S.att0, (double)NAN);
     } else {
         for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
             const AT v = sm_ins[i];
@@ -455,18 +503,31 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y, double *__restrict__ z,
                                                      double *__restrict__ z2, const LsqrState *__restrict__ st,
-                                                     int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word)
+                                                     int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word,
+                                                     int32_t fxs)
 {
-    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false>(S, y, z, z2, st, tiles_per_warp, fx_word);
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false>(S, y, z, z2, st, tiles_per_warp, fx_word, fxs);
 }
 
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
 __global__ void __launch_bounds__(256, 2) k_aprod2_star_sv(SysView<VT> S, const UT *__restrict__ y,
                                                            double *__restrict__ z, double *__restrict__ z2,
                                                            const LsqrState *__restrict__ st, int64_t tiles_per_warp,
-                                                           const uint32_t *__restrict__ fx_word)
+                                                           const uint32_t *__restrict__ fx_word, int32_t fxs)
 {
-    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, true>(S, y, z, z2, st, tiles_per_warp, fx_word);
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, true>(S, y, z, z2, st, tiles_per_warp, fx_word, fxs);
+}
+
+// The star pass that also takes the attitude columns (binary32 fixed point, standard row): the whole
+// aprod 2 in one pass over the row tiles, two blocks per SM as the plain star pass.
+template <typename VT, int MODE, bool LSQR>
+__global__ void __launch_bounds__(256, 2) k_aprod2_star_att(SysView<VT> S, const float *__restrict__ y,
+                                                            double *__restrict__ z, double *__restrict__ z2,
+                                                            const LsqrState *__restrict__ st, int64_t tiles_per_warp,
+                                                            const uint32_t *__restrict__ fx_word, int32_t fxs)
+{
+    aprod2_star_body<VT, float, float, true, MODE, LSQR, true, false, true>(S, y, z, z2, st, tiles_per_warp, fx_word,
+                                                                            fxs);
 }
 
 // Add a warp's run sums of the 12 attitude columns of knot k (warp-collective).
@@ -526,15 +587,27 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
     for (int j = 0; j < NA; ++j) acc[j] = (AT)0;
 #pragma unroll
     for (int j = 0; j < (BOTH ? NA : 1); ++j) sacc[j] = (AT)0;
+    // the row permutation is read one tile ahead, so that the gather of y through it is issued
+    // together with the tile's coefficient loads instead of after a dependent load
+    int32_t pr_next[R];
+    if (!SQUARE) load_ints<R>(S.atiles + t0 * Tile<VT>::ABYTES + NA * Tile<VT>::VBLK, 0, pr_next);
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.atiles + t * Tile<VT>::ABYTES;
         const int64_t q = t * T;
         const int64_t lastp = min(q + T - 1, n - 1);
         const int64_t pl = q + lane * R;
+        int32_t pr[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) pr[i] = pr_next[i];
+        AT yr[R];
+        if (!SQUARE) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)y[pr[i]] : (AT)0;
+            if (t + 1 < t1) load_ints<R>(tb + Tile<VT>::ABYTES + NA * Tile<VT>::VBLK, 0, pr_next);
+        }
         AT a[NA][R];
 #pragma unroll
         for (int j = 0; j < NA; ++j) load_vals<VT, AT>(tb, j, a[j]);
-        AT yr[R];
         if (SQUARE) {
 #pragma unroll
             for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)1 : (AT)0;
@@ -543,10 +616,6 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
 #pragma unroll
                 for (int i = 0; i < R; ++i) a[j][i] = a[j][i] * a[j][i];
         } else {
-            int32_t pr[R];
-            load_ints<R>(tb + NA * Tile<VT>::VBLK, 0, pr);
-#pragma unroll
-            for (int i = 0; i < R; ++i) yr[i] = (pl + i < n) ? (AT)y[pr[i]] : (AT)0;
             if constexpr (BOTH) {
 #pragma unroll
                 for (int i = 0; i < R; ++i)
@@ -641,7 +710,7 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
         }
         if (!x || !y) return cudaErrorInvalidValue;
         // the inner iteration's star pass reads max |u| (fixed-point instrumental sums)
-        uint32_t *ymax = (sizeof(AT) == 4 && st && c->fx_bits) ? c->fx_word + 2 * (size_t)c->n_instr : nullptr;
+        uint32_t *ymax = (sizeof(AT) == 4 && st) ? fx_ymax(c) : nullptr;
         kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part, ymax);
         return cudaGetLastError();
     };
@@ -693,7 +762,23 @@ static cudaError_t aprod2_star_launch_t(const gsr_ctx *c, const void *y, double 
     } else {
         tile_ranges(c, kern, dyn, &per, &blocks);
     }
-    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per, c->fx_word);
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per, c->fx_word, c->fx_nc);
+    return cudaGetLastError();
+}
+
+// the whole binary32 aprod 2 as one star pass with the attitude columns (att_fused)
+template <int MODE, bool LS>
+static cudaError_t aprod2_fused_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
+                                       cudaStream_t s)
+{
+    auto kern = k_aprod2_star_att<float, MODE, LS>;
+    const int32_t ncol = c->n_instr + NAXES * c->n_dfa;
+    // accumulators of every column (twice for products and squares), scales of the instrumental ones
+    const size_t dyn = sizeof(float) * ((size_t)ncol + (size_t)c->n_instr) * (MODE == A2_BOTH ? 2 : 1);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)c->fx_blocks, kThreads, dyn, s>>>(view<float>(c), (const float *)y, x, x2, st, c->fx_per,
+                                                      c->fx_word, c->fx_nc);
     return cudaGetLastError();
 }
 
@@ -724,16 +809,29 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     if (MODE != A2_SQUARE && !y) return cudaErrorInvalidValue;
     if (MODE == A2_BOTH && !x2) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    constexpr bool F32 = sizeof(AT) == 4 && (MODE == A2_PROD || MODE == A2_BOTH);
+    constexpr bool F32 = sizeof(AT) == 4;
+    if constexpr (F32 && sizeof(VT) == 4) {
+        if (att_fused(c)) {
+            // one pass: the star pass takes the attitude columns too (no attitude pass); max |y| comes
+            // from the LSQR aprod 1 of the same iteration (the LSQR colA clears it for the next one),
+            // else from a pass over y here, cleared after the star pass
+            if (MODE != A2_SQUARE && !LS) {
+                k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows, fx_ymax(c));
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+            if ((e = aprod2_fused_launch<MODE, LS>(c, y, x, x2, st, s)) != cudaSuccess) return e;
+            if (MODE != A2_SQUARE && !LS) e = cudaMemsetAsync(fx_ymax(c), 0, sizeof(uint32_t), s);
+            return e;
+        }
+    }
     // the combined pass needs twice the shared words; it keeps binary32 atomics when they do not fit
     const bool fx = F32 && c->fx_bits > 0 &&
-                    (MODE == A2_PROD || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
+                    (MODE != A2_BOTH || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
     if (fx) {
         // fixed-point instrumental sums: max |y| comes from the LSQR aprod 1 of the same iteration,
         // else from a pass over y here
-        if (!LS) {
-            k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows,
-                                                                 c->fx_word + 2 * (size_t)c->n_instr);
+        if (MODE != A2_SQUARE && !LS) {
+            k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows, fx_ymax(c));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if constexpr (F32) e = aprod2_star_launch<VT, UT, AT, true, MODE, LS, true>(c, y, x, x2, st, s);
@@ -748,7 +846,7 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     int64_t per = 0, blocks = 0;
     tile_ranges(c, kern, 0, &per, &blocks);
     kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), (const UT *)y, x, x2, st, per,
-                                               fx ? c->fx_word + 2 * (size_t)c->n_instr : nullptr);
+                                               fx && MODE != A2_SQUARE ? fx_ymax(c) : nullptr);
     return cudaGetLastError();
 }
 

@@ -260,6 +260,7 @@ static gsr_status set_rows_mapped(gsr_ctx *c, int64_t row0, int64_t nrows, const
     if (hw[0] || hw[1] || hw[2]) {
         unmark_rows(c, row0, row0 + nrows);
         c->att_valid = false;
+        c->fx_valid = false;
         if (hw[0]) return fail(c, GSR_EINVAL, "att_knot out of range [0, n_dfa-4] (the rows are not loaded)");
         if (hw[1]) return fail(c, GSR_EINVAL, "instr_col out of range [0, n_instr) (the rows are not loaded)");
         return fail(c, GSR_ENUMERIC, "non-finite coefficient (the rows are not loaded)");
@@ -550,6 +551,7 @@ GSR_API gsr_status gsr_set_rows(gsr_ctx *c, int64_t row0, int64_t nrows, const v
     if (rc == GSR_OK) {
         mark_rows(c, row0, row0 + nrows);
         c->att_valid = false;
+        c->fx_valid = false;
     }
     return rc;
 }
@@ -611,7 +613,7 @@ GSR_API gsr_status gsr_aprod2(gsr_ctx *c, const double *y, double *x, void *stre
     if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream);
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream, true);
     if (rc != GSR_OK) return rc;
     if ((e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(c, e, "aprod2");
@@ -638,7 +640,7 @@ GSR_API gsr_status gsr_aprod2_f32(gsr_ctx *c, const float *y, double *x, void *s
     if ((!x || !y) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream);
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream, false);
     if (rc != GSR_OK) return rc;
     if ((e = launch_aprod2(c, y, x, false, nullptr, (cudaStream_t)stream, true)) != cudaSuccess)
         return cuda_fail(c, e, "aprod2_f32");
@@ -687,7 +689,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         (e = cudaStreamWaitEvent(c->own, c->ev, 0)) != cudaSuccess)
         return cuda_fail(c, e, "stream ordering");
     {
-        const gsr_status rl = ensure_att_layout(c, c->own);
+        // binary64 aprod 2 passes (the plain solver) read the knot-ordered attitude copy
+        const gsr_status rl = ensure_att_layout(c, c->own, prm.mode == GSR_PLAIN);
         if (rl != GSR_OK) return rl;
     }
     // warm start: x0 on the device from the features (and the network)

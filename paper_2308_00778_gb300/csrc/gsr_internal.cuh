@@ -130,6 +130,7 @@ struct gsr_ctx {
     int32_t *first_star = nullptr;   // [n_tiles + 1] star of the first row of each tile
     int64_t *knot_ptr = nullptr;     // [n_dfa-2] first position of each knot
     bool att_valid = false;          // atiles / knot_ptr match the loaded rows
+    int32_t fx_sig = -1;             // kernel choice the cached graphs were captured with
     // fixed-point instrumental sums of the binary32 star pass (layout.cu): the fewest bits per
     // contribution over the columns (0: binary32 shared atomics instead), the pass's fixed
     // partition, and device words: [n_instr] max |coefficient| per column (binary32 bits),
@@ -137,6 +138,13 @@ struct gsr_ctx {
     int32_t fx_bits = 0;
     int64_t fx_per = 0, fx_blocks = 0;
     uint32_t *fx_word = nullptr;
+    // fixed-point columns: the instrumental ones, then (fx_att) the 3 n_dfa attitude columns, whose
+    // products the star pass then adds into shared memory as well (no attitude pass; the knot-ordered
+    // copy is built only for the binary64 aprod 2). fx_word holds [fx_nc] max |a| per column, [fx_nc]
+    // bits per column, max |y|, [fx_nc] scratch.
+    int32_t fx_nc = 0;
+    bool fx_att = false;
+    bool fx_valid = false;           // the statistics match the loaded rows
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -199,8 +207,14 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
 cudaError_t launch_aprod2_both(const gsr_ctx *c, const void *y, double *x, double *sq, cudaStream_t s, bool inner32);
 int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 
-// knot-ordered attitude copy (layout.cu); built once per loaded system
-gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s);
+// per-system layout work (layout.cu), once per loaded system: the fixed-point statistics of binary32
+// storage, and the knot-ordered attitude copy when binary64 aprod 2 passes will run (binary64) or the
+// binary32 star pass does not take the attitude columns (fx_att false)
+gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64);
+// the binary32 aprod 2 adds the attitude products in its star pass (no attitude pass)
+inline bool att_fused(const gsr_ctx *c) { return c->prec == GSR_FP32 && c->fx_bits > 0 && c->fx_att && !c->sv; }
+// max |y| word of the fixed-point sums (nullptr when they are off)
+inline uint32_t *fx_ymax(const gsr_ctx *c) { return c->fx_bits > 0 ? c->fx_word + 2 * (size_t)c->fx_nc : nullptr; }
 
 // LSQR driver (lsqr.cu)
 // x0_dev: x0 is device memory whatever prm->where says (the warm start's vector)
@@ -210,6 +224,7 @@ gsr_status lsqr_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0,
                       double *se_out, gsr_solve_info *info, cudaStream_t s, bool p_ready = false);
 gsr_status ensure_workspace(gsr_ctx *c);
 void free_workspace(gsr_ctx *c);
+void drop_graphs(gsr_ctx *c);  // forget the cached iteration graphs (recaptured on next use)
 void default_params(gsr_solve_params *p);
 int col_grid(const gsr_ctx *c, int64_t n);
 // with y (and use): the same pass also adds A^T y to z (binary32 products when f32)

@@ -105,21 +105,23 @@ __global__ void k_gather_att(const VT *__restrict__ rec, const int32_t *__restri
     }
 }
 
-// For the fixed-point instrumental sums of the binary32 star pass (aprod.cu),
-// per instrumental column j over the pass's partition (each warp a contiguous
-// range of `per` tiles, 8 warps a block): the largest number of contributions
-// one block adds to column j (kmax[j]) and the largest |coefficient| of column
-// j (amax[j], binary32 bits). Both arrays are zero on entry.
+// For the fixed-point sums of the binary32 star pass (aprod.cu), per column j
+// over the pass's partition (each warp a contiguous range of `per` tiles, 8
+// warps a block): the largest number of contributions one block adds to
+// column j (kmax[j]) and the largest |coefficient| of column j (amax[j],
+// binary32 bits). Columns [0, n_instr) are the instrumental unknowns; with
+// att, columns n_instr + a*n_dfa + k the attitude unknowns. Both arrays are
+// zero on entry.
 template <bool SV>
 __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t per, uint32_t *__restrict__ kmax,
-                                                     uint32_t *__restrict__ amax)
+                                                     uint32_t *__restrict__ amax, int32_t nc, int32_t att)
 {
     const Sec<SV> G(S);
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
-    extern __shared__ uint32_t cnt[];  // [n_instr] counts, then [n_instr] max |a| bits
-    uint32_t *am = cnt + S.n_instr;
-    for (int32_t i = threadIdx.x; i < 2 * S.n_instr; i += blockDim.x) cnt[i] = 0u;
+    extern __shared__ uint32_t cnt[];  // [nc] counts, then [nc] max |a| bits
+    uint32_t *am = cnt + nc;
+    for (int32_t i = threadIdx.x; i < 2 * nc; i += blockDim.x) cnt[i] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -141,47 +143,87 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
                     atomicMax(am + ic[i], __float_as_uint(fabsf(a[i])));
                 }
         }
+        if (att) {
+            int32_t kn[R];
+            load_ints<R>(tb + (int64_t)G.npl * Tile<float>::VBLK, 0, kn);
+#pragma unroll
+            for (int q = 0; q < NAXES * NPARAXIS; ++q) {
+                float a[R];
+                load_vals<float, float>(tb, G.p_att + q, a);
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    if (r0 + i < S.n_rows) {
+                        const int32_t col = S.n_instr + (q / NPARAXIS) * S.n_dfa + kn[i] + (q % NPARAXIS);
+                        atomicAdd(cnt + col, 1u);
+                        atomicMax(am + col, __float_as_uint(fabsf(a[i])));
+                    }
+            }
+        }
     }
     __syncthreads();
-    for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+    uint32_t am_att = 0u;
+    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
         if (cnt[i]) atomicMax(kmax + i, cnt[i]);
         if (am[i]) atomicMax(amax + i, am[i]);
+        if (i >= S.n_instr) am_att = max(am_att, am[i]);
+    }
+    // the largest |coefficient| over all attitude columns (one scale serves them all): after the
+    // scratch counts, kmax + nc
+    if (att) {
+        am_att = __reduce_max_sync(0xffffffffu, am_att);
+        if ((threadIdx.x & 31) == 0 && am_att) atomicMax(kmax + nc, am_att);
     }
 }
 
+// Shared memory of the fixed-point star pass (aprod.cu) per block: accumulators and scales of
+// every column, twice for the pass that sums products and squares together.
+static constexpr size_t kFxSmemOne = 100 * 1024;   // two blocks per SM
+static constexpr size_t kFxSmemBoth = 200 * 1024;  // one block per SM
+
 // Per-column bits of the fixed-point sums (all 0: keep binary32 atomics):
 // bits_j = 31 - ceil(log2(kmax_j + 1)), so that no block can overflow column j;
-// the sums are used only when every column gets at least 20 bits. Launches the
-// statistics and the copy of kmax into *kmax_h (asynchronous); the caller
-// synchronises s and calls fixed_point_finish.
+// the instrumental sums are used only when every instrumental column gets at
+// least 20 bits, the attitude columns join them (fx_att) when every attitude
+// column does too. Launches the statistics and the copy of kmax into *kmax_h
+// (asynchronous); the caller synchronises s and calls fixed_point_finish.
 static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uint32_t> *kmax_h)
 {
     c->fx_bits = 0;
+    c->fx_att = false;
     kmax_h->clear();
     if (c->prec != GSR_FP32 || c->n_rows == 0 || c->n_ipr == 0 || c->n_instr == 0) return GSR_OK;
     const int32_t ni = c->n_instr;
-    const size_t smem = 2 * sizeof(uint32_t) * (size_t)ni;  // the stats kernel's and the star pass's
-    if (smem > 100 * 1024) return GSR_OK;
+    if (2 * sizeof(uint32_t) * (size_t)ni > kFxSmemOne) return GSR_OK;
+    // the attitude columns join when their accumulators fit beside the instrumental ones
+    const int64_t nc_att = (int64_t)ni + (int64_t)NAXES * c->n_dfa;
+    const bool att = !c->sv && 2 * sizeof(uint32_t) * (size_t)nc_att <= kFxSmemOne &&
+                     4 * sizeof(uint32_t) * (size_t)nc_att <= kFxSmemBoth;
+    const int32_t nc = att ? (int32_t)nc_att : ni;
     cudaError_t e = cudaSuccess;
-    // device words: [0, ni) max |a| per column, [ni, 2ni) bits per column, [2ni] max |y| of the
-    // current aprod 2, then [ni] scratch counts
-    if (!c->fx_word && (e = cudaMalloc(&c->fx_word, sizeof(uint32_t) * (3 * (size_t)ni + 1))) != cudaSuccess)
+    // device words: [0, nc) max |a| per column, [nc, 2nc) bits per column, [2nc] max |y| of the
+    // current aprod 2, then [nc] scratch counts, then the attitude columns' largest |a| and fewest bits
+    if (c->fx_word && c->fx_nc != nc) {
+        cudaFree(c->fx_word);
+        c->fx_word = nullptr;
+    }
+    if (!c->fx_word && (e = cudaMalloc(&c->fx_word, sizeof(uint32_t) * (3 * (size_t)nc + 3))) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point words");
-    uint32_t *kcnt = c->fx_word + 2 * ni + 1;
+    c->fx_nc = nc;
+    uint32_t *kcnt = c->fx_word + 2 * nc + 1;
     // the partition: two blocks of 8 warps per SM, contiguous ranges of at least 8 tiles per warp
     const int64_t warps = (int64_t)c->sm_count * 2 * 8;
     c->fx_per = std::max<int64_t>((c->n_tiles + warps - 1) / warps, 8);
     c->fx_blocks = std::max<int64_t>(((c->n_tiles + c->fx_per - 1) / c->fx_per + 7) / 8, 1);
-    if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)ni + 1), s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)nc + 3), s)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)nc;
     auto stats = c->sv ? k_instr_stats<true> : k_instr_stats<false>;
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
-    stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word);
-    kmax_h->resize((size_t)ni);
+    stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word, nc, att ? 1 : 0);
+    kmax_h->resize((size_t)nc);
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * (size_t)ni, cudaMemcpyDeviceToHost, s)) !=
+        (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * (size_t)nc, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
     return GSR_OK;
@@ -191,25 +233,33 @@ static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vect
 {
     if (kmax.empty()) return GSR_OK;
     std::vector<uint32_t> bits(kmax.size());
-    int min_bits = 30;
+    int min_ins = 30, min_att = 30;
     for (size_t j = 0; j < kmax.size(); ++j) {
         int lg = 0;  // ceil(log2(kmax + 1))
         while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax[j] + 1) ++lg;
         bits[j] = (uint32_t)std::min(31 - lg, 30);
-        min_bits = std::min(min_bits, (int)bits[j]);
+        if ((int64_t)j < c->n_instr)
+            min_ins = std::min(min_ins, (int)bits[j]);
+        else
+            min_att = std::min(min_att, (int)bits[j]);
     }
-    if (min_bits < 20) return GSR_OK;
+    if (min_ins < 20) return GSR_OK;
     // pageable source: the call returns once the bytes are staged, the kernels that read them follow on s
-    const cudaError_t e = cudaMemcpyAsync(c->fx_word + kmax.size(), bits.data(), sizeof(uint32_t) * bits.size(),
-                                          cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(c->fx_word + kmax.size(), bits.data(), sizeof(uint32_t) * bits.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && (int64_t)kmax.size() > c->n_instr) {
+        const uint32_t att_bits = (uint32_t)min_att;
+        e = cudaMemcpyAsync(c->fx_word + 3 * kmax.size() + 2, &att_bits, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "fixed-point setup");
-    c->fx_bits = min_bits;
+    c->fx_bits = min_ins;
+    c->fx_att = (int64_t)kmax.size() > c->n_instr && min_att >= 20;
     return GSR_OK;
 }
 
-gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
+// the knot-ordered attitude copy of the loaded rows
+static gsr_status build_att_copy(gsr_ctx *c, cudaStream_t s)
 {
-    if (c->att_valid) return GSR_OK;
     const int64_t n = c->n_rows;
     const int32_t nk = c->n_dfa - 3;  // knots a row may start at: 0..n_dfa-4
     cudaError_t e = cudaSuccess;
@@ -217,7 +267,6 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
         e = cudaMemsetAsync(c->knot_ptr, 0, sizeof(int64_t) * (size_t)(nk + 1), s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(c, e, "attitude layout");
-        c->att_valid = true;
         return GSR_OK;
     }
     int32_t *keys_in = nullptr, *keys_out = nullptr, *vals_in = nullptr, *perm = nullptr;
@@ -227,8 +276,6 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
     const bool f32 = c->prec == GSR_FP32;
     const uint8_t *tiles = (const uint8_t *)c->tiles;
     int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 8);
-    std::vector<uint32_t> kmax_h;
-    gsr_status rf = GSR_OK;
     // scratch from the context's stream-ordered pool, which keeps its memory between builds (a
     // reloaded system rebuilds the layout without new device allocations or a device-wide sync)
     if (!c->pool) {
@@ -269,8 +316,7 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s)
         k_att_rows<double><<<g, 256, 0, s>>>(tiles, c->tile_bytes, view<double>(c).p_att, n, (double *)rec);
         k_gather_att<double><<<g, 256, 0, s>>>((const double *)rec, perm, n, (uint8_t *)c->atiles);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) goto done;
-    rf = fixed_point_launch(c, s, &kmax_h);
+    e = cudaGetLastError();
 done:
     if (keys_in) cudaFreeAsync(keys_in, s);
     if (keys_out) cudaFreeAsync(keys_out, s);
@@ -283,9 +329,31 @@ done:
         if (e == cudaSuccess) e = es;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "attitude layout");
-    if (rf != GSR_OK) return rf;
-    if ((rf = fixed_point_finish(c, s, kmax_h)) != GSR_OK) return rf;
-    c->att_valid = true;
+    return GSR_OK;
+}
+
+gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64)
+{
+    if (!c->fx_valid) {
+        std::vector<uint32_t> kmax_h;
+        gsr_status rf = fixed_point_launch(c, s, &kmax_h);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (rf != GSR_OK) return rf;
+        if (e != cudaSuccess) return cuda_fail(c, e, "fixed-point statistics");
+        if ((rf = fixed_point_finish(c, s, kmax_h)) != GSR_OK) return rf;
+        c->fx_valid = true;
+        // the cached iteration graphs hold the kernel choice they were captured with
+        const int32_t sig = (c->fx_bits > 0 ? 1 : 0) | (c->fx_att ? 2 : 0);
+        if (sig != c->fx_sig) {
+            drop_graphs(c);
+            c->fx_sig = sig;
+        }
+    }
+    if ((binary64 || !att_fused(c)) && !c->att_valid) {
+        const gsr_status rc = build_att_copy(c, s);
+        if (rc != GSR_OK) return rc;
+        c->att_valid = true;
+    }
     return GSR_OK;
 }
 

@@ -185,14 +185,19 @@ __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_
 // per-block sums of squares of vhat (alpha) and of w (for the condition estimate). In the
 // iterations (first=0) the block that finishes last also runs the scalar step (the grid's
 // partials are complete then): `counter` counts finished blocks and is reset by that block.
+//
+// ymax_reset (may be null): the max |y| word of the fixed-point aprod 2 sums; the aprod 2 of this
+// iteration has read it, the next iteration's aprod 1 rebuilds it from zero.
 __global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *__restrict__ z,
                        const double *__restrict__ p, double *__restrict__ v, const double *__restrict__ w, int64_t n,
                        LsqrState *__restrict__ st, double *__restrict__ part_v, double *__restrict__ part_w,
-                       int32_t first, uint32_t *__restrict__ counter, int32_t *__restrict__ flag)
+                       int32_t first, uint32_t *__restrict__ counter, int32_t *__restrict__ flag,
+                       uint32_t *__restrict__ ymax_reset)
 {
     __shared__ double sm32[32];
     __shared__ double s_beta, s_ib;
     __shared__ int s_last;
+    if (ymax_reset && blockIdx.x == 0 && threadIdx.x == 0) *ymax_reset = 0u;
     if (!first && st->done) {  // stopped: the x / w update of this iteration is skipped as well
         if (blockIdx.x == 0 && threadIdx.x == 0) st->colb_skip = 1;
         return;
@@ -417,6 +422,13 @@ void free_workspace(gsr_ctx *c)
     ws = Workspace();
 }
 
+void drop_graphs(gsr_ctx *c)
+{
+    for (auto &gc : c->ws.graphs)
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    c->ws.graphs.clear();
+}
+
 // The executable graph of `k` LSQR iterations (aprod 1, the two aprod 2 passes, colA
 // with the scalar step, colB: 5 kernels each), captured on
 // first use and cached on the context (kernel arguments are the context's
@@ -433,6 +445,8 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
     }
     const int gu = aprod1_grid(c, inner32);
     const int gc = col_grid(c, c->n_cols);
+    // the fused binary32 aprod 2 leaves the max |y| word to colA (the attitude pass clears it otherwise)
+    uint32_t *ymax_reset = inner32 && att_fused(c) ? fx_ymax(c) : nullptr;
     void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
     const void *pv = inner32 ? (const void *)ws.pv32 : (const void *)ws.pv;
     float *pv32 = c->prec == GSR_FP32 ? ws.pv32 : nullptr;
@@ -444,7 +458,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
         if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
         if ((e = launch_aprod2(c, u, ws.z, false, ws.st, s, inner32)) != cudaSuccess) break;
         k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gu, ws.z, ws.p, ws.v, ws.w, c->n_cols, ws.st, ws.part_v,
-                                          ws.part_w, 0, ws.counter, ws.flag_d);
+                                          ws.part_w, 0, ws.counter, ws.flag_d, ymax_reset);
         k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr,
                                           c->n_cols, ws.st, 0);
         e = cudaGetLastError();
@@ -523,7 +537,7 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
     if ((e = launch_aprod2(c, u, ws.z, false, nullptr, s, inner32)) != cudaSuccess) return cuda_fail(c, e, "start");
     k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, n_part_u, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1,
-                                      ws.counter, ws.flag_d);
+                                      ws.counter, ws.flag_d, nullptr);
     k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);
     k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr, nc, ws.st, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "LSQR start");

@@ -388,7 +388,8 @@ gsr_status warm_features_dev(gsr_ctx *c, cudaStream_t s, bool keep_z)
 {
     gsr_status rc = ensure_workspace(c);
     if (rc != GSR_OK) return rc;
-    if ((rc = ensure_att_layout(c, s)) != GSR_OK) return rc;
+    // binary64 storage: the combined pass below runs in binary64 (attitude pass, knot-ordered copy)
+    if ((rc = ensure_att_layout(c, s, c->prec == GSR_FP64)) != GSR_OK) return rc;
     Workspace &ws = c->ws;
     cudaError_t e = cudaSuccess;
     if (!ws.feats) {
