@@ -54,10 +54,11 @@ BYTES = {
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu on the
 # 2e7-row workload (one-pass capture of the standalone launches the benchmark times); a launch's traffic is
-# this figure times its rows. aprod2_f32 is the max pass, the star pass and the attitude pass together.
+# this figure times its rows. aprod2_f32 is the max pass and the one-pass star pass with the attitude columns;
+# aprod2_f64 the binary64 star pass and the attitude pass.
 TRAFFIC_WORKLOAD = "c2"
-TRAFFIC_PER_ROW = {"aprod1_f32": 117.3, "aprod2_f32": 128.2, "residual_df": 121.4, "aprod1_f64": 221.4,
-                   "aprod2_f64": 275.2}
+TRAFFIC_PER_ROW = {"aprod1_f32": 117.3, "aprod2_f32": 120.4, "residual_df": 121.4, "aprod1_f64": 221.4,
+                   "aprod2_f64": 275.9}
 
 
 def parse_args():
