@@ -292,6 +292,36 @@ __device__ __forceinline__ double block_sum(double v, double *sm32)
     return r;
 }
 
+// Two block-wide sums at once (one pair of barriers and one shuffle tree); every thread must call it;
+// results valid in thread 0. sm64: 64 doubles of shared memory.
+__device__ __forceinline__ double2 block_sum2(double a, double b, double *sm64)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sm64[wid] = a;
+        sm64[32 + wid] = b;
+    }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r.x = lane < nw ? sm64[lane] : 0.0;
+        r.y = lane < nw ? sm64[32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+            r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+        }
+    }
+    return r;
+}
+
 // Block-wide maximum of non-negative values; every thread must call it; result valid in thread 0.
 __device__ __forceinline__ float block_max(float v, float *sm32)
 {

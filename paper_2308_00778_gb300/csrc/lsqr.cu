@@ -194,7 +194,7 @@ __global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *
                        int32_t first, uint32_t *__restrict__ counter, int32_t *__restrict__ flag,
                        uint32_t *__restrict__ ymax_reset)
 {
-    __shared__ double sm32[32];
+    __shared__ double sm64[64];
     __shared__ double s_beta, s_ib;
     __shared__ int s_last;
     if (ymax_reset && blockIdx.x == 0 && threadIdx.x == 0) *ymax_reset = 0u;
@@ -243,11 +243,10 @@ __global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *
             }
         }
     }
-    const double tv = block_sum(sv, sm32);
-    const double tw = block_sum(sw, sm32);
+    const double2 t = block_sum2(sv, sw, sm64);
     if (threadIdx.x == 0) {
-        part_v[blockIdx.x] = tv;
-        part_w[blockIdx.x] = tw;
+        part_v[blockIdx.x] = t.x;
+        part_w[blockIdx.x] = t.y;
         if (first && blockIdx.x == 0) st->beta = beta;
         if (!first) {
             __threadfence();  // the partials are visible before the count

@@ -172,3 +172,24 @@ def test_binary32_instrumental_sums_are_order_independent():
     err = np.abs(outs[0][a0:a1] - want[a0:a1])
     assert np.all(err <= bound + 2.0 ** -23 * scale[a0:a1]), (err / (bound + 1e-300)).max()
     ctx.close()
+
+
+def test_reload_that_changes_the_one_pass_choice():
+    """The binary32 aprod 2 runs in one pass when every attitude column gets at least 20 fixed-point
+    bits over the pass's partition. A reload whose rows all start at knot 0 (every row on the same
+    4 columns per axis) leaves too few, so the context falls back to the two passes and drops the
+    iteration graphs it captured for the one-pass kernel. Mixed solves before and after the reload,
+    and after reloading the first system again, match the oracle."""
+    w = gsrgen.workloads()["c1"]
+    h, s, b, ctx = _setup32(w.cfg)
+    knot0 = np.zeros_like(h.knot)
+    s0 = oracle.System(s.star_ptr, h.A, knot0, h.instr, s.n_dfa, s.n_instr, s.n_glob)
+    b0 = oracle.rhs(s0, h.x_true, h.eps)
+    for sys_, bb, kn in ((s, b, h.knot), (s0, b0, knot0), (s, b, h.knot)):
+        ctx.set_system(h.A32, kn, h.instr, bb)
+        x = np.zeros(s.n_cols)
+        info = ctx.solve(x, mode=g.GSR_MIXED, damp=w.damp, inner_itn=30, max_outer=4)
+        xo, _ = oracle.lsqr(sys_, bb, 2000, 1e-14, 1e-14, 0.0, w.damp)
+        errs = block_errors(x, xo, sys_)
+        assert max(errs.values()) <= 1e-9, (errs, info)
+    ctx.close()
