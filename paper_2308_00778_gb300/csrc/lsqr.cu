@@ -428,10 +428,10 @@ void drop_graphs(gsr_ctx *c)
     c->ws.graphs.clear();
 }
 
-// The executable graph of `k` LSQR iterations (aprod 1, the two aprod 2 passes, colA
-// with the scalar step, colB: 5 kernels each), captured on
-// first use and cached on the context (kernel arguments are the context's
-// fixed buffers; the iteration state lives in device memory).
+// The executable graph of `k` LSQR iterations (aprod 1, aprod 2 in one pass or two, colA
+// with the scalar step, colB: 4 or 5 kernels each), captured on first use and cached on
+// the context (kernel arguments are the context's fixed buffers; the iteration state lives
+// in device memory); dropped when a reload changes the fixed-point kernel choice.
 static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner32, cudaStream_t s,
                                    cudaGraphExec_t *out)
 {
