@@ -203,7 +203,7 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV,
-          bool ATT = false>
+          bool ATT = false, bool UNI = false>
 __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
                                                  double *__restrict__ z, double *__restrict__ z2,
                                                  const LsqrState *__restrict__ st, int64_t tiles_per_warp,
@@ -229,24 +229,33 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     const int32_t nsm = INSTR_SMEM ? (BOTH ? 2 * ncol : ncol) : 0;
     for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) sm_ins[i] = (AT)0;  // also integer zero
     // FX: per-column scales of the instrumental columns after the accumulators (BOTH: products', then
-    // squares'); fx_word holds fxs columns of max |a| and of bits, then max |y|. The attitude columns
-    // share one scale (their bounds differ little): from their largest |a| and fewest bits, the two
-    // words at 3 fxs + 1 and 3 fxs + 2 (one shared-memory read less per product).
-    __shared__ float s_att_sc, s_att_qsc;
+    // squares'); fx_word holds fxs columns of max |a| and of bits, then max |y|. In the one-pass form
+    // the attitude columns share one scale, and the instrumental ones too when the statistics allow
+    // (group bits > 0: no column loses more than the spread of |a| in its group): from the group's
+    // largest |a| and bits (fx_word[3 fxs + 1 ...], FX_GROUP words), one shared-memory read less per
+    // product.
+    __shared__ float s_att_sc, s_att_qsc, s_ins_sc, s_ins_qsc;
     float *sm_scale = reinterpret_cast<float *>(smem_raw) + nsm;
     float *sm_qscale = sm_scale + S.n_instr;
     if (FX) {
         const float ymax = SQUARE ? 1.f : __uint_as_float(fx_word[2 * fxs]);
         if (threadIdx.x == 0) s_bad = !(ymax < INFINITY);  // non-finite y: the sums are made NaN below
-        if (ATT && threadIdx.x == 0) {
-            const float am = __uint_as_float(fx_word[3 * fxs + 1]);
-            const float lim = (float)((1u << fx_word[3 * fxs + 2]) - 1u);
+        if (ATT && threadIdx.x < 2) {  // thread 0: the attitude group, thread 1: the instrumental group
+            const uint32_t *gw = fx_word + 3 * fxs + 1;
+            const float am = __uint_as_float(gw[2 * threadIdx.x]);
+            const uint32_t bits = gw[4 + threadIdx.x];
+            const float lim = (float)((1u << bits) - 1u);
             const float bound = SQUARE ? am * am : am * ymax;
             float sc = 1.f, qs = 1.f;
             if (bound > 0.f && bound < INFINITY) sc = ldexpf(1.f, min(ilogbf(lim / bound), 126));
             if (am * am > 0.f && am * am < INFINITY) qs = ldexpf(1.f, min(ilogbf(lim / (am * am)), 126));
-            s_att_sc = sc;
-            s_att_qsc = qs;
+            if (threadIdx.x == 0) {
+                s_att_sc = sc;
+                s_att_qsc = qs;
+            } else {
+                s_ins_sc = sc;
+                s_ins_qsc = qs;
+            }
         }
         for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
             // the largest power of two with bound * scale <= 2^b_j - 1, bound = max|a_j| max|y|
@@ -266,6 +275,9 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
         }
     }
     __syncthreads();
+    // UNI: the instrumental group scale applies (the host chose this instance from the statistics)
+    const bool ins_uni = ATT && UNI;
+    const float ins_sc = ins_uni ? s_ins_sc : 1.f, ins_qsc = ins_uni ? s_ins_qsc : 1.f;
 
     const int lane = threadIdx.x & 31;
     AT *wbuf = wred[threadIdx.x >> 5];
@@ -356,7 +368,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                 if (in[i]) {
                     if (FX)
                         atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
-                                  __float2int_rn(av * yr[i] * sm_scale[ic[j][i]]));
+                                  __float2int_rn(av * yr[i] * (ATT && ins_uni ? ins_sc : sm_scale[ic[j][i]])));
                     else if (INSTR_SMEM)
                         atomicAdd(sm_ins + ic[j][i], av * yr[i]);
                     else
@@ -364,7 +376,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                     if constexpr (BOTH) {
                         if (FX)
                             atomicAdd(reinterpret_cast<int *>(sm_sq) + ic[j][i],
-                                      __float2int_rn(av * av * sm_qscale[ic[j][i]]));
+                                      __float2int_rn(av * av * (ATT && ins_uni ? ins_qsc : sm_qscale[ic[j][i]])));
                         else if (INSTR_SMEM)
                             atomicAdd(sm_sq + ic[j][i], av * av);
                         else
@@ -475,7 +487,8 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
             // column col of the block-private space: instrumental, or (ATT) attitude
             const bool ins = col < S.n_instr;
             const int64_t dst = ins ? S.instr0 + col : S.att0 + (col - S.n_instr);
-            const float sc = ins ? (sq ? sm_qscale[col] : sm_scale[col]) : (sq ? s_att_qsc : s_att_sc);
+            const float sc = !ins ? (sq ? s_att_qsc : s_att_sc)
+                             : ATT && ins_uni ? (sq ? s_ins_qsc : s_ins_sc) : (sq ? sm_qscale[col] : sm_scale[col]);
             atomicAdd((sq ? z2 : z) + dst, (double)q / (double)sc);  // the scale is a power of two: exact
         }
         if (s_bad && threadIdx.x == 0) atomicAdd(S.n_instr ? zi : z + S.att0, (double)NAN);
@@ -520,14 +533,14 @@ __global__ void __launch_bounds__(256, 2) k_aprod2_star_sv(SysView<VT> S, const 
 
 // The star pass that also takes the attitude columns (binary32 fixed point, standard row): the whole
 // aprod 2 in one pass over the row tiles, two blocks per SM as the plain star pass.
-template <typename VT, int MODE, bool LSQR>
+template <typename VT, int MODE, bool LSQR, bool UNI>
 __global__ void __launch_bounds__(256, 2) k_aprod2_star_att(SysView<VT> S, const float *__restrict__ y,
                                                             double *__restrict__ z, double *__restrict__ z2,
                                                             const LsqrState *__restrict__ st, int64_t tiles_per_warp,
                                                             const uint32_t *__restrict__ fx_word, int32_t fxs)
 {
-    aprod2_star_body<VT, float, float, true, MODE, LSQR, true, false, true>(S, y, z, z2, st, tiles_per_warp, fx_word,
-                                                                            fxs);
+    aprod2_star_body<VT, float, float, true, MODE, LSQR, true, false, true, UNI>(S, y, z, z2, st, tiles_per_warp,
+                                                                                 fx_word, fxs);
 }
 
 // Add a warp's run sums of the 12 attitude columns of knot k (warp-collective).
@@ -771,7 +784,8 @@ template <int MODE, bool LS>
 static cudaError_t aprod2_fused_launch(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                        cudaStream_t s)
 {
-    auto kern = k_aprod2_star_att<float, MODE, LS>;
+    // one scale for the instrumental columns too when the statistics allow it (fx_uni)
+    auto kern = c->fx_uni ? k_aprod2_star_att<float, MODE, LS, true> : k_aprod2_star_att<float, MODE, LS, false>;
     const int32_t ncol = c->n_instr + NAXES * c->n_dfa;
     // accumulators of every column (twice for products and squares), scales of the instrumental ones
     const size_t dyn = sizeof(float) * ((size_t)ncol + (size_t)c->n_instr) * (MODE == A2_BOTH ? 2 : 1);

@@ -25,6 +25,10 @@ constexpr int NGLOB_MAX = GSR_MAX_GLOB;  // global unknowns of a section variant
 // register slots of a row's coefficients in the kernels, by section (the standard row's slots)
 constexpr int A_ATT = NASTRO, A_INS = NASTRO + NAXES * NPARAXIS, A_GLOB = NPAR - 1;
 constexpr int MAX_PARTIALS = 4096;  // per-block partial sums kept for the norms
+// fixed-point words after the per-column ones (fx_word[3 nc + 1 ...]): the attitude columns' largest
+// |a| and smallest |a| (complemented), the instrumental columns' likewise, then the bits of the
+// attitude group scale and of the instrumental group scale (0: per-column scales)
+constexpr int FX_GROUP = 6;
 
 // ---------------------------------------------------------------- device views
 // The coefficient matrix lives in tiles of rows (tiles.cuh): `tiles` holds the
@@ -141,9 +145,10 @@ struct gsr_ctx {
     // fixed-point columns: the instrumental ones, then (fx_att) the 3 n_dfa attitude columns, whose
     // products the star pass then adds into shared memory as well (no attitude pass; the knot-ordered
     // copy is built only for the binary64 aprod 2). fx_word holds [fx_nc] max |a| per column, [fx_nc]
-    // bits per column, max |y|, [fx_nc] scratch.
+    // bits per column, max |y|, [fx_nc] scratch, then FX_GROUP words of the group scales.
     int32_t fx_nc = 0;
     bool fx_att = false;
+    bool fx_uni = false;             // the one-pass aprod 2 gives the instrumental columns one scale too
     bool fx_valid = false;           // the statistics match the loaded rows
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy

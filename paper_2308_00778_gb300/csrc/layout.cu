@@ -161,17 +161,33 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
         }
     }
     __syncthreads();
-    uint32_t am_att = 0u;
+    // the largest and the smallest nonzero |coefficient| of this block's attitude and instrumental
+    // columns (binary32 bits order as integers; the smallest kept as its complement, so that both
+    // are maxima), for the one scale the one-pass aprod 2 gives each group: after the scratch
+    // counts, kmax[nc .. nc+4)
+    uint32_t hi_a = 0u, lo_a = 0u, hi_i = 0u, lo_i = 0u;
     for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
         if (cnt[i]) atomicMax(kmax + i, cnt[i]);
         if (am[i]) atomicMax(amax + i, am[i]);
-        if (i >= S.n_instr) am_att = max(am_att, am[i]);
+        if (am[i]) {
+            if (i >= S.n_instr) {
+                hi_a = max(hi_a, am[i]);
+                lo_a = max(lo_a, ~am[i]);
+            } else {
+                hi_i = max(hi_i, am[i]);
+                lo_i = max(lo_i, ~am[i]);
+            }
+        }
     }
-    // the largest |coefficient| over all attitude columns (one scale serves them all): after the
-    // scratch counts, kmax + nc
-    if (att) {
-        am_att = __reduce_max_sync(0xffffffffu, am_att);
-        if ((threadIdx.x & 31) == 0 && am_att) atomicMax(kmax + nc, am_att);
+    hi_a = __reduce_max_sync(0xffffffffu, hi_a);
+    lo_a = __reduce_max_sync(0xffffffffu, lo_a);
+    hi_i = __reduce_max_sync(0xffffffffu, hi_i);
+    lo_i = __reduce_max_sync(0xffffffffu, lo_i);
+    if ((threadIdx.x & 31) == 0) {
+        if (hi_a) atomicMax(kmax + nc, hi_a);
+        if (lo_a) atomicMax(kmax + nc + 1, lo_a);
+        if (hi_i) atomicMax(kmax + nc + 2, hi_i);
+        if (lo_i) atomicMax(kmax + nc + 3, lo_i);
     }
 }
 
@@ -190,6 +206,7 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
 {
     c->fx_bits = 0;
     c->fx_att = false;
+    c->fx_uni = false;
     kmax_h->clear();
     if (c->prec != GSR_FP32 || c->n_rows == 0 || c->n_ipr == 0 || c->n_instr == 0) return GSR_OK;
     const int32_t ni = c->n_instr;
@@ -201,12 +218,14 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
     const int32_t nc = att ? (int32_t)nc_att : ni;
     cudaError_t e = cudaSuccess;
     // device words: [0, nc) max |a| per column, [nc, 2nc) bits per column, [2nc] max |y| of the
-    // current aprod 2, then [nc] scratch counts, then the attitude columns' largest |a| and fewest bits
+    // current aprod 2, then [nc] scratch counts, then (FX_GROUP words) the attitude and the
+    // instrumental columns' largest and smallest |a| and the bits of their group scales
     if (c->fx_word && c->fx_nc != nc) {
         cudaFree(c->fx_word);
         c->fx_word = nullptr;
     }
-    if (!c->fx_word && (e = cudaMalloc(&c->fx_word, sizeof(uint32_t) * (3 * (size_t)nc + 3))) != cudaSuccess)
+    if (!c->fx_word &&
+        (e = cudaMalloc(&c->fx_word, sizeof(uint32_t) * (3 * (size_t)nc + 1 + FX_GROUP))) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point words");
     c->fx_nc = nc;
     uint32_t *kcnt = c->fx_word + 2 * nc + 1;
@@ -214,29 +233,40 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
     const int64_t warps = (int64_t)c->sm_count * 2 * 8;
     c->fx_per = std::max<int64_t>((c->n_tiles + warps - 1) / warps, 8);
     c->fx_blocks = std::max<int64_t>(((c->n_tiles + c->fx_per - 1) / c->fx_per + 7) / 8, 1);
-    if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)nc + 3), s)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(c->fx_word, 0, sizeof(uint32_t) * (3 * (size_t)nc + 1 + FX_GROUP), s)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
     const size_t smem = 2 * sizeof(uint32_t) * (size_t)nc;
     auto stats = c->sv ? k_instr_stats<true> : k_instr_stats<false>;
     if ((e = cudaFuncSetAttribute(stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
     stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word, nc, att ? 1 : 0);
-    kmax_h->resize((size_t)nc);
+    kmax_h->resize((size_t)nc + 4);  // the counts, then the four group extremes
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * (size_t)nc, cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess)
+        (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * ((size_t)nc + 4), cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
     return GSR_OK;
 }
 
-static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vector<uint32_t> &kmax)
+// bits lost by one scale for a group of columns: ceil(log2(largest / smallest |a|)) (binary32 bits,
+// the smallest stored as its complement; 99 when the group has no coefficient)
+static int group_loss(uint32_t hi_bits, uint32_t lo_compl)
 {
-    if (kmax.empty()) return GSR_OK;
-    std::vector<uint32_t> bits(kmax.size());
+    if (!hi_bits || !lo_compl) return 99;
+    const double hi = (double)__builtin_bit_cast(float, hi_bits), lo = (double)__builtin_bit_cast(float, ~lo_compl);
+    if (!(lo > 0.0) || !(hi >= lo)) return 99;
+    return (int)std::ceil(std::log2(hi / lo));
+}
+
+static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vector<uint32_t> &kmax_ext)
+{
+    if (kmax_ext.empty()) return GSR_OK;
+    const size_t nc = kmax_ext.size() - 4;
+    std::vector<uint32_t> bits(nc);
     int min_ins = 30, min_att = 30;
-    for (size_t j = 0; j < kmax.size(); ++j) {
+    for (size_t j = 0; j < nc; ++j) {
         int lg = 0;  // ceil(log2(kmax + 1))
-        while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax[j] + 1) ++lg;
+        while (lg < 32 && ((uint64_t)1 << lg) < (uint64_t)kmax_ext[j] + 1) ++lg;
         bits[j] = (uint32_t)std::min(31 - lg, 30);
         if ((int64_t)j < c->n_instr)
             min_ins = std::min(min_ins, (int)bits[j]);
@@ -244,16 +274,24 @@ static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vect
             min_att = std::min(min_att, (int)bits[j]);
     }
     if (min_ins < 20) return GSR_OK;
-    // pageable source: the call returns once the bytes are staged, the kernels that read them follow on s
-    cudaError_t e = cudaMemcpyAsync(c->fx_word + kmax.size(), bits.data(), sizeof(uint32_t) * bits.size(),
-                                    cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && (int64_t)kmax.size() > c->n_instr) {
-        const uint32_t att_bits = (uint32_t)min_att;
-        e = cudaMemcpyAsync(c->fx_word + 3 * kmax.size() + 2, &att_bits, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    }
+    // One scale per group (the attitude columns; the instrumental ones in the one-pass pass) from the
+    // group's largest |a| and fewest bits: no column can overflow, and a column's contributions keep
+    // at least 20 bits of its own bound when the group's fewest bits minus the bits lost to the
+    // spread of |a| stay >= 20. Otherwise the attitude columns take the two-pass aprod 2 and the
+    // instrumental ones their per-column scales.
+    const bool att_cols = (int64_t)nc > c->n_instr;
+    const int loss_att = group_loss(kmax_ext[nc], kmax_ext[nc + 1]);
+    const int loss_ins = group_loss(kmax_ext[nc + 2], kmax_ext[nc + 3]);
+    const uint32_t group_bits[2] = {att_cols && min_att - loss_att >= 20 ? (uint32_t)min_att : 0u,
+                                    min_ins - loss_ins >= 20 ? (uint32_t)min_ins : 0u};
+    // pageable sources: each call returns once the bytes are staged, the kernels that read them follow on s
+    cudaError_t e = cudaMemcpyAsync(c->fx_word + nc, bits.data(), sizeof(uint32_t) * nc, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->fx_word + 3 * nc + 5, group_bits, sizeof(group_bits), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "fixed-point setup");
     c->fx_bits = min_ins;
-    c->fx_att = (int64_t)kmax.size() > c->n_instr && min_att >= 20;
+    c->fx_att = group_bits[0] > 0;
+    c->fx_uni = group_bits[1] > 0;
     return GSR_OK;
 }
 
@@ -343,7 +381,7 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64)
         if ((rf = fixed_point_finish(c, s, kmax_h)) != GSR_OK) return rf;
         c->fx_valid = true;
         // the cached iteration graphs hold the kernel choice they were captured with
-        const int32_t sig = (c->fx_bits > 0 ? 1 : 0) | (c->fx_att ? 2 : 0);
+        const int32_t sig = (c->fx_bits > 0 ? 1 : 0) | (c->fx_att ? 2 : 0) | (c->fx_uni ? 4 : 0);
         if (sig != c->fx_sig) {
             drop_graphs(c);
             c->fx_sig = sig;

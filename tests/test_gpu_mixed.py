@@ -193,3 +193,51 @@ def test_reload_that_changes_the_one_pass_choice():
         errs = block_errors(x, xo, sys_)
         assert max(errs.values()) <= 1e-9, (errs, info)
     ctx.close()
+
+
+@pytest.mark.parametrize("spread", ["instr", "instr_and_att"])
+def test_spread_coefficients_keep_per_column_precision(spread):
+    """The one-pass aprod 2 gives the attitude columns one fixed-point scale, and the instrumental
+    ones too, only when no column then loses precision: the group's fewest bits minus log2(largest /
+    smallest column max |a|) must stay >= 20. Here the odd instrumental columns (and, in the second
+    case, the third attitude axis) have coefficients 2^-4 times the others (4 bits of spread against
+    about 21 bits on this system): the instrumental sums keep their per-column scales in the
+    one-pass aprod 2 (first case), the attitude columns take the two passes (second case).
+    aprod2_f32 keeps its bounds (binary32 sums 2e3 u, the instrumental fixed point 2^-20 of each
+    column's own bound) and the mixed solve matches the oracle. (The mixed solver's accuracy on
+    columns of small norm is limited by the binary32 rounding of the refinement's right-hand side,
+    about 2^-24 |r*| / |A_:,j| for the noise residual r*: 5e-10 here, 1.2e-7 with a spread of
+    2^-12.)"""
+    cfg = gsrgen.workloads()["c1"].cfg
+    h = gsrgen.generate(cfg, fp32=True)
+    A32 = h.A32.copy()
+    small = (h.instr % 2) == 1                        # odd instrumental columns: 2^-4 smaller
+    A32[:, 17:23][small] *= np.float32(2.0 ** -4)
+    if spread == "instr_and_att":
+        A32[:, 13:17] *= np.float32(2.0 ** -4)       # attitude axis 2
+    A = A32.astype(np.float64)
+    s = oracle.System(h.star_ptr, A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    ctx = context_for(h, fp32=True)
+    ctx.set_system(A32, h.knot, h.instr, b)
+    u = 2.0 ** -24
+    rng = np.random.default_rng(17)
+    y = rng.standard_normal(s.n_rows).astype(np.float32)
+    z = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+    ctx.aprod2_f32(torch.tensor(y, device="cuda"), z)
+    want = oracle.aprod2(s, y.astype(np.float64), np.zeros(s.n_cols))
+    scale = oracle.aprod2(_abs_sys(s), np.abs(y).astype(np.float64), np.zeros(s.n_cols))
+    err = np.abs(z.cpu().numpy() - want)
+    a0, a1 = s.blocks()["instr"]
+    assert np.all(err[:a0] <= 2e3 * u * scale[:a0])
+    amax = np.zeros(s.n_instr)
+    np.maximum.at(amax, h.instr.ravel(), np.abs(A[:, 17:23]).ravel())
+    count = np.bincount(h.instr.ravel(), minlength=s.n_instr)
+    bound = count * 2.0 ** -20 * amax * np.abs(y).max() + 2.0 ** -23 * scale[a0:a1]
+    assert np.all(err[a0:a1] <= bound)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, mode=g.GSR_MIXED, damp=1e-6, inner_itn=30, max_outer=4)
+    xo, _ = oracle.lsqr(s, b, 3000, 1e-14, 1e-14, 0.0, 1e-6)
+    errs = block_errors(x, xo, s)
+    assert max(errs.values()) <= 1e-9, (errs, info)
+    ctx.close()
