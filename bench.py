@@ -57,7 +57,7 @@ FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # this figure times its rows. aprod2_f32 is the max pass and the one-pass star pass with the attitude columns;
 # aprod2_f64 the binary64 star pass and the attitude pass.
 TRAFFIC_WORKLOAD = "c2"
-TRAFFIC_PER_ROW = {"aprod1_f32": 117.3, "aprod2_f32": 120.4, "residual_df": 121.4, "aprod1_f64": 221.4,
+TRAFFIC_PER_ROW = {"aprod1_f32": 117.3, "aprod2_f32": 120.8, "residual_df": 121.4, "aprod1_f64": 221.4,
                    "aprod2_f64": 275.9}
 
 

@@ -190,11 +190,37 @@ gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
 gsr_status gsr_aprod1_f32(gsr_ctx *ctx, const float *x, float *y, void *stream);
 
 /*
- * gsr_aprod2_f32 -- x += A^T y with binary32 products and per-block binary32
- * partial sums added into binary64 x (Eq. 3). FP32-stored contexts only.
+ * gsr_aprod2_f32 -- x += A^T y with binary32 products (Eq. 3), added into
+ * binary64 x. FP32-stored contexts only.
  *   y  device array of n_rows binary32.   x  device array of n_cols binary64.
+ * Astrometric and global partial sums are binary32. The instrumental sums,
+ * and the attitude sums when the row tiles are read in one pass, are 32-bit
+ * fixed point per block (each contribution rounded to 2^-20 or finer of its
+ * column's bound max|a_j| max|y|) and then exact in binary64, so those
+ * entries do not depend on the order of the additions; gsr_aprod2_plan says
+ * which form the loaded rows take.
  */
 gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream);
+
+/*
+ * gsr_aprod2_plan -- the form gsr_aprod2_f32 (and the inner iterations of
+ * GSR_MIXED) takes on the loaded rows. FP32-stored contexts only.
+ *   passes     1: one pass over the row tiles also sums the attitude columns
+ *              (block-private fixed point, one scale for all of them);
+ *              2: a second pass over a knot-ordered copy sums them.
+ *   fx_bits    fewest fixed-point bits of an instrumental column's per-block
+ *              sums (>= 20), or 0 when those sums are binary32.
+ *   ins_group  1 when the instrumental columns share one scale (one-pass form
+ *              only), else 0.
+ * Any pointer may be NULL. The choice rests on per-column statistics of the
+ * rows (the largest count a block adds to a column, the largest |a_j|); a
+ * group shares one scale only if its smallest column still keeps >= 20 bits.
+ * When the rows changed since the statistics were taken, computes them (one
+ * pass over the tiles on stream, then a synchronisation of stream).
+ * Errors: GSR_EINVAL (binary64-stored context), GSR_ESTATE (rows not
+ * loaded), GSR_ECUDA.
+ */
+gsr_status gsr_aprod2_plan(gsr_ctx *ctx, void *stream, int32_t *passes, int32_t *fx_bits, int32_t *ins_group);
 
 /*
  * gsr_residual -- r = b - A x for the loaded b, with every product and sum

@@ -10,7 +10,7 @@ import os as _os
 from .gsr import (  # noqa: F401
     GSR_AOS, GSR_DEVICE, GSR_FP32, GSR_FP64, GSR_HOST, GSR_MIXED, GSR_PLAIN, GSR_SOA, GSR_WARM_JACOBI,
     GSR_WARM_LEARNED, GSR_WARM_NONE, GsrError, SolveInfo, SolveParams, Status, gsr_aprod1, gsr_aprod1_f32,
-    gsr_aprod2, gsr_aprod2_f32, gsr_residual, gsr_residual_static, gsr_create, gsr_create_sections, gsr_sections,
+    gsr_aprod2, gsr_aprod2_f32, gsr_aprod2_plan, gsr_residual, gsr_residual_static, gsr_create, gsr_create_sections, gsr_sections,
     gsr_default_params, gsr_destroy, gsr_dims, gsr_last_error, gsr_lsqr_solve, gsr_set_rhs, gsr_set_rows,
     gsr_set_system, lib, library_path, Context, Net, gsr_net_create, gsr_net_destroy, gsr_net_forward,
     gsr_net_gradients, gsr_net_get_params, gsr_net_last_error, gsr_net_load, gsr_net_num_params, gsr_net_save,

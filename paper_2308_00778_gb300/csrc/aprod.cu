@@ -295,6 +295,9 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current run
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
+        // the one-pass form: the next tile of the warp's range into L2 (measured: 0.430 -> 0.422 ms
+        // on 2e7 rows; in the grid-stride kernels and the two-pass forms it made the pass slower)
+        if (ATT && t + 1 < t1) prefetch_l2(tb + S.tile_bytes, S.tile_bytes);
         int32_t ic[NINSTR][R];
         AT a[NASTRO][R], ai[NINSTR][R], ag[MG][R];
         if constexpr (SV) {

@@ -647,6 +647,22 @@ GSR_API gsr_status gsr_aprod2_f32(gsr_ctx *c, const float *y, double *x, void *s
     return GSR_OK;
 }
 
+GSR_API gsr_status gsr_aprod2_plan(gsr_ctx *c, void *stream, int32_t *passes, int32_t *fx_bits,
+                                   int32_t *ins_group)
+{
+    if (!c) return GSR_EINVAL;
+    if (c->prec != GSR_FP32) return fail(c, GSR_EINVAL, "binary32 kernels need an FP32-stored context");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    const cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream, false);
+    if (rc != GSR_OK) return rc;
+    if (passes) *passes = att_fused(c) ? 1 : 2;
+    if (fx_bits) *fx_bits = c->fx_bits;
+    if (ins_group) *ins_group = att_fused(c) && c->fx_uni ? 1 : 0;
+    return GSR_OK;
+}
+
 GSR_API gsr_status gsr_residual(gsr_ctx *c, const double *x, float *r, void *stream)
 {
     if (!c) return GSR_EINVAL;

@@ -161,22 +161,30 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
         }
     }
     __syncthreads();
-    // the largest and the smallest nonzero |coefficient| of this block's attitude and instrumental
-    // columns (binary32 bits order as integers; the smallest kept as its complement, so that both
-    // are maxima), for the one scale the one-pass aprod 2 gives each group: after the scratch
-    // counts, kmax[nc .. nc+4)
-    uint32_t hi_a = 0u, lo_a = 0u, hi_i = 0u, lo_i = 0u;
     for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
         if (cnt[i]) atomicMax(kmax + i, cnt[i]);
         if (am[i]) atomicMax(amax + i, am[i]);
-        if (am[i]) {
-            if (i >= S.n_instr) {
-                hi_a = max(hi_a, am[i]);
-                lo_a = max(lo_a, ~am[i]);
-            } else {
-                hi_i = max(hi_i, am[i]);
-                lo_i = max(lo_i, ~am[i]);
-            }
+    }
+}
+
+// The largest and the smallest nonzero column max |coefficient| (amax, after every block of
+// k_instr_stats) of the attitude and of the instrumental columns, for the one scale the one-pass
+// aprod 2 gives each group: binary32 bits order as integers, the smallest kept as its complement so
+// that all four are maxima; into ext[0..4) = hi_att, ~lo_att, hi_ins, ~lo_ins (zero on entry). One
+// block.
+__global__ void __launch_bounds__(1024) k_group_extremes(const uint32_t *__restrict__ amax, int32_t nc,
+                                                         int32_t n_instr, uint32_t *__restrict__ ext)
+{
+    uint32_t hi_a = 0u, lo_a = 0u, hi_i = 0u, lo_i = 0u;
+    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        const uint32_t a = amax[i];
+        if (!a) continue;
+        if (i >= n_instr) {
+            hi_a = max(hi_a, a);
+            lo_a = max(lo_a, ~a);
+        } else {
+            hi_i = max(hi_i, a);
+            lo_i = max(lo_i, ~a);
         }
     }
     hi_a = __reduce_max_sync(0xffffffffu, hi_a);
@@ -184,10 +192,10 @@ __global__ void __launch_bounds__(256) k_instr_stats(SysView<float> S, int64_t p
     hi_i = __reduce_max_sync(0xffffffffu, hi_i);
     lo_i = __reduce_max_sync(0xffffffffu, lo_i);
     if ((threadIdx.x & 31) == 0) {
-        if (hi_a) atomicMax(kmax + nc, hi_a);
-        if (lo_a) atomicMax(kmax + nc + 1, lo_a);
-        if (hi_i) atomicMax(kmax + nc + 2, hi_i);
-        if (lo_i) atomicMax(kmax + nc + 3, lo_i);
+        if (hi_a) atomicMax(ext + 0, hi_a);
+        if (lo_a) atomicMax(ext + 1, lo_a);
+        if (hi_i) atomicMax(ext + 2, hi_i);
+        if (lo_i) atomicMax(ext + 3, lo_i);
     }
 }
 
@@ -240,6 +248,8 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
     if ((e = cudaFuncSetAttribute(stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_fail(c, e, "fixed-point statistics");
     stats<<<(unsigned)c->fx_blocks, 256, smem, s>>>(view<float>(c), c->fx_per, kcnt, c->fx_word, nc, att ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "fixed-point statistics");
+    k_group_extremes<<<1, 1024, 0, s>>>(c->fx_word, nc, c->n_instr, kcnt + nc);
     kmax_h->resize((size_t)nc + 4);  // the counts, then the four group extremes
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(kmax_h->data(), kcnt, sizeof(uint32_t) * ((size_t)nc + 4), cudaMemcpyDeviceToHost,

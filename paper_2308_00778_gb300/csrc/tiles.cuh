@@ -24,6 +24,13 @@
 
 namespace gsr {
 
+// Ask L2 to fetch bytes at p (16-byte aligned, a multiple of 16 bytes) ahead of their use: one bulk
+// prefetch by the warp's lane 0, nothing returned and nothing to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes)
+{
+    if ((threadIdx.x & 31) == 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)bytes));
+}
+
 template <typename VT>
 struct Tile {
     static constexpr int R = 16 / (int)sizeof(VT);                   // rows per lane

@@ -100,6 +100,7 @@ def lib():
             "gsr_aprod2": (I32, [P, P, P, P]),
             "gsr_aprod1_f32": (I32, [P, P, P, P]),
             "gsr_aprod2_f32": (I32, [P, P, P, P]),
+            "gsr_aprod2_plan": (I32, [P, P, P, P, P]),
             "gsr_residual": (I32, [P, P, P, P]),
             "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
@@ -148,6 +149,13 @@ def gsr_sections(ctx):
     """Returns (status, n_astro, n_ipr, n_glob, row_width)."""
     v = [ctypes.c_int32() for _ in range(4)]
     st = lib().gsr_sections(ctx, *[ctypes.byref(q) for q in v])
+    return (st, *[q.value for q in v])
+
+
+def gsr_aprod2_plan(ctx, stream=0):
+    """Returns (status, passes, fx_bits, ins_group)."""
+    v = [ctypes.c_int32() for _ in range(3)]
+    st = lib().gsr_aprod2_plan(ctx, stream, *[ctypes.byref(q) for q in v])
     return (st, *[q.value for q in v])
 
 
@@ -420,6 +428,12 @@ class Context:
 
     def aprod2_f32(self, y, x, stream=0):
         self._check(gsr_aprod2_f32(self.h, _ptr(y), _ptr(x), stream))
+
+    def aprod2_plan(self, stream=0):
+        """The binary32 aprod 2's form on the loaded rows: {"passes", "fx_bits", "ins_group"}."""
+        st, passes, bits, grp = gsr_aprod2_plan(self.h, stream)
+        self._check(st)
+        return {"passes": passes, "fx_bits": bits, "ins_group": grp}
 
     def residual(self, x, r, stream=0):
         self._check(gsr_residual(self.h, _ptr(x), _ptr(r), stream))

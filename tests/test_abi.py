@@ -72,6 +72,7 @@ def test_errors_without_gpu_are_status_codes():
     assert cs(None, 1, 1, None, 5, 4, 6, 6, 1, 0, 0) == g.Status.EINVAL
     assert h.value is None
     assert g.gsr_sections(0)[0] == g.Status.EINVAL
+    assert g.gsr_aprod2_plan(0)[0] == g.Status.EINVAL
     assert g.gsr_aprod1(0, 0, 0) == g.Status.EINVAL
     assert g.gsr_lsqr_solve(0, g.gsr_default_params(), 0, 0, 0, g.SolveInfo()) == g.Status.EINVAL
     assert g.gsr_destroy(0) == g.Status.OK

@@ -220,6 +220,9 @@ def test_spread_coefficients_keep_per_column_precision(spread):
     b = oracle.rhs(s, h.x_true, h.eps)
     ctx = context_for(h, fp32=True)
     ctx.set_system(A32, h.knot, h.instr, b)
+    plan = ctx.aprod2_plan()
+    assert plan["fx_bits"] >= 20 and plan["ins_group"] == 0
+    assert plan["passes"] == (1 if spread == "instr" else 2)
     u = 2.0 ** -24
     rng = np.random.default_rng(17)
     y = rng.standard_normal(s.n_rows).astype(np.float32)
