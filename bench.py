@@ -74,9 +74,10 @@ def parse_args():
                     help="skip the section-variant measurement (c2-shaped systems with other row sections)")
     ap.add_argument("--n-stars", type=int, default=0,
                     help="profiling mode only: override the workload's number of stars (a smaller case for ncu)")
-    ap.add_argument("--profile", default=None, choices=["f32", "f64"],
+    ap.add_argument("--profile", default=None, choices=["f32", "f64", "mixed"],
                     help="profiling mode for ncu: load the system with binary32 (f32) or binary64 (f64) storage "
-                         "and launch each hot kernel --steps times inside an NVTX range 'prof'; prints timings")
+                         "and launch each hot kernel --steps times inside an NVTX range 'prof', or (mixed) run the "
+                         "default mixed solve from the learned start --steps times; prints timings")
     return ap.parse_args()
 
 
@@ -645,13 +646,17 @@ def run_profile(args):
     if args.n_stars:
         cfg = gsrgen.make_cfg(cfg.seed, args.n_stars, (cfg.obs_min, cfg.obs_max), cfg.n_dfa, cfg.n_instr,
                               cfg.n_glob, cfg.att_kind, cfg.noise_sigma, n_astro=cfg.n_astro, n_ipr=cfg.n_ipr)
-    f32 = args.profile == "f32"
+    f32 = args.profile in ("f32", "mixed")
     ctx, b, _ = _device_system(g, gsrgen, torch, cfg, f32, True, dev, sh)
     n, nc = ctx.n_rows, ctx.n_cols
     x = torch.randn(nc, dtype=torch.float64, device=dev)
     u = torch.randn(n, dtype=torch.float64, device=dev)
     z = torch.zeros(nc, dtype=torch.float64, device=dev)
-    if f32:
+    if args.profile == "mixed":
+        xm = torch.zeros(nc, dtype=torch.float64, device=dev)
+        kw = dict(mode=g.GSR_MIXED, damp=w.damp, warm=g.GSR_WARM_LEARNED, weights_path=g.WARM_WEIGHTS)
+        ops = {"mixed_solve": lambda: ctx.solve(xm, stream=sh, **kw)}
+    elif f32:
         x32, u32, r32 = x.float(), u.float(), torch.empty(n, dtype=torch.float32, device=dev)
         ops = {"aprod1_f32": lambda: ctx.aprod1_f32(x32, u32, stream=sh),
                "aprod2_f32": lambda: ctx.aprod2_f32(u32, z, stream=sh),

@@ -30,6 +30,7 @@
 namespace gsr {
 
 static constexpr int kColThreads = 256;
+static constexpr int kColElems = 4;  // columns per thread and round in k_colA and k_colB
 
 // ---------------------------------------------------------------- column kernels
 // u <- b - (A x0 is added by a separate aprod1 on -x0); here: u <- src, partial sums of squares
@@ -214,17 +215,35 @@ __global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *
     double sv = 0.0, sw = 0.0;
     if (beta > 0.0 && isfinite(beta)) {
         const double ib = s_ib;
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            const double zj = z[j];
-            z[j] = 0.0;
-            double vh = p[j] * zj * ib;
-            if (!first) vh = fma(-beta, v[j], vh);
-            v[j] = vh;
-            sv = fma(vh, vh, sv);
-            if (!first) {
-                const double wj = w[j];
-                sw = fma(wj, wj, sw);
+        // kColElems columns per thread and round, all loaded before any is used: the loop is
+        // latency-bound (a few MB per call), so the loads of a round are issued together
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += kColElems * stride) {
+            double zr[kColElems], pr[kColElems], vr[kColElems], wr[kColElems];
+#pragma unroll
+            for (int q = 0; q < kColElems; ++q) {
+                const int64_t j = j0 + q * stride;
+                zr[q] = pr[q] = vr[q] = wr[q] = 0.0;
+                if (j < n) {
+                    zr[q] = z[j];
+                    pr[q] = p[j];
+                    if (!first) {
+                        vr[q] = v[j];
+                        wr[q] = w[j];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kColElems; ++q) {
+                const int64_t j = j0 + q * stride;
+                if (j < n) {
+                    z[j] = 0.0;
+                    double vh = pr[q] * zr[q] * ib;
+                    if (!first) vh = fma(-beta, vr[q], vh);
+                    v[j] = vh;
+                    sv = fma(vh, vh, sv);
+                    sw = fma(wr[q], wr[q], sw);
+                }
             }
         }
     } else {
@@ -310,25 +329,44 @@ __global__ void k_colB(double *__restrict__ v, double *__restrict__ pv, float *_
     const double ia = st->inv_alpha;
     const double t1 = st->t1, t2 = st->t2, ir = st->inv_rho;
     const bool has_alpha = st->alpha > 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const double vh = v[j];
-        const double vj = has_alpha ? vh * ia : vh;
-        v[j] = vj;
-        const double pvj = p[j] * vj;
-        pv[j] = pvj;
-        if (pv32) pv32[j] = (float)pvj;
-        if (first) {
-            w[j] = vj;
-            x[j] = 0.0;
-            if (var) var[j] = 0.0;
-        } else {
-            const double wj = w[j];
-            if (var) {
-                const double d = wj * ir;
-                var[j] = fma(d, d, var[j]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += kColElems * stride) {
+        double vr[kColElems], pr[kColElems], wr[kColElems], xr[kColElems];
+#pragma unroll
+        for (int q = 0; q < kColElems; ++q) {
+            const int64_t j = j0 + q * stride;
+            vr[q] = pr[q] = wr[q] = xr[q] = 0.0;
+            if (j < n) {
+                vr[q] = v[j];
+                pr[q] = p[j];
+                if (!first) {
+                    wr[q] = w[j];
+                    xr[q] = x[j];
+                }
             }
-            x[j] = fma(t1, wj, x[j]);
-            w[j] = fma(t2, wj, vj);
+        }
+#pragma unroll
+        for (int q = 0; q < kColElems; ++q) {
+            const int64_t j = j0 + q * stride;
+            if (j >= n) continue;
+            const double vj = has_alpha ? vr[q] * ia : vr[q];
+            v[j] = vj;
+            const double pvj = pr[q] * vj;
+            pv[j] = pvj;
+            if (pv32) pv32[j] = (float)pvj;
+            if (first) {
+                w[j] = vj;
+                x[j] = 0.0;
+                if (var) var[j] = 0.0;
+            } else {
+                const double wj = wr[q];
+                if (var) {
+                    const double d = wj * ir;
+                    var[j] = fma(d, d, var[j]);
+                }
+                x[j] = fma(t1, wj, xr[q]);
+                w[j] = fma(t2, wj, vj);
+            }
         }
     }
 }
@@ -354,6 +392,16 @@ __global__ void k_negate(const double *__restrict__ a, double *__restrict__ out,
 }
 
 // ---------------------------------------------------------------- host side
+// k_colA / k_colB: two blocks per SM (each thread takes kColElems columns a round)
+static int colab_grid(const gsr_ctx *c, int64_t n)
+{
+    int64_t g = (n + (int64_t)kColThreads * kColElems - 1) / ((int64_t)kColThreads * kColElems);
+    const int64_t cap = (int64_t)c->sm_count * 2;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
 int col_grid(const gsr_ctx *c, int64_t n)
 {
     int64_t g = (n + kColThreads - 1) / kColThreads;
@@ -443,7 +491,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
         }
     }
     const int gu = aprod1_grid(c, inner32);
-    const int gc = col_grid(c, c->n_cols);
+    const int gc = colab_grid(c, c->n_cols);
     // the fused binary32 aprod 2 leaves the max |y| word to colA (the attitude pass clears it otherwise)
     uint32_t *ymax_reset = inner32 && att_fused(c) ? fx_ymax(c) : nullptr;
     void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
@@ -528,7 +576,7 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     using clk = std::chrono::steady_clock;
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols;
-    const int gc = col_grid(c, nc);
+    const int gc = colab_grid(c, nc);
     float *pv32 = c->prec == GSR_FP32 ? ws.pv32 : nullptr;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(ws.st, &init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess)
