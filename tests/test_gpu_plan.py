@@ -3,7 +3,7 @@
 The fixed-point sums of the binary32 aprod 2 give column j b_j = min(30, 31 -
 ceil(log2(k_j + 1))) bits, k_j being the largest number of contributions one
 block of the pass's fixed partition (8 warps a block, each warp a contiguous
-range of max(ceil(tiles / (16 SMs)), 8) tiles of 128 rows) adds to column j;
+range of max(ceil(tiles / (16 x SM count)), 8) tiles of 128 rows) adds to column j;
 they are used when every instrumental column gets >= 20 bits. One pass over
 the tiles sums the attitude columns too, with one scale for all of them, when
 their fewest bits minus ceil(log2(largest / smallest column max |a|)) stay >=
