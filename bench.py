@@ -72,6 +72,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sections", action="store_true",
                     help="skip the section-variant measurement (c2-shaped systems with other row sections)")
+    ap.add_argument("--sequential", action="store_true",
+                    help="one context at a time: the binary64 legs and kernels first, then, after freeing that "
+                         "context, the binary32 ones (systems whose two contexts do not fit in device memory "
+                         "together); no e2e, CPU baseline or section measurement")
     ap.add_argument("--n-stars", type=int, default=0,
                     help="profiling mode only: override the workload's number of stars (a smaller case for ncu)")
     ap.add_argument("--profile", default=None, choices=["f32", "f64", "mixed"],
@@ -419,11 +423,19 @@ def run_ours(args):
     damp = w.damp
 
     # ---- one system, coefficients rounded to binary32; every solver sees the same values
+    seq = args.sequential
+    if seq:
+        args.no_e2e = args.no_cpu_baseline = args.no_sections = True
     ctx64, b64, host = _device_system(g, gsrgen, torch, cfg, False, True, dev, sh, keep_host=False)
-    ctx32, b32, host = _device_system(g, gsrgen, torch, cfg, True, True, dev, sh,
-                                      keep_host=(not args.no_e2e) or (rank == 0 and world == 1
-                                                                       and not args.no_cpu_baseline))
-    n = ctx32.n_rows
+    ctx32 = b32 = host = None
+
+    def load32():
+        return _device_system(g, gsrgen, torch, cfg, True, True, dev, sh,
+                              keep_host=(not args.no_e2e) or (rank == 0 and world == 1 and not args.no_cpu_baseline))
+
+    if not seq:
+        ctx32, b32, host = load32()
+    n = ctx64.n_rows
 
     # ---- reference solution x* (binary64, tight) and the schedules that first reach 1e-9 (untimed)
     xs = torch.zeros(nc, dtype=torch.float64, device=dev)
@@ -472,6 +484,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         return max_block_err(x, xs, cfg)
 
+    solvers = {}
+    clk = Clocks(local)
+
+    def time_legs(todo):
+        if world > 1:
+            dist.barrier()
+        with clk:
+            for name, (ctx, kw, meta) in todo.items():
+                ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh,
+                                            nvtx=f"timed_{name}")
+                solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
+                                     final_block_err=max_block_err(x, xs, cfg), eq5_q_max=eq5_q(x, xs, se_ref, cfg))
+
+    u64 = torch.randn(n, dtype=torch.float64, device=dev)
+    z = torch.zeros(nc, dtype=torch.float64, device=dev)
+    t = {}
+
+    def time_kernels64():
+        t["aprod1_f64"] = _time_kernel(torch, lambda: ctx64.aprod1(xs, u64, stream=sh), stream)
+        t["aprod2_f64"] = _time_kernel(torch, lambda: ctx64.aprod2(u64, z, stream=sh), stream)
+
     # each solver: (context, keyword arguments, description) at the fewest iterations reaching 1e-9
     legs = {}
     n9 = first_k(lambda k: err_of(ctx64, plain_kw(k)))
@@ -479,6 +512,13 @@ def run_ours(args):
     if learned:
         nl = first_k(lambda k: err_of(ctx64, plain_kw(k, learned)))
         legs["fp64_learned"] = (ctx64, plain_kw(nl, learned), {"iterations": nl, "start": "learned"})
+    if seq:  # the binary64 legs and kernels now, then the binary32 context in the binary64 one's place
+        time_legs(dict(legs))
+        time_kernels64()
+        ctx64.close()
+        del b64
+        torch.cuda.empty_cache()
+        ctx32, b32, host = load32()
     for name, warm, outers in (("mixed", None, (2, 3)), ("mixed_learned", learned, (1, 2, 3))):
         if name == "mixed_learned" and not learned:
             continue
@@ -503,30 +543,19 @@ def run_ours(args):
                            "start": "learned" if warm else "x0 = 0"})
 
     # ---- timed region: every solver, the same K steps after W warm-up steps each
-    if world > 1:
-        dist.barrier()
-    solvers = {}
-    with Clocks(local) as clk:
-        for name, (ctx, kw, meta) in legs.items():
-            ms_l, info_l = _time_solves(torch, ctx, x, kw, args.steps, args.warmup, stream, sh, nvtx=f"timed_{name}")
-            solvers[name] = dict(meta, s=ms_l / 1e3, ms_warm_start=info_l["ms_warm"] if kw.get("warm") else 0.0,
-                                 final_block_err=max_block_err(x, xs, cfg), eq5_q_max=eq5_q(x, xs, se_ref, cfg))
+    time_legs({nm: leg for nm, leg in legs.items() if nm not in solvers})
     headline = min(solvers, key=lambda nm: solvers[nm]["s"])
     ms = max_over_ranks(torch, dist, solvers[headline]["s"] * 1e3, world, dev)
 
     # ---- per-kernel timing (same kernels, standalone launches, CUDA events on their stream)
-    u64 = torch.randn(n, dtype=torch.float64, device=dev)
     u32 = u64.float()
     x32 = xs.float()
-    z = torch.zeros(nc, dtype=torch.float64, device=dev)
     r32 = torch.empty(n, dtype=torch.float32, device=dev)
-    t = {
-        "aprod1_f64": _time_kernel(torch, lambda: ctx64.aprod1(xs, u64, stream=sh), stream),
-        "aprod2_f64": _time_kernel(torch, lambda: ctx64.aprod2(u64, z, stream=sh), stream),
-        "aprod1_f32": _time_kernel(torch, lambda: ctx32.aprod1_f32(x32, u32, stream=sh), stream),
-        "aprod2_f32": _time_kernel(torch, lambda: ctx32.aprod2_f32(u32, z, stream=sh), stream),
-        "residual_df": _time_kernel(torch, lambda: ctx32.residual(xs, r32, stream=sh), stream),
-    }
+    if not seq:
+        time_kernels64()
+    t["aprod1_f32"] = _time_kernel(torch, lambda: ctx32.aprod1_f32(x32, u32, stream=sh), stream)
+    t["aprod2_f32"] = _time_kernel(torch, lambda: ctx32.aprod2_f32(u32, z, stream=sh), stream)
+    t["residual_df"] = _time_kernel(torch, lambda: ctx32.residual(xs, r32, stream=sh), stream)
     traffic = TRAFFIC_PER_ROW if args.workload == TRAFFIC_WORKLOAD else {}
     kern = {}
     for name, kms in t.items():
@@ -562,7 +591,7 @@ def run_ours(args):
                 "algorithmic": kern[dom]["bytes_per_row"] * n, "peak_src": peaks["src"]}
 
     # ---- kernel launches of one headline step, counted from the device's activity record (CUPTI)
-    launches = count_launches(torch, lambda: hctx.solve(x, stream=sh, **hkw))
+    launches = count_launches(torch, lambda: hctx.solve(x, stream=sh, **hkw)) if hctx.h else None
 
     # ---- end to end through the C ABI with host buffers (upload + solve + download every step)
     e2e = None

@@ -68,4 +68,5 @@ def device_system(cfg, fp32_store: bool, round32: bool, device, stream=0, keep_h
                 "instr": ins[:cfg.n_ipr * n].view(cfg.n_ipr, n).t().contiguous().cpu().pin_memory(),
                 "b": b.cpu().pin_memory(), "star_ptr": sp}
     del vals, ins, knot
+    torch.cuda.empty_cache()  # the staging planes: give them back for the library's own allocations
     return ctx, b, host
