@@ -434,7 +434,8 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
         (e = cudaMalloc(&c->errw, 4 * sizeof(int32_t))) != cudaSuccess ||
         (e = cudaMalloc(&c->knot_ptr, sizeof(int64_t) * (size_t)(n_dfa - 2))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreate(&c->ev_w0)) != cudaSuccess || (e = cudaEventCreate(&c->ev_w1)) != cudaSuccess) {
         cudaGetLastError();
         gsr_destroy(c);
         return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
@@ -509,6 +510,8 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
         cudaMemPoolDestroy(c->pool);
     }
     if (c->ev) cudaEventDestroy(c->ev);
+    if (c->ev_w0) cudaEventDestroy(c->ev_w0);
+    if (c->ev_w1) cudaEventDestroy(c->ev_w1);
     cudaGetLastError();
     delete c;
     return GSR_OK;
@@ -678,6 +681,7 @@ GSR_API gsr_status gsr_residual(gsr_ctx *c, const double *x, float *r, void *str
 GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, const double *x0, double *x_out,
                                   double *se_out, gsr_solve_info *info, void *stream)
 {
+    const auto t_call = std::chrono::steady_clock::now();
     if (!c) return GSR_EINVAL;
     if (!x_out) return fail(c, GSR_EINVAL, "null x_out");
     gsr_solve_params prm;
@@ -715,7 +719,7 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     int r0_parts = 0;  // mixed solve from a warm start on binary32 storage: the start's residual is ready
     double ms_warm = 0.0;
     if (prm.warm != GSR_WARM_NONE) {
-        const auto tw = std::chrono::steady_clock::now();
+        if ((e = cudaEventRecord(c->ev_w0, c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
         gsr_status rw = ensure_workspace(c);
         if (rw != GSR_OK) return rw;
         if (!c->ws.x0w && (e = cudaMalloc(&c->ws.x0w, sizeof(double) * (size_t)c->n_cols)) != cudaSuccess)
@@ -739,10 +743,10 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
         }
         if ((rw = warm_start_dev(c, net, c->ws.x0w, c->own, prm.mode == GSR_MIXED ? &r0_parts : nullptr)) != GSR_OK)
             return rw;
-        if ((e = cudaStreamSynchronize(c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
+        // no host wait here: the warm start's time comes from events once the solve has synchronised
+        if ((e = cudaEventRecord(c->ev_w1, c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
         x0_use = c->ws.x0w;
         x0_dev = true;
-        ms_warm = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
     }
     // the warm start computed p with binary32 sums on binary32 storage and binary64 sums otherwise: the
     // mixed solver (binary32 storage) and the plain solver on binary64 storage reuse it
@@ -751,9 +755,14 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     const gsr_status rc = prm.mode == GSR_MIXED
                               ? mixed_solve(c, &prm, x0_use, x0_dev, x_out, info, c->own, p_ready, r0_parts)
                               : lsqr_solve(c, &prm, x0_use, x0_dev, x_out, se_out, info, c->own, p_ready);
-    if (info) {
+    if (prm.warm != GSR_WARM_NONE) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_w0, c->ev_w1) == cudaSuccess) ms_warm = ms;
+        cudaGetLastError();
+    }
+    if (info) {  // the solve ended with a synchronisation: the call's wall time so far is the whole of it
         info->ms_warm = ms_warm;
-        info->ms_total += ms_warm;
+        info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call).count();
     }
     // the caller's stream continues after the solve's last kernel
     if (cudaEventRecord(c->ev, c->own) == cudaSuccess) cudaStreamWaitEvent((cudaStream_t)stream, c->ev, 0);

@@ -108,6 +108,8 @@ struct Workspace {
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped
     int32_t *flag_d = nullptr;  // device alias of flag_h
+    LsqrState *fin_h = nullptr;   // pinned: the final state of the last run_lsqr
+    double *blk_h = nullptr;      // pinned, 8: the mixed solver's correction and solution norms per block
     uint32_t *counter = nullptr;  // finished-block count of k_colA (zero between launches)
 };
 
@@ -161,6 +163,7 @@ struct gsr_ctx {
     struct gsr_net *warm_net = nullptr;  // network of GSR_WARM_LEARNED solves, loaded from warm_path
     std::string warm_path;
     cudaEvent_t ev = nullptr;        // orders `own` after the caller's stream
+    cudaEvent_t ev_w0 = nullptr, ev_w1 = nullptr;  // the warm start's span inside a solve (timing)
     cudaMemPool_t pool = nullptr;    // stream-ordered scratch of the layout build, kept between builds
     gsr::Workspace ws;
     std::string err;
@@ -236,8 +239,11 @@ int col_grid(const gsr_ctx *c, int64_t n);
 gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false, const void *y = nullptr,
                         double *z = nullptr);
 LsqrState initial_state(const gsr_solve_params *prm);
+// defer_fin: leave the final state's download (into ws.fin_h) pending on s, for a caller that
+// synchronises s itself after more work; *fin is then not written
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
-                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin);
+                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
+                    bool defer_fin = false);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
 // warm start (warm.cu)
 // r0_parts (may be null): for binary32 storage the residual of x0 is also left in ws.u32, in

@@ -426,6 +426,8 @@ gsr_status ensure_workspace(gsr_ctx *c)
     ws.part_w = ws.part_v + MAX_PARTIALS;
     if ((e = cudaMalloc(&ws.st, sizeof(LsqrState))) != cudaSuccess) goto oom;
     if ((e = cudaHostAlloc(&ws.flag_h, sizeof(int32_t), cudaHostAllocMapped)) != cudaSuccess) goto oom;
+    if ((e = cudaHostAlloc(&ws.fin_h, sizeof(LsqrState), cudaHostAllocDefault)) != cudaSuccess) goto oom;
+    if ((e = cudaHostAlloc(&ws.blk_h, 8 * sizeof(double), cudaHostAllocDefault)) != cudaSuccess) goto oom;
     if ((e = cudaHostGetDevicePointer(&ws.flag_d, ws.flag_h, 0)) != cudaSuccess) goto oom;
     if ((e = cudaMalloc(&ws.counter, sizeof(uint32_t))) != cudaSuccess) goto oom;
     if ((e = cudaMemset(ws.counter, 0, sizeof(uint32_t))) != cudaSuccess) goto oom;
@@ -464,6 +466,8 @@ void free_workspace(gsr_ctx *c)
     if (ws.st) cudaFree(ws.st);
     if (ws.counter) cudaFree(ws.counter);
     if (ws.flag_h) cudaFreeHost(ws.flag_h);
+    if (ws.fin_h) cudaFreeHost(ws.fin_h);
+    if (ws.blk_h) cudaFreeHost(ws.blk_h);
     for (auto &gc : ws.graphs)
         if (gc.exec) cudaGraphExecDestroy(gc.exec);
     ws = Workspace();
@@ -571,7 +575,8 @@ gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32, const vo
 // squares. Runs the start (alpha_1 v_1 = A~^T u_1) and the iterations; leaves
 // the scaled solution in ws.x and the final scalars in *fin.
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
-                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin)
+                    double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
+                    bool defer_fin)
 {
     using clk = std::chrono::steady_clock;
     Workspace &ws = c->ws;
@@ -594,28 +599,36 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     if (k < 1) k = 1;
     cudaGraphExec_t exec = nullptr;
     if ((e = iteration_graph(c, k, want_var, inner32, s, &exec)) != cudaSuccess) return cuda_fail(c, e, "graph capture");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "LSQR start");
+    // No host round trip between the start and the first launch, nor after the last one: errors of the
+    // start surface at the next synchronisation, and the graph's kernels skip their work once the
+    // device-side state says the solve has stopped. The host waits between launches only to read the
+    // stop flag.
     gsr_status status = GSR_OK;
     int launched = 0;
     const int max_launch = init.itnlim > 0 ? (init.itnlim + k - 1) / k : 0;
-    while (!*(volatile int32_t *)ws.flag_h && launched < max_launch) {
+    while (launched < max_launch) {
         if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
             status = cuda_fail(c, e, "graph launch");
             break;
         }
-        ++launched;
+        if (++launched == max_launch) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
             status = cuda_fail(c, e, "LSQR iteration");
             break;
         }
+        if (*(volatile int32_t *)ws.flag_h) break;
         if (timeout_s > 0.0 && std::chrono::duration<double>(clk::now() - t0).count() > timeout_s) {
             status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
             break;
         }
     }
-    if ((e = cudaMemcpyAsync(fin, ws.st, sizeof(*fin), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(ws.fin_h, ws.st, sizeof(LsqrState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(c, e, "state download");
+    if (defer_fin) return status;  // the caller synchronises s and reads ws.fin_h
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "state download");
+    *fin = *ws.fin_h;
+    if (status == GSR_OK && timeout_s > 0.0 && std::chrono::duration<double>(clk::now() - t0).count() > timeout_s)
+        status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
     return status;
 }
 

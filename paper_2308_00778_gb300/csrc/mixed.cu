@@ -280,15 +280,22 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
                 return cuda_fail(c, e, "residual");
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
-        status = run_lsqr(c, init, true, false, nr > 0 ? n_part : 0, prm->graph_k, prm->timeout_s, t0, s, &fin);
-        total_itn += fin.itn;
+        // one host synchronisation per refinement step: the inner solve's final state and the
+        // correction's norms come back together
+        status = run_lsqr(c, init, true, false, nr > 0 ? n_part : 0, prm->graph_k, prm->timeout_s, t0, s, &fin,
+                          true);
         if (status != GSR_OK && status != GSR_ETIMEOUT) return status;
-        double hb[8];
         if ((e = cudaMemsetAsync(ws.blk, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
         k_correct<<<gcol, kThreads, 0, s>>>(ws.xo, ws.p, ws.x, nc, att0, instr0, glob0, ws.blk);
-        if ((e = cudaMemcpyAsync(hb, ws.blk, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        if ((e = cudaMemcpyAsync(ws.blk_h, ws.blk, 8 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(c, e, "refinement");
+        fin = *ws.fin_h;
+        total_itn += fin.itn;
+        const double *hb = ws.blk_h;
+        if (status == GSR_OK && prm->timeout_s > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > prm->timeout_s)
+            status = fail(c, GSR_ETIMEOUT, "solve exceeded timeout_s");
         if (status == GSR_ETIMEOUT) {
             ++outer;
             break;
