@@ -159,30 +159,55 @@ __global__ void k_rhs32(const double *__restrict__ b, float *__restrict__ r, dou
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// x += p * y (the inner solution, scaled back); per-block sums of squares of
-// the correction (blk[0..3]) and of the new x (blk[4..7]).
+// x += p * y (the inner solution, scaled back); per-block sums of squares of the
+// correction (blk[0..3]) and of the new x (blk[4..7]). Four columns per thread and
+// round with their loads issued together (the pass is latency-bound), one block
+// reduction for the eight sums.
 __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, const double *__restrict__ y,
                           int64_t n, int64_t att0, int64_t instr0, int64_t glob0, double *__restrict__ blk)
 {
-    __shared__ double sm32[32];
-    double sd[4] = {0.0, 0.0, 0.0, 0.0}, sx[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const double d = p[j] * y[j];
-        const double xn = x[j] + d;
-        x[j] = xn;
-        const int b = j < att0 ? 0 : (j < instr0 ? 1 : (j < glob0 ? 2 : 3));
+    constexpr int E = 4;
+    __shared__ double sm[kThreads / 32][8];
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += E * stride) {
+        double pr[E], yr[E], xr[E];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            sd[q] += (q == b) ? d * d : 0.0;
-            sx[q] += (q == b) ? xn * xn : 0.0;
+        for (int q = 0; q < E; ++q) {
+            const int64_t j = j0 + q * stride;
+            pr[q] = yr[q] = xr[q] = 0.0;
+            if (j < n) {
+                pr[q] = p[j];
+                yr[q] = y[j];
+                xr[q] = x[j];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int64_t j = j0 + q * stride;
+            if (j >= n) continue;
+            const double d = pr[q] * yr[q];
+            const double xn = xr[q] + d;
+            x[j] = xn;
+            const int b = j < att0 ? 0 : (j < instr0 ? 1 : (j < glob0 ? 2 : 3));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[k] += (k == b) ? d * d : 0.0;
+                acc[4 + k] += (k == b) ? xn * xn : 0.0;
+            }
         }
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const double a = block_sum(sd[q], sm32);
-        if (threadIdx.x == 0 && a != 0.0) atomicAdd(blk + q, a);
-        const double bx = block_sum(sx[q], sm32);
-        if (threadIdx.x == 0 && bx != 0.0) atomicAdd(blk + 4 + q, bx);
+    for (int k = 0; k < 8; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sm[w][threadIdx.x];
+        if (tot != 0.0) atomicAdd(blk + threadIdx.x, tot);
     }
 }
 
@@ -236,6 +261,9 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols, nr = c->n_rows;
     const int gcol = col_grid(c, nc);
+    // k_correct: four columns per thread and round, two blocks per SM
+    const int gcor = (int)std::min<int64_t>(std::max<int64_t>((nc + 4 * kThreads - 1) / (4 * kThreads), 1),
+                                            2 * (int64_t)c->sm_count);
     const bool dev_io = prm->where == GSR_DEVICE;
     cudaError_t e;
 
@@ -286,7 +314,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
                           true);
         if (status != GSR_OK && status != GSR_ETIMEOUT) return status;
         if ((e = cudaMemsetAsync(ws.blk, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
-        k_correct<<<gcol, kThreads, 0, s>>>(ws.xo, ws.p, ws.x, nc, att0, instr0, glob0, ws.blk);
+        k_correct<<<gcor, kThreads, 0, s>>>(ws.xo, ws.p, ws.x, nc, att0, instr0, glob0, ws.blk);
         if ((e = cudaMemcpyAsync(ws.blk_h, ws.blk, 8 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(c, e, "refinement");
