@@ -1,0 +1,63 @@
+"""bench.py's JSON line on a small workload (c1: 1e5 rows): the keys of the contract, the
+reference arm on the host (the oracle), and the GPU arm in its default and sequential
+forms (every solver within 1e-9 per block of the binary64 reference)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+             "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+
+
+def _run(*args, timeout=900):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                       text=True, timeout=timeout)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-3000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    line = _run("--impl", "reference", "--workload", "c1", "--steps", "1", "--warmup", "3")
+    assert BASE_KEYS <= set(line)
+    assert line["impl"] == "reference" and line["unit"] == "s" and line["higher_is_better"] is False
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("c1:")
+
+
+def _check_gpu_line(line):
+    assert BASE_KEYS <= set(line)
+    assert {"roofline", "clocks", "gpu_launches", "solvers", "kernels"} <= set(line)
+    assert line["unit"] == "s" and line["higher_is_better"] is False and line["scaling"] == "weak"
+    assert line["value"] > 0 and line["gpu_launches"] > 0
+    assert set(line["solvers"]) >= {"fp64_plain", "mixed"}
+    for name, leg in line["solvers"].items():
+        assert leg["final_block_err"] <= 1e-9, (name, leg)
+    best = min(leg["s"] for leg in line["solvers"].values())
+    assert abs(line["value"] - best) <= 1e-12 * best
+    roof = line["roofline"]
+    assert roof["bound"] in ("hbm", "alu") and roof["peak"] > 0 and roof["achieved"] > 0
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
+    assert set(line["kernels"]) == {"aprod1_f64", "aprod2_f64", "aprod1_f32", "aprod2_f32", "residual_df"}
+    assert "sm_mhz" in line["clocks"]
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    line = _run("--workload", "c1", "--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--no-sections")
+    _check_gpu_line(line)
+    assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["value"] > 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_sequential_line():
+    line = _run("--workload", "c1", "--sequential", "--steps", "1", "--warmup", "3")
+    _check_gpu_line(line)
+    assert line["e2e"] is None and line["cpu_baseline"] is None and line["sections"] is None
