@@ -96,7 +96,8 @@ def load_peaks():
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi sampling (200 ms) during the timed region."""
+    """nvidia-smi sampling (every 50 ms) during the timed region; entering waits for the first sample,
+    so that the sampling covers the whole region however long nvidia-smi takes to start."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -110,10 +111,14 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            n0 = len(self.lines)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.monotonic() + 5.0
+            while len(self.lines) == n0 and self.proc.poll() is None and time.monotonic() < deadline:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
