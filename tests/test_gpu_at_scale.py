@@ -86,10 +86,22 @@ def _star_system(cfg, sp, stars, x):
     return sub, xs
 
 
+def _bytes_needed(cfg):
+    """Peak device memory of the test: two binary32 contexts (116 B a row each), the generator's
+    staging planes with the int64 index copy of the statistics (24 + 4 + 24 + 48 B a row), then the
+    knot-ordered attitude copies and their temporaries (52 + 64 B a row per context) and row vectors."""
+    n = int(gsrgen.star_ptr(cfg)[-1])
+    return max(2 * 116 * n + 100 * n, 2 * 116 * n + 2 * 52 * n + 64 * n + 40 * n)
+
+
 @pytest.mark.parametrize("name", ["c3", "c5"])
 def test_aprods_at_scale(name):
     cfg = gsrgen.workloads()[name].cfg
     dev = torch.device("cuda", 0)
+    torch.cuda.empty_cache()  # what earlier tests left cached is free for this one
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 1.1 * _bytes_needed(cfg):
+        pytest.skip(f"needs about {_bytes_needed(cfg) / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
     sp, ctx, cabs, count, cmax = _load(cfg, dev)
     try:
         _check(cfg, dev, sp, ctx, cabs, count, cmax)
