@@ -166,7 +166,8 @@ gsr_status gsr_set_system(gsr_ctx *ctx, const void *values, int32_t values_fp32,
  *   x  device array of n_cols binary64 (read only).
  *   y  device array of n_rows binary64, updated in place.
  * Runs on stream; does not synchronise. Arithmetic is binary64 whatever the
- * storage precision. GSR_ESTATE before every row has been set.
+ * storage precision. Errors: GSR_EINVAL (null vector), GSR_ESTATE (before
+ * every row has been set), GSR_ECUDA.
  */
 gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
 
@@ -177,7 +178,11 @@ gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
  * Runs on stream. Partial sums (per star segment, per attitude knot run,
  * per block for the instrumental and global unknowns) are added with atomic
  * adds, so the low bits of the results can differ from run to run (the sums
- * are reordered).
+ * are reordered). The first call after the rows change builds the
+ * knot-ordered attitude copy (52 B a row for binary32 storage, 100 B for
+ * binary64, plus temporaries while it is sorted) and synchronises stream.
+ * Errors: GSR_EINVAL (null vector), GSR_ESTATE (rows not loaded),
+ * GSR_ENOMEM, GSR_ECUDA.
  */
 gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
 
@@ -186,6 +191,8 @@ gsr_status gsr_aprod2(gsr_ctx *ctx, const double *y, double *x, void *stream);
  * solves of GSR_MIXED; Eq. 2). FP32-stored contexts only (GSR_EINVAL
  * otherwise).
  *   x  device array of n_cols binary32.   y  device array of n_rows binary32.
+ * Errors: GSR_EINVAL (binary64-stored context, null vector), GSR_ESTATE (rows
+ * not loaded), GSR_ECUDA.
  */
 gsr_status gsr_aprod1_f32(gsr_ctx *ctx, const float *x, float *y, void *stream);
 
@@ -198,7 +205,10 @@ gsr_status gsr_aprod1_f32(gsr_ctx *ctx, const float *x, float *y, void *stream);
  * fixed point per block (each contribution rounded to 2^-20 or finer of its
  * column's bound max|a_j| max|y|) and then exact in binary64, so those
  * entries do not depend on the order of the additions; gsr_aprod2_plan says
- * which form the loaded rows take.
+ * which form the loaded rows take. The first call after the rows change
+ * takes the statistics of that choice (one pass, then a synchronisation of
+ * stream), and builds the knot-ordered copy when the two-pass form applies.
+ * Errors: as gsr_aprod1_f32, and GSR_ENOMEM.
  */
 gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream);
 
@@ -223,11 +233,15 @@ gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream)
 gsr_status gsr_aprod2_plan(gsr_ctx *ctx, void *stream, int32_t *passes, int32_t *fx_bits, int32_t *ins_group);
 
 /*
- * gsr_residual -- r = b - A x for the loaded b, with every product and sum
- * carried in double-float (pairs of binary32 with error-free transforms:
- * about 2^-44 relative to the sum of |terms|), the outer residual of the
- * GSR_MIXED refinement. FP32-stored contexts only; b must be loaded.
+ * gsr_residual -- r = b - A x (the residual of Eq. 1) for the loaded b, with
+ * every product and sum carried in double-float (pairs of binary32 with
+ * error-free transforms: about 2^-44 relative to the sum of |terms|), the
+ * outer residual of the GSR_MIXED refinement. FP32-stored contexts only; b
+ * must be loaded.
  *   x  device array of n_cols binary64.   r  device array of n_rows binary32.
+ * Errors: GSR_EINVAL (binary64-stored context, null vector), GSR_ESTATE (rows
+ * or b not loaded), GSR_ENOMEM (the workspace, allocated on first use),
+ * GSR_ECUDA.
  */
 gsr_status gsr_residual(gsr_ctx *ctx, const double *x, float *r, void *stream);
 
