@@ -254,11 +254,15 @@ gsr_status gsr_residual(gsr_ctx *ctx, const double *x, float *r, void *stream);
  * convenience.) gsr_residual takes its scratch from the context's workspace,
  * allocated on first use; this entry point calls no allocating routine.
  *   - Its scratch is a file-scope device array of 2^20 binary32 pairs
- *     (8 MiB), present on every GPU that loads the library until the process
- *     exits: n_cols above 1048576 is rejected with GSR_EINVAL.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, once per device, with that device current); make
- *     that first call before any stream capture.
+ *     (8 MiB): n_cols above 1048576 is rejected with GSR_EINVAL.
+ *   - Set-up: creating a context (gsr_create / gsr_create_sections) places
+ *     the array on that context's device and loads the two kernels this
+ *     entry point launches, once per device, while allocating is expected;
+ *     the array then stays there until the process exits. A call looks the
+ *     array's device address up again (cudaGetSymbolAddress, a host-side
+ *     lookup while it is loaded) and allocates nothing. A cudaDeviceReset
+ *     removes the array with every context of the device: create a context
+ *     again, which places it anew, before the next call.
  *   - Every call shares the one array, which keeps the last call's contents;
  *     each call writes every element it reads first, so nothing needs
  *     clearing. Calls that overlap on the GPU (different streams, or

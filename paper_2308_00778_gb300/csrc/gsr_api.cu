@@ -419,6 +419,8 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
 
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // the scratch array of gsr_residual_static is placed on the device here, while allocating is expected
+    if (e == cudaSuccess) e = static_scratch_load(sv);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;

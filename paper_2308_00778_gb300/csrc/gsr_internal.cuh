@@ -224,6 +224,13 @@ inline bool att_fused(const gsr_ctx *c) { return c->prec == GSR_FP32 && c->fx_bi
 // max |y| word of the fixed-point sums (nullptr when they are off)
 inline uint32_t *fx_ymax(const gsr_ctx *c) { return c->fx_bits > 0 ? c->fx_word + 2 * (size_t)c->fx_nc : nullptr; }
 
+// the allocation-free residual's scratch array (residual_static.cu): load its module and the kernels
+// the entry point launches on the current device and look up the array's address (context creation
+// calls it, so that no later call of the entry point loads anything)
+cudaError_t static_scratch_load(bool sv);
+// load the split and residual kernels (mixed.cu) of a context with (sv) or without run-time sections
+cudaError_t residual_kernels_load(bool sv);
+
 // LSQR driver (lsqr.cu)
 // x0_dev: x0 is device memory whatever prm->where says (the warm start's vector)
 // p_ready: ws.p already holds this solve's column scaling (computed by the warm

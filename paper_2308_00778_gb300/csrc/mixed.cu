@@ -233,6 +233,15 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b
 }
 
 // x (binary64) -> (hi, lo) binary32 pairs. Allocates nothing.
+cudaError_t residual_kernels_load(bool sv)
+{
+    // cudaFuncGetAttributes loads a kernel that lazy module loading has not loaded yet
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_split);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, sv ? k_residual<true> : k_residual<false>);
+    return e;
+}
+
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;

@@ -36,21 +36,48 @@ MUTANTS = {
                                       "x[glob0 + j] = x[glob0 + j] + a[k] * yi;"),
 }
 
+# mistakes in the warm-start oracle (oracle/warm.c), caught by tests/test_oracle_warm.py
+WARM_MUTANTS = {
+    "adam bias correction of step 1": ("const double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);",
+                                       "const double c1 = 1.0 - pow(b1, 1), c2 = 1.0 - pow(b2, step);"),
+    "adam second moment without square": ("(1.0 - b2) * g[i] * g[i];", "(1.0 - b2) * fabs(g[i]);"),
+    "mirrored backward skips the dout rounding": ("const double g = rnd(dout[(b * L + p) * cout + co], mirrored);",
+                                                  "const double g = dout[(b * L + p) * cout + co];"),
+    "mirrored backward rounds the bias gradient": ("dbias[co] = dbias[co] + dout[(b * L + p) * cout + co];",
+                                                   "dbias[co] = dbias[co] + rnd(dout[(b * L + p) * cout + co], "
+                                                   "mirrored);"),
+    "forward tap reversed": ("const int64_t q = p + t - 2;\n                    if (q < 0 || q >= L) continue;\n"
+                             "                    for (int ci = 0; ci < cin; ++ci)\n                        s = s",
+                             "const int64_t q = p - t + 2;\n                    if (q < 0 || q >= L) continue;\n"
+                             "                    for (int ci = 0; ci < cin; ++ci)\n                        s = s"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_reject_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+
+def _run_pins_on_mutant(tmp_path, fname, old, new, test_file):
     for f in glob.glob(os.path.join(ROOT, "oracle", "*.[ch]")):
         shutil.copy(f, tmp_path)
-    src = (tmp_path / "oracle.c").read_text()
-    assert old in src, f"mutation site for '{name}' not found"
-    (tmp_path / "oracle.c").write_text(src.replace(old, new, 1))
+    src = (tmp_path / fname).read_text()
+    assert old in src, f"mutation site not found: {old!r}"
+    (tmp_path / fname).write_text(src.replace(old, new, 1))
     lib = tmp_path / "liboracle_mutant.so"
     srcs = sorted(str(p) for p in tmp_path.glob("*.c"))
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(lib), *srcs, "-lm"],
                    check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle.py")], env=env, capture_output=True, text=True,
-                       cwd=ROOT)
-    assert r.returncode != 0, f"pins did not catch mutant '{name}'"
+                        os.path.join(ROOT, "tests", test_file)], env=env, capture_output=True, text=True, cwd=ROOT)
+    return r.returncode
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    assert _run_pins_on_mutant(tmp_path, "oracle.c", old, new, "test_oracle.py") != 0, \
+        f"pins did not catch mutant '{name}'"
+
+
+@pytest.mark.parametrize("name", sorted(WARM_MUTANTS))
+def test_warm_pins_reject_mutant(name, tmp_path):
+    old, new = WARM_MUTANTS[name]
+    assert _run_pins_on_mutant(tmp_path, "warm.c", old, new, "test_oracle_warm.py") != 0, \
+        f"warm-start pins did not catch mutant '{name}'"

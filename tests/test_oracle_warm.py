@@ -174,3 +174,73 @@ def test_jacobi_features_dense():
         np.testing.assert_allclose(f[:, ax] * scale, jac[ax * 10:(ax + 1) * 10], rtol=1e-11)
         lg = np.log(colsq) - np.log(colsq).mean()
         np.testing.assert_allclose(f[:, 3 + ax], lg[ax * 10:(ax + 1) * 10], rtol=1e-11, atol=1e-12)
+
+
+def _bf16_torch(a):
+    """Round to bfloat16 (nearest even) with torch's own conversion, independent of the oracle's."""
+    import torch
+
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _conv_bwd_numpy(x, dout, W):
+    """din, dW, db of one layer (kernel 5, zero padding 2) written as shifted products."""
+    nb, L, cin = x.shape
+    xp = np.zeros((nb, L + 4, cin))
+    xp[:, 2:L + 2] = x
+    dW = np.zeros_like(W)
+    dinp = np.zeros((nb, L + 4, cin))
+    for t in range(5):
+        # out[p] takes in[p + t - 2] = xp[p + t] through W[:, :, t]
+        dW[:, :, t] = np.einsum("bpo,bpc->oc", dout, xp[:, t:t + L])
+        dinp[:, t:t + L] += np.einsum("bpo,oc->bpc", dout, W[:, :, t])
+    return dinp[:, 2:L + 2], dW, dout.sum(axis=(0, 1))
+
+
+def test_mirrored_conv_backward_rounding_points():
+    """The mirrored backward rounds the output gradient, the layer input and the weights to bfloat16 in the
+    products (the points where the GPU stores bfloat16 operands) and sums the bias gradient from the
+    unrounded output gradient; an independent restatement with torch's bfloat16 conversion agrees, and
+    moving any one rounding point changes the result by far more than the tolerance."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((2, 23, 6))
+    W = rng.standard_normal((7, 6, 5))
+    dout = rng.standard_normal((2, 23, 7))
+    din, dW, db = oracle.conv_bwd(x, dout, W, mirrored=True)
+    rin, rW, rb = _conv_bwd_numpy(_bf16_torch(x), _bf16_torch(dout), _bf16_torch(W))
+    np.testing.assert_allclose(din, rin, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(dW, rW, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(db, dout.sum(axis=(0, 1)), rtol=1e-13)
+    # each rounding point matters: leaving one out moves the result by ~2^-9 relative
+    for alt in (_conv_bwd_numpy(x, _bf16_torch(dout), _bf16_torch(W)),
+                _conv_bwd_numpy(_bf16_torch(x), dout, _bf16_torch(W)),
+                _conv_bwd_numpy(_bf16_torch(x), _bf16_torch(dout), W)):
+        moved = max(np.abs(alt[0] - din).max() / np.abs(din).max(), np.abs(alt[1] - dW).max() / np.abs(dW).max())
+        assert moved > 1e-5
+    # the bias gradient is not taken from the rounded dout
+    assert np.abs(_bf16_torch(dout).sum(axis=(0, 1)) - db).max() > 1e-6
+
+
+def test_adam_later_steps_closed_form():
+    """Adam over three steps with changing gradients against the unrolled moments
+    m_t = (1 - b1) sum_k b1^(t-k) g_k, v_t = (1 - b2) sum_k b2^(t-k) g_k^2 and the bias corrections
+    1 - b^t of each step (the recursive form in the oracle must reproduce them at t = 2, 3)."""
+    b1, b2, eps, lr = 0.9, 0.999, 1e-8, 0.01
+    w0 = np.array([1.0, -2.0, 0.5, 3.0])
+    gs = [np.array([0.3, -4.0, 1e-3, 1e-6]), np.array([-0.1, -2.0, 2e-3, 1.0]),
+          np.array([0.25, 1.0, -5e-4, 1e-6])]
+    w, m, v = w0.copy(), np.zeros(4), np.zeros(4)
+    ref = w0.copy()
+    for t in range(1, 4):
+        oracle.adam(w, m, v, gs[t - 1], lr, b1=b1, b2=b2, eps=eps, step=t)
+        mt = (1 - b1) * sum(b1 ** (t - k) * gs[k - 1] for k in range(1, t + 1))
+        vt = (1 - b2) * sum(b2 ** (t - k) * gs[k - 1] ** 2 for k in range(1, t + 1))
+        ref = ref - lr * (mt / (1 - b1 ** t)) / (np.sqrt(vt / (1 - b2 ** t)) + eps)
+        np.testing.assert_allclose(m, mt, rtol=1e-13)
+        np.testing.assert_allclose(v, vt, rtol=1e-13)
+        np.testing.assert_allclose(w, ref, rtol=1e-13, atol=1e-15)
+    # a stale bias correction (step 1's at step 3) would move the last update visibly
+    w2, m2, v2 = w0.copy(), np.zeros(4), np.zeros(4)
+    for t in range(1, 4):
+        oracle.adam(w2, m2, v2, gs[t - 1], lr, b1=b1, b2=b2, eps=eps, step=1 if t == 3 else t)
+    assert np.abs(w2 - ref).max() > 1e-4
