@@ -68,6 +68,37 @@ gsr_status gsr_net_gradients(gsr_net *net, const float *in, const float *target,
                              float *grads, int64_t count, double *loss, void *stream);
 
 /*
+ * gsr_net_layer_forward -- one layer of the network on caller data, for
+ * checking the tensor-core convolution layer by layer: out = bias_l +
+ * conv(W_l, in) before the ReLU and before any rounding of the output.
+ * layer 0..5; in [batch][len][cin_l] fp32 device (rounded to bf16 as the
+ * network rounds its layer inputs), out [batch][len][cout_l] fp32 device;
+ * (cin_l, cout_l) = (6, 64), (64, 64) x 4, (64, 3). GSR_EINVAL on a bad layer.
+ */
+gsr_status gsr_net_layer_forward(gsr_net *net, int32_t layer, const float *in, int64_t batch, int64_t len, float *out,
+                                 void *stream);
+
+/*
+ * gsr_net_layer_backward -- the gradients of one layer given dout =
+ * dLoss/d(layer output before the ReLU), [batch][len][cout_l] fp32 device:
+ * dout is rounded to bf16 for both products (as in training) and summed
+ * unrounded for the bias gradient. din (NULL: skipped) [batch][len][cin_l]
+ * fp32, not masked by the previous layer's ReLU; dW [cout_l][cin_l][5] and
+ * db [cout_l] fp32 device, overwritten. The network's parameters and Adam
+ * state are unchanged.
+ */
+gsr_status gsr_net_layer_backward(gsr_net *net, int32_t layer, const float *in, const float *dout, int64_t batch,
+                                  int64_t len, float *din, float *dW, float *db, void *stream);
+
+/*
+ * gsr_net_apply_gradients -- one Adam step (as in gsr_net_train_step) with
+ * caller-provided gradients: grads is a host fp32 array in the parameter
+ * layout (count = gsr_net_num_params()), e.g. gradients summed over several
+ * batches with gsr_net_gradients. Synchronous.
+ */
+gsr_status gsr_net_apply_gradients(gsr_net *net, const float *grads, int64_t count, float lr, void *stream);
+
+/*
  * gsr_warm_features -- the network input of the loaded system: for every
  * attitude knot k (n_dfa rows) and axis a, the Jacobi estimate
  * (A^T b)_j / |A_:,j|^2 of column j = (a, k) divided by `scale` (the root mean

@@ -103,7 +103,8 @@ struct Workspace {
     float *netout = nullptr;    // n_dfa x 3: network output
     double *wacc = nullptr;     // 4: feature sums [0..1], scale [2]
     double *x0w = nullptr;      // n_cols: warm start vector
-    float *astro_n = nullptr;   // n_stars x 20: per-star normal equations of the warm start
+    void *astro_n = nullptr;    // n_stars x 20: per-star normal equations of the warm start (binary32 for
+                                // binary32 storage, binary64 for binary64 storage)
     std::vector<GraphCache> graphs;
     LsqrState *st = nullptr;    // device
     int32_t *flag_h = nullptr;  // pinned mapped host word: 1 when the solve has stopped

@@ -58,7 +58,7 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 }
 
 // ---------------------------------------------------------------- convolution (forward / backward-data)
-enum { CONV_RELU = 0, CONV_LAST = 1, CONV_BWD = 2 };
+enum { CONV_RELU = 0, CONV_LAST = 1, CONV_BWD = 2, CONV_RAW = 3 };
 
 constexpr int CONV_POS = 64;  // positions per block (4 warps x 16)
 
@@ -66,6 +66,7 @@ constexpr int CONV_POS = 64;  // positions per block (4 warps x 16)
 //   CONV_RELU: out16 = bf16(relu(acc + bias))                     [B][L][COUT]
 //   CONV_LAST: out32 = acc + bias (fp32)                          [B][L][COUT]
 //   CONV_BWD : v = acc * (mask > 0): out32 = v, out16 = bf16(v)   [B][L][COUT]
+//   CONV_RAW : out32 = acc (fp32)                                  [B][L][COUT]
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16 *__restrict__ in, int64_t L,
                                               const __nv_bfloat16 *__restrict__ Bm, const float *__restrict__ bias,
@@ -137,6 +138,8 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16 *__restrict__ 
                     out16[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
                 } else if (MODE == CONV_LAST) {
                     out32[o] = v + bias[co];
+                } else if (MODE == CONV_RAW) {
+                    out32[o] = v;
                 } else {
                     v = (__bfloat162float(mask[o]) > 0.f) ? v : 0.f;
                     out32[o] = v;
@@ -260,6 +263,36 @@ __global__ void k_pack_input(const float *__restrict__ x, int64_t n, __nv_bfloat
         const int64_t p = i / CHP(0);
         const int c = (int)(i % CHP(0));
         out[i] = __float2bfloat16_rn(c < CH(0) ? x[p * CH(0) + c] : 0.f);
+    }
+}
+
+// fp32 [n][c] -> bf16 [n][cp] and (f32 non-null) fp32 [n][cp], zero padding
+__global__ void k_pack_any(const float *__restrict__ x, int64_t n, int c, int cp, __nv_bfloat16 *__restrict__ out,
+                           float *__restrict__ f32)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * cp; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / cp;
+        const int ch = (int)(i % cp);
+        const float v = ch < c ? x[p * c + ch] : 0.f;
+        out[i] = __float2bfloat16_rn(v);
+        if (f32) f32[i] = v;
+    }
+}
+
+// fp32 [n][cp] -> fp32 [n][c]
+__global__ void k_unpack_any(const float *__restrict__ y, int64_t n, int c, int cp, float *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * c; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = y[(i / c) * cp + i % c];
+}
+
+// padded dW [coutp][5 cinp] (tap-major) -> W layout [cout][cin][5]
+__global__ void k_unpack_dw(const float *__restrict__ dwp, int cin, int cout, int cinp, float *__restrict__ dw)
+{
+    const int64_t n = (int64_t)cout * cin * KW;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(i / (cin * KW)), ci = (int)((i / KW) % cin), t = (int)(i % KW);
+        dw[i] = dwp[(int64_t)co * (KW * cinp) + t * cinp + ci];
     }
 }
 
@@ -498,6 +531,48 @@ static cudaError_t net_train_dev(gsr_net *n, const float *in, const float *targe
     return cudaGetLastError();
 }
 
+// one layer on caller data (the per-layer checks of gsr_net_layer_forward / _backward)
+template <int CINP, int COUTP>
+static cudaError_t layer_fwd_t(gsr_net *n, int l, const float *in, int64_t B, int64_t L, float *out, cudaStream_t s)
+{
+    const int64_t P = B * L;
+    k_pack_any<<<grid_n(P * CINP), 256, 0, s>>>(in, P, CH(l), CINP, n->act[l], nullptr);
+    const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
+    conv_launch<CINP, COUTP, CONV_LAST>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, nullptr, n->d32, s);
+    k_unpack_any<<<grid_n(P * CH(l + 1)), 256, 0, s>>>(n->d32, P, CH(l + 1), COUTP, out);
+    return cudaGetLastError();
+}
+
+template <int CINP, int COUTP>
+static cudaError_t layer_bwd_t(gsr_net *n, int l, const float *in, const float *dout, int64_t B, int64_t L, float *din,
+                               float *dW, float *db, cudaStream_t s)
+{
+    const int64_t P = B * L;
+    cudaError_t e = cudaMemsetAsync(n->dW[l], 0, sizeof(float) * (size_t)COUTP * KW * CINP, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->db[l], 0, sizeof(float) * CH(l + 1), s);
+    if (e != cudaSuccess) return e;
+    k_pack_any<<<grid_n(P * CINP), 256, 0, s>>>(in, P, CH(l), CINP, n->act[l], nullptr);
+    // the output gradient in bf16 for both products, in fp32 for the bias gradient
+    k_pack_any<<<grid_n(P * COUTP), 256, 0, s>>>(dout, P, CH(l + 1), COUTP, n->d16a, n->d32);
+    const unsigned wg = (unsigned)std::min<int64_t>(std::max<int64_t>((P + WG_POS - 1) / WG_POS, 1), 1024);
+    k_conv_wgrad<CINP, COUTP><<<dim3(wg, (unsigned)((KW * CINP / 8 + 9) / 10)), 128, 0, s>>>(n->act[l], n->d16a, B, L,
+                                                                                         n->dW[l]);
+    k_bias_grad<<<grid_n(P * CH(l + 1)), 256, sizeof(float) * CH(l + 1), s>>>(n->d32, P, CH(l + 1), COUTP, n->db[l]);
+    k_unpack_dw<<<grid_n(layer_wsize(l)), 256, 0, s>>>(n->dW[l], CH(l), CH(l + 1), CINP, dW);
+    if ((e = cudaMemcpyAsync(db, n->db[l], sizeof(float) * CH(l + 1), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    if (din) {  // the flipped-weight product, unmasked, fp32 (after the bias gradient has read d32)
+        const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
+        conv_launch<COUTP, CINP, CONV_RAW>(grid, n->d16a, L, n->Bb[l], nullptr, nullptr, nullptr, n->d32, s);
+        k_unpack_any<<<grid_n(P * CH(l)), 256, 0, s>>>(n->d32, P, CH(l), CINP, din);
+    }
+    // leave the accumulators zero for training
+    if ((e = cudaMemsetAsync(n->dW[l], 0, sizeof(float) * (size_t)COUTP * KW * CINP, s)) == cudaSuccess)
+        e = cudaMemsetAsync(n->db[l], 0, sizeof(float) * CH(l + 1), s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 static gsr_status net_fail(gsr_net *n, gsr_status st, const std::string &m)
 {
     if (n) n->err = m;
@@ -682,6 +757,84 @@ GSR_API gsr_status gsr_net_gradients(gsr_net *n, const float *in, const float *t
     if (e != cudaSuccess) {
         cudaGetLastError();
         return net_fail(n, GSR_ECUDA, std::string("gradients: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_layer_forward(gsr_net *n, int32_t layer, const float *in, int64_t batch, int64_t len,
+                                         float *out, void *stream)
+{
+    if (!n || !in || !out || batch < 1 || len < 1 || layer < 0 || layer >= NLAYER) return GSR_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = net_reserve(n, batch * len);
+    if (e == cudaSuccess) {
+        if (layer == 0)
+            e = layer_fwd_t<16, 64>(n, layer, in, batch, len, out, s);
+        else if (layer == NLAYER - 1)
+            e = layer_fwd_t<64, 16>(n, layer, in, batch, len, out, s);
+        else
+            e = layer_fwd_t<64, 64>(n, layer, in, batch, len, out, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA,
+                        std::string("layer_forward: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_layer_backward(gsr_net *n, int32_t layer, const float *in, const float *dout, int64_t batch,
+                                          int64_t len, float *din, float *dW, float *db, void *stream)
+{
+    if (!n || !in || !dout || !dW || !db || batch < 1 || len < 1 || layer < 0 || layer >= NLAYER) return GSR_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e == cudaSuccess) e = net_reserve(n, batch * len);
+    if (e == cudaSuccess) {
+        if (layer == 0)
+            e = layer_bwd_t<16, 64>(n, layer, in, dout, batch, len, din, dW, db, s);
+        else if (layer == NLAYER - 1)
+            e = layer_bwd_t<64, 16>(n, layer, in, dout, batch, len, din, dW, db, s);
+        else
+            e = layer_bwd_t<64, 64>(n, layer, in, dout, batch, len, din, dW, db, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA,
+                        std::string("layer_backward: ") + cudaGetErrorString(e));
+    }
+    return GSR_OK;
+}
+
+GSR_API gsr_status gsr_net_apply_gradients(gsr_net *n, const float *grads, int64_t count, float lr, void *stream)
+{
+    if (!n || !grads || !(lr >= 0.f)) return GSR_EINVAL;
+    if (count != total_params()) return net_fail(n, GSR_EINVAL, "parameter count mismatch");
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(n->device);
+    // host layout [cout][cin][5] + bias -> the padded accumulators the Adam kernel reads
+    int64_t off = 0;
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        const int cin = CH(l), cout = CH(l + 1), cinp = CHP(l);
+        std::vector<float> dWp((size_t)CHP(l + 1) * KW * cinp, 0.f);
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int t = 0; t < KW; ++t)
+                    dWp[(size_t)co * KW * cinp + t * cinp + ci] = grads[off + ((int64_t)co * cin + ci) * KW + t];
+        e = cudaMemcpy(n->dW[l], dWp.data(), sizeof(float) * dWp.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(n->db[l], grads + off + layer_wsize(l), sizeof(float) * cout, cudaMemcpyHostToDevice);
+        off += layer_wsize(l) + cout;
+    }
+    if (e == cudaSuccess) {
+        n->step += 1;
+        e = refresh_operands(n, true, lr, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return net_fail(n, GSR_ECUDA, std::string("apply_gradients: ") + cudaGetErrorString(e));
     }
     return GSR_OK;
 }

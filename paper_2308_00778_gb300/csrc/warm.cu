@@ -107,7 +107,10 @@ __global__ void k_rest_guess(const double *__restrict__ z, const double *__restr
 // pass with the astrometric part of x0 still zero), k_astro_normal
 // accumulates for every star G = sum a a^T (upper triangle, 15 values) and
 // h = sum a r (5 values) over the star's rows (a = the row's 5 astrometric
-// coefficients; binary32 products and sums) into N[star][20]; k_astro_chol
+// coefficients) into N[star][20], in binary32 for binary32 storage (the mixed
+// solver's start, refined afterwards) and in binary64 for binary64 storage
+// (the plain solver's start, whose products are exact and whose sums are then
+// good to ~n_obs 2^-53 relative); k_astro_chol
 // adds lambda = 1e-12 trace(G)/5 to the diagonal and solves G x = h by
 // Cholesky in binary64, one thread per star (x = 0 when G is not positive
 // definite).
@@ -116,18 +119,19 @@ static constexpr int NNORM = 20;
 // Add a warp's per-lane partial sums of the 20 normal-equation values of star
 // k to N (through a per-warp shared buffer: lanes 0..19 each sum one value).
 // Warp-collective.
-__device__ __forceinline__ void flush_normal_run(float (&acc)[NNORM], int64_t k, float *__restrict__ wbuf,
-                                                 float *__restrict__ N)
+template <typename NT>
+__device__ __forceinline__ void flush_normal_run(NT (&acc)[NNORM], int64_t k, NT *__restrict__ wbuf,
+                                                 NT *__restrict__ N)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NNORM; ++j) {
         wbuf[j * 32 + lane] = acc[j];
-        acc[j] = 0.f;
+        acc[j] = (NT)0;
     }
     __syncwarp();
     if (lane < NNORM) {
-        float t = 0.f;
+        NT t = (NT)0;
 #pragma unroll 8
         for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
         atomicAdd(N + NNORM * k + lane, t);
@@ -136,7 +140,8 @@ __device__ __forceinline__ void flush_normal_run(float (&acc)[NNORM], int64_t k,
 }
 
 // the 20 products of one row: a_p a_q (p <= q), then a_p r
-__device__ __forceinline__ void normal_terms(const float (&a)[NASTRO], float r, float (&out)[NNORM])
+template <typename NT>
+__device__ __forceinline__ void normal_terms(const NT (&a)[NASTRO], NT r, NT (&out)[NNORM])
 {
     int q = 0;
 #pragma unroll
@@ -147,12 +152,12 @@ __device__ __forceinline__ void normal_terms(const float (&a)[NASTRO], float r, 
     for (int p = 0; p < NASTRO; ++p) out[15 + p] = a[p] * r;
 }
 
-// this lane's R consecutive entries of a row vector as binary32 (0 past n_rows)
-template <typename RT, int R>
-__device__ __forceinline__ void load_rows(const RT *__restrict__ r, int64_t r0, int64_t n, float (&out)[R])
+// this lane's R consecutive entries of a row vector as NT (0 past n_rows)
+template <typename RT, typename NT, int R>
+__device__ __forceinline__ void load_rows(const RT *__restrict__ r, int64_t r0, int64_t n, NT (&out)[R])
 {
 #pragma unroll
-    for (int i = 0; i < R; ++i) out[i] = r0 + i < n ? (float)__ldcs(r + r0 + i) : 0.f;
+    for (int i = 0; i < R; ++i) out[i] = r0 + i < n ? (NT)__ldcs(r + r0 + i) : (NT)0;
 }
 
 // Each warp owns a contiguous range of row tiles (as the star pass of aprod 2):
@@ -165,46 +170,46 @@ __device__ __forceinline__ void load_rows(const RT *__restrict__ r, int64_t r0, 
 // A section variant with n_astro < 5 keeps the 20-value layout: its missing
 // astrometric coefficients are zero, so their rows and columns of G and
 // entries of h stay zero (k_astro_chol solves only the leading n_astro).
-template <typename VT, typename RT, bool SV = false>
+template <typename VT, typename RT, typename NT, bool SV = false>
 __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *__restrict__ r,
-                                                      float *__restrict__ N, int64_t tiles_per_warp)
+                                                      NT *__restrict__ N, int64_t tiles_per_warp)
 {
     const int na = SV ? S.na : NASTRO;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
-    __shared__ float wred[8][NNORM * 32];
+    __shared__ NT wred[8][NNORM * 32];
     const int lane = threadIdx.x & 31;
-    float *wbuf = wred[threadIdx.x >> 5];
+    NT *wbuf = wred[threadIdx.x >> 5];
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t t0 = gw * tiles_per_warp;
     const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
-    float acc[NNORM];
+    NT acc[NNORM];
 #pragma unroll
-    for (int j = 0; j < NNORM; ++j) acc[j] = 0.f;
+    for (int j = 0; j < NNORM; ++j) acc[j] = (NT)0;
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         const int64_t r0 = t * T + lane * R;
-        float rv[R];
-        load_rows<RT, R>(r, r0, S.n_rows, rv);
-        float a[NASTRO][R];
+        NT rv[R];
+        load_rows<RT, NT, R>(r, r0, S.n_rows, rv);
+        NT a[NASTRO][R];
 #pragma unroll
         for (int j = 0; j < NASTRO; ++j) {
             // a variant's absent slots read an attitude plane (always present), zeroed after the load
-            load_vals<VT, float>(tb, j < na ? j : (SV ? S.p_att : A_ATT), a[j]);
+            load_vals<VT, NT>(tb, j < na ? j : (SV ? S.p_att : A_ATT), a[j]);
 #pragma unroll
-            for (int i = 0; i < R; ++i) a[j][i] = j < na ? a[j][i] : 0.f;
+            for (int i = 0; i < R; ++i) a[j][i] = j < na ? a[j][i] : (NT)0;
         }
 #pragma unroll
         for (int i = 0; i < R; ++i)
             if (r0 + i >= S.n_rows)
 #pragma unroll
-                for (int j = 0; j < NASTRO; ++j) a[j][i] = 0.f;
+                for (int j = 0; j < NASTRO; ++j) a[j][i] = (NT)0;
         const int64_t tile_end = min((t + 1) * T, S.n_rows);
         if (__ldg(S.star_ptr + k + 1) >= tile_end) {  // the whole tile belongs to star k
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                float ar[NASTRO], tr[NNORM];
+                NT ar[NASTRO], tr[NNORM];
 #pragma unroll
                 for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
                 normal_terms(ar, rv[i], tr);
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (sr[i] == k) {
-                    float ar[NASTRO], tr[NNORM];
+                    NT ar[NASTRO], tr[NNORM];
 #pragma unroll
                     for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
                     normal_terms(ar, rv[i], tr);
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 if (sr[i] == k) continue;
-                float ar[NASTRO], tr[NNORM];
+                NT ar[NASTRO], tr[NNORM];
 #pragma unroll
                 for (int j = 0; j < NASTRO; ++j) ar[j] = a[j][i];
                 normal_terms(ar, rv[i], tr);
@@ -304,11 +309,12 @@ __global__ void __launch_bounds__(256) k_astro_residual(SysView<float> S, const 
 
 // na: astrometric unknowns per star (5 in the standard row); a section variant's
 // trailing rows and columns (zero in N) get a unit diagonal and give x = 0
-__global__ void k_astro_chol(const float *__restrict__ N, int64_t n_stars, double *__restrict__ x0, int na)
+template <typename NT>
+__global__ void k_astro_chol(const NT *__restrict__ N, int64_t n_stars, double *__restrict__ x0, int na)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_stars;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const float *n = N + NNORM * s;
+        const NT *n = N + NNORM * s;
         double M[NASTRO][NASTRO], L[NASTRO][NASTRO], y[NASTRO], xs[NASTRO];
         int q = 0;
 #pragma unroll
@@ -366,10 +372,10 @@ static int grid_for(const gsr_ctx *c, int64_t n)
 }
 
 // k_astro_normal over contiguous tile ranges, one range per resident warp (at least 8 tiles each)
-template <typename VT, typename RT>
+template <typename VT, typename RT, typename NT>
 static cudaError_t astro_normal_launch(const gsr_ctx *c, const RT *r, cudaStream_t s)
 {
-    auto kern = c->sv ? k_astro_normal<VT, RT, true> : k_astro_normal<VT, RT, false>;
+    auto kern = c->sv ? k_astro_normal<VT, RT, NT, true> : k_astro_normal<VT, RT, NT, false>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -378,7 +384,7 @@ static cudaError_t astro_normal_launch(const gsr_ctx *c, const RT *r, cudaStream
     const int64_t per = std::max<int64_t>((c->n_tiles + max_warps - 1) / max_warps, 8);
     const int64_t warps = (c->n_tiles + per - 1) / per;
     const int64_t blocks = std::max<int64_t>((warps + wpb - 1) / wpb, 1);
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), r, c->ws.astro_n, per);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<VT>(c), r, static_cast<NT *>(c->ws.astro_n), per);
     return cudaGetLastError();
 }
 
@@ -429,9 +435,11 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
     k_rest_guess<<<grid_for(c, c->n_cols - instr0), kThreads, 0, s>>>(ws.z, ws.p, instr0, c->n_cols, x0);
     cudaError_t ez = cudaMemsetAsync(ws.z, 0, sizeof(double) * (size_t)c->n_cols, s);
     if (ez != cudaSuccess) return cuda_fail(c, ez, "memset");
-    if (!ws.astro_n && (ez = cudaMalloc(&ws.astro_n, sizeof(float) * NNORM * (size_t)c->n_stars)) != cudaSuccess)
+    // per-star normal equations: binary32 for binary32 storage, binary64 for binary64 storage
+    const size_t nt_size = c->prec == GSR_FP32 ? sizeof(float) : sizeof(double);
+    if (!ws.astro_n && (ez = cudaMalloc(&ws.astro_n, nt_size * NNORM * (size_t)c->n_stars)) != cudaSuccess)
         return cuda_fail(c, ez, "normal-equation buffer");
-    if ((ez = cudaMemsetAsync(ws.astro_n, 0, sizeof(float) * NNORM * (size_t)c->n_stars, s)) != cudaSuccess)
+    if ((ez = cudaMemsetAsync(ws.astro_n, 0, nt_size * NNORM * (size_t)c->n_stars, s)) != cudaSuccess)
         return cuda_fail(c, ez, "memset");
     if (c->n_rows > 0 && c->n_astro > 0) {
         // r = b - A x0 with the astrometric part of x0 still zero: the residual of the other parts
@@ -440,18 +448,24 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
             // ws.u32 still holds b rounded to binary32 (the features' pass only read it)
             k_neg_f32<<<grid_for(c, nc), kThreads, 0, s>>>(x0, ws.pv32, nc);
             if ((ez = launch_aprod1(c, ws.pv32, ws.u32, nullptr, nullptr, s, true)) == cudaSuccess)
-                ez = astro_normal_launch<float, float>(c, ws.u32, s);
+                ez = astro_normal_launch<float, float, float>(c, ws.u32, s);
         } else {
             k_neg_f64<<<grid_for(c, nc), kThreads, 0, s>>>(x0, ws.tmp, nc);
             if ((ez = cudaMemcpyAsync(ws.u, c->b, sizeof(double) * (size_t)c->n_rows, cudaMemcpyDeviceToDevice,
                                       s)) == cudaSuccess &&
                 (ez = launch_aprod1(c, ws.tmp, ws.u, nullptr, nullptr, s, false)) == cudaSuccess)
-                ez = astro_normal_launch<double, double>(c, ws.u, s);
+                ez = astro_normal_launch<double, double, double>(c, ws.u, s);
         }
         if (ez != cudaSuccess) return cuda_fail(c, ez, "warm start: normal equations");
     }
-    if (c->n_astro > 0)
-        k_astro_chol<<<grid_for(c, c->n_stars), kThreads, 0, s>>>(ws.astro_n, c->n_stars, x0, c->n_astro);
+    if (c->n_astro > 0) {
+        if (c->prec == GSR_FP32)
+            k_astro_chol<float><<<grid_for(c, c->n_stars), kThreads, 0, s>>>(static_cast<const float *>(ws.astro_n),
+                                                                             c->n_stars, x0, c->n_astro);
+        else
+            k_astro_chol<double><<<grid_for(c, c->n_stars), kThreads, 0, s>>>(
+                static_cast<const double *>(ws.astro_n), c->n_stars, x0, c->n_astro);
+    }
     if (r0_parts && c->prec == GSR_FP32 && c->n_rows > 0 && c->n_astro > 0) {
         // ws.u32 holds the residual of the non-astrometric parts: complete it (binary32) into the
         // residual of x0, with its per-block sums of squares in ws.part_u

@@ -115,6 +115,9 @@ def lib():
             "gsr_net_forward": (I32, [P, P, I64, I64, P, P]),
             "gsr_net_train_step": (I32, [P, P, P, I64, I64, ctypes.c_float, P, P]),
             "gsr_net_gradients": (I32, [P, P, P, I64, I64, P, I64, P, P]),
+            "gsr_net_layer_forward": (I32, [P, I32, P, I64, I64, P, P]),
+            "gsr_net_layer_backward": (I32, [P, I32, P, P, I64, I64, P, P, P, P]),
+            "gsr_net_apply_gradients": (I32, [P, P, I64, ctypes.c_float, P]),
             "gsr_warm_features": (I32, [P, P, P, P]),
             "gsr_warm_start": (I32, [P, P, P, P]),
             "gsr_lsqr_solve": (I32, [P, ctypes.POINTER(SolveParams), P, P, P, ctypes.POINTER(SolveInfo), P]),
@@ -272,6 +275,19 @@ def gsr_net_gradients(net, x, target, batch, length, grads, count, loss_ptr, str
                                    loss_ptr or None, stream or None)
 
 
+def gsr_net_layer_forward(net, layer, x, batch, length, out, stream=0):
+    return lib().gsr_net_layer_forward(net, layer, x or None, batch, length, out or None, stream or None)
+
+
+def gsr_net_layer_backward(net, layer, x, dout, batch, length, din, dW, db, stream=0):
+    return lib().gsr_net_layer_backward(net, layer, x or None, dout or None, batch, length, din or None, dW or None,
+                                        db or None, stream or None)
+
+
+def gsr_net_apply_gradients(net, grads, count, lr, stream=0):
+    return lib().gsr_net_apply_gradients(net, grads or None, count, lr, stream or None)
+
+
 def gsr_warm_features(ctx, feats, scale_ptr, stream=0):
     return lib().gsr_warm_features(ctx, feats or None, scale_ptr or None, stream or None)
 
@@ -364,6 +380,25 @@ class Net:
         self._check(gsr_net_gradients(self.h, x.data_ptr(), target.data_ptr(), b, n, g.ctypes.data, g.size,
                                       ctypes.addressof(loss), stream))
         return g, loss.value
+
+    def layer_forward(self, layer, x, out, stream=0):
+        """One layer before its ReLU: x CUDA float32 [batch, len, cin], out [batch, len, cout]."""
+        b, n, _ = x.shape
+        self._check(gsr_net_layer_forward(self.h, layer, x.data_ptr(), b, n, out.data_ptr(), stream))
+
+    def layer_backward(self, layer, x, dout, din, dW, db, stream=0):
+        """Gradients of one layer given dout (w.r.t. its output before the ReLU); din may be None."""
+        b, n, _ = x.shape
+        self._check(gsr_net_layer_backward(self.h, layer, x.data_ptr(), dout.data_ptr(), b, n,
+                                           din.data_ptr() if din is not None else 0, dW.data_ptr(), db.data_ptr(),
+                                           stream))
+
+    def apply_gradients(self, grads, lr, stream=0):
+        """One Adam step with the given gradients (host float32, parameter layout)."""
+        import numpy as np
+
+        g = np.ascontiguousarray(grads, dtype=np.float32)
+        self._check(gsr_net_apply_gradients(self.h, g.ctypes.data, g.size, lr, stream))
 
 
 class Context:

@@ -2,12 +2,14 @@
 against the oracle in mirrored mode (bf16 rounding of weights, layer inputs and
 fed-back output gradients at the same points; binary64 accumulation).
 
-Both sides see identical bf16 operands; only the FP32 (GPU) vs FP64 (oracle)
-summation differs, so per tensor |gpu - ref| / |ref| is ~1e-6. A bf16 rounding
-tie flipped by that difference moves one activation by one bf16 ulp (2^-8
-relative), which propagates; the bars (2e-3 forward, 1e-2 gradients, per
-tensor in the 2-norm) leave room for a few such flips and still catch a wrong
-tap, channel, sign or layout.
+Layer by layer (gsr_net_layer_forward / _backward) both sides see identical
+bf16 operands and only the FP32 (GPU) vs FP64 (oracle) summation differs: each
+element is within k 2^-23 of its sum of |terms| (k = the number of terms; one
+unit of binary32 rounding or truncation per addition), and
+each tensor within 1e-4 relative in the 2-norm. Through the whole network a
+bf16 rounding tie flipped by that difference moves one activation by one bf16
+ulp (2^-8 relative), which propagates; the whole-network checks (2e-3 forward,
+1e-2 gradients) are smoke checks of the composition.
 """
 import numpy as np
 import pytest
@@ -83,6 +85,79 @@ def test_gradients_vs_mirrored_oracle(shape):
         assert _rel(db, rb) <= 1e-2, (layer, _rel(db, rb))
     # the gradient query leaves the parameters and the optimiser untouched
     np.testing.assert_array_equal(net.get_params(), flat)
+    net.close()
+
+
+LAYERS = list(zip(oracle.NET_CHANNELS[:-1], oracle.NET_CHANNELS[1:]))
+
+
+@pytest.mark.parametrize("layer", range(6))
+def test_layer_forward_backward_vs_mirrored_oracle(layer):
+    """One layer at a time on identical bf16 operands: forward (before the ReLU), din, dW and db."""
+    rng = np.random.default_rng(20 + layer)
+    flat = _flat(_random_params(rng))
+    ps = _unflat(flat)
+    net = g.Net()
+    net.set_params(flat)
+    cin, cout = LAYERS[layer]
+    B, L = 2, 131  # three 64-position blocks, the last one ragged
+    x = rng.standard_normal((B, L, cin)).astype(np.float32)
+    if layer > 0:
+        x = np.maximum(x, 0.0)  # the output of the previous layer's ReLU
+    dout = (rng.standard_normal((B, L, cout)) * 1e-2).astype(np.float32)
+    xd, dd = torch.tensor(x, device="cuda"), torch.tensor(dout, device="cuda")
+    out = torch.zeros((B, L, cout), dtype=torch.float32, device="cuda")
+    din = torch.zeros((B, L, cin), dtype=torch.float32, device="cuda")
+    dW = torch.zeros((cout, cin, 5), dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    net.layer_forward(layer, xd, out)
+    net.layer_backward(layer, xd, dd, din, dW, db)
+    torch.cuda.synchronize()
+    W, bias = ps[layer]
+    x64, d64 = x.astype(np.float64), dout.astype(np.float64)
+    # the tensor cores' fp32 accumulation may truncate instead of rounding: 2^-23 per addition
+    u = 2.0 ** -23
+    # forward: K = 5 cin products and the bias per element
+    ref = oracle.conv_fwd(x64, W, bias, relu=False, mirrored=True)
+    mag = oracle.conv_fwd(np.abs(x64), np.abs(W), np.abs(bias), relu=False, mirrored=True)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= (5 * cin + 1) * u * mag + 1e-30), layer
+    assert _rel(got, ref) <= 1e-4
+    # backward: din has 5 cout products per element, dW B*L, db B*L unrounded terms
+    rin, rW, rb = oracle.conv_bwd(x64, d64, W, mirrored=True)
+    min_, mW, mb = oracle.conv_bwd(np.abs(x64), np.abs(d64), np.abs(W), mirrored=True)
+    gin, gW, gb = (t.cpu().numpy().astype(np.float64) for t in (din, dW, db))
+    assert np.all(np.abs(gin - rin) <= 5 * cout * u * min_ + 1e-30), layer
+    assert np.all(np.abs(gW - rW) <= (B * L + 64) * u * mW + 1e-30), layer
+    assert np.all(np.abs(gb - rb) <= B * L * u * mb + 1e-30), layer
+    for a, r in ((gin, rin), (gW, rW), (gb, rb)):
+        assert _rel(a, r) <= 1e-4, layer
+    # the layer calls leave the parameters untouched
+    np.testing.assert_array_equal(net.get_params(), flat)
+    net.close()
+
+
+def test_adam_three_steps_match_oracle():
+    """Three Adam steps with caller gradients spanning 1e-6..1 in magnitude, against the oracle's
+    binary64 Adam; the GPU keeps the moments and weights in binary32, so each parameter is within a few
+    2^-24 of its value plus lr times the binary32 error of the update direction."""
+    rng = np.random.default_rng(3)
+    flat = _flat(_random_params(rng))
+    net = g.Net()
+    net.set_params(flat)
+    n = flat.size
+    w = flat.astype(np.float64)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    lr = 1e-3
+    for step in range(1, 4):
+        mag = 10.0 ** rng.uniform(-6, 0, n)
+        gr = (mag * rng.choice([-1.0, 1.0], n)).astype(np.float32)
+        net.apply_gradients(gr, lr)
+        oracle.adam(w, m, v, gr.astype(np.float64), lr, step=step)
+        got = net.get_params().astype(np.float64)
+        tol = 4 * 2.0 ** -24 * np.abs(w) + lr * 1e-5
+        assert np.all(np.abs(got - w) <= tol), (step, np.max(np.abs(got - w) - tol))
     net.close()
 
 

@@ -166,9 +166,10 @@ def test_warm_start_astro_solve_sections(fp32):
     ref = np.zeros(s.n_cols)
     ref[a0:] = got[a0:]
     assert oracle.astro_solve(s, b, ref) == 0
+    bar = 1e-4 if fp32 else 1e-12  # binary32 / binary64 normal equations (as in test_gpu_warm.py)
     for st in range(cfg.n_stars):
         r, gg = ref[3 * st:3 * st + 3], got[3 * st:3 * st + 3]
-        assert np.linalg.norm(gg - r) <= 1e-4 * np.linalg.norm(r) + 1e-9, st
+        assert np.linalg.norm(gg - r) <= bar * np.linalg.norm(r) + bar * 1e-5, st
     ctx.close()
 
 

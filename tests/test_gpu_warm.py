@@ -53,10 +53,15 @@ def test_astro_solve_vs_oracle(fp32):
     ref = np.zeros(s.n_cols)
     ref[a0:] = got[a0:]
     assert oracle.astro_solve(s, b, ref) == 0
-    # binary32 accumulation of the 5x5 normal equations: ~1e-6 relative per star
+    # binary64 storage: binary64 normal equations and Cholesky, so each star's 5 unknowns agree to
+    # rounding (1e-12). Binary32 storage accumulates them in binary32 (the mixed solver's start, which
+    # the refinement corrects): recursive summation of n <= 120 terms is good to n 2^-24 = 7e-6 of the
+    # sum of |terms|, and the well-conditioned 5x5 systems (cond(G) ~ 10 with 20+ observations) keep
+    # the solution within 1e-4.
+    bar = 1e-4 if fp32 else 1e-12
     for st in range(cfg.n_stars):
         r, gg = ref[5 * st:5 * st + 5], got[5 * st:5 * st + 5]
-        assert np.linalg.norm(gg - r) <= 1e-4 * np.linalg.norm(r) + 1e-9, st
+        assert np.linalg.norm(gg - r) <= bar * np.linalg.norm(r) + bar * 1e-5, st
     ctx.close()
 
 
