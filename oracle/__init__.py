@@ -90,6 +90,13 @@ def _load():
         lib.oracle_scale_columns.argtypes = [S, P, P]
         lib.oracle_lsqr.restype = ctypes.c_int
         lib.oracle_lsqr.argtypes = [S, P, ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Info)]
+        lib.oracle_lsqr_omp.restype = ctypes.c_int
+        lib.oracle_lsqr_omp.argtypes = [S, P, ctypes.POINTER(_Params), P, P, ctypes.POINTER(_Info), ctypes.c_int32]
+        lib.oracle_omp_threads.restype = ctypes.c_int32
+        lib.oracle_omp_threads.argtypes = []
+        for f in (lib.oracle_aprod1_omp, lib.oracle_aprod2_omp):
+            f.restype = None
+            f.argtypes = [S, P, P]
         _extra_signatures(lib)
         _lib = lib
     return _lib
@@ -222,6 +229,41 @@ def lsqr(s: System, b: np.ndarray, itnlim: int, atol: float = 0.0, btol: float =
     if want_var:
         return x, info.as_dict(), var
     return x, info.as_dict()
+
+
+def lsqr_omp(s: System, b: np.ndarray, itnlim: int, atol: float = 0.0, btol: float = 0.0, conlim: float = 0.0,
+             damp: float = 0.0, precond: bool = True, threads: int = 0):
+    """The same LSQR with its loops split over the host cores (oracle_omp.c; threads 0 = all);
+    returns (x, info dict)."""
+    lib = _load()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(s.n_cols, dtype=np.float64)
+    prm = _Params(int(itnlim), atol, btol, conlim, damp, 1 if precond else 0)
+    info = _Info()
+    rc = lib.oracle_lsqr_omp(ctypes.byref(s._s), _p(b), ctypes.byref(prm), _p(x), None, ctypes.byref(info),
+                             int(threads))
+    if rc != 0:
+        raise MemoryError("oracle_lsqr_omp: allocation failed")
+    return x, info.as_dict()
+
+
+def omp_threads() -> int:
+    """Threads the all-cores LSQR uses (1 when the oracle was built without OpenMP)."""
+    return int(_load().oracle_omp_threads())
+
+
+def aprod1_omp(s: System, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert y.dtype == np.float64 and y.flags["C_CONTIGUOUS"] and y.shape == (s.n_rows,)
+    _load().oracle_aprod1_omp(ctypes.byref(s._s), _p(x), _p(y))
+    return y
+
+
+def aprod2_omp(s: System, y: np.ndarray, x: np.ndarray) -> np.ndarray:
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"] and x.shape == (s.n_cols,)
+    _load().oracle_aprod2_omp(ctypes.byref(s._s), _p(y), _p(x))
+    return x
 
 
 # ---------------------------------------------------------------- warm start (warm.c)

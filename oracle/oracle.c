@@ -161,6 +161,40 @@ ORACLE_API void oracle_scale_columns(const oracle_sys *s, const double *p, doubl
     }
 }
 
+/* the elementary vector steps of the LSQR driver, one plain loop each */
+static void vec_scale(int64_t n, double a, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = a * x[i];
+}
+
+static void vec_copy(int64_t n, const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+}
+
+static void vec_div(int64_t n, double *x, double d)
+{
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] / d;
+}
+
+/* dk = w / rho (var += dk^2), x += t1 w, w = v + t2 w; returns sum dk^2 */
+static double vec_xw_update(int64_t n, double rho, double t1, double t2, const double *v, double *w, double *x,
+                            double *var)
+{
+    double dknorm = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        const double dk = w[j] / rho;
+        dknorm = dknorm + dk * dk;
+        if (var) var[j] = var[j] + dk * dk;
+        x[j] = x[j] + t1 * w[j];
+        w[j] = v[j] + t2 * w[j];
+    }
+    return dknorm;
+}
+
+static const oracle_ops plain_ops = {aprod1_impl, aprod2_impl, oracle_precond, oracle_scale_columns, oracle_norm2,
+                                     vec_scale, vec_copy, vec_div, vec_xw_update};
+
 /*
  * LSQR (Paige & Saunders 1982, the algorithm the paper's solver runs, Sec. 1
  * and Alg. 1) for min |A~ y - b|^2 + damp^2 |y|^2 with A~ = A diag(p) when
@@ -178,8 +212,8 @@ ORACLE_API void oracle_scale_columns(const oracle_sys *s, const double *p, doubl
  * scaled variables.
  * Returns 0 on success, -1 on allocation failure.
  */
-ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
-                           oracle_lsqr_info *info)
+int oracle_lsqr_core(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
+                     oracle_lsqr_info *info, const oracle_ops *ops)
 {
     const int64_t m = s->n_rows, n = oracle_ncols(s);
     double *p = (double *)malloc(sizeof(double) * (size_t)n);
@@ -194,9 +228,9 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
     }
 
     /* preconditioning (Alg. 1: p, then normalisation of A by p) */
-    if (prm->precond) oracle_precond(s, p);
+    if (prm->precond) ops->precond(s, p);
     else for (int64_t j = 0; j < n; ++j) p[j] = 1.0;
-    oracle_scale_columns(s, p, At);
+    ops->scale_columns(s, p, At);
     oracle_sys st = *s;
     st.A = At;
 
@@ -206,14 +240,14 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
     for (int64_t j = 0; j < n; ++j) { x[j] = 0.0; if (var) var[j] = 0.0; }
 
     /* beta_1 u_1 = b */
-    for (int64_t i = 0; i < m; ++i) u[i] = b[i];
-    double beta = oracle_norm2(m, u);
-    if (beta > 0.0) for (int64_t i = 0; i < m; ++i) u[i] = u[i] / beta;
+    ops->copy(m, b, u);
+    double beta = ops->norm2(m, u);
+    if (beta > 0.0) ops->div(m, u, beta);
     /* alpha_1 v_1 = A~^T u_1 (the start through aprod 2, Alg. 1) */
     for (int64_t j = 0; j < n; ++j) v[j] = 0.0;
-    if (beta > 0.0) aprod2_impl(&st, u, v);
-    double alpha = oracle_norm2(n, v);
-    if (alpha > 0.0) for (int64_t j = 0; j < n; ++j) v[j] = v[j] / alpha;
+    if (beta > 0.0) ops->aprod2(&st, u, v);
+    double alpha = ops->norm2(n, v);
+    if (alpha > 0.0) ops->div(n, v, alpha);
     for (int64_t j = 0; j < n; ++j) w[j] = v[j];
 
     double rhobar = alpha, phibar = beta;
@@ -227,19 +261,19 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
         while (itn < prm->itnlim) {
             itn = itn + 1;
             /* beta u = A~ v - alpha u */
-            for (int64_t i = 0; i < m; ++i) t[i] = -alpha * u[i];
-            aprod1_impl(&st, v, t);
-            for (int64_t i = 0; i < m; ++i) u[i] = t[i];
-            beta = oracle_norm2(m, u);
+            ops->scale(m, -alpha, u, t);
+            ops->aprod1(&st, v, t);
+            ops->copy(m, t, u);
+            beta = ops->norm2(m, u);
             if (beta > 0.0) {
-                for (int64_t i = 0; i < m; ++i) u[i] = u[i] / beta;
+                ops->div(m, u, beta);
                 anorm = sqrt(anorm * anorm + alpha * alpha + beta * beta + dampsq);
                 /* alpha v = A~^T u - beta v */
-                for (int64_t j = 0; j < n; ++j) t[j] = -beta * v[j];
-                aprod2_impl(&st, u, t);
-                for (int64_t j = 0; j < n; ++j) v[j] = t[j];
-                alpha = oracle_norm2(n, v);
-                if (alpha > 0.0) for (int64_t j = 0; j < n; ++j) v[j] = v[j] / alpha;
+                ops->scale(n, -beta, v, t);
+                ops->aprod2(&st, u, t);
+                ops->copy(n, t, v);
+                alpha = ops->norm2(n, v);
+                if (alpha > 0.0) ops->div(n, v, alpha);
             }
 
             /* rotation eliminating the damping parameter */
@@ -262,15 +296,7 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
             /* x and w updates */
             const double t1 = phi / rho;
             const double t2 = -theta / rho;
-            double dknorm = 0.0;
-            for (int64_t j = 0; j < n; ++j) {
-                const double dk = w[j] / rho;
-                dknorm = dknorm + dk * dk;
-                if (var) var[j] = var[j] + dk * dk;
-                x[j] = x[j] + t1 * w[j];
-                w[j] = v[j] + t2 * w[j];
-            }
-            ddnorm = ddnorm + dknorm;
+            ddnorm = ddnorm + ops->xw_update(n, rho, t1, t2, v, w, x, var);
 
             /* estimate of |x| from the plane rotation on the right */
             const double delta = sn2 * rho;
@@ -331,4 +357,11 @@ ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_ls
     }
     free(p); free(At); free(u); free(v); free(w); free(t);
     return 0;
+}
+
+/* the plain single-threaded LSQR: the core with the plain loops above */
+ORACLE_API int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
+                           oracle_lsqr_info *info)
+{
+    return oracle_lsqr_core(s, b, prm, x, var, info, &plain_ops);
 }

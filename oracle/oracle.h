@@ -59,4 +59,35 @@ void oracle_scale_columns(const oracle_sys *s, const double *p, double *A_out);
 int oracle_lsqr(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
                 oracle_lsqr_info *info);
 
+/*
+ * The steps the LSQR driver delegates: the two products, the preconditioner,
+ * the column scaling, the Eq. 4 norm and the elementary vector loops. The
+ * plain oracle passes its single-threaded loops; oracle_omp.c passes the same
+ * loops with the rows (and vector elements) split over threads.
+ */
+typedef struct {
+    void (*aprod1)(const oracle_sys *s, const double *x, double *y);
+    void (*aprod2)(const oracle_sys *s, const double *y, double *x);
+    void (*precond)(const oracle_sys *s, double *p);
+    void (*scale_columns)(const oracle_sys *s, const double *p, double *A_out);
+    double (*norm2)(int64_t n, const double *a);
+    void (*scale)(int64_t n, double a, const double *x, double *y);   /* y = a x            */
+    void (*copy)(int64_t n, const double *x, double *y);              /* y = x              */
+    void (*div)(int64_t n, double *x, double d);                      /* x = x / d          */
+    double (*xw_update)(int64_t n, double rho, double t1, double t2, const double *v, double *w, double *x,
+                        double *var);  /* dk = w/rho, var += dk^2, x += t1 w, w = v + t2 w; returns sum dk^2 */
+} oracle_ops;
+
+/* the LSQR driver of oracle_lsqr with its steps taken from ops */
+int oracle_lsqr_core(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
+                     oracle_lsqr_info *info, const oracle_ops *ops);
+
+/* oracle_omp.c: the same LSQR with the steps split over `threads` threads (0: all); the threads the
+ * library was built to use (1 when it was built without OpenMP) */
+int oracle_lsqr_omp(const oracle_sys *s, const double *b, const oracle_lsqr_params *prm, double *x, double *var,
+                    oracle_lsqr_info *info, int32_t threads);
+int32_t oracle_omp_threads(void);
+void oracle_aprod1_omp(const oracle_sys *s, const double *x, double *y);
+void oracle_aprod2_omp(const oracle_sys *s, const double *y, double *x);
+
 #endif
