@@ -217,7 +217,13 @@ gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream)
  * GSR_MIXED) takes on the loaded rows. FP32-stored contexts only.
  *   passes     1: one pass over the row tiles also sums the attitude columns
  *              (block-private fixed point, one scale for all of them);
- *              2: a second pass over a knot-ordered copy sums them.
+ *              2: a second pass over a knot-ordered copy sums them (section
+ *              variants whose attitude columns do not fit the one-pass form);
+ *              3: one pass over the row tiles adds each row's attitude
+ *              products per axis as one 4-wide binary32 reduction into window
+ *              accumulators that stay in L2, then a pass over the attitude
+ *              columns folds the windows into x (binary64): the standard row
+ *              when the attitude columns do not fit the one-pass form.
  *   fx_bits    fewest fixed-point bits of an instrumental column's per-block
  *              sums (>= 20), or 0 when those sums are binary32.
  *   ins_group  1 when the instrumental columns share one scale (one-pass form
@@ -271,6 +277,17 @@ gsr_status gsr_residual(gsr_ctx *ctx, const double *x, float *r, void *stream);
  * FP32-stored contexts only; b must be loaded. Runs on stream.
  */
 gsr_status gsr_residual_static(gsr_ctx *ctx, const double *x, float *r, void *stream);
+
+/*
+ * gsr_fp64_fma_rate -- the binary64 fused multiply-add rate of `device`, in
+ * TFLOP/s (2 flops per FMA): the arithmetic ceiling of the binary64 aprods
+ * (Eq. 2 / Eq. 3 with binary64 values and products: 24 multiply-adds per row).
+ * Runs a probe kernel of independent FMA chains for a few tens of ms on the
+ * default stream; synchronous. (The paper has no counterpart; it measures the
+ * roofline the binary64 kernels are reported against.)
+ * Errors: GSR_EINVAL (null tflops), GSR_ECUDA.
+ */
+gsr_status gsr_fp64_fma_rate(int32_t device, double *tflops);
 
 typedef struct {
     int32_t itnlim;     /* maximum LSQR iterations (>= 0)                               */

@@ -36,6 +36,13 @@ namespace gsr {
 // what an aprod 2 pass accumulates per column: sum a y, sum a^2, or both (into a second vector)
 enum { A2_PROD = 0, A2_SQUARE = 1, A2_BOTH = 2 };
 
+// four binary32 additions at a 16-byte aligned global address in one reduction (no value returned)
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v)
 {
@@ -44,7 +51,7 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool SV = false>
+template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool SV = false, bool ATTW = false>
 __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
                                                 uint32_t *__restrict__ ymax)
@@ -118,9 +125,18 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
             }
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
-                const XT *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + kn[i];
+                if constexpr (ATTW) {
+                    // the axis's 4 consecutive unknowns in one 16-byte load of the window copy
+                    const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
+                    v = fma(a[A_ATT + NPARAXIS * ax + 0][i], (AT)w.x, v);
+                    v = fma(a[A_ATT + NPARAXIS * ax + 1][i], (AT)w.y, v);
+                    v = fma(a[A_ATT + NPARAXIS * ax + 2][i], (AT)w.z, v);
+                    v = fma(a[A_ATT + NPARAXIS * ax + 3][i], (AT)w.w, v);
+                } else {
+                    const XT *__restrict__ xk = xt + (int64_t)ax * S.n_dfa + kn[i];
 #pragma unroll
-                for (int j = 0; j < NPARAXIS; ++j) v = fma(a[A_ATT + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
+                    for (int j = 0; j < NPARAXIS; ++j) v = fma(a[A_ATT + NPARAXIS * ax + j][i], (AT)__ldg(xk + j), v);
+                }
             }
 #pragma unroll
             for (int j = 0; j < NINSTR; ++j) {
@@ -203,7 +219,7 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV,
-          bool ATT = false, bool UNI = false>
+          bool ATT = false, bool UNI = false, bool ATTRED = false>
 __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
                                                  double *__restrict__ z, double *__restrict__ z2,
                                                  const LsqrState *__restrict__ st, int64_t tiles_per_warp,
@@ -215,6 +231,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     const Sec<SV> G(S);
     static_assert(!FX || (INSTR_SMEM && sizeof(AT) == 4), "fixed point: binary32 products and squares");
     static_assert(!ATT || (FX && !SV), "attitude columns: fixed point, standard row");
+    static_assert(!ATTRED || (!ATT && !SV && sizeof(AT) == 4), "attitude reductions: binary32, standard row");
     __shared__ int s_bad;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
@@ -475,6 +492,29 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                     }
             }
         }
+        if constexpr (ATTRED) {
+            // the 12 attitude products of each row as three 16-byte reductions (one per axis) into the
+            // window accumulators, which stay in L2 (aw[a][k][q] collects column k + q of axis a from the
+            // rows starting at knot k; k_att_fold adds the windows into z)
+            int32_t knot[R];
+            load_ints<R>(tb + NPAR * Tile<VT>::VBLK, 0, knot);
+#pragma unroll
+            for (int ax = 0; ax < NAXES; ++ax) {
+                AT at[NPARAXIS][R];
+#pragma unroll
+                for (int j = 0; j < NPARAXIS; ++j) load_vals<VT, AT>(tb, A_ATT + NPARAXIS * ax + j, at[j]);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (!in[i]) continue;
+                    const int64_t wi = ((int64_t)ax * S.n_dfa + knot[i]) * 4;
+                    AT q[NPARAXIS];
+#pragma unroll
+                    for (int j = 0; j < NPARAXIS; ++j) q[j] = SQUARE ? at[j][i] * at[j][i] : at[j][i];
+                    red_add_v4(S.aw + wi, q[0] * yr[i], q[1] * yr[i], q[2] * yr[i], q[3] * yr[i]);
+                    if constexpr (BOTH) red_add_v4(S.aw2 + wi, q[0] * q[0], q[1] * q[1], q[2] * q[2], q[3] * q[3]);
+                }
+            }
+        }
     }
     if (t0 < t1) {
         flush_astro_run(acc, k, wbuf, z, G.na);
@@ -516,13 +556,59 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
 
 // The standard row's instance, and a section variant's (run-time geometry) with
 // its registers capped for two resident blocks per SM, as the standard one has.
-template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
+template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false,
+          bool ATTRED = false>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y, double *__restrict__ z,
                                                      double *__restrict__ z2, const LsqrState *__restrict__ st,
                                                      int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word,
                                                      int32_t fxs)
 {
-    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false>(S, y, z, z2, st, tiles_per_warp, fx_word, fxs);
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false, false, false, ATTRED>(S, y, z, z2, st,
+                                                                                        tiles_per_warp, fx_word, fxs);
+}
+
+// z[att] += the window accumulators of the attitude reductions: column k of axis a collects
+// aw[a][k - q][q] for q = 0..3 (the rows starting q knots before it), summed in binary64 in that fixed
+// order; each window entry is read once and cleared for the next aprod 2. After the star pass, which
+// also no longer needs the max |y| word: cleared here for the next aprod 2 (ymax_reset).
+template <int MODE, bool LSQR>
+__global__ void k_att_fold(SysView<float> S, double *__restrict__ z, double *__restrict__ z2,
+                           const LsqrState *__restrict__ st, uint32_t *__restrict__ ymax_reset)
+{
+    if (LSQR && st->done) return;
+    if (ymax_reset && blockIdx.x == 0 && threadIdx.x == 0) *ymax_reset = 0u;
+    const int64_t nat = (int64_t)NAXES * S.n_dfa;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nat; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = (int32_t)(c % S.n_dfa);
+        double s = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < NPARAXIS; ++q) {
+            const int32_t k0 = k - q;  // the window starting at knot k0 (rows start at knots 0..n_dfa-4)
+            if (k0 < 0 || k0 > S.n_dfa - NPARAXIS) continue;
+            const int64_t wi = (c - q) * 4 + q;
+            s += (double)S.aw[wi];
+            S.aw[wi] = 0.f;
+            if (MODE == A2_BOTH) {
+                s2 += (double)S.aw2[wi];
+                S.aw2[wi] = 0.f;
+            }
+        }
+        if (s != 0.0) z[S.att0 + c] += s;
+        if (MODE == A2_BOTH && s2 != 0.0) z2[S.att0 + c] += s2;
+    }
+}
+
+// the window copy of the binary32 attitude unknowns: xw[a n_dfa + k] = x[att0 + a n_dfa + k .. +3]
+// (zero past the axis's end)
+__global__ void k_att_window(const float *__restrict__ x, int64_t att0, int32_t n_dfa, float4 *__restrict__ xw)
+{
+    const int64_t nat = (int64_t)NAXES * n_dfa;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nat; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = (int32_t)(c % n_dfa);
+        const float *xa = x + att0 + c;
+        xw[c] = make_float4(xa[0], k + 1 < n_dfa ? xa[1] : 0.f, k + 2 < n_dfa ? xa[2] : 0.f,
+                            k + 3 < n_dfa ? xa[3] : 0.f);
+    }
 }
 
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false>
@@ -734,6 +820,21 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
         if (st) return pick(k_aprod1<VT, XT, UT, AT, true, true>);
         return pick(k_aprod1<VT, XT, UT, AT, false, true>);
     }
+    if constexpr (sizeof(XT) == 4 && sizeof(VT) == 4) {
+        if (att_window(c)) {
+            // wide attitude block: the window copy of x first (a few MB, stays in L2), then one 16-byte
+            // gather per axis and row
+            if (!grid_out) {
+                if (!x) return cudaErrorInvalidValue;
+                k_att_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(
+                    (const float *)x, S.att0, c->n_dfa, reinterpret_cast<float4 *>(c->xwin));
+                const cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+            if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, true>);
+            return pick(k_aprod1<VT, XT, UT, AT, false, false, true>);
+        }
+    }
     if (st) return pick(k_aprod1<VT, XT, UT, AT, true>);
     return pick(k_aprod1<VT, XT, UT, AT, false>);
 }
@@ -761,11 +862,12 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
     return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX, bool SV>
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX, bool SV, bool ATTRED = false>
 static cudaError_t aprod2_star_launch_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                         cudaStream_t s)
 {
-    auto kern = SV ? k_aprod2_star_sv<VT, UT, AT, INS, MODE, LS, FX> : k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX>;
+    auto kern = SV ? k_aprod2_star_sv<VT, UT, AT, INS, MODE, LS, FX>
+                   : k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX, ATTRED>;
     const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX ? 2 : 1)) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -818,6 +920,31 @@ __global__ void k_absmax(const float *__restrict__ y, int64_t n, uint32_t *__res
     if (threadIdx.x == 0) atomicMax(ymax, __float_as_uint(m));
 }
 
+// the binary32 aprod 2 of a wide attitude block (att_red): one star pass whose attitude products go to the
+// window accumulators by vector reductions, then the fold into z (which also clears max |y|)
+template <int MODE, bool LS>
+static cudaError_t aprod2_red_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    const bool fx = c->fx_bits > 0 && (MODE != A2_BOTH || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
+    if (fx) {
+        if (MODE != A2_SQUARE && !LS) {
+            k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows, fx_ymax(c));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        e = aprod2_star_launch_t<float, float, float, true, MODE, LS, true, false, true>(c, y, x, x2, st, s);
+    } else if (sizeof(float) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget) {
+        e = aprod2_star_launch_t<float, float, float, true, MODE, LS, false, false, true>(c, y, x, x2, st, s);
+    } else {
+        e = aprod2_star_launch_t<float, float, float, false, MODE, LS, false, false, true>(c, y, x, x2, st, s);
+    }
+    if (e != cudaSuccess) return e;
+    k_att_fold<MODE, LS><<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(
+        view<float>(c), x, x2, st, fx && MODE != A2_SQUARE ? fx_ymax(c) : nullptr);
+    return cudaGetLastError();
+}
+
 template <typename VT, typename UT, typename AT, int MODE, bool LS>
 static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                             cudaStream_t s)
@@ -828,6 +955,7 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     cudaError_t e = cudaSuccess;
     constexpr bool F32 = sizeof(AT) == 4;
     if constexpr (F32 && sizeof(VT) == 4) {
+        if (att_red(c)) return aprod2_red_t<MODE, LS>(c, y, x, x2, st, s);
         if (att_fused(c)) {
             // one pass: the star pass takes the attitude columns too (no attitude pass); max |y| comes
             // from the LSQR aprod 1 of the same iteration (the LSQR colA clears it for the next one),
@@ -858,7 +986,9 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
         e = aprod2_star_launch<VT, UT, AT, false, MODE, LS>(c, y, x, x2, st, s);
     }
     if (e != cudaSuccess) return e;
-    // attitude pass (resets the max |y| word after a fixed-point star pass)
+    // attitude pass (resets the max |y| word after a fixed-point star pass) over the knot-ordered copy,
+    // which the caller built (ensure_att_layout)
+    if (!c->atiles || !c->att_valid) return cudaErrorNotReady;
     auto kern = k_aprod2_att<VT, UT, AT, MODE, LS>;
     int64_t per = 0, blocks = 0;
     tile_ranges(c, kern, 0, &per, &blocks);

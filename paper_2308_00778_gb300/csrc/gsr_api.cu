@@ -428,8 +428,9 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
     }
     const size_t tbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * (size_t)tile_bytes;
     const size_t abytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * (size_t)atile_bytes;
+    // the knot-ordered attitude copy (atiles) is allocated when a binary64 aprod 2 first needs it (layout.cu)
+    (void)abytes;
     if ((e = cudaMalloc(&c->tiles, tbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&c->atiles, abytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->first_star, sizeof(int32_t) * first_star.size())) != cudaSuccess ||
         (e = cudaMalloc(&c->star_ptr, sizeof(int64_t) * (size_t)(n_stars + 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->b, sizeof(double) * (size_t)std::max<int64_t>(c->n_rows, 1))) != cudaSuccess ||
@@ -442,9 +443,15 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
         gsr_destroy(c);
         return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
     }
+    // the window copy of a wide binary32 attitude block (aprod 1 gathers one 16-byte window per axis)
+    if (value_precision == GSR_FP32 && !sv && (int64_t)NAXES * n_dfa > ATT_WINDOW_MIN_COLS &&
+        (e = cudaMalloc(&c->xwin, sizeof(float) * 4 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess) {
+        cudaGetLastError();
+        gsr_destroy(c);
+        return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
+    }
     // padding rows of the last tile hold zeros (zero coefficients contribute nothing)
     e = cudaMemset(c->tiles, 0, tbytes);
-    if (e == cudaSuccess) e = cudaMemset(c->atiles, 0, abytes);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->first_star, first_star.data(), sizeof(int32_t) * first_star.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -506,6 +513,8 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->errw);
     cudaFree(c->knot_ptr);
     cudaFree(c->fx_word);
+    cudaFree(c->attw);
+    cudaFree(c->xwin);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->pool) {
         cudaDeviceSynchronize();
@@ -662,7 +671,7 @@ GSR_API gsr_status gsr_aprod2_plan(gsr_ctx *c, void *stream, int32_t *passes, in
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream, false);
     if (rc != GSR_OK) return rc;
-    if (passes) *passes = att_fused(c) ? 1 : 2;
+    if (passes) *passes = att_fused(c) ? 1 : att_red(c) ? 3 : 2;
     if (fx_bits) *fx_bits = c->fx_bits;
     if (ins_group) *ins_group = att_fused(c) && c->fx_uni ? 1 : 0;
     return GSR_OK;

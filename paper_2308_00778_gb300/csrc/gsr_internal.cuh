@@ -54,6 +54,11 @@ struct SysView {
     int32_t na, ni;               // astrometric / instrumental coefficients per row
     int32_t npl;                  // value planes per tile record
     int32_t p_att, p_ins, p_glob; // plane of the first attitude / instrumental / global coefficient
+    // wide attitude blocks of binary32 storage (att_red / att_window below): the window accumulators
+    // aw[(a n_dfa + k) 4 + q] (squares: aw2) of the column k + q of axis a from the rows starting at
+    // knot k, and the window copy xw[a n_dfa + k] = x_att[a][k .. k+3] of the vector aprod 1 gathers
+    float *aw, *aw2;
+    const float4 *xw;
 };
 
 // LSQR scalars shared between the kernels of one solve (one instance in device
@@ -153,6 +158,11 @@ struct gsr_ctx {
     bool fx_att = false;
     bool fx_uni = false;             // the one-pass aprod 2 gives the instrumental columns one scale too
     bool fx_valid = false;           // the statistics match the loaded rows
+    // wide attitude blocks (binary32 storage, standard row): attw holds the window accumulators of the
+    // binary32 aprod 2 (2 x 3 n_dfa x 4 binary32: products, then squares; zero between uses), xwin the
+    // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)
+    float *attw = nullptr;
+    float *xwin = nullptr;
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -203,6 +213,9 @@ SysView<VT> view(const gsr_ctx *c)
     s.p_att = c->sv ? c->n_astro : A_ATT;
     s.p_ins = s.p_att + NAXES * NPARAXIS;
     s.p_glob = c->sv ? s.p_ins + c->n_ipr : A_GLOB;
+    s.aw = c->attw;
+    s.aw2 = c->attw ? c->attw + (size_t)NAXES * c->n_dfa * 4 : nullptr;
+    s.xw = reinterpret_cast<const float4 *>(c->xwin);
     return s;
 }
 
@@ -222,6 +235,17 @@ int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64);
 // the binary32 aprod 2 adds the attitude products in its star pass (no attitude pass)
 inline bool att_fused(const gsr_ctx *c) { return c->prec == GSR_FP32 && c->fx_bits > 0 && c->fx_att && !c->sv; }
+// the binary32 aprod 2 adds each row's attitude products with vector reductions into the window
+// accumulators (the attitude columns do not fit the one-pass form's shared memory)
+inline bool att_red(const gsr_ctx *c)
+{
+    return c->prec == GSR_FP32 && !c->sv && c->fx_valid && !att_fused(c) && c->attw;
+}
+// the binary32 aprod 1 gathers the attitude unknowns through the window copy (one 16-byte load per axis)
+inline bool att_window(const gsr_ctx *c) { return c->prec == GSR_FP32 && !c->sv && c->xwin; }
+// attitude columns above which the binary32 aprod 1 uses the window copy: beyond ~16K binary32 values
+// the gathered attitude vector no longer stays in L1 beside the streamed tiles
+constexpr int64_t ATT_WINDOW_MIN_COLS = 16384;
 // max |y| word of the fixed-point sums (nullptr when they are off)
 inline uint32_t *fx_ymax(const gsr_ctx *c) { return c->fx_bits > 0 ? c->fx_word + 2 * (size_t)c->fx_nc : nullptr; }
 

@@ -320,6 +320,16 @@ static gsr_status build_att_copy(gsr_ctx *c, cudaStream_t s)
     int32_t *keys_in = nullptr, *keys_out = nullptr, *vals_in = nullptr, *perm = nullptr;
     void *tmp = nullptr, *rec = nullptr;
     size_t tmp_bytes = 0;
+    if (!c->atiles) {  // first use: the copy's tiles, zero in the padding positions of the last tile
+        const size_t abytes = (size_t)std::max<int64_t>(c->n_tiles, 1) *
+                              (size_t)(c->prec == GSR_FP32 ? Tile<float>::ABYTES : Tile<double>::ABYTES);
+        if ((e = cudaMalloc(&c->atiles, abytes)) != cudaSuccess ||
+            (e = cudaMemsetAsync(c->atiles, 0, abytes, s)) != cudaSuccess) {
+            if (c->atiles) cudaFree(c->atiles);
+            c->atiles = nullptr;
+            return cuda_fail(c, e, "attitude layout");
+        }
+    }
     const int bits = 32 - __builtin_clz((unsigned)(nk > 1 ? nk : 1));
     const bool f32 = c->prec == GSR_FP32;
     const uint8_t *tiles = (const uint8_t *)c->tiles;
@@ -397,7 +407,20 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64)
             c->fx_sig = sig;
         }
     }
-    if ((binary64 || !att_fused(c)) && !c->att_valid) {
+    // a wide attitude block of binary32 storage: the window accumulators of the vector reductions
+    if (c->prec == GSR_FP32 && !c->sv && !att_fused(c) && !c->attw) {
+        const size_t bytes = sizeof(float) * 2 * 4 * (size_t)NAXES * (size_t)c->n_dfa;
+        cudaError_t e = cudaMalloc(&c->attw, bytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->attw, 0, bytes, s);
+        if (e != cudaSuccess) {
+            if (c->attw) cudaFree(c->attw);
+            c->attw = nullptr;
+            return cuda_fail(c, e, "attitude window accumulators");
+        }
+    }
+    // the knot-ordered copy: for binary64 aprod 2 passes, and binary32 section variants whose
+    // attitude columns do not fit the one-pass form
+    if ((binary64 || (!att_fused(c) && !att_red(c))) && !c->att_valid) {
         const gsr_status rc = build_att_copy(c, s);
         if (rc != GSR_OK) return rc;
         c->att_valid = true;

@@ -53,6 +53,27 @@ def set_rhs_from_truth(ctx, cfg, device, stream=0):
     return b, xt
 
 
+def host_copies(cfg, vals, knot, ins, b, sp, chunk_rows: int = 1 << 25):
+    """Pinned host copies of a generated system in the paper's row storage (A_d row-major, the
+    instrumental columns row-major), transposed from the device planes chunk by chunk (so that no
+    full-size transposed copy is made on the device)."""
+    n = knot.numel()
+    A = torch.empty((n, cfg.npar), dtype=vals.dtype, pin_memory=True)
+    I = torch.empty((n, cfg.n_ipr), dtype=torch.int32, pin_memory=True)
+    V = vals.view(cfg.npar, n)
+    Iv = ins[:cfg.n_ipr * n].view(cfg.n_ipr, n)
+    for r0 in range(0, n, chunk_rows):
+        r1 = min(n, r0 + chunk_rows)
+        A[r0:r1].copy_(V[:, r0:r1].t().contiguous())
+        if cfg.n_ipr:
+            I[r0:r1].copy_(Iv[:, r0:r1].t().contiguous())
+    kh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    kh.copy_(knot)
+    bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b)
+    return {"A": A, "knot": kh, "instr": I, "b": bh, "star_ptr": sp}
+
+
 def device_system(cfg, fp32_store: bool, round32: bool, device, stream=0, keep_host=False, ctx=None):
     """Build (or reload into ctx) the system of cfg. Returns (ctx, b, host copies or None)."""
     if ctx is None:
@@ -60,13 +81,7 @@ def device_system(cfg, fp32_store: bool, round32: bool, device, stream=0, keep_h
     vals, knot, ins, sp = load_rows(ctx, cfg, round32, device, stream)
     b, _ = set_rhs_from_truth(ctx, cfg, device, stream)
     torch.cuda.synchronize(device)
-    host = None
-    if keep_host:
-        n = ctx.n_rows
-        host = {"A": vals.view(cfg.npar, n).t().contiguous().cpu().pin_memory(),
-                "knot": knot.cpu().pin_memory(),
-                "instr": ins[:cfg.n_ipr * n].view(cfg.n_ipr, n).t().contiguous().cpu().pin_memory(),
-                "b": b.cpu().pin_memory(), "star_ptr": sp}
+    host = host_copies(cfg, vals, knot, ins, b, sp) if keep_host else None
     del vals, ins, knot
     torch.cuda.empty_cache()  # the staging planes: give them back for the library's own allocations
     return ctx, b, host

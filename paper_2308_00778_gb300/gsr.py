@@ -104,6 +104,7 @@ def lib():
             "gsr_residual": (I32, [P, P, P, P]),
             "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
+            "gsr_fp64_fma_rate": (I32, [I32, P]),
             "gsr_net_num_params": (I64, []),
             "gsr_net_create": (I32, [ctypes.POINTER(P), I32]),
             "gsr_net_destroy": (I32, [P]),
@@ -294,6 +295,19 @@ def gsr_warm_features(ctx, feats, scale_ptr, stream=0):
 
 def gsr_warm_start(ctx, net, x0, stream=0):
     return lib().gsr_warm_start(ctx, net or None, x0 or None, stream or None)
+
+
+def gsr_fp64_fma_rate(device, tflops_ptr):
+    return lib().gsr_fp64_fma_rate(device, tflops_ptr or None)
+
+
+def dfma_probe_tflops(device=0) -> float:
+    """The device's binary64 FMA rate in TFLOP/s (the ceiling of the binary64 aprods)."""
+    v = ctypes.c_double()
+    st = gsr_fp64_fma_rate(device, ctypes.addressof(v))
+    if st != 0:
+        raise GsrError(st, "gsr_fp64_fma_rate failed")
+    return v.value
 
 
 # ---------------------------------------------------------------- convenience wrapper

@@ -1,6 +1,7 @@
 """bench.py's JSON line on a small workload (c1: 1e5 rows): the keys of the contract, the
-reference arm on the host (the oracle), and the GPU arm in its default and sequential
-forms (every solver within 1e-9 per block of the binary64 reference)."""
+reference arm on the host (the oracle), and the GPU arm with both contexts resident and in
+the sequential form (every solver within 1e-9 per block of the binary64 reference, with
+every Eq. 5 ratio below 0.1)."""
 import json
 import os
 import subprocess
@@ -28,6 +29,7 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["unit"] == "s" and line["higher_is_better"] is False
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["config"]["sample_rows"] == 100_000 and line["config"]["iterations"] > 0
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["workload"].startswith("c1:")
 
@@ -37,9 +39,10 @@ def _check_gpu_line(line):
     assert {"roofline", "clocks", "gpu_launches", "solvers", "kernels"} <= set(line)
     assert line["unit"] == "s" and line["higher_is_better"] is False and line["scaling"] == "weak"
     assert line["value"] > 0 and line["gpu_launches"] > 0
-    assert set(line["solvers"]) >= {"fp64_plain", "mixed"}
+    assert set(line["solvers"]) >= {"fp64_plain", "fp64_jacobi", "mixed", "mixed_jacobi"}
     for name, leg in line["solvers"].items():
         assert leg["final_block_err"] <= 1e-9, (name, leg)
+        assert max(leg["eq5_q_max"].values()) <= 0.1, (name, leg)
     best = min(leg["s"] for leg in line["solvers"].values())
     assert abs(line["value"] - best) <= 1e-12 * best
     roof = line["roofline"]
@@ -51,13 +54,20 @@ def _check_gpu_line(line):
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    line = _run("--workload", "c1", "--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--no-sections")
+    line = _run("--workload", "c1", "--also", "", "--sequential", "no", "--steps", "1", "--warmup", "3",
+                "--no-cpu-baseline", "--no-sections")
     _check_gpu_line(line)
     assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["value"] > 0
+    assert line["cpu_baseline"] is None and "c2" not in line
 
 
 @pytest.mark.gpu
 def test_gpu_arm_sequential_line():
-    line = _run("--workload", "c1", "--sequential", "--steps", "1", "--warmup", "3")
+    line = _run("--workload", "c1", "--also", "", "--sequential", "yes", "--steps", "1", "--warmup", "3",
+                "--no-sections")
     _check_gpu_line(line)
-    assert line["e2e"] is None and line["cpu_baseline"] is None and line["sections"] is None
+    assert line["config"]["contexts"].startswith("binary64 legs first")
+    assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["value"] > 0
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
+    assert cpu["single_thread"]["cores"] == 1 and cpu["single_thread"]["value"] > 0

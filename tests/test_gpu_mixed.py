@@ -177,8 +177,8 @@ def test_binary32_instrumental_sums_are_order_independent():
 def test_reload_that_changes_the_one_pass_choice():
     """The binary32 aprod 2 runs in one pass when every attitude column gets at least 20 fixed-point
     bits over the pass's partition. A reload whose rows all start at knot 0 (every row on the same
-    4 columns per axis) leaves too few, so the context falls back to the two passes and drops the
-    iteration graphs it captured for the one-pass kernel. Mixed solves before and after the reload,
+    4 columns per axis) leaves too few, so the context switches to the attitude reductions into L2
+    windows and drops the iteration graphs it captured for the one-pass kernel. Mixed solves before and after the reload,
     and after reloading the first system again, match the oracle."""
     w = gsrgen.workloads()["c1"]
     h, s, b, ctx = _setup32(w.cfg)
@@ -202,7 +202,8 @@ def test_spread_coefficients_keep_per_column_precision(spread):
     smallest column max |a|) must stay >= 20. Here the odd instrumental columns (and, in the second
     case, the third attitude axis) have coefficients 2^-4 times the others (4 bits of spread against
     about 21 bits on this system): the instrumental sums keep their per-column scales in the
-    one-pass aprod 2 (first case), the attitude columns take the two passes (second case).
+    one-pass aprod 2 (first case), the attitude columns go to the vector reductions into L2 windows
+    (form 3, second case).
     aprod2_f32 keeps its bounds (binary32 sums 2e3 u, the instrumental fixed point 2^-20 of each
     column's own bound) and the mixed solve matches the oracle. (The mixed solver's accuracy on
     columns of small norm is limited by the binary32 rounding of the refinement's right-hand side,
@@ -222,7 +223,7 @@ def test_spread_coefficients_keep_per_column_precision(spread):
     ctx.set_system(A32, h.knot, h.instr, b)
     plan = ctx.aprod2_plan()
     assert plan["fx_bits"] >= 20 and plan["ins_group"] == 0
-    assert plan["passes"] == (1 if spread == "instr" else 2)
+    assert plan["passes"] == (1 if spread == "instr" else 3)
     u = 2.0 ** -24
     rng = np.random.default_rng(17)
     y = rng.standard_normal(s.n_rows).astype(np.float32)

@@ -21,9 +21,11 @@ def _setup(cfg, fp32):
     return h, s, b, ctx
 
 
-@pytest.mark.parametrize("fp32", [False, True])
-def test_features_vs_oracle(fp32):
-    cfg = gsrgen.make_cfg(81, 2000, (50, 150), 400, 60, att_kind=1)
+@pytest.mark.parametrize("fp32,wide", [(False, False), (True, False), (True, True)])
+def test_features_vs_oracle(fp32, wide):
+    # wide: 24,000 attitude columns, past the one-pass shared-memory form: the binary32 pass that sums
+    # A^T b and the column norms adds the attitude products by vector reductions into L2 windows
+    cfg = gsrgen.make_cfg(81, 2000, (50, 150), 8000 if wide else 400, 60, att_kind=1)
     h, s, b, ctx = _setup(cfg, fp32)
     f = torch.zeros((cfg.n_dfa, 6), dtype=torch.float32, device="cuda")
     scale = ctx.warm_features(f)
