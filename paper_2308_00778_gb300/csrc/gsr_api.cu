@@ -445,7 +445,8 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
     }
     // the window copy of a wide binary32 attitude block (aprod 1 gathers one 16-byte window per axis)
     if (value_precision == GSR_FP32 && !sv && (int64_t)NAXES * n_dfa > ATT_WINDOW_MIN_COLS &&
-        (e = cudaMalloc(&c->xwin, sizeof(float) * 4 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess) {
+        ((e = cudaMalloc(&c->xwin, sizeof(float) * 4 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess ||
+         (e = cudaMalloc(&c->xhlwin, sizeof(float4) * 2 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess)) {
         cudaGetLastError();
         gsr_destroy(c);
         return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
@@ -515,6 +516,7 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->fx_word);
     cudaFree(c->attw);
     cudaFree(c->xwin);
+    cudaFree(c->xhlwin);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->pool) {
         cudaDeviceSynchronize();

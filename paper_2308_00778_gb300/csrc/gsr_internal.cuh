@@ -59,6 +59,7 @@ struct SysView {
     // knot k, and the window copy xw[a n_dfa + k] = x_att[a][k .. k+3] of the vector aprod 1 gathers
     float *aw, *aw2;
     const float4 *xw;
+    const float4 *xw2;  // the double-float residual's window: x_att[a][k .. k+3] as (hi, lo) pairs, 2 float4
 };
 
 // LSQR scalars shared between the kernels of one solve (one instance in device
@@ -163,6 +164,7 @@ struct gsr_ctx {
     // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)
     float *attw = nullptr;
     float *xwin = nullptr;
+    float4 *xhlwin = nullptr;  // the double-float residual's window copy (3 n_dfa x 2 float4), with xwin
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -216,6 +218,7 @@ SysView<VT> view(const gsr_ctx *c)
     s.aw = c->attw;
     s.aw2 = c->attw ? c->attw + (size_t)NAXES * c->n_dfa * 4 : nullptr;
     s.xw = reinterpret_cast<const float4 *>(c->xwin);
+    s.xw2 = c->xhlwin;
     return s;
 }
 
@@ -283,9 +286,13 @@ void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_c
 gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, int *r0_parts);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
+// window: the attitude gathers read the context's window copy (split_launch with window built it);
+// without, only xhl is read (the allocation-free entry point's path)
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
-                            double *part, cudaStream_t s, int *grid_out);
-cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s);
+                            double *part, cudaStream_t s, int *grid_out, bool window = false);
+// x -> (hi, lo) pairs into out; window (wide attitude blocks, att_window): also the window copy
+cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s,
+                         bool window = false);
 // r0_parts > 0: ws.u32 / ws.part_u already hold the residual of x0 (from the warm start) for the
 // first refinement step
 gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0, bool x0_dev, double *x_out,

@@ -36,7 +36,24 @@ __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ out, 
 // b is read in binary64 and split here (the same 8 bytes per row as a pre-split
 // copy, without the pass that would make it); `part` (may be null) receives
 // per-block sums of squares of r.
-template <bool SV = false>
+// the window copy of the attitude unknowns as (hi, lo) pairs: xw2[2 c], xw2[2 c + 1] = the pairs of
+// x[att0 + c .. c + 3] (zero past the axis's end), c = a n_dfa + k
+__global__ void k_split_window(const double *__restrict__ x, int64_t att0, int32_t n_dfa, float4 *__restrict__ xw2)
+{
+    const int64_t nat = (int64_t)NAXES * n_dfa;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nat; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = (int32_t)(c % n_dfa);
+        float2 v[NPARAXIS];
+#pragma unroll
+        for (int q = 0; q < NPARAXIS; ++q) v[q] = k + q < n_dfa ? split_double(x[att0 + c + q]) : make_float2(0.f, 0.f);
+        xw2[2 * c] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        xw2[2 * c + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    }
+}
+
+// ATTW: the attitude pairs come from the window copy (two 16-byte loads per axis and row instead of
+// four 8-byte gathers); the terms and their order are the same, so the result is bitwise the same.
+template <bool SV = false, bool ATTW = false>
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
                                                   const double *__restrict__ b64, float *__restrict__ r_out,
                                                   double *__restrict__ part)
@@ -105,12 +122,25 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
                 }
             }
 #pragma unroll
-        for (int ax = 0; ax < NAXES; ++ax)
+        for (int ax = 0; ax < NAXES; ++ax) {
+            if constexpr (ATTW) {
 #pragma unroll
-            for (int j = 0; j < NPARAXIS; ++j)
+                for (int i = 0; i < R; ++i) {
+                    const float4 *w = S.xw2 + 2 * ((int64_t)ax * S.n_dfa + kn[i]);
+                    const float4 p = __ldg(w), q = __ldg(w + 1);
+                    acc_term(a[A_ATT + NPARAXIS * ax + 0][i], make_float2(p.x, p.y), sh[i], c[i]);
+                    acc_term(a[A_ATT + NPARAXIS * ax + 1][i], make_float2(p.z, p.w), sh[i], c[i]);
+                    acc_term(a[A_ATT + NPARAXIS * ax + 2][i], make_float2(q.x, q.y), sh[i], c[i]);
+                    acc_term(a[A_ATT + NPARAXIS * ax + 3][i], make_float2(q.z, q.w), sh[i], c[i]);
+                }
+            } else {
 #pragma unroll
-                for (int i = 0; i < R; ++i)
-                    acc_term(a[A_ATT + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
+                for (int j = 0; j < NPARAXIS; ++j)
+#pragma unroll
+                    for (int i = 0; i < R; ++i)
+                        acc_term(a[A_ATT + NPARAXIS * ax + j][i], xt[(int64_t)ax * S.n_dfa + kn[i] + j], sh[i], c[i]);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < NINSTR; ++j)
 #pragma unroll
@@ -213,10 +243,10 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 
 // Launch (or, with grid_out, only size) the residual kernel. Allocates nothing.
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
-                            double *part, cudaStream_t s, int *grid_out)
+                            double *part, cudaStream_t s, int *grid_out, bool window)
 {
-    // a section variant runs the run-time-geometry instance
-    auto kern = c->sv ? k_residual<true> : k_residual<false>;
+    // a section variant runs the run-time-geometry instance; a wide attitude block the window instance
+    auto kern = c->sv ? k_residual<true> : (window && att_window(c) ? k_residual<false, true> : k_residual<false>);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -242,10 +272,13 @@ cudaError_t residual_kernels_load(bool sv)
     return e;
 }
 
-cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s)
+cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s, bool window)
 {
     if (n <= 0) return cudaSuccess;
     k_split<<<col_grid(c, n), kThreads, 0, s>>>(x, out, n);
+    if (window && att_window(c))
+        k_split_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(
+            x, (int64_t)c->n_astro * c->n_stars, c->n_dfa, c->xhlwin);
     return cudaGetLastError();
 }
 
@@ -255,8 +288,8 @@ gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s)
     if (rc != GSR_OK) return rc;
     if (c->n_rows == 0) return GSR_OK;
     Workspace &ws = c->ws;
-    k_split<<<col_grid(c, c->n_cols), kThreads, 0, s>>>(x, ws.xhl, c->n_cols);
-    const cudaError_t e = residual_launch(c, ws.xhl, c->b, r, ws.part_u, s, nullptr);
+    cudaError_t e = split_launch(c, x, ws.xhl, c->n_cols, s, true);
+    if (e == cudaSuccess) e = residual_launch(c, ws.xhl, c->b, r, ws.part_u, s, nullptr, true);
     if (e != cudaSuccess) return cuda_fail(c, e, "residual");
     return GSR_OK;
 }
@@ -269,7 +302,6 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     if (rc != GSR_OK) return rc;
     Workspace &ws = c->ws;
     const int64_t nc = c->n_cols, nr = c->n_rows;
-    const int gcol = col_grid(c, nc);
     // k_correct: four columns per thread and round, two blocks per SM
     const int gcor = (int)std::min<int64_t>(std::max<int64_t>((nc + 4 * kThreads - 1) / (4 * kThreads), 1),
                                             2 * (int64_t)c->sm_count);
@@ -296,7 +328,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
     const double refine_tol = prm->refine_tol != 0.0 ? prm->refine_tol : 1e-10;
     int gres = 1;
-    residual_launch(c, nullptr, nullptr, nullptr, nullptr, s, &gres);
+    residual_launch(c, nullptr, nullptr, nullptr, nullptr, s, &gres, true);  // the grid of the launches below
     const int64_t att0 = (int64_t)c->n_astro * c->n_stars, instr0 = att0 + (int64_t)NAXES * c->n_dfa,
                   glob0 = instr0 + c->n_instr;
 
@@ -311,9 +343,9 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
         } else if (outer == 0 && !x0) {
             if (nr > 0) k_rhs32<<<gres, kThreads, 0, s>>>(c->b, ws.u32, ws.part_u, nr);
         } else {
-            k_split<<<gcol, kThreads, 0, s>>>(ws.xo, ws.xhl, nc);
+            if ((e = split_launch(c, ws.xo, ws.xhl, nc, s, true)) != cudaSuccess) return cuda_fail(c, e, "split");
             if (nr > 0 &&
-                (e = residual_launch(c, ws.xhl, c->b, ws.u32, ws.part_u, s, nullptr)) != cudaSuccess)
+                (e = residual_launch(c, ws.xhl, c->b, ws.u32, ws.part_u, s, nullptr, true)) != cudaSuccess)
                 return cuda_fail(c, e, "residual");
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
