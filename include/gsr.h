@@ -309,6 +309,15 @@ typedef struct {
     int32_t inner_itn_next; /* MIXED: inner iteration limit of the refinement steps after
                                the first (0 = inner_itn); the first step solves for the whole
                                error of x0, the later ones only for its binary32 residue     */
+    int32_t refine_grad;    /* MIXED: the start of each inner solve after the first,
+                               alpha_1 v_1 = A~^T r / |r|: 0 = binary32 until the refinement
+                               stalls (a step's largest block |dx|/|x| above half the previous
+                               step's), binary64 from then on; 1 = binary64 from the second
+                               step on; -1 = always binary32. The binary64 gradient of the
+                               double-float residual r keeps the solution within the inner
+                               solve's relative accuracy of the least-squares solution when
+                               the column norms spread widely (the binary32 rounding of r
+                               otherwise limits column j to about 2^-24 |r| / |A_:,j|)     */
 } gsr_solve_params;
 
 typedef struct {

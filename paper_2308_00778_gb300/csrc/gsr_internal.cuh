@@ -275,10 +275,11 @@ gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false, 
                         double *z = nullptr);
 LsqrState initial_state(const gsr_solve_params *prm);
 // defer_fin: leave the final state's download (into ws.fin_h) pending on s, for a caller that
-// synchronises s itself after more work; *fin is then not written
+// synchronises s itself after more work; *fin is then not written. start64 (inner32 only): the
+// start's aprod 2 reads the binary64 right-hand side in ws.u with binary64 products and sums
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
-                    bool defer_fin = false);
+                    bool defer_fin = false, bool start64 = false);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
 // warm start (warm.cu)
 // r0_parts (may be null): for binary32 storage the residual of x0 is also left in ws.u32, in
@@ -288,8 +289,10 @@ gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, 
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
 // window: the attitude gathers read the context's window copy (split_launch with window built it);
 // without, only xhl is read (the allocation-free entry point's path)
+// r64 (may be null): the double-float residual also in binary64 (before its rounding to binary32)
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
-                            double *part, cudaStream_t s, int *grid_out, bool window = false);
+                            double *part, cudaStream_t s, int *grid_out, bool window = false,
+                            double *r64 = nullptr);
 // x -> (hi, lo) pairs into out; window (wide attitude blocks, att_window): also the window copy
 cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t n, cudaStream_t s,
                          bool window = false);

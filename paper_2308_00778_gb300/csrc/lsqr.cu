@@ -549,6 +549,7 @@ void default_params(gsr_solve_params *p)
     p->refine_tol = 0.0;
     p->max_outer = 0;
     p->inner_itn_next = 0;
+    p->refine_grad = 0;
 }
 
 // p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in
@@ -576,7 +577,7 @@ gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32, const vo
 // the scaled solution in ws.x and the final scalars in *fin.
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
-                    bool defer_fin)
+                    bool defer_fin, bool start64)
 {
     using clk = std::chrono::steady_clock;
     Workspace &ws = c->ws;
@@ -586,8 +587,11 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     cudaError_t e;
     if ((e = cudaMemcpyAsync(ws.st, &init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(c, e, "state upload");
-    void *u = inner32 ? (void *)ws.u32 : (void *)ws.u;
-    if ((e = launch_aprod2(c, u, ws.z, false, nullptr, s, inner32)) != cudaSuccess) return cuda_fail(c, e, "start");
+    // start64: the start's A^T u reads the binary64 copy of the right-hand side (ws.u) with binary64
+    // products and sums, the iterations the binary32 one (inner32)
+    void *u = inner32 && !start64 ? (void *)ws.u32 : (void *)ws.u;
+    if ((e = launch_aprod2(c, u, ws.z, false, nullptr, s, inner32 && !start64)) != cudaSuccess)
+        return cuda_fail(c, e, "start");
     k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, n_part_u, ws.z, ws.p, ws.v, ws.w, nc, ws.st, ws.part_v, ws.part_w, 1,
                                       ws.counter, ws.flag_d, nullptr);
     k_scalar_init<<<1, 32, 0, s>>>(ws.st, ws.part_v, gc, ws.flag_d);

@@ -56,7 +56,7 @@ __global__ void k_split_window(const double *__restrict__ x, int64_t att0, int32
 template <bool SV = false, bool ATTW = false>
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
                                                   const double *__restrict__ b64, float *__restrict__ r_out,
-                                                  double *__restrict__ part)
+                                                  double *__restrict__ part, double *__restrict__ r64)
 {
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
                 const float lo = __fadd_rn(__fadd_rn(e, bb.y), -c[i]);
                 const float rv = __fadd_rn(tt, lo);
                 r_out[r] = rv;
+                if (r64) r64[r] = (double)tt + (double)lo;  // exact in binary64
                 ssq = fmaf(rv, rv, ssq);
             }
         }
@@ -243,7 +244,7 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 
 // Launch (or, with grid_out, only size) the residual kernel. Allocates nothing.
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
-                            double *part, cudaStream_t s, int *grid_out, bool window)
+                            double *part, cudaStream_t s, int *grid_out, bool window, double *r64)
 {
     // a section variant runs the run-time-geometry instance; a wide attitude block the window instance
     auto kern = c->sv ? k_residual<true> : (window && att_window(c) ? k_residual<false, true> : k_residual<false>);
@@ -258,7 +259,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b
         *grid_out = (int)blocks;
         return cudaSuccess;
     }
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part);
+    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part, r64);
     return cudaGetLastError();
 }
 
@@ -335,24 +336,32 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     LsqrState fin = LsqrState();
     int total_itn = 0, outer = 0;
     gsr_status status = GSR_OK;
+    // the binary64 gradient of the inner solves' start (refine_grad): once on, every later step's
+    // residual is also kept in binary64 (ws.u) and A~^T r is summed in binary64 from it
+    bool grad64 = false;
+    double prev_ratio = -1.0;
     for (; outer < max_outer; ++outer) {
         init.itnlim = outer == 0 ? itn_first : itn_next;
         int n_part = gres;
+        const bool start64 = outer > 0 && (grad64 || prm->refine_grad > 0);
+        if (start64 && !c->att_valid) {  // the binary64 aprod 2 of binary32 storage: knot-ordered copy
+            if ((rc = ensure_att_layout(c, s, true)) != GSR_OK) return rc;
+        }
         if (outer == 0 && r0_parts > 0) {
             n_part = r0_parts;  // the warm start left the residual of x0 (binary32) in ws.u32
         } else if (outer == 0 && !x0) {
             if (nr > 0) k_rhs32<<<gres, kThreads, 0, s>>>(c->b, ws.u32, ws.part_u, nr);
         } else {
             if ((e = split_launch(c, ws.xo, ws.xhl, nc, s, true)) != cudaSuccess) return cuda_fail(c, e, "split");
-            if (nr > 0 &&
-                (e = residual_launch(c, ws.xhl, c->b, ws.u32, ws.part_u, s, nullptr, true)) != cudaSuccess)
+            if (nr > 0 && (e = residual_launch(c, ws.xhl, c->b, ws.u32, ws.part_u, s, nullptr, true,
+                                               start64 ? ws.u : nullptr)) != cudaSuccess)
                 return cuda_fail(c, e, "residual");
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "residual");
         // one host synchronisation per refinement step: the inner solve's final state and the
         // correction's norms come back together
         status = run_lsqr(c, init, true, false, nr > 0 ? n_part : 0, prm->graph_k, prm->timeout_s, t0, s, &fin,
-                          true);
+                          true, start64);
         if (status != GSR_OK && status != GSR_ETIMEOUT) return status;
         if ((e = cudaMemsetAsync(ws.blk, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
         k_correct<<<gcor, kThreads, 0, s>>>(ws.xo, ws.p, ws.x, nc, att0, instr0, glob0, ws.blk);
@@ -375,10 +384,17 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
             break;
         }
         bool converged = refine_tol > 0.0;
+        double ratio = 0.0;  // the largest block |dx| / |x| of this step
         for (int q = 0; q < 4; ++q) {
             const double dn = std::sqrt(hb[q]), xn = std::sqrt(hb[4 + q]);
             if (dn > refine_tol * xn) converged = false;
+            if (xn > 0.0) ratio = std::max(ratio, dn / xn);
         }
+        // refine_grad 0: a step that did not halve the largest block correction of the one before has
+        // met the binary32 rounding of the residual; the binary64 gradient takes over
+        if (prm->refine_grad == 0 && !grad64 && outer >= 1 && prev_ratio > 0.0 && ratio > 0.5 * prev_ratio)
+            grad64 = true;
+        prev_ratio = ratio;
         if (converged) {
             ++outer;
             break;

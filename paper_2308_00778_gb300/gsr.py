@@ -53,6 +53,7 @@ class SolveParams(ctypes.Structure):
         ("refine_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
         ("inner_itn_next", ctypes.c_int32),
+        ("refine_grad", ctypes.c_int32),
     ]
 
 

@@ -14,6 +14,13 @@ of a tightly converged reference, from x0 = 0, from the Jacobi start and from
 the learned start.
 
     python -m paper_2308_00778_gb300.train --out paper_2308_00778_gb300/weights/warmstart.bin
+
+The shipped network can also be evaluated, without training, on held-out systems of another
+shape, e.g. the combined-at-scale configuration's (60,000 knots per axis, 20,000 instrumental
+unknowns, 250 observations per star) with fewer stars:
+
+    python -m paper_2308_00778_gb300.train --evaluate-only --shape 80000,250,60000,20000 \
+        --eval-seeds 500:505 --eval-out paper_2308_00778_gb300/weights/eval_60000_knots.json
 """
 from __future__ import annotations
 
@@ -194,12 +201,31 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--evaluate-only", action="store_true",
+                    help="evaluate the weights at --out on the held-out seeds, without training")
+    ap.add_argument("--shape", default=None,
+                    help="n_stars,obs,n_dfa,n_instr of the evaluation systems (default: the training shape)")
+    ap.add_argument("--eval-out", default=None, help="--evaluate-only: where to write the record (JSON)")
     args = ap.parse_args()
     a, b = map(int, args.train_seeds.split(":"))
     ea, eb = map(int, args.eval_seeds.split(":"))
     log = lambda m: print(m, flush=True)  # noqa: E731
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.evaluate_only:
+        shape = SHAPE
+        if args.shape:
+            ns, ob, nd, ni = map(int, args.shape.split(","))
+            shape = dict(n_stars=ns, obs=ob, n_dfa=nd, n_instr=ni)
+        rows = evaluate(args.out, range(ea, eb), shape=shape, device=dev, log=log)
+        rec = {"weights": os.path.relpath(args.out, os.path.dirname(os.path.dirname(os.path.abspath(__file__)))),
+               "shape": shape, "fp32_storage": True, "eval_seeds": [ea, eb], "tolerance": TOL, "evaluation": rows,
+               "mean_iterations": {k: float(np.mean([r[k] for r in rows])) for k in ("cold", "jacobi", "learned")}}
+        if args.eval_out:
+            with open(args.eval_out, "w") as f:
+                json.dump(rec, f, indent=1)
+        log(json.dumps(rec["mean_iterations"]))
+        return
     t0 = time.time()
     log(f"training examples: seeds {a}..{b - 1}")
     X, Y = make_dataset(range(a, b), device=dev, log=log)

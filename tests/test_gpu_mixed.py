@@ -245,3 +245,39 @@ def test_spread_coefficients_keep_per_column_precision(spread):
     errs = block_errors(x, xo, s)
     assert max(errs.values()) <= 1e-9, (errs, info)
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["odd_instr_2^-12", "glob_2^-10"])
+def test_mixed_reaches_1e9_on_ill_scaled_columns(case):
+    """Columns of very different norm: the odd instrumental columns 2^-12 times the others, or the
+    global column 2^-10 times its usual size. Rounding the refinement's residual r to binary32 limits
+    column j to about 2^-24 |r| / |A_:,j| (1.2e-7 in the instrumental block in the first case); the
+    binary64 gradient A~^T r of the inner solves' start, which the refinement switches to when a step
+    stops halving the correction (refine_grad 0) or uses from the second step on (refine_grad 1),
+    brings every block within 1e-9 of the binary64 solution. With refine_grad -1 (binary32 start
+    throughout) the first case stays above 1e-9."""
+    cfg = gsrgen.workloads()["c1"].cfg
+    h = gsrgen.generate(cfg, fp32=True)
+    A32 = h.A32.copy()
+    if case.startswith("odd_instr"):
+        small = (h.instr % 2) == 1
+        A32[:, 17:23][small] *= np.float32(2.0 ** -12)
+    else:
+        A32[:, 23] *= np.float32(2.0 ** -10)
+    A = A32.astype(np.float64)
+    s = oracle.System(h.star_ptr, A, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    xo, _ = oracle.lsqr(s, b, 5000, 1e-15, 1e-15, 0.0, 1e-6)
+    ctx = context_for(h, fp32=True)
+    ctx.set_system(A32, h.knot, h.instr, b)
+    for grad in (0, 1):
+        x = np.zeros(s.n_cols)
+        info = ctx.solve(x, mode=g.GSR_MIXED, damp=1e-6, refine_grad=grad)
+        errs = block_errors(x, xo, s)
+        assert max(errs.values()) <= 1e-9, (grad, errs, info)
+    if case.startswith("odd_instr"):
+        x = np.zeros(s.n_cols)
+        info = ctx.solve(x, mode=g.GSR_MIXED, damp=1e-6, refine_grad=-1, max_outer=8)
+        errs = block_errors(x, xo, s)
+        assert errs["instr"] > 1e-9, (errs, info)
+    ctx.close()
