@@ -318,6 +318,11 @@ typedef struct {
                                solve's relative accuracy of the least-squares solution when
                                the column norms spread widely (the binary32 rounding of r
                                otherwise limits column j to about 2^-24 |r| / |A_:,j|)     */
+    int32_t inner_fused;    /* MIXED, attitude blocks too wide for the one-pass shared-memory
+                               aprod 2 (gsr_aprod2_plan passes 3): each inner iteration's
+                               aprod 1 and aprod 2 in one pass over the row tiles, the new u's
+                               contributions to A^T u added while its coefficients are in
+                               registers. 1 = on, -1 = off, 0 = the library's choice (on)   */
 } gsr_solve_params;
 
 typedef struct {

@@ -763,9 +763,164 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
     if constexpr (BOTH) flush_att_run(sacc, k, S.n_dfa, z2t);
 }
 
+// One LSQR iteration's two products in one pass over the row tiles (the binary32 inner solve of a
+// wide attitude block, att_red). The Golub-Kahan step u_{i+1} = A v_i - alpha_i u_i depends on each
+// row alone, so once a tile's new u is formed its contributions to A^T u_{i+1} can be added from the
+// coefficients still in registers: the tile is read once instead of twice. The 1/beta_{i+1} of the
+// normalised u is applied afterwards (k_colA takes z = A^T u unnormalised, with beta from the
+// per-block sums of squares written here). Per tile: the aprod 1 part as k_aprod1 (attitude
+// unknowns through the window copy), then the aprod 2 part as the star pass with the attitude
+// reductions (astrometric runs in registers, instrumental sums in shared memory, the global column
+// per block, the attitude products as three 16-byte reductions per row into the L2 windows).
+// Each warp owns a contiguous range of tiles (the astrometric runs need them in order).
+template <bool INSTR_SMEM>
+__global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const float *__restrict__ x,
+                                                    float *__restrict__ y, double *__restrict__ z,
+                                                    const LsqrState *__restrict__ st, double *__restrict__ part,
+                                                    int64_t tiles_per_warp)
+{
+    constexpr int R = Tile<float>::R;
+    constexpr int T = Tile<float>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sm64[64];
+    __shared__ float wred[8][NASTRO * 32];
+    if (st->done) return;
+    const float coef = (float)st->coef_u;
+    float *sm_ins = reinterpret_cast<float *>(smem_raw);
+    if (INSTR_SMEM)
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_ins[i] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float *wbuf = wred[threadIdx.x >> 5];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t t0 = gw * tiles_per_warp;
+    const int64_t t1 = min(S.n_tiles, t0 + tiles_per_warp);
+    const float *__restrict__ xi = x + S.instr0;
+    double *__restrict__ zi = z + S.instr0;
+    const float xg = S.n_glob ? __ldg(x + S.glob0) : 0.f;
+    float gsum = 0.f, ssq = 0.f;
+    float acc[NASTRO], acc2[NASTRO];
+#pragma unroll
+    for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = 0.f;
+    int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current astrometric run
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
+        int32_t kn[R];
+        load_ints<R>(tb + NPAR * Tile<float>::VBLK, 0, kn);
+        int32_t ic[NINSTR][R];
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
+        float a[NPAR][R];
+#pragma unroll
+        for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
+        const int64_t r0 = t * T + lane * R;
+        int64_t sr[R];
+        stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+        bool in[R];
+        float yr[R];
+        // aprod 1: the new u of this lane's rows
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const float *__restrict__ xa = x + NASTRO * sr[i];
+            float v = a[0][i] * __ldg(xa);
+#pragma unroll
+            for (int j = 1; j < NASTRO; ++j) v = fmaf(a[j][i], __ldg(xa + j), v);
+#pragma unroll
+            for (int ax = 0; ax < NAXES; ++ax) {
+                const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
+                v = fmaf(a[A_ATT + NPARAXIS * ax + 0][i], w.x, v);
+                v = fmaf(a[A_ATT + NPARAXIS * ax + 1][i], w.y, v);
+                v = fmaf(a[A_ATT + NPARAXIS * ax + 2][i], w.z, v);
+                v = fmaf(a[A_ATT + NPARAXIS * ax + 3][i], w.w, v);
+            }
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) v = fmaf(a[A_INS + j][i], __ldg(xi + ic[j][i]), v);
+            v = fmaf(a[A_GLOB][i], xg, v);
+            const int64_t r = r0 + i;
+            in[i] = r < S.n_rows;
+            float yn = 0.f;
+            if (in[i]) {
+                yn = fmaf(coef, y[r], v);
+                y[r] = yn;
+                ssq = fmaf(yn, yn, ssq);
+            }
+            yr[i] = yn;
+        }
+        // aprod 2 with the new u: instrumental and global columns
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) {
+                if (!in[i]) continue;
+                if (INSTR_SMEM)
+                    atomicAdd(sm_ins + ic[j][i], a[A_INS + j][i] * yr[i]);
+                else
+                    atomicAdd(zi + ic[j][i], (double)(a[A_INS + j][i] * yr[i]));
+            }
+            gsum = fmaf(a[A_GLOB][i], yr[i], gsum);
+        }
+        // attitude columns: one 16-byte reduction per axis and row into the windows
+#pragma unroll
+        for (int ax = 0; ax < NAXES; ++ax)
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (!in[i]) continue;
+                const int64_t wi = ((int64_t)ax * S.n_dfa + kn[i]) * 4;
+                red_add_v4(S.aw + wi, a[A_ATT + NPARAXIS * ax + 0][i] * yr[i], a[A_ATT + NPARAXIS * ax + 1][i] * yr[i],
+                           a[A_ATT + NPARAXIS * ax + 2][i] * yr[i], a[A_ATT + NPARAXIS * ax + 3][i] * yr[i]);
+            }
+        // astrometric columns: runs of the current star in registers (as the star pass)
+        const int64_t tile_end = min((t + 1) * T, S.n_rows);
+        if (__ldg(S.star_ptr + k + 1) >= tile_end) {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < NASTRO; ++j) acc[j] = fmaf(a[j][i], yr[i], acc[j]);
+        } else {
+            const int64_t kl = star_of_row(S.star_ptr, S.first_star, t, tile_end - 1);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+#pragma unroll
+                for (int j = 0; j < NASTRO; ++j) {
+                    const float pv = a[j][i] * yr[i];
+                    if (sr[i] == k)
+                        acc[j] += pv;
+                    else if (sr[i] == kl)
+                        acc2[j] += pv;
+                    else if (in[i])
+                        atomicAdd(z + (int64_t)NASTRO * sr[i] + j, (double)pv);
+                }
+            }
+            flush_astro_run(acc, k, wbuf, z);
+#pragma unroll
+            for (int j = 0; j < NASTRO; ++j) {
+                acc[j] = acc2[j];
+                acc2[j] = 0.f;
+            }
+            k = kl;
+        }
+    }
+    if (t0 < t1) flush_astro_run(acc, k, wbuf, z);
+    __syncthreads();
+    if (INSTR_SMEM) {
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+            const float v = sm_ins[i];
+            if (v != 0.f) atomicAdd(zi + i, (double)v);
+        }
+    }
+    const double2 tot = block_sum2((double)ssq, (double)gsum, sm64);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot.x;
+        if (S.n_glob && tot.y != 0.0) atomicAdd(z + S.glob0, tot.y);
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 static constexpr int kThreads = 256;
 static constexpr size_t kSmemBudget = 100 * 1024;  // bytes of block-private accumulators
+// the pass that sums products and squares together (the warm start's, once per solve) keeps its
+// block-private accumulators in shared memory up to one block per SM
+static constexpr size_t kSmemBudgetBoth = 200 * 1024;
 
 template <typename KernelT>
 static int persistent_blocks(const gsr_ctx *c, KernelT kern, size_t dyn_smem)
@@ -934,7 +1089,8 @@ static cudaError_t aprod2_red_t(const gsr_ctx *c, const void *y, double *x, doub
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         e = aprod2_star_launch_t<float, float, float, true, MODE, LS, true, false, true>(c, y, x, x2, st, s);
-    } else if (sizeof(float) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget) {
+    } else if (sizeof(float) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <=
+               (MODE == A2_BOTH ? kSmemBudgetBoth : kSmemBudget)) {
         e = aprod2_star_launch_t<float, float, float, true, MODE, LS, false, false, true>(c, y, x, x2, st, s);
     } else {
         e = aprod2_star_launch_t<float, float, float, false, MODE, LS, false, false, true>(c, y, x, x2, st, s);
@@ -980,7 +1136,8 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if constexpr (F32) e = aprod2_star_launch<VT, UT, AT, true, MODE, LS, true>(c, y, x, x2, st, s);
-    } else if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <= kSmemBudget) {
+    } else if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <=
+               (MODE == A2_BOTH ? kSmemBudgetBoth : kSmemBudget)) {
         e = aprod2_star_launch<VT, UT, AT, true, MODE, LS>(c, y, x, x2, st, s);
     } else {
         e = aprod2_star_launch<VT, UT, AT, false, MODE, LS>(c, y, x, x2, st, s);
@@ -1014,6 +1171,33 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
     if (square) return aprod2_t<double, double, double, A2_SQUARE, false>(c, y, x, nullptr, nullptr, s);
     if (st) return aprod2_t<double, double, double, A2_PROD, true>(c, y, x, nullptr, st, s);
     return aprod2_t<double, double, double, A2_PROD, false>(c, y, x, nullptr, nullptr, s);
+}
+
+// The fused iteration pass of a wide attitude block (k_iter_fused): the window copy of p v, the pass,
+// the fold of the attitude windows into z. grid_out: only the pass's block count (its partials).
+cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, double *z, const LsqrState *st,
+                              double *part, cudaStream_t s, int *grid_out)
+{
+    const bool ins = sizeof(float) * (size_t)c->n_instr <= kSmemBudget;
+    auto kern = ins ? k_iter_fused<true> : k_iter_fused<false>;
+    const size_t dyn = ins ? sizeof(float) * (size_t)c->n_instr : 0;
+    if (dyn > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
+    int64_t per = 0, blocks = 0;
+    tile_ranges(c, kern, dyn, &per, &blocks);
+    if (grid_out) {
+        *grid_out = (int)blocks;
+        return cudaSuccess;
+    }
+    if (!att_red(c) || !att_window(c)) return cudaErrorInvalidValue;
+    const SysView<float> S = view<float>(c);
+    k_att_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(pv, S.att0, c->n_dfa,
+                                                                           reinterpret_cast<float4 *>(c->xwin));
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(S, pv, u, z, st, part, per);
+    k_att_fold<A2_PROD, true><<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(S, z, nullptr, st, nullptr);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_aprod2_both(const gsr_ctx *c, const void *y, double *x, double *sq, cudaStream_t s, bool inner32)

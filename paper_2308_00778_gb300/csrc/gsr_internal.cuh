@@ -83,7 +83,7 @@ struct LsqrState {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int k = 0;
-    bool var = false, inner32 = false;
+    bool var = false, inner32 = false, fused = false;
 };
 
 struct Workspace {
@@ -159,6 +159,7 @@ struct gsr_ctx {
     bool fx_att = false;
     bool fx_uni = false;             // the one-pass aprod 2 gives the instrumental columns one scale too
     bool fx_valid = false;           // the statistics match the loaded rows
+    bool fused_inner = false;        // the current solve's inner iterations take the fused pass
     // wide attitude blocks (binary32 storage, standard row): attw holds the window accumulators of the
     // binary32 aprod 2 (2 x 3 n_dfa x 4 binary32: products, then squares; zero between uses), xwin the
     // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)
@@ -231,6 +232,10 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
 // one pass computing x += A^T y and sq += the column sums of squares (the warm start)
 cudaError_t launch_aprod2_both(const gsr_ctx *c, const void *y, double *x, double *sq, cudaStream_t s, bool inner32);
 int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
+// one LSQR iteration's aprod 1 and aprod 2 in one pass over the tiles (binary32 inner solve of a wide
+// attitude block: att_red and att_window); with grid_out only the number of partials it writes
+cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, double *z, const LsqrState *st,
+                              double *part, cudaStream_t s, int *grid_out = nullptr);
 
 // per-system layout work (layout.cu), once per loaded system: the fixed-point statistics of binary32
 // storage, and the knot-ordered attitude copy when binary64 aprod 2 passes will run (binary64) or the
@@ -246,6 +251,8 @@ inline bool att_red(const gsr_ctx *c)
 }
 // the binary32 aprod 1 gathers the attitude unknowns through the window copy (one 16-byte load per axis)
 inline bool att_window(const gsr_ctx *c) { return c->prec == GSR_FP32 && !c->sv && c->xwin; }
+// the inner solves take the fused iteration pass (set per solve from gsr_solve_params.inner_fused)
+inline bool iter_fused(const gsr_ctx *c) { return c->fused_inner && att_red(c) && att_window(c); }
 // attitude columns above which the binary32 aprod 1 uses the window copy: beyond ~16K binary32 values
 // the gathered attitude vector no longer stays in L1 beside the streamed tiles
 constexpr int64_t ATT_WINDOW_MIN_COLS = 16384;

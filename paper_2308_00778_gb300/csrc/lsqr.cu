@@ -488,13 +488,15 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
                                    cudaGraphExec_t *out)
 {
     Workspace &ws = c->ws;
+    const bool fused = inner32 && iter_fused(c);
     for (auto &gc : ws.graphs) {
-        if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32) {
+        if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32 && gc.fused == fused) {
             *out = gc.exec;
             return cudaSuccess;
         }
     }
-    const int gu = aprod1_grid(c, inner32);
+    int gu = aprod1_grid(c, inner32);
+    if (fused) launch_iter_fused(c, nullptr, nullptr, nullptr, nullptr, nullptr, s, &gu);
     const int gc = colab_grid(c, c->n_cols);
     // the fused binary32 aprod 2 leaves the max |y| word to colA (the attitude pass clears it otherwise)
     uint32_t *ymax_reset = inner32 && att_fused(c) ? fx_ymax(c) : nullptr;
@@ -506,8 +508,13 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < k && e == cudaSuccess; ++i) {
-        if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
-        if ((e = launch_aprod2(c, u, ws.z, false, ws.st, s, inner32)) != cudaSuccess) break;
+        if (fused) {  // both products in one pass over the tiles
+            if ((e = launch_iter_fused(c, (const float *)pv, (float *)u, ws.z, ws.st, ws.part_u, s)) != cudaSuccess)
+                break;
+        } else {
+            if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
+            if ((e = launch_aprod2(c, u, ws.z, false, ws.st, s, inner32)) != cudaSuccess) break;
+        }
         k_colA<<<gc, kColThreads, 0, s>>>(ws.part_u, gu, ws.z, ws.p, ws.v, ws.w, c->n_cols, ws.st, ws.part_v,
                                           ws.part_w, 0, ws.counter, ws.flag_d, ymax_reset);
         k_colB<<<gc, kColThreads, 0, s>>>(ws.v, ws.pv, pv32, ws.p, ws.w, ws.x, want_var ? ws.var : nullptr,
@@ -524,6 +531,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
     gcache.k = k;
     gcache.var = want_var;
     gcache.inner32 = inner32;
+    gcache.fused = fused;
     ws.graphs.push_back(gcache);
     *out = exec;
     return cudaSuccess;
@@ -550,6 +558,7 @@ void default_params(gsr_solve_params *p)
     p->max_outer = 0;
     p->inner_itn_next = 0;
     p->refine_grad = 0;
+    p->inner_fused = 0;
 }
 
 // p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in

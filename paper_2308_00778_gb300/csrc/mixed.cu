@@ -181,7 +181,22 @@ __global__ void k_rhs32(const double *__restrict__ b, float *__restrict__ r, dou
 {
     __shared__ double sm32[32];
     float ssq = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // four rows per thread and round: two 16-byte loads of b and one 16-byte store of r (the grid is the
+    // residual kernel's, a few blocks per SM, so each thread keeps several loads in flight)
+    const int64_t n4 = n / 4;
+    const double2 *__restrict__ b2 = reinterpret_cast<const double2 *>(b);
+    float4 *__restrict__ r4 = reinterpret_cast<float4 *>(r);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+        const double2 lo = __ldcs(b2 + 2 * q), hi = __ldcs(b2 + 2 * q + 1);
+        const float4 v = make_float4((float)lo.x, (float)lo.y, (float)hi.x, (float)hi.y);
+        r4[q] = v;
+        ssq = fmaf(v.x, v.x, ssq);
+        ssq = fmaf(v.y, v.y, ssq);
+        ssq = fmaf(v.z, v.z, ssq);
+        ssq = fmaf(v.w, v.w, ssq);
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const float v = (float)__ldcs(b + i);
         r[i] = v;
         ssq = fmaf(v, v, ssq);
@@ -310,6 +325,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     cudaError_t e;
 
     if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
+    c->fused_inner = prm->inner_fused >= 0;  // the inner iterations' pass (iteration_graph reads it)
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
                             (dev_io || x0_dev) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);

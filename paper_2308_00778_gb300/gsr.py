@@ -54,6 +54,7 @@ class SolveParams(ctypes.Structure):
         ("max_outer", ctypes.c_int32),
         ("inner_itn_next", ctypes.c_int32),
         ("refine_grad", ctypes.c_int32),
+        ("inner_fused", ctypes.c_int32),
     ]
 
 
