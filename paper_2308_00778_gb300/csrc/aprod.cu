@@ -773,14 +773,18 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
 // reductions (astrometric runs in registers, instrumental sums in shared memory, the global column
 // per block, the attitude products as three 16-byte reductions per row into the L2 windows).
 // Each warp owns a contiguous range of tiles (the astrometric runs need them in order).
-template <bool INSTR_SMEM>
-__global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const float *__restrict__ x,
-                                                    float *__restrict__ y, double *__restrict__ z,
-                                                    const LsqrState *__restrict__ st, double *__restrict__ part,
-                                                    int64_t tiles_per_warp)
+// HALF: a warp takes each tile in two halves of 64 rows, each lane two rows of a half with 8-byte
+// loads (half the registers: two resident blocks per SM instead of one).
+template <bool INSTR_SMEM, bool HALF>
+__device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const float *__restrict__ x,
+                                                float *__restrict__ y, double *__restrict__ z,
+                                                const LsqrState *__restrict__ st, double *__restrict__ part,
+                                                int64_t tiles_per_warp)
 {
-    constexpr int R = Tile<float>::R;
+    constexpr int R = HALF ? 2 : Tile<float>::R;
     constexpr int T = Tile<float>::T;
+    constexpr int NH = HALF ? 2 : 1;   // parts a tile is taken in
+    constexpr int TH = T / NH;         // rows of a part
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm64[64];
     __shared__ float wred[8][NASTRO * 32];
@@ -805,99 +809,112 @@ __global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const floa
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current astrometric run
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
-        int32_t kn[R];
-        load_ints<R>(tb + NPAR * Tile<float>::VBLK, 0, kn);
-        int32_t ic[NINSTR][R];
+        if (t + 1 < t1) prefetch_l2(tb + S.tile_bytes, S.tile_bytes);  // the warp's next tile into L2
+#pragma unroll 1
+        for (int h = 0; h < NH; ++h) {
+            int32_t kn[R];
+            int32_t ic[NINSTR][R];
+            float a[NPAR][R];
+            if constexpr (HALF) {
+                load_knot_half(tb, NPAR, h, kn);
 #pragma unroll
-        for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
-        float a[NPAR][R];
+                for (int j = 0; j < NINSTR; ++j) load_instr_half(tb, NPAR, S.iw16, j, h, ic[j]);
 #pragma unroll
-        for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
-        const int64_t r0 = t * T + lane * R;
-        int64_t sr[R];
-        stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
-        bool in[R];
-        float yr[R];
-        // aprod 1: the new u of this lane's rows
+                for (int j = 0; j < NPAR; ++j) load_vals_half(tb, j, h, a[j]);
+            } else {
+                load_ints<R>(tb + NPAR * Tile<float>::VBLK, 0, kn);
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const float *__restrict__ xa = x + NASTRO * sr[i];
-            float v = a[0][i] * __ldg(xa);
+                for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
 #pragma unroll
-            for (int j = 1; j < NASTRO; ++j) v = fmaf(a[j][i], __ldg(xa + j), v);
-#pragma unroll
-            for (int ax = 0; ax < NAXES; ++ax) {
-                const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
-                v = fmaf(a[A_ATT + NPARAXIS * ax + 0][i], w.x, v);
-                v = fmaf(a[A_ATT + NPARAXIS * ax + 1][i], w.y, v);
-                v = fmaf(a[A_ATT + NPARAXIS * ax + 2][i], w.z, v);
-                v = fmaf(a[A_ATT + NPARAXIS * ax + 3][i], w.w, v);
+                for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
             }
-#pragma unroll
-            for (int j = 0; j < NINSTR; ++j) v = fmaf(a[A_INS + j][i], __ldg(xi + ic[j][i]), v);
-            v = fmaf(a[A_GLOB][i], xg, v);
-            const int64_t r = r0 + i;
-            in[i] = r < S.n_rows;
-            float yn = 0.f;
-            if (in[i]) {
-                yn = fmaf(coef, y[r], v);
-                y[r] = yn;
-                ssq = fmaf(yn, yn, ssq);
-            }
-            yr[i] = yn;
-        }
-        // aprod 2 with the new u: instrumental and global columns
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-#pragma unroll
-            for (int j = 0; j < NINSTR; ++j) {
-                if (!in[i]) continue;
-                if (INSTR_SMEM)
-                    atomicAdd(sm_ins + ic[j][i], a[A_INS + j][i] * yr[i]);
-                else
-                    atomicAdd(zi + ic[j][i], (double)(a[A_INS + j][i] * yr[i]));
-            }
-            gsum = fmaf(a[A_GLOB][i], yr[i], gsum);
-        }
-        // attitude columns: one 16-byte reduction per axis and row into the windows
-#pragma unroll
-        for (int ax = 0; ax < NAXES; ++ax)
+            const int64_t r0 = t * T + h * TH + lane * R;
+            int64_t sr[R];
+            stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
+            bool in[R];
+            float yr[R];
+            // aprod 1: the new u of this lane's rows
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                if (!in[i]) continue;
-                const int64_t wi = ((int64_t)ax * S.n_dfa + kn[i]) * 4;
-                red_add_v4(S.aw + wi, a[A_ATT + NPARAXIS * ax + 0][i] * yr[i], a[A_ATT + NPARAXIS * ax + 1][i] * yr[i],
-                           a[A_ATT + NPARAXIS * ax + 2][i] * yr[i], a[A_ATT + NPARAXIS * ax + 3][i] * yr[i]);
+                const float *__restrict__ xa = x + NASTRO * sr[i];
+                float v = a[0][i] * __ldg(xa);
+#pragma unroll
+                for (int j = 1; j < NASTRO; ++j) v = fmaf(a[j][i], __ldg(xa + j), v);
+#pragma unroll
+                for (int ax = 0; ax < NAXES; ++ax) {
+                    const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
+                    v = fmaf(a[A_ATT + NPARAXIS * ax + 0][i], w.x, v);
+                    v = fmaf(a[A_ATT + NPARAXIS * ax + 1][i], w.y, v);
+                    v = fmaf(a[A_ATT + NPARAXIS * ax + 2][i], w.z, v);
+                    v = fmaf(a[A_ATT + NPARAXIS * ax + 3][i], w.w, v);
+                }
+#pragma unroll
+                for (int j = 0; j < NINSTR; ++j) v = fmaf(a[A_INS + j][i], __ldg(xi + ic[j][i]), v);
+                v = fmaf(a[A_GLOB][i], xg, v);
+                const int64_t r = r0 + i;
+                in[i] = r < S.n_rows;
+                float yn = 0.f;
+                if (in[i]) {
+                    yn = fmaf(coef, y[r], v);
+                    y[r] = yn;
+                    ssq = fmaf(yn, yn, ssq);
+                }
+                yr[i] = yn;
             }
-        // astrometric columns: runs of the current star in registers (as the star pass)
-        const int64_t tile_end = min((t + 1) * T, S.n_rows);
-        if (__ldg(S.star_ptr + k + 1) >= tile_end) {
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-#pragma unroll
-                for (int j = 0; j < NASTRO; ++j) acc[j] = fmaf(a[j][i], yr[i], acc[j]);
-        } else {
-            const int64_t kl = star_of_row(S.star_ptr, S.first_star, t, tile_end - 1);
+            // aprod 2 with the new u: instrumental and global columns
 #pragma unroll
             for (int i = 0; i < R; ++i) {
+#pragma unroll
+                for (int j = 0; j < NINSTR; ++j) {
+                    if (!in[i]) continue;
+                    if (INSTR_SMEM)
+                        atomicAdd(sm_ins + ic[j][i], a[A_INS + j][i] * yr[i]);
+                    else
+                        atomicAdd(zi + ic[j][i], (double)(a[A_INS + j][i] * yr[i]));
+                }
+                gsum = fmaf(a[A_GLOB][i], yr[i], gsum);
+            }
+            // attitude columns: one 16-byte reduction per axis and row into the windows
+#pragma unroll
+            for (int ax = 0; ax < NAXES; ++ax)
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    if (!in[i]) continue;
+                    const int64_t wi = ((int64_t)ax * S.n_dfa + kn[i]) * 4;
+                    red_add_v4(S.aw + wi, a[A_ATT + NPARAXIS * ax + 0][i] * yr[i],
+                               a[A_ATT + NPARAXIS * ax + 1][i] * yr[i], a[A_ATT + NPARAXIS * ax + 2][i] * yr[i],
+                               a[A_ATT + NPARAXIS * ax + 3][i] * yr[i]);
+                }
+            // astrometric columns: runs of the current star in registers (as the star pass), per part
+            const int64_t part_end = min(t * T + (h + 1) * TH, S.n_rows);
+            if (__ldg(S.star_ptr + k + 1) >= part_end) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+#pragma unroll
+                    for (int j = 0; j < NASTRO; ++j) acc[j] = fmaf(a[j][i], yr[i], acc[j]);
+            } else {
+                const int64_t kl = star_of_row(S.star_ptr, S.first_star, t, part_end - 1);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+#pragma unroll
+                    for (int j = 0; j < NASTRO; ++j) {
+                        const float pv = a[j][i] * yr[i];
+                        if (sr[i] == k)
+                            acc[j] += pv;
+                        else if (sr[i] == kl)
+                            acc2[j] += pv;
+                        else if (in[i])
+                            atomicAdd(z + (int64_t)NASTRO * sr[i] + j, (double)pv);
+                    }
+                }
+                flush_astro_run(acc, k, wbuf, z);
 #pragma unroll
                 for (int j = 0; j < NASTRO; ++j) {
-                    const float pv = a[j][i] * yr[i];
-                    if (sr[i] == k)
-                        acc[j] += pv;
-                    else if (sr[i] == kl)
-                        acc2[j] += pv;
-                    else if (in[i])
-                        atomicAdd(z + (int64_t)NASTRO * sr[i] + j, (double)pv);
+                    acc[j] = acc2[j];
+                    acc2[j] = 0.f;
                 }
+                k = kl;
             }
-            flush_astro_run(acc, k, wbuf, z);
-#pragma unroll
-            for (int j = 0; j < NASTRO; ++j) {
-                acc[j] = acc2[j];
-                acc2[j] = 0.f;
-            }
-            k = kl;
         }
     }
     if (t0 < t1) flush_astro_run(acc, k, wbuf, z);
@@ -913,6 +930,24 @@ __global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const floa
         part[blockIdx.x] = tot.x;
         if (S.n_glob && tot.y != 0.0) atomicAdd(z + S.glob0, tot.y);
     }
+}
+
+template <bool INSTR_SMEM>
+__global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const float *__restrict__ x,
+                                                    float *__restrict__ y, double *__restrict__ z,
+                                                    const LsqrState *__restrict__ st, double *__restrict__ part,
+                                                    int64_t tiles_per_warp)
+{
+    iter_fused_body<INSTR_SMEM, false>(S, x, y, z, st, part, tiles_per_warp);
+}
+
+template <bool INSTR_SMEM>
+__global__ void __launch_bounds__(256, 2) k_iter_fused_half(SysView<float> S, const float *__restrict__ x,
+                                                            float *__restrict__ y, double *__restrict__ z,
+                                                            const LsqrState *__restrict__ st,
+                                                            double *__restrict__ part, int64_t tiles_per_warp)
+{
+    iter_fused_body<INSTR_SMEM, true>(S, x, y, z, st, part, tiles_per_warp);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1179,7 +1214,8 @@ cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, doubl
                               double *part, cudaStream_t s, int *grid_out)
 {
     const bool ins = sizeof(float) * (size_t)c->n_instr <= kSmemBudget;
-    auto kern = ins ? k_iter_fused<true> : k_iter_fused<false>;
+    auto kern = c->fused_inner == 2 ? (ins ? k_iter_fused_half<true> : k_iter_fused_half<false>)
+                                    : (ins ? k_iter_fused<true> : k_iter_fused<false>);
     const size_t dyn = ins ? sizeof(float) * (size_t)c->n_instr : 0;
     if (dyn > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

@@ -83,7 +83,8 @@ struct LsqrState {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int k = 0;
-    bool var = false, inner32 = false, fused = false;
+    bool var = false, inner32 = false;
+    int fused = 0;
 };
 
 struct Workspace {
@@ -159,7 +160,7 @@ struct gsr_ctx {
     bool fx_att = false;
     bool fx_uni = false;             // the one-pass aprod 2 gives the instrumental columns one scale too
     bool fx_valid = false;           // the statistics match the loaded rows
-    bool fused_inner = false;        // the current solve's inner iterations take the fused pass
+    int32_t fused_inner = 0;         // the current solve's inner iterations take the fused pass (> 0)
     // wide attitude blocks (binary32 storage, standard row): attw holds the window accumulators of the
     // binary32 aprod 2 (2 x 3 n_dfa x 4 binary32: products, then squares; zero between uses), xwin the
     // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)

@@ -488,7 +488,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
                                    cudaGraphExec_t *out)
 {
     Workspace &ws = c->ws;
-    const bool fused = inner32 && iter_fused(c);
+    const int fused = inner32 && iter_fused(c) ? c->fused_inner : 0;
     for (auto &gc : ws.graphs) {
         if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32 && gc.fused == fused) {
             *out = gc.exec;

@@ -53,7 +53,7 @@ __global__ void k_split_window(const double *__restrict__ x, int64_t att0, int32
 
 // ATTW: the attitude pairs come from the window copy (two 16-byte loads per axis and row instead of
 // four 8-byte gathers); the terms and their order are the same, so the result is bitwise the same.
-template <bool SV = false, bool ATTW = false>
+template <bool SV = false, bool ATTW = false, bool R64 = false>
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
                                                   const double *__restrict__ b64, float *__restrict__ r_out,
                                                   double *__restrict__ part, double *__restrict__ r64)
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
                 const float lo = __fadd_rn(__fadd_rn(e, bb.y), -c[i]);
                 const float rv = __fadd_rn(tt, lo);
                 r_out[r] = rv;
-                if (r64) r64[r] = (double)tt + (double)lo;  // exact in binary64
+                if constexpr (R64) r64[r] = (double)tt + (double)lo;  // exact in binary64
                 ssq = fmaf(rv, rv, ssq);
             }
         }
@@ -261,10 +261,16 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out, bool window, double *r64)
 {
-    // a section variant runs the run-time-geometry instance; a wide attitude block the window instance
-    auto kern = c->sv ? k_residual<true> : (window && att_window(c) ? k_residual<false, true> : k_residual<false>);
+    // a section variant runs the run-time-geometry instance; a wide attitude block the window instance;
+    // r64: the instance that also keeps the residual in binary64
+    const bool w = window && att_window(c);
+    auto kern = c->sv ? (r64 ? k_residual<true, false, true> : k_residual<true>)
+                      : w ? (r64 ? k_residual<false, true, true> : k_residual<false, true>)
+                          : (r64 ? k_residual<false, false, true> : k_residual<false>);
+    // the grid (and so the number of partial sums) is the instance without r64's, whichever runs
+    auto sized = c->sv ? k_residual<true> : w ? k_residual<false, true> : k_residual<false>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sized, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * c->sm_count;
     blocks = std::min<int64_t>(blocks, (c->n_tiles + (kThreads / 32) - 1) / (kThreads / 32));
@@ -325,7 +331,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     cudaError_t e;
 
     if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
-    c->fused_inner = prm->inner_fused >= 0;  // the inner iterations' pass (iteration_graph reads it)
+    c->fused_inner = prm->inner_fused >= 0 ? (prm->inner_fused > 0 ? prm->inner_fused : 1) : 0;  // iteration_graph reads it
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
                             (dev_io || x0_dev) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
