@@ -773,18 +773,16 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
 // reductions (astrometric runs in registers, instrumental sums in shared memory, the global column
 // per block, the attitude products as three 16-byte reductions per row into the L2 windows).
 // Each warp owns a contiguous range of tiles (the astrometric runs need them in order).
-// HALF: a warp takes each tile in two halves of 64 rows, each lane two rows of a half with 8-byte
-// loads (half the registers: two resident blocks per SM instead of one).
-template <bool INSTR_SMEM, bool HALF>
+// (A form in which a warp takes each tile in two halves, each lane two rows with 8-byte loads, half
+// the registers and two resident blocks per SM, ran 40% slower on 5e8 rows: 31.6 vs 22.7 ms.)
+template <bool INSTR_SMEM>
 __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const float *__restrict__ x,
                                                 float *__restrict__ y, double *__restrict__ z,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
                                                 int64_t tiles_per_warp)
 {
-    constexpr int R = HALF ? 2 : Tile<float>::R;
+    constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
-    constexpr int NH = HALF ? 2 : 1;   // parts a tile is taken in
-    constexpr int TH = T / NH;         // rows of a part
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm64[64];
     __shared__ float wred[8][NASTRO * 32];
@@ -810,25 +808,16 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         if (t + 1 < t1) prefetch_l2(tb + S.tile_bytes, S.tile_bytes);  // the warp's next tile into L2
-#pragma unroll 1
-        for (int h = 0; h < NH; ++h) {
+        {
             int32_t kn[R];
             int32_t ic[NINSTR][R];
             float a[NPAR][R];
-            if constexpr (HALF) {
-                load_knot_half(tb, NPAR, h, kn);
+            load_ints<R>(tb + NPAR * Tile<float>::VBLK, 0, kn);
 #pragma unroll
-                for (int j = 0; j < NINSTR; ++j) load_instr_half(tb, NPAR, S.iw16, j, h, ic[j]);
+            for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
 #pragma unroll
-                for (int j = 0; j < NPAR; ++j) load_vals_half(tb, j, h, a[j]);
-            } else {
-                load_ints<R>(tb + NPAR * Tile<float>::VBLK, 0, kn);
-#pragma unroll
-                for (int j = 0; j < NINSTR; ++j) load_instr<float>(tb, S.iw16, j, ic[j]);
-#pragma unroll
-                for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
-            }
-            const int64_t r0 = t * T + h * TH + lane * R;
+            for (int j = 0; j < NPAR; ++j) load_vals<float, float>(tb, j, a[j]);
+            const int64_t r0 = t * T + lane * R;
             int64_t sr[R];
             stars_of_rows<R>(S.star_ptr, S.first_star, t, r0, sr);
             bool in[R];
@@ -885,8 +874,8 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
                                a[A_ATT + NPARAXIS * ax + 1][i] * yr[i], a[A_ATT + NPARAXIS * ax + 2][i] * yr[i],
                                a[A_ATT + NPARAXIS * ax + 3][i] * yr[i]);
                 }
-            // astrometric columns: runs of the current star in registers (as the star pass), per part
-            const int64_t part_end = min(t * T + (h + 1) * TH, S.n_rows);
+            // astrometric columns: runs of the current star in registers (as the star pass)
+            const int64_t part_end = min((t + 1) * T, S.n_rows);
             if (__ldg(S.star_ptr + k + 1) >= part_end) {
 #pragma unroll
                 for (int i = 0; i < R; ++i)
@@ -938,16 +927,7 @@ __global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const floa
                                                     const LsqrState *__restrict__ st, double *__restrict__ part,
                                                     int64_t tiles_per_warp)
 {
-    iter_fused_body<INSTR_SMEM, false>(S, x, y, z, st, part, tiles_per_warp);
-}
-
-template <bool INSTR_SMEM>
-__global__ void __launch_bounds__(256, 2) k_iter_fused_half(SysView<float> S, const float *__restrict__ x,
-                                                            float *__restrict__ y, double *__restrict__ z,
-                                                            const LsqrState *__restrict__ st,
-                                                            double *__restrict__ part, int64_t tiles_per_warp)
-{
-    iter_fused_body<INSTR_SMEM, true>(S, x, y, z, st, part, tiles_per_warp);
+    iter_fused_body<INSTR_SMEM>(S, x, y, z, st, part, tiles_per_warp);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1214,8 +1194,7 @@ cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, doubl
                               double *part, cudaStream_t s, int *grid_out)
 {
     const bool ins = sizeof(float) * (size_t)c->n_instr <= kSmemBudget;
-    auto kern = c->fused_inner == 2 ? (ins ? k_iter_fused_half<true> : k_iter_fused_half<false>)
-                                    : (ins ? k_iter_fused<true> : k_iter_fused<false>);
+    auto kern = ins ? k_iter_fused<true> : k_iter_fused<false>;
     const size_t dyn = ins ? sizeof(float) * (size_t)c->n_instr : 0;
     if (dyn > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);

@@ -100,44 +100,6 @@ __device__ __forceinline__ void load_vals(const uint8_t *__restrict__ tile, int 
     for (int i = 0; i < Tile<VT>::R; ++i) out[i] = (AT)v[i];
 }
 
-// Half-tile access (binary32 tiles): lane l reads rows 64 h + 2 l and 64 h + 2 l + 1 of plane j with
-// one 8-byte load (a warp still reads 256 contiguous bytes of each plane), so that a warp can take a
-// tile in two halves with half the registers of the 16-byte form.
-__device__ __forceinline__ void load_vals_half(const uint8_t *__restrict__ tile, int j, int h, float (&out)[2])
-{
-    const float2 v = __ldcs(reinterpret_cast<const float2 *>(tile + (int64_t)j * Tile<float>::VBLK) + h * 32 +
-                            (threadIdx.x & 31));
-    out[0] = v.x;
-    out[1] = v.y;
-}
-
-// the knot plane (int32) of a binary32 tile record with npl value planes, half h
-__device__ __forceinline__ void load_knot_half(const uint8_t *__restrict__ tile, int npl, int h, int32_t (&out)[2])
-{
-    const int2 v = __ldcs(reinterpret_cast<const int2 *>(tile + (int64_t)npl * Tile<float>::VBLK) + h * 32 +
-                          (threadIdx.x & 31));
-    out[0] = v.x;
-    out[1] = v.y;
-}
-
-// instrumental plane j (16- or 32-bit indices) of a binary32 tile record with npl value planes, half h
-__device__ __forceinline__ void load_instr_half(const uint8_t *__restrict__ tb, int npl, bool iw16, int j, int h,
-                                                int32_t (&out)[2])
-{
-    constexpr int T = Tile<float>::T;
-    const int lane = threadIdx.x & 31;
-    const uint8_t *p = tb + (int64_t)npl * Tile<float>::VBLK + Tile<float>::IBLK;  // the first instrumental plane
-    if (iw16) {
-        const uint32_t v = __ldcs(reinterpret_cast<const uint32_t *>(p + (int64_t)j * T * 2) + h * 32 + lane);
-        out[0] = (int32_t)(v & 0xffffu);
-        out[1] = (int32_t)(v >> 16);
-    } else {
-        const int2 v = __ldcs(reinterpret_cast<const int2 *>(p + (int64_t)j * T * 4) + h * 32 + lane);
-        out[0] = v.x;
-        out[1] = v.y;
-    }
-}
-
 // int32 plane q of a tile whose int planes start at `ints`, this lane's R entries
 template <int R>
 __device__ __forceinline__ void load_ints(const uint8_t *__restrict__ ints, int q, int32_t (&out)[R])
