@@ -58,6 +58,9 @@ BYTES = {
     "aprod1_f32": 24 * 4 + 28 + 8,       # binary32 values, u (binary32) read + write          = 132
     "aprod2_f32": 24 * 4 + 28 + 4,       # binary32 values, u (binary32) read                  = 128
     "residual_df": 24 * 4 + 28 + 8 + 8,  # binary32 values, b (binary64) read, r written       = 140
+    # one inner iteration's two products from one read of the tiles (the fused pass): the matrix and the
+    # row vector once                                                                         = 132
+    "aprod12_f32": 24 * 4 + 28 + 8,
 }
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row of one launch (dram__bytes_read.sum + dram__bytes_write.sum), from single-pass ncu
@@ -488,8 +491,13 @@ def dominant_kernel(env, meta, kw, t):
     if kw.get("mode") == g.GSR_MIXED:
         m, its = meta["outer"], sum(meta["inner_iterations"])
         n_res = m if kw.get("warm") else m - 1  # the cold start's first residual is b itself
-        share = {"aprod1_f32": (its + warm_aprod2) * t["aprod1_f32"],
-                 "aprod2_f32": (its + m + 1 + warm_aprod2) * t["aprod2_f32"], "residual_df": n_res * t["residual_df"]}
+        if meta.get("fused"):  # the inner iterations take the fused pass; the starts, the norms and A^T b the aprod 2
+            share = {"aprod12_f32": its * t["aprod12_f32"], "aprod1_f32": warm_aprod2 * t["aprod1_f32"],
+                     "aprod2_f32": (m + 1 + warm_aprod2) * t["aprod2_f32"], "residual_df": n_res * t["residual_df"]}
+        else:
+            share = {"aprod1_f32": (its + warm_aprod2) * t["aprod1_f32"],
+                     "aprod2_f32": (its + m + 1 + warm_aprod2) * t["aprod2_f32"],
+                     "residual_df": n_res * t["residual_df"]}
     else:
         k = meta["iterations"]
         share = {"aprod1_f64": (k + warm_aprod2) * t["aprod1_f64"], "aprod2_f64": (k + 2 + warm_aprod2) * t["aprod2_f64"]}
@@ -588,6 +596,8 @@ def measure_workload(env, args, name, headline_mode):
         torch.cuda.empty_cache()
     # the binary32 context (and, for e2e, pinned host copies of its rows in the paper's storage)
     ctx32, b32, host = device_system(cfg, True, True, dev, stream=sh, keep_host=want_e2e)
+    plan = ctx32.aprod2_plan()  # form 3: the library's inner iterations take the fused pass by default
+    fused_inner = plan["passes"] == 3 and FUSED_DEFAULT
     for nm, warm, outers in (("mixed", None, (2, 3)), ("mixed_jacobi", jacobi, (1, 2, 3)),
                              ("mixed_learned", learned, (1, 2, 3))):
         if nm != "mixed" and not warm:
@@ -617,7 +627,7 @@ def measure_workload(env, args, name, headline_mode):
             _, m, k1, k2 = min(cands)
             legs[nm] = (ctx32, mixed_kw(k1, m, warm, k2),
                         {"outer": m, "inner_iterations": [k1] + [k2] * (m - 1),
-                         "start": nm.split("_")[1] if warm else "x0 = 0"})
+                         "start": nm.split("_")[1] if warm else "x0 = 0", "fused": fused_inner})
 
     # ---- timed region: every solver, the same K steps after W warm-up steps each
     time_legs({nm: leg for nm, leg in legs.items() if nm not in solvers})
@@ -632,6 +642,8 @@ def measure_workload(env, args, name, headline_mode):
     t["aprod1_f32"] = _time_kernel(torch, lambda: ctx32.aprod1_f32(x32, u32, stream=sh), stream)
     t["aprod2_f32"] = _time_kernel(torch, lambda: ctx32.aprod2_f32(u32, z, stream=sh), stream)
     t["residual_df"] = _time_kernel(torch, lambda: ctx32.residual(xs, r32, stream=sh), stream)
+    if plan["passes"] == 3:  # the fused pass (y <- A x - 0.5 y, z += A^T y)
+        t["aprod12_f32"] = _time_kernel(torch, lambda: ctx32.aprod12_f32(x32, u32, z, -0.5, stream=sh), stream)
     shape = TRAFFIC_SHAPE.get(name)
     traffic = TRAFFIC_PER_ROW.get(shape, {}) if shape else {}
     kern = {}
@@ -639,7 +651,8 @@ def measure_workload(env, args, name, headline_mode):
         bpr = BYTES[kn]
         kern[kn] = {"ms": kms, "GB/s": bpr * n / (kms * 1e-3) / 1e9, "bytes_per_row": bpr,
                     "frac_of_measured_hbm": bpr * n / (kms * 1e-3) / 1e9 / env.peaks["hbm_gbs"],
-                    "TFLOP/s": FLOPS_PER_ROW * n / (kms * 1e-3) / 1e12, "ncu_dram_bytes_per_row": traffic.get(kn)}
+                    "TFLOP/s": FLOPS_PER_ROW * (2 if kn == "aprod12_f32" else 1) * n / (kms * 1e-3) / 1e12,
+                    "ncu_dram_bytes_per_row": traffic.get(kn)}
     hctx, hkw, hmeta = legs[headline]
     dom, share = dominant_kernel(env, hmeta, hkw, t)
     if dom.endswith("f64"):
@@ -692,6 +705,10 @@ def measure_workload(env, args, name, headline_mode):
     torch.cuda.empty_cache()
     return out
 
+
+# whether the library's default (gsr_solve_params.inner_fused = 0) runs the inner iterations of a form-3
+# system as the fused pass
+FUSED_DEFAULT = True
 
 # stars of the CPU baseline's sample per workload (about 10-30 s of oracle work on the host cores)
 CPU_SAMPLE_STARS = {"c5": 80_000, "c3": 100_000, "c2": 100_000}

@@ -213,6 +213,22 @@ gsr_status gsr_aprod1_f32(gsr_ctx *ctx, const float *x, float *y, void *stream);
 gsr_status gsr_aprod2_f32(gsr_ctx *ctx, const float *y, double *x, void *stream);
 
 /*
+ * gsr_aprod12_f32 -- one Golub-Kahan step's two products (Eq. 2 then Eq. 3,
+ * the bidiagonalisation of Sec. 1): y <- A x + coef y, then z += A^T y with
+ * the new y; binary32 values, products and y, binary64 z. On attitude blocks
+ * too wide for the one-pass shared-memory aprod 2 (gsr_aprod2_plan passes 3)
+ * both products come from one read of each row tile (the inner iterations'
+ * fused pass, gsr_solve_params.inner_fused); otherwise y is scaled and the
+ * two products run as gsr_aprod1_f32 and gsr_aprod2_f32.
+ *   x  device, n_cols binary32.   y  device, n_rows binary32 (read, written).
+ *   z  device, n_cols binary64 (accumulated).
+ * FP32-stored contexts only. The first call after the rows change takes the
+ * statistics of the aprod 2 form (as gsr_aprod2_f32). Errors: as
+ * gsr_aprod2_f32.
+ */
+gsr_status gsr_aprod12_f32(gsr_ctx *ctx, const float *x, float *y, double *z, float coef, void *stream);
+
+/*
  * gsr_aprod2_plan -- the form gsr_aprod2_f32 (and the inner iterations of
  * GSR_MIXED) takes on the loaded rows. FP32-stored contexts only.
  *   passes     1: one pass over the row tiles also sums the attitude columns

@@ -776,19 +776,21 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
 // Each warp owns a contiguous range of tiles (the astrometric runs need them in order).
 // (A form in which a warp takes each tile in two halves, each lane two rows with 8-byte loads, half
 // the registers and two resident blocks per SM, ran 40% slower on 5e8 rows: 31.6 vs 22.7 ms.)
-template <bool INSTR_SMEM>
+// LSQR: coef = -alpha/beta from the solver state (and nothing to do once it has stopped), the per-block
+// sums of squares of the new u into part; otherwise coef_arg, and part may be null.
+template <bool INSTR_SMEM, bool LSQR>
 __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const float *__restrict__ x,
                                                 float *__restrict__ y, double *__restrict__ z,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
-                                                int64_t tiles_per_warp)
+                                                int64_t tiles_per_warp, float coef_arg)
 {
     constexpr int R = Tile<float>::R;
     constexpr int T = Tile<float>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm64[64];
     __shared__ float wred[8][NASTRO * 32];
-    if (st->done) return;
-    const float coef = (float)st->coef_u;
+    if (LSQR && st->done) return;
+    const float coef = LSQR ? (float)st->coef_u : coef_arg;
     float *sm_ins = reinterpret_cast<float *>(smem_raw);
     if (INSTR_SMEM)
         for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_ins[i] = 0.f;
@@ -917,18 +919,18 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
     }
     const double2 tot = block_sum2((double)ssq, (double)gsum, sm64);
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = tot.x;
+        if (part) part[blockIdx.x] = tot.x;
         if (S.n_glob && tot.y != 0.0) atomicAdd(z + S.glob0, tot.y);
     }
 }
 
-template <bool INSTR_SMEM>
+template <bool INSTR_SMEM, bool LSQR>
 __global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const float *__restrict__ x,
                                                     float *__restrict__ y, double *__restrict__ z,
                                                     const LsqrState *__restrict__ st, double *__restrict__ part,
-                                                    int64_t tiles_per_warp)
+                                                    int64_t tiles_per_warp, float coef_arg)
 {
-    iter_fused_body<INSTR_SMEM>(S, x, y, z, st, part, tiles_per_warp);
+    iter_fused_body<INSTR_SMEM, LSQR>(S, x, y, z, st, part, tiles_per_warp, coef_arg);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1197,13 +1199,36 @@ cudaError_t launch_aprod2(const gsr_ctx *c, const void *y, double *x, bool squar
     return aprod2_t<double, double, double, A2_PROD, false>(c, y, x, nullptr, nullptr, s);
 }
 
+// y <- coef y (binary32)
+__global__ void k_scale_f32(float *__restrict__ y, float coef, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] *= coef;
+}
+
+// y <- A x + coef y, then z += A^T y with the new y (binary32 storage and products): the fused pass when
+// the context's form allows it, else the two products after scaling y
+cudaError_t launch_aprod12_f32(const gsr_ctx *c, const float *x, float *y, double *z, float coef, cudaStream_t s)
+{
+    if (c->n_rows == 0) return cudaSuccess;
+    if (att_red(c) && att_window(c)) return launch_iter_fused(c, x, y, z, nullptr, nullptr, s, nullptr, coef);
+    cudaError_t e = cudaSuccess;
+    if (coef != 1.f) {
+        k_scale_f32<<<col_grid(c, c->n_rows), kThreads, 0, s>>>(y, coef, c->n_rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = launch_aprod1(c, x, y, nullptr, nullptr, s, true)) != cudaSuccess) return e;
+    return launch_aprod2(c, y, z, false, nullptr, s, true);
+}
+
 // The fused iteration pass of a wide attitude block (k_iter_fused): the window copy of p v, the pass,
 // the fold of the attitude windows into z. grid_out: only the pass's block count (its partials).
 cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, double *z, const LsqrState *st,
-                              double *part, cudaStream_t s, int *grid_out)
+                              double *part, cudaStream_t s, int *grid_out, float coef)
 {
     const bool ins = sizeof(float) * (size_t)c->n_instr <= kSmemBudget;
-    auto kern = ins ? k_iter_fused<true> : k_iter_fused<false>;
+    auto kern = st ? (ins ? k_iter_fused<true, true> : k_iter_fused<false, true>)
+                   : (ins ? k_iter_fused<true, false> : k_iter_fused<false, false>);
     const size_t dyn = ins ? sizeof(float) * (size_t)c->n_instr : 0;
     if (dyn > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -1219,8 +1244,13 @@ cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, doubl
     const SysView<float> S = view<float>(c);
     k_att_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(pv, S.att0, c->n_dfa,
                                                                            reinterpret_cast<float4 *>(c->xwin));
-    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(S, pv, u, z, st, part, per);
-    k_att_fold<A2_PROD, true><<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(S, z, nullptr, st, nullptr);
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(S, pv, u, z, st, part, per, coef);
+    if (st)
+        k_att_fold<A2_PROD, true><<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(S, z, nullptr, st,
+                                                                                            nullptr);
+    else
+        k_att_fold<A2_PROD, false><<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(S, z, nullptr,
+                                                                                             nullptr, nullptr);
     return cudaGetLastError();
 }
 

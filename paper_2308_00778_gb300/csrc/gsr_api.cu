@@ -663,6 +663,21 @@ GSR_API gsr_status gsr_aprod2_f32(gsr_ctx *c, const float *y, double *x, void *s
     return GSR_OK;
 }
 
+GSR_API gsr_status gsr_aprod12_f32(gsr_ctx *c, const float *x, float *y, double *z, float coef, void *stream)
+{
+    if (!c) return GSR_EINVAL;
+    if (c->prec != GSR_FP32) return fail(c, GSR_EINVAL, "binary32 kernels need an FP32-stored context");
+    if (!rows_complete(c)) return fail(c, GSR_ESTATE, "rows not loaded");
+    if ((!x || !y || !z) && c->n_rows > 0) return fail(c, GSR_EINVAL, "null vector");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const gsr_status rc = ensure_att_layout(c, (cudaStream_t)stream, false);
+    if (rc != GSR_OK) return rc;
+    if ((e = launch_aprod12_f32(c, x, y, z, coef, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(c, e, "aprod12_f32");
+    return GSR_OK;
+}
+
 GSR_API gsr_status gsr_aprod2_plan(gsr_ctx *c, void *stream, int32_t *passes, int32_t *fx_bits,
                                    int32_t *ins_group)
 {

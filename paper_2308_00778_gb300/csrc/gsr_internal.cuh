@@ -236,7 +236,9 @@ int aprod1_grid(const gsr_ctx *c, bool inner32 = false);
 // one LSQR iteration's aprod 1 and aprod 2 in one pass over the tiles (binary32 inner solve of a wide
 // attitude block: att_red and att_window); with grid_out only the number of partials it writes
 cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, double *z, const LsqrState *st,
-                              double *part, cudaStream_t s, int *grid_out = nullptr);
+                              double *part, cudaStream_t s, int *grid_out = nullptr, float coef = 1.f);
+// y <- A x + coef y, z += A^T y (binary32 storage, products and y): the fused pass or the two products
+cudaError_t launch_aprod12_f32(const gsr_ctx *c, const float *x, float *y, double *z, float coef, cudaStream_t s);
 
 // per-system layout work (layout.cu), once per loaded system: the fixed-point statistics of binary32
 // storage, and the knot-ordered attitude copy when binary64 aprod 2 passes will run (binary64) or the

@@ -103,6 +103,7 @@ def lib():
             "gsr_aprod1_f32": (I32, [P, P, P, P]),
             "gsr_aprod2_f32": (I32, [P, P, P, P]),
             "gsr_aprod2_plan": (I32, [P, P, P, P, P]),
+            "gsr_aprod12_f32": (I32, [P, P, P, P, ctypes.c_float, P]),
             "gsr_residual": (I32, [P, P, P, P]),
             "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
@@ -208,6 +209,10 @@ def gsr_aprod1_f32(ctx, x, y, stream=0):
 
 def gsr_aprod2_f32(ctx, y, x, stream=0):
     return lib().gsr_aprod2_f32(ctx, y or None, x or None, stream or None)
+
+
+def gsr_aprod12_f32(ctx, x, y, z, coef, stream=0):
+    return lib().gsr_aprod12_f32(ctx, x or None, y or None, z or None, coef, stream or None)
 
 
 def gsr_residual(ctx, x, r, stream=0):
@@ -479,6 +484,10 @@ class Context:
 
     def aprod2_f32(self, y, x, stream=0):
         self._check(gsr_aprod2_f32(self.h, _ptr(y), _ptr(x), stream))
+
+    def aprod12_f32(self, x, y, z, coef=1.0, stream=0):
+        """y <- A x + coef y, then z += A^T y with the new y (binary32; z binary64)."""
+        self._check(gsr_aprod12_f32(self.h, _ptr(x), _ptr(y), _ptr(z), coef, stream))
 
     def aprod2_plan(self, stream=0):
         """The binary32 aprod 2's form on the loaded rows: {"passes", "fx_bits", "ins_group"}."""

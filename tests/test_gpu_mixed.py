@@ -293,3 +293,33 @@ def test_mixed_reaches_1e9_on_ill_scaled_columns(case):
         errs = block_errors(x, xo, s)
         assert errs["instr"] > 1e-9, (errs, info)
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "wide_one_scale", "wide_ragged"])
+def test_aprod12_f32_vs_oracle(name):
+    """One Golub-Kahan step's two products (gsr_aprod12_f32): y <- A x + coef y, then z += A^T y with
+    the new y. On the wide systems (60,000 attitude columns) both come from one read of each tile (the
+    inner iterations' fused pass); on c1 the two separate products run. y within 25 u sum|terms| of the
+    oracle's; z within 2e3 u sum|terms| of the oracle's A^T y for the GPU's own new y."""
+    cfg = {"c1": gsrgen.workloads()["c1"].cfg, "wide_one_scale": gsrgen.make_cfg(64, 3000, 100, 20000, 15000),
+           "wide_ragged": gsrgen.make_cfg(65, 4000, (1, 300), 20000, 40000)}[name]
+    h, s, b, ctx = _setup32(cfg)
+    assert ctx.aprod2_plan()["passes"] == (1 if name == "c1" else 3)
+    u = 2.0 ** -24
+    rng = np.random.default_rng(23)
+    x = rng.standard_normal(s.n_cols).astype(np.float32).astype(np.float64)
+    y0 = rng.standard_normal(s.n_rows).astype(np.float32).astype(np.float64)
+    z0 = rng.standard_normal(s.n_cols)
+    coef = -0.75
+    yd = torch.tensor(y0, dtype=torch.float32, device="cuda")
+    zd = torch.tensor(z0, device="cuda")
+    ctx.aprod12_f32(torch.tensor(x, dtype=torch.float32, device="cuda"), yd, zd, coef)
+    torch.cuda.synchronize()
+    want = oracle.aprod1(s, x, coef * y0)
+    scale = oracle.aprod1(_abs_sys(s), np.abs(x), np.abs(coef * y0))
+    yn = yd.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yn - want) <= 25 * u * scale)
+    want2 = oracle.aprod2(s, yn, z0.copy())
+    scale2 = oracle.aprod2(_abs_sys(s), np.abs(yn), np.abs(z0).copy())
+    assert np.all(np.abs(zd.cpu().numpy() - want2) <= 2e3 * u * scale2)
+    ctx.close()
