@@ -61,6 +61,7 @@ BYTES = {
     # one inner iteration's two products from one read of the tiles (the fused pass): the matrix and the
     # row vector once                                                                         = 132
     "aprod12_f32": 24 * 4 + 28 + 8,
+    "aprod2_f64_on_f32": 24 * 4 + 28 + 8,  # binary32 values, binary64 u read                = 132
 }
 FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # DRAM bytes per row of one launch (dram__bytes_read.sum + dram__bytes_write.sum), from single-pass ncu
@@ -644,6 +645,10 @@ def measure_workload(env, args, name, headline_mode):
     t["residual_df"] = _time_kernel(torch, lambda: ctx32.residual(xs, r32, stream=sh), stream)
     if plan["passes"] == 3:  # the fused pass (y <- A x - 0.5 y, z += A^T y)
         t["aprod12_f32"] = _time_kernel(torch, lambda: ctx32.aprod12_f32(x32, u32, z, -0.5, stream=sh), stream)
+    # the mixed refinement's binary64 gradient (used on ill-scaled columns): binary64 aprod 2 on binary32 storage
+    u64b = u32.double()
+    t["aprod2_f64_on_f32"] = _time_kernel(torch, lambda: ctx32.aprod2(u64b, z, stream=sh), stream)
+    del u64b
     shape = TRAFFIC_SHAPE.get(name)
     traffic = TRAFFIC_PER_ROW.get(shape, {}) if shape else {}
     kern = {}

@@ -48,7 +48,9 @@ def _check_gpu_line(line):
     roof = line["roofline"]
     assert roof["bound"] in ("hbm", "alu") and roof["peak"] > 0 and roof["achieved"] > 0
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
-    assert set(line["kernels"]) == {"aprod1_f64", "aprod2_f64", "aprod1_f32", "aprod2_f32", "residual_df"}
+    assert {"aprod1_f64", "aprod2_f64", "aprod1_f32", "aprod2_f32", "residual_df",
+            "aprod2_f64_on_f32"} <= set(line["kernels"]) <= {"aprod1_f64", "aprod2_f64", "aprod1_f32", "aprod2_f32",
+                                                            "residual_df", "aprod2_f64_on_f32", "aprod12_f32"}
     assert "sm_mhz" in line["clocks"]
 
 
