@@ -242,10 +242,8 @@ gsr_status gsr_aprod12_f32(gsr_ctx *ctx, const float *x, float *y, double *z, fl
  *              when the attitude columns do not fit the one-pass form.
  *   fx_bits    fewest fixed-point bits of an instrumental column's per-block
  *              sums (>= 20), or 0 when those sums are binary32.
- *   ins_group  1 when the instrumental columns share one scale (forms 1 and
- *              3), else 0. With more instrumental columns than per-column
- *              scales leave room for in shared memory (over 12,800), their
- *              sums are fixed point only with the shared scale.
+ *   ins_group  1 when the instrumental columns share one scale (one-pass form
+ *              only), else 0.
  * Any pointer may be NULL. The choice rests on per-column statistics of the
  * rows (the largest count a block adds to a column, the largest |a_j|); a
  * group shares one scale only if its smallest column still keeps >= 20 bits.

@@ -257,7 +257,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     if (FX) {
         const float ymax = SQUARE ? 1.f : __uint_as_float(fx_word[2 * fxs]);
         if (threadIdx.x == 0) s_bad = !(ymax < INFINITY);  // non-finite y: the sums are made NaN below
-        if ((ATT || (ATTRED && UNI)) && threadIdx.x < 2) {  // thread 0: attitude group, 1: instrumental group
+        if (ATT && threadIdx.x < 2) {  // thread 0: the attitude group, thread 1: the instrumental group
             const uint32_t *gw = fx_word + 3 * fxs + 1;
             const float am = __uint_as_float(gw[2 * threadIdx.x]);
             const uint32_t bits = gw[4 + threadIdx.x];
@@ -274,8 +274,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                 s_ins_qsc = qs;
             }
         }
-        // (the attitude-reduction form with one instrumental scale keeps no per-column scales)
-        for (int32_t i = threadIdx.x; i < (ATTRED && UNI ? 0 : S.n_instr); i += blockDim.x) {
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
             // the largest power of two with bound * scale <= 2^b_j - 1, bound = max|a_j| max|y|
             // for the products and max|a_j|^2 for the squares (and for the squares' pass)
             const float am = __uint_as_float(fx_word[i]);
@@ -294,7 +293,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     }
     __syncthreads();
     // UNI: the instrumental group scale applies (the host chose this instance from the statistics)
-    const bool ins_uni = (ATT || ATTRED) && UNI;
+    const bool ins_uni = ATT && UNI;
     const float ins_sc = ins_uni ? s_ins_sc : 1.f, ins_qsc = ins_uni ? s_ins_qsc : 1.f;
 
     const int lane = threadIdx.x & 31;
@@ -389,7 +388,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                 if (in[i]) {
                     if (FX)
                         atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
-                                  __float2int_rn(av * yr[i] * (ins_uni ? ins_sc : sm_scale[ic[j][i]])));
+                                  __float2int_rn(av * yr[i] * (ATT && ins_uni ? ins_sc : sm_scale[ic[j][i]])));
                     else if (INSTR_SMEM)
                         atomicAdd(sm_ins + ic[j][i], av * yr[i]);
                     else
@@ -397,7 +396,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                     if constexpr (BOTH) {
                         if (FX)
                             atomicAdd(reinterpret_cast<int *>(sm_sq) + ic[j][i],
-                                      __float2int_rn(av * av * (ins_uni ? ins_qsc : sm_qscale[ic[j][i]])));
+                                      __float2int_rn(av * av * (ATT && ins_uni ? ins_qsc : sm_qscale[ic[j][i]])));
                         else if (INSTR_SMEM)
                             atomicAdd(sm_sq + ic[j][i], av * av);
                         else
@@ -532,7 +531,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
             const bool ins = col < S.n_instr;
             const int64_t dst = ins ? S.instr0 + col : S.att0 + (col - S.n_instr);
             const float sc = !ins ? (sq ? s_att_qsc : s_att_sc)
-                             : ins_uni ? (sq ? s_ins_qsc : s_ins_sc) : (sq ? sm_qscale[col] : sm_scale[col]);
+                             : ATT && ins_uni ? (sq ? s_ins_qsc : s_ins_sc) : (sq ? sm_qscale[col] : sm_scale[col]);
             atomicAdd((sq ? z2 : z) + dst, (double)q / (double)sc);  // the scale is a power of two: exact
         }
         if (s_bad && threadIdx.x == 0) atomicAdd(S.n_instr ? zi : z + S.att0, (double)NAN);
@@ -558,14 +557,14 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
 // The standard row's instance, and a section variant's (run-time geometry) with
 // its registers capped for two resident blocks per SM, as the standard one has.
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX = false,
-          bool ATTRED = false, bool UNI = false>
+          bool ATTRED = false>
 __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__restrict__ y, double *__restrict__ z,
                                                      double *__restrict__ z2, const LsqrState *__restrict__ st,
                                                      int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word,
                                                      int32_t fxs)
 {
-    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false, false, UNI, ATTRED>(S, y, z, z2, st,
-                                                                                      tiles_per_warp, fx_word, fxs);
+    aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false, false, false, ATTRED>(S, y, z, z2, st,
+                                                                                        tiles_per_warp, fx_word, fxs);
 }
 
 // z[att] += the window accumulators of the attitude reductions: column k of axis a collects
@@ -1035,16 +1034,13 @@ cudaError_t launch_aprod1(const gsr_ctx *c, const void *x, void *y, const LsqrSt
     return aprod1_dispatch(c, x, y, st, part, s, inner32, nullptr);
 }
 
-template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX, bool SV, bool ATTRED = false,
-          bool UNI = false>
+template <typename VT, typename UT, typename AT, bool INS, int MODE, bool LS, bool FX, bool SV, bool ATTRED = false>
 static cudaError_t aprod2_star_launch_t(const gsr_ctx *c, const void *y, double *x, double *x2, const LsqrState *st,
                                         cudaStream_t s)
 {
     auto kern = SV ? k_aprod2_star_sv<VT, UT, AT, INS, MODE, LS, FX>
-                   : k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX, ATTRED, UNI>;
-    // accumulators (twice for products and squares), then per-column scales unless one scale serves
-    const size_t dyn =
-        INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX && !(ATTRED && UNI) ? 2 : 1)) : 0;
+                   : k_aprod2_star<VT, UT, AT, INS, MODE, LS, FX, ATTRED>;
+    const size_t dyn = INS ? sizeof(AT) * (size_t)c->n_instr * ((MODE == A2_BOTH ? 2 : 1) * (FX ? 2 : 1)) : 0;
     if (dyn > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -1103,18 +1099,13 @@ static cudaError_t aprod2_red_t(const gsr_ctx *c, const void *y, double *x, doub
                                 cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    // fixed-point instrumental sums: accumulators (and per-column scales unless one scale serves them all)
-    const size_t fx_smem = sizeof(float) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) * (c->fx_uni ? 1 : 2);
-    const bool fx = c->fx_bits > 0 && fx_smem <= (MODE == A2_BOTH ? kSmemBudgetBoth : kSmemBudget);
+    const bool fx = c->fx_bits > 0 && (MODE != A2_BOTH || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
     if (fx) {
         if (MODE != A2_SQUARE && !LS) {
             k_absmax<<<col_grid(c, c->n_rows), kThreads, 0, s>>>((const float *)y, c->n_rows, fx_ymax(c));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if (c->fx_uni)
-            e = aprod2_star_launch_t<float, float, float, true, MODE, LS, true, false, true, true>(c, y, x, x2, st, s);
-        else
-            e = aprod2_star_launch_t<float, float, float, true, MODE, LS, true, false, true>(c, y, x, x2, st, s);
+        e = aprod2_star_launch_t<float, float, float, true, MODE, LS, true, false, true>(c, y, x, x2, st, s);
     } else if (sizeof(float) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <=
                (MODE == A2_BOTH ? kSmemBudgetBoth : kSmemBudget)) {
         e = aprod2_star_launch_t<float, float, float, true, MODE, LS, false, false, true>(c, y, x, x2, st, s);

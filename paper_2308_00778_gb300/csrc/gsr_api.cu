@@ -690,7 +690,7 @@ GSR_API gsr_status gsr_aprod2_plan(gsr_ctx *c, void *stream, int32_t *passes, in
     if (rc != GSR_OK) return rc;
     if (passes) *passes = att_fused(c) ? 1 : att_red(c) ? 3 : 2;
     if (fx_bits) *fx_bits = c->fx_bits;
-    if (ins_group) *ins_group = (att_fused(c) || att_red(c)) && c->fx_bits > 0 && c->fx_uni ? 1 : 0;
+    if (ins_group) *ins_group = att_fused(c) && c->fx_uni ? 1 : 0;
     return GSR_OK;
 }
 

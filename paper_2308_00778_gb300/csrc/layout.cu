@@ -218,9 +218,7 @@ static gsr_status fixed_point_launch(gsr_ctx *c, cudaStream_t s, std::vector<uin
     kmax_h->clear();
     if (c->prec != GSR_FP32 || c->n_rows == 0 || c->n_ipr == 0 || c->n_instr == 0) return GSR_OK;
     const int32_t ni = c->n_instr;
-    // more instrumental columns than the per-column form's shared memory holds: only one scale for
-    // all of them will do (decided in fixed_point_finish), and only in the standard row's passes
-    if (2 * sizeof(uint32_t) * (size_t)ni > (c->sv ? kFxSmemOne : kFxSmemBoth)) return GSR_OK;
+    if (2 * sizeof(uint32_t) * (size_t)ni > kFxSmemOne) return GSR_OK;
     // the attitude columns join when their accumulators fit beside the instrumental ones
     const int64_t nc_att = (int64_t)ni + (int64_t)NAXES * c->n_dfa;
     const bool att = !c->sv && 2 * sizeof(uint32_t) * (size_t)nc_att <= kFxSmemOne &&
@@ -296,8 +294,6 @@ static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vect
     const int loss_ins = group_loss(kmax_ext[nc + 2], kmax_ext[nc + 3]);
     const uint32_t group_bits[2] = {att_cols && min_att - loss_att >= 20 ? (uint32_t)min_att : 0u,
                                     min_ins - loss_ins >= 20 ? (uint32_t)min_ins : 0u};
-    // per-column scales beside the accumulators do not fit: fixed point only with the group scale
-    if (2 * sizeof(uint32_t) * (size_t)c->n_instr > kFxSmemOne && group_bits[1] == 0) return GSR_OK;
     // pageable sources: each call returns once the bytes are staged, the kernels that read them follow on s
     cudaError_t e = cudaMemcpyAsync(c->fx_word + nc, bits.data(), sizeof(uint32_t) * nc, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)

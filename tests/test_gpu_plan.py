@@ -8,9 +8,9 @@ they are used when every instrumental column gets >= 20 bits. One pass over
 the tiles sums the attitude columns too, with one scale for all of them, when
 their fewest bits minus ceil(log2(largest / smallest column max |a|)) stay >=
 20 and their accumulators fit in shared memory (8 bytes per column, 100 KB);
-the instrumental columns share one scale on the same condition (in that form
-and in form 3). Otherwise the standard row adds the attitude products by
-vector reductions into L2 window accumulators (form 3). The expected plan is recomputed here from the rows on
+the instrumental columns share one scale on the same condition. Otherwise the
+standard row adds the attitude products by vector reductions into L2 window
+accumulators (form 3). The expected plan is recomputed here from the rows on
 the host.
 """
 import math
@@ -39,8 +39,6 @@ def _loss(colmax):
 def expected_plan(A32, knot, instr, n_dfa, n_instr, sm_count):
     n = len(knot)
     T = 128
-    if 8 * n_instr > 200 * 1024:  # no room for the statistics' counts and maxima
-        return {"passes": 3, "fx_bits": 0, "ins_group": 0}
     n_tiles = -(-n // T)
     per = max(-(-n_tiles // (sm_count * 16)), 8)
     blk = np.arange(n, dtype=np.int64) // (8 * per * T)
@@ -59,9 +57,7 @@ def expected_plan(A32, knot, instr, n_dfa, n_instr, sm_count):
     np.maximum.at(am_a, cols.ravel(), np.abs(A32[:, 5:17]).ravel())
     fits = 8 * (n_instr + na) <= 100 * 1024
     one = fits and min_att - _loss(am_a) >= 20
-    grp = min_ins - _loss(am_i) >= 20  # one scale for the instrumental columns (forms 1 and 3)
-    if 8 * n_instr > 100 * 1024 and not grp:  # per-column scales do not fit beside the accumulators
-        return {"passes": 3, "fx_bits": 0, "ins_group": 0}
+    grp = one and min_ins - _loss(am_i) >= 20
     return {"passes": 1 if one else 3, "fx_bits": min_ins, "ins_group": 1 if grp else 0}
 
 
@@ -71,22 +67,19 @@ def _c2_shape(n_stars):
                            c.noise_sigma)
 
 
-@pytest.mark.parametrize("name", ["c1", "c2_10k_stars", "wide_15000_instr"])
+@pytest.mark.parametrize("name", ["c1", "c2_10k_stars"])
 def test_plan_matches_the_statistics(name):
     """c1 and a 2e6-row system of the 2e7-row workload's shape (8,192 rows per block: edge knots
     appear in few rows of a block, which must not shrink the attitude group's smallest column
-    bound, a global maximum) both take the one-pass form with one instrumental scale; a system with
-    60,000 attitude and 15,000 instrumental columns takes the attitude reductions (form 3), with its
-    instrumental sums in fixed point under one scale (per-column scales would not fit)."""
-    cfg = {"c1": gsrgen.workloads()["c1"].cfg, "c2_10k_stars": _c2_shape(10000),
-           "wide_15000_instr": gsrgen.make_cfg(64, 3000, 100, 20000, 15000)}[name]
+    bound, a global maximum) both take the one-pass form with one instrumental scale."""
+    cfg = gsrgen.workloads()["c1"].cfg if name == "c1" else _c2_shape(10000)
     h = gsrgen.generate(cfg, fp32=True)
     ctx = context_for(h, fp32=True)
     ctx.set_system(h.A32, h.knot, h.instr)
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     want = expected_plan(h.A32, h.knot, h.instr, cfg.n_dfa, cfg.n_instr, sm)
     assert ctx.aprod2_plan() == want
-    assert want["passes"] == (3 if name.startswith("wide") else 1) and want["ins_group"] == 1
+    assert want["passes"] == 1 and want["ins_group"] == 1
     ctx.close()
 
 
