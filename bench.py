@@ -95,7 +95,7 @@ def parse_args():
                          "contexts do not fit in device memory together)")
     ap.add_argument("--n-stars", type=int, default=0,
                     help="profiling mode only: override the workload's number of stars (a smaller case for ncu)")
-    ap.add_argument("--profile", default=None, choices=["f32", "f64", "mixed"],
+    ap.add_argument("--profile", default=None, choices=["f32", "f64", "mixed", "net"],
                     help="profiling mode for ncu: load the system with binary32 (f32) or binary64 (f64) storage "
                          "and launch each hot kernel --steps times inside an NVTX range 'prof', or (mixed) run the "
                          "default mixed solve from the learned start --steps times; prints timings")
@@ -712,8 +712,8 @@ def measure_workload(env, args, name, headline_mode):
 
 
 # whether the library's default (gsr_solve_params.inner_fused = 0) runs the inner iterations of a form-3
-# system as the fused pass
-FUSED_DEFAULT = True
+# system as the fused pass (it does not: the fused pass is opt-in, inner_fused = 1)
+FUSED_DEFAULT = False
 
 # stars of the CPU baseline's sample per workload (about 10-30 s of oracle work on the host cores)
 CPU_SAMPLE_STARS = {"c5": 80_000, "c3": 100_000, "c2": 100_000}
@@ -828,6 +828,45 @@ def run_profile(args):
     return 0
 
 
+def run_profile_net(args):
+    """The warm start's network alone: a forward over the workload's knot series (batch 1) and a training
+    step (batch 16 of 2,000 knots), --steps times each inside an NVTX range 'prof'; prints times and the
+    achieved dense BF16 rate (2 flops per multiply-add of the six convolutions)."""
+    import torch
+
+    import gsrgen
+    import paper_2308_00778_gb300 as g
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    L = gsrgen.workloads()[args.workload].cfg.n_dfa
+    net = g.Net()
+    net.load(g.WARM_WEIGHTS)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    xf = torch.randn((1, L, 6), device=dev, generator=gen)
+    out = torch.empty((1, L, 3), device=dev)
+    xt = torch.randn((16, 2000, 6), device=dev, generator=gen)
+    tt = torch.randn((16, 2000, 3), device=dev, generator=gen)
+    ch = [6, 64, 64, 64, 64, 64, 3]
+    fl_pos = sum(2 * ci * co * 5 for ci, co in zip(ch[:-1], ch[1:]))  # forward flops per position
+    net.forward(xf, out, stream=stream.cuda_stream)
+    net.train_step(xt, tt, 0.0, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("prof")
+    ms_f = _time_kernel(torch, lambda: net.forward(xf, out, stream=stream.cuda_stream), stream, reps=max(args.steps, 1))
+    ms_t = _time_kernel(torch, lambda: net.train_step(xt, tt, 0.0, stream=stream.cuda_stream), stream,
+                        reps=max(args.steps, 1))
+    torch.cuda.nvtx.range_pop()
+    # a training step: forward, backward-data (five layers) and backward-weight, about 3x the forward
+    print(json.dumps({"profile": "net", "knots": L, "forward_ms": ms_f,
+                      "forward_tflops": fl_pos * L / (ms_f * 1e-3) / 1e12, "train_step_ms": ms_t,
+                      "train_step_tflops": 3 * fl_pos * 16 * 2000 / (ms_t * 1e-3) / 1e12}), flush=True)
+    net.close()
+    return 0
+
+
 def run_dfma_probe(args):
     import torch
 
@@ -842,6 +881,8 @@ def main():
     args = parse_args()
     if args.dfma_probe:
         return run_dfma_probe(args)
+    if args.profile == "net":
+        return run_profile_net(args)
     if args.profile:
         return run_profile(args)
     if args.impl == "reference":

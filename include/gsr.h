@@ -338,7 +338,9 @@ typedef struct {
                                aprod 2 (gsr_aprod2_plan passes 3): each inner iteration's
                                aprod 1 and aprod 2 in one pass over the row tiles, the new u's
                                contributions to A^T u added while its coefficients are in
-                               registers. 1 = on, -1 = off, 0 = the library's choice (on)   */
+                               registers (4-6% faster per iteration on 2e8-5e8 rows, but
+                               latency-bound at one block per SM). 1 = on; 0 (default) or
+                               -1 = the two separate passes                                  */
 } gsr_solve_params;
 
 typedef struct {

@@ -331,7 +331,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
     cudaError_t e;
 
     if (!p_ready && (rc = precond_pass(c, prm->precond != 0, s, true)) != GSR_OK) return rc;
-    c->fused_inner = prm->inner_fused >= 0 ? 1 : 0;  // the inner iterations' pass (iteration_graph reads it)
+    c->fused_inner = prm->inner_fused > 0 ? 1 : 0;  // the inner iterations' pass (iteration_graph reads it)
     if (x0)
         e = cudaMemcpyAsync(ws.xo, x0, nc * sizeof(double),
                             (dev_io || x0_dev) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
