@@ -23,7 +23,10 @@
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default
  *     stream). Calls that take a stream are asynchronous with respect to the
  *     host unless stated otherwise.
- *   - A context is not thread-safe; use one context per host thread.
+ *   - A context is not thread-safe; use one context per host thread. Its
+ *     calls must not overlap on the GPU either (they share the context's
+ *     scratch: the workspace, the attitude window accumulators and window
+ *     copies); calls on one stream are ordered.
  */
 #ifndef GSR_H
 #define GSR_H
