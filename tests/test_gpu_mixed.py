@@ -320,3 +320,51 @@ def test_aprod12_f32_vs_oracle(name):
     scale2 = oracle.aprod2(_abs_sys(s), np.abs(yn), np.abs(z0).copy())
     assert np.all(np.abs(zd.cpu().numpy() - want2) <= 2e3 * u * scale2)
     ctx.close()
+
+
+def test_wide_attitude_windows_at_the_edge_knots():
+    """The attitude window accumulators and window copies at the ends of each axis: a wide system
+    (20,000 knots per axis: the window forms) whose first 300 rows start at knot 0 and last 300 rows at
+    knot n_dfa - 4 (the last window, whose columns end the axis), so the fold's first and last windows
+    of every axis carry many products. The binary32 kernels and the fused pair against the oracle,
+    and aprod 2 run twice (its binary32 sums in L2 arrive in any order) agreeing within that bound."""
+    cfg = gsrgen.make_cfg(66, 2000, 100, 20000, 500)
+    h = gsrgen.generate(cfg, fp32=True)
+    knot = h.knot.copy()
+    knot[:300] = 0
+    knot[-300:] = cfg.n_dfa - 4
+    s = oracle.System(h.star_ptr, h.A, knot, h.instr, cfg.n_dfa, cfg.n_instr, cfg.n_glob)
+    b = oracle.rhs(s, h.x_true, h.eps)
+    ctx = context_for(h, fp32=True)
+    ctx.set_system(h.A32, knot, h.instr, b)
+    assert ctx.aprod2_plan()["passes"] == 3
+    u = 2.0 ** -24
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(s.n_cols).astype(np.float32).astype(np.float64)
+    y0 = rng.standard_normal(s.n_rows).astype(np.float32).astype(np.float64)
+    yd = torch.tensor(y0, dtype=torch.float32, device="cuda")
+    ctx.aprod1_f32(torch.tensor(x, dtype=torch.float32, device="cuda"), yd)
+    want = oracle.aprod1(s, x, y0.copy())
+    scale = oracle.aprod1(_abs_sys(s), np.abs(x), np.abs(y0).copy())
+    assert np.all(np.abs(yd.cpu().numpy() - want) <= 25 * u * scale)
+    y32 = torch.tensor(y0, dtype=torch.float32, device="cuda")
+    want2 = oracle.aprod2(s, y0, np.zeros(s.n_cols))
+    scale2 = oracle.aprod2(_abs_sys(s), np.abs(y0), np.zeros(s.n_cols))
+    runs = []
+    for _ in range(2):
+        zd = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+        ctx.aprod2_f32(y32, zd)
+        runs.append(zd.cpu().numpy())
+        assert np.all(np.abs(runs[-1] - want2) <= 2e3 * u * scale2)
+    assert np.all(np.abs(runs[0] - runs[1]) <= 4e3 * u * scale2)
+    a0 = s.blocks()["att"][0]
+    for ax in range(3):  # the first and the last column of each axis got contributions
+        for col in (a0 + ax * cfg.n_dfa, a0 + ax * cfg.n_dfa + cfg.n_dfa - 1):
+            assert scale2[col] > 0 and abs(runs[0][col] - want2[col]) <= 2e3 * u * scale2[col]
+    xs = rng.standard_normal(s.n_cols)
+    rd = torch.zeros(s.n_rows, dtype=torch.float32, device="cuda")
+    ctx.residual(torch.tensor(xs, device="cuda"), rd)
+    r_ref = b - oracle.aprod1(s, xs, np.zeros(s.n_rows))
+    rscale = oracle.aprod1(_abs_sys(s), np.abs(xs), np.abs(b).copy())
+    assert np.all(np.abs(rd.cpu().numpy() - r_ref) <= u * np.abs(r_ref) + 2.0 ** -40 * rscale)
+    ctx.close()
