@@ -488,20 +488,23 @@ def dominant_kernel(env, meta, kw, t):
     """Launches of each hot kernel in one step of a solver times their standalone time: the kernel that
     takes most of the step."""
     g = env.g
-    warm_aprod2 = 1 if kw.get("warm") else 0  # A^T b and the column norms of the warm start
+    warm_aprod2 = 1 if kw.get("warm") else 0  # the warm start's aprod 1 over the non-astrometric columns
     if kw.get("mode") == g.GSR_MIXED:
         m, its = meta["outer"], sum(meta["inner_iterations"])
-        n_res = m if kw.get("warm") else m - 1  # the cold start's first residual is b itself
+        # the first step's residual is b itself (cold) or the warm start's own (its astrometric residual and
+        # one aprod 1 over the other columns); the warm start's A^T b pass also gives the column norms, so
+        # it stands in for the norm pass (profiles/launches_c5.md)
+        n_res = m - 1
         if meta.get("fused"):  # the inner iterations take the fused pass; the starts, the norms and A^T b the aprod 2
             share = {"aprod12_f32": its * t["aprod12_f32"], "aprod1_f32": warm_aprod2 * t["aprod1_f32"],
-                     "aprod2_f32": (m + 1 + warm_aprod2) * t["aprod2_f32"], "residual_df": n_res * t["residual_df"]}
+                     "aprod2_f32": (m + 1) * t["aprod2_f32"], "residual_df": n_res * t["residual_df"]}
         else:
             share = {"aprod1_f32": (its + warm_aprod2) * t["aprod1_f32"],
-                     "aprod2_f32": (its + m + 1 + warm_aprod2) * t["aprod2_f32"],
+                     "aprod2_f32": (its + m + 1) * t["aprod2_f32"],
                      "residual_df": n_res * t["residual_df"]}
     else:
         k = meta["iterations"]
-        share = {"aprod1_f64": (k + warm_aprod2) * t["aprod1_f64"], "aprod2_f64": (k + 2 + warm_aprod2) * t["aprod2_f64"]}
+        share = {"aprod1_f64": (k + warm_aprod2) * t["aprod1_f64"], "aprod2_f64": (k + 2) * t["aprod2_f64"]}
     return max(share, key=share.get), share
 
 
