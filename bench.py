@@ -814,6 +814,8 @@ def run_profile(args):
         ops = {"aprod1_f32": lambda: ctx.aprod1_f32(x32, u32, stream=sh),
                "aprod2_f32": lambda: ctx.aprod2_f32(u32, z, stream=sh),
                "residual_df": lambda: ctx.residual(x, r32, stream=sh)}
+        if ctx.aprod2_plan()["passes"] == 3:  # the fused pass (y <- A x - 0.5 y, z += A^T y)
+            ops["aprod12_f32"] = lambda: ctx.aprod12_f32(x32, u32, z, -0.5, stream=sh)
     else:
         ops = {"aprod1_f64": lambda: ctx.aprod1(x, u, stream=sh), "aprod2_f64": lambda: ctx.aprod2(u, z, stream=sh)}
     for fn in ops.values():  # warm-up outside the profiled range (builds layouts, loads modules)

@@ -310,6 +310,9 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
 #pragma unroll
     for (int j = 0; j < NASTRO; ++j) acc[j] = acc2[j] = sacc[j] = sacc2[j] = (AT)0;
     int64_t k = t0 < S.n_tiles ? S.first_star[t0] : 0;  // the star of the current run
+    // a lane's R = 4 binary32 values of y in one 16-byte load where y is 16-byte aligned (the caller's
+    // vector may be a view at any offset; measured 12.75 -> 12.65 ms on 5e8 rows)
+    const bool y4 = (reinterpret_cast<uintptr_t>(y) & 15) == 0;
     for (int64_t t = t0; t < t1; ++t) {
         const uint8_t *tb = S.tiles + t * S.tile_bytes;
         // the one-pass form: the next tile of the warp's range into L2 (measured: 0.430 -> 0.422 ms
@@ -350,9 +353,21 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
         bool in[R];
         AT yr[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            in[i] = r0 + i < S.n_rows;
-            yr[i] = SQUARE ? (in[i] ? (AT)1 : (AT)0) : (in[i] ? (AT)y[r0 + i] : (AT)0);
+        for (int i = 0; i < R; ++i) in[i] = r0 + i < S.n_rows;
+        if constexpr (!SQUARE && R == 4 && sizeof(UT) == 4) {
+            if (y4 && r0 + R <= S.n_rows) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(y + r0));
+                yr[0] = (AT)v.x;
+                yr[1] = (AT)v.y;
+                yr[2] = (AT)v.z;
+                yr[3] = (AT)v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) yr[i] = in[i] ? (AT)y[r0 + i] : (AT)0;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) yr[i] = SQUARE ? (in[i] ? (AT)1 : (AT)0) : (in[i] ? (AT)y[r0 + i] : (AT)0);
         }
 #pragma unroll
         for (int i = 0; i < R; ++i) {

@@ -322,6 +322,57 @@ def test_aprod12_f32_vs_oracle(name):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", ["c1", "wide_ragged"])
+def test_f32_products_on_vectors_at_odd_offsets(name):
+    """The binary32 products on caller vectors that start 4 bytes past a 16-byte boundary (views at
+    offset 1 of larger buffers): the kernels' 16-byte row-vector loads and stores apply only to aligned
+    vectors, so these take the per-row path. aprod 1, aprod 2 and the fused pair against the oracle
+    with the bounds of the aligned tests."""
+    cfg = {"c1": gsrgen.workloads()["c1"].cfg, "wide_ragged": gsrgen.make_cfg(65, 4000, (1, 300), 20000, 40000)}[name]
+    h, s, b, ctx = _setup32(cfg)
+    u = 2.0 ** -24
+    rng = np.random.default_rng(29)
+    x = rng.standard_normal(s.n_cols).astype(np.float32).astype(np.float64)
+    y0 = rng.standard_normal(s.n_rows).astype(np.float32).astype(np.float64)
+    z0 = rng.standard_normal(s.n_cols)
+
+    def view(v, dtype):
+        buf = torch.zeros(v.size + 1, dtype=dtype, device="cuda")
+        buf[1:] = torch.tensor(v, dtype=dtype, device="cuda")
+        out = buf[1:]
+        assert out.data_ptr() % 16 == 4
+        return out
+
+    xd, yd = view(x, torch.float32), view(y0, torch.float32)
+    ctx.aprod1_f32(xd, yd)
+    torch.cuda.synchronize()
+    want = oracle.aprod1(s, x, y0)
+    scale = oracle.aprod1(_abs_sys(s), np.abs(x), np.abs(y0))
+    assert np.all(np.abs(yd.cpu().numpy().astype(np.float64) - want) <= 25 * u * scale)
+
+    yv = view(y0, torch.float32)
+    zd = torch.tensor(z0, device="cuda")
+    ctx.aprod2_f32(yv, zd)
+    torch.cuda.synchronize()
+    want2 = oracle.aprod2(s, y0, z0.copy())
+    scale2 = oracle.aprod2(_abs_sys(s), np.abs(y0), np.abs(z0).copy())
+    assert np.all(np.abs(zd.cpu().numpy() - want2) <= 2e3 * u * scale2)
+
+    coef = -0.75
+    yv = view(y0, torch.float32)
+    zd = torch.tensor(z0, device="cuda")
+    ctx.aprod12_f32(xd, yv, zd, coef)
+    torch.cuda.synchronize()
+    want = oracle.aprod1(s, x, coef * y0)
+    scale = oracle.aprod1(_abs_sys(s), np.abs(x), np.abs(coef * y0))
+    yn = yv.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yn - want) <= 25 * u * scale)
+    want2 = oracle.aprod2(s, yn, z0.copy())
+    scale2 = oracle.aprod2(_abs_sys(s), np.abs(yn), np.abs(z0).copy())
+    assert np.all(np.abs(zd.cpu().numpy() - want2) <= 2e3 * u * scale2)
+    ctx.close()
+
+
 def test_wide_attitude_windows_at_the_edge_knots():
     """The attitude window accumulators and window copies at the ends of each axis: a wide system
     (20,000 knots per axis: the window forms) whose first 300 rows start at knot 0 and last 300 rows at
