@@ -51,7 +51,8 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool SV = false, bool ATTW = false>
+template <typename VT, typename XT, typename UT, typename AT, bool LSQR, bool SV = false, bool ATTW = false,
+          bool XS = false>
 __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restrict__ x, UT *__restrict__ y,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
                                                 uint32_t *__restrict__ ymax)
@@ -71,6 +72,13 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const XT *__restrict__ xt = x + S.att0;
     const XT *__restrict__ xi = x + S.instr0;
+    // XS: x of the instrumental columns copied to shared memory, its 6 gathers a row shared-memory loads
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    XT *sm_xi = reinterpret_cast<XT *>(smem_raw);
+    if constexpr (XS) {
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_xi[i] = __ldg(xi + i);
+        __syncthreads();
+    }
     AT xg[MG];
 #pragma unroll
     for (int q = 0; q < MG; ++q) xg[q] = q < S.n_glob ? (AT)__ldg(x + S.glob0 + q) : (AT)0;
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
                     const AT xv = (AT)__ldg(j < G.ni ? xi + ic[j][i] : x);
                     v = fma(a[A_INS + j][i], j < G.ni ? xv : (AT)0, v);
                 } else {
-                    v = fma(a[A_INS + j][i], (AT)__ldg(xi + ic[j][i]), v);
+                    v = fma(a[A_INS + j][i], (AT)(XS ? sm_xi[ic[j][i]] : __ldg(xi + ic[j][i])), v);
                 }
             }
 #pragma unroll
@@ -792,7 +800,10 @@ __global__ void __launch_bounds__(256) k_aprod2_att(SysView<VT> S, const UT *__r
 // the registers and two resident blocks per SM, ran 40% slower on 5e8 rows: 31.6 vs 22.7 ms.)
 // LSQR: coef = -alpha/beta from the solver state (and nothing to do once it has stopped), the per-block
 // sums of squares of the new u into part; otherwise coef_arg, and part may be null.
-template <bool INSTR_SMEM, bool LSQR>
+// XS: the block also keeps x of the instrumental columns in shared memory (after its sums), so that
+// the 6 gathers a row makes of it are shared-memory loads: a random 4-byte gather from global memory
+// costs the L1 data pipe about one pass per lane, and that pipe, not DRAM, bounds this pass.
+template <bool INSTR_SMEM, bool LSQR, bool XS = false>
 __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const float *__restrict__ x,
                                                 float *__restrict__ y, double *__restrict__ z,
                                                 const LsqrState *__restrict__ st, double *__restrict__ part,
@@ -805,9 +816,13 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
     __shared__ float wred[8][NASTRO * 32];
     if (LSQR && st->done) return;
     const float coef = LSQR ? (float)st->coef_u : coef_arg;
+    static_assert(!XS || INSTR_SMEM, "x in shared memory follows the block's sums");
     float *sm_ins = reinterpret_cast<float *>(smem_raw);
+    float *sm_xi = sm_ins + S.n_instr;
     if (INSTR_SMEM)
         for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_ins[i] = 0.f;
+    if (XS)
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_xi[i] = __ldg(x + S.instr0 + i);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     float *wbuf = wred[threadIdx.x >> 5];
@@ -855,7 +870,7 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
                     v = fmaf(a[A_ATT + NPARAXIS * ax + 3][i], w.w, v);
                 }
 #pragma unroll
-                for (int j = 0; j < NINSTR; ++j) v = fmaf(a[A_INS + j][i], __ldg(xi + ic[j][i]), v);
+                for (int j = 0; j < NINSTR; ++j) v = fmaf(a[A_INS + j][i], XS ? sm_xi[ic[j][i]] : __ldg(xi + ic[j][i]), v);
                 v = fmaf(a[A_GLOB][i], xg, v);
                 const int64_t r = r0 + i;
                 in[i] = r < S.n_rows;
@@ -938,13 +953,13 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
     }
 }
 
-template <bool INSTR_SMEM, bool LSQR>
+template <bool INSTR_SMEM, bool LSQR, bool XS>
 __global__ void __launch_bounds__(256) k_iter_fused(SysView<float> S, const float *__restrict__ x,
                                                     float *__restrict__ y, double *__restrict__ z,
                                                     const LsqrState *__restrict__ st, double *__restrict__ part,
                                                     int64_t tiles_per_warp, float coef_arg)
 {
-    iter_fused_body<INSTR_SMEM, LSQR>(S, x, y, z, st, part, tiles_per_warp, coef_arg);
+    iter_fused_body<INSTR_SMEM, LSQR, XS>(S, x, y, z, st, part, tiles_per_warp, coef_arg);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -953,6 +968,8 @@ static constexpr size_t kSmemBudget = 100 * 1024;  // bytes of block-private acc
 // the pass that sums products and squares together (the warm start's, once per solve) keeps its
 // block-private accumulators in shared memory up to one block per SM
 static constexpr size_t kSmemBudgetBoth = 200 * 1024;
+// aprod 1 of a wide attitude block keeps x of the instrumental columns in shared memory
+static constexpr bool kAprod1Xs = true;
 
 template <typename KernelT>
 static int persistent_blocks(const gsr_ctx *c, KernelT kern, size_t dyn_smem)
@@ -991,8 +1008,12 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
                             cudaStream_t s, int *grid_out)
 {
     const SysView<VT> S = view<VT>(c);
-    auto pick = [&](auto kern) -> cudaError_t {
-        const int g = persistent_blocks(c, kern, 0);
+    auto pick = [&](auto kern, size_t dyn) -> cudaError_t {
+        if (dyn > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+        }
+        const int g = persistent_blocks(c, kern, dyn);
         if (grid_out) {
             *grid_out = g;
             return cudaSuccess;
@@ -1000,17 +1021,17 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
         if (!x || !y) return cudaErrorInvalidValue;
         // the inner iteration's star pass reads max |u| (fixed-point instrumental sums)
         uint32_t *ymax = (sizeof(AT) == 4 && st) ? fx_ymax(c) : nullptr;
-        kern<<<g, kThreads, 0, s>>>(S, (const XT *)x, (UT *)y, st, part, ymax);
+        kern<<<g, kThreads, dyn, s>>>(S, (const XT *)x, (UT *)y, st, part, ymax);
         return cudaGetLastError();
     };
     if (c->sv) {  // a section variant (run-time section geometry)
-        if (st) return pick(k_aprod1<VT, XT, UT, AT, true, true>);
-        return pick(k_aprod1<VT, XT, UT, AT, false, true>);
+        if (st) return pick(k_aprod1<VT, XT, UT, AT, true, true>, 0);
+        return pick(k_aprod1<VT, XT, UT, AT, false, true>, 0);
     }
     if constexpr (sizeof(XT) == 4 && sizeof(VT) == 4) {
         if (att_window(c)) {
             // wide attitude block: the window copy of x first (a few MB, stays in L2), then one 16-byte
-            // gather per axis and row
+            // gather per axis and row; x of the instrumental columns in shared memory where it fits
             if (!grid_out) {
                 if (!x) return cudaErrorInvalidValue;
                 k_att_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(
@@ -1018,12 +1039,17 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
                 const cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) return e;
             }
-            if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, true>);
-            return pick(k_aprod1<VT, XT, UT, AT, false, false, true>);
+            const size_t dxs = sizeof(XT) * (size_t)c->n_instr;
+            if (kAprod1Xs && dxs <= kSmemBudget) {
+                if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, true, true>, dxs);
+                return pick(k_aprod1<VT, XT, UT, AT, false, false, true, true>, dxs);
+            }
+            if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, true>, 0);
+            return pick(k_aprod1<VT, XT, UT, AT, false, false, true>, 0);
         }
     }
-    if (st) return pick(k_aprod1<VT, XT, UT, AT, true>);
-    return pick(k_aprod1<VT, XT, UT, AT, false>);
+    if (st) return pick(k_aprod1<VT, XT, UT, AT, true>, 0);
+    return pick(k_aprod1<VT, XT, UT, AT, false>, 0);
 }
 
 static cudaError_t aprod1_dispatch(const gsr_ctx *c, const void *x, void *y, const LsqrState *st, double *part,
@@ -1233,9 +1259,13 @@ cudaError_t launch_iter_fused(const gsr_ctx *c, const float *pv, float *u, doubl
                               double *part, cudaStream_t s, int *grid_out, float coef)
 {
     const bool ins = sizeof(float) * (size_t)c->n_instr <= kSmemBudget;
-    auto kern = st ? (ins ? k_iter_fused<true, true> : k_iter_fused<false, true>)
-                   : (ins ? k_iter_fused<true, false> : k_iter_fused<false, false>);
-    const size_t dyn = ins ? sizeof(float) * (size_t)c->n_instr : 0;
+    // the instrumental x beside the sums where both fit (the pass runs one block per SM either way)
+    const bool xs = ins && 2 * sizeof(float) * (size_t)c->n_instr <= kSmemBudgetBoth;
+    auto kern = st ? (xs ? k_iter_fused<true, true, true> : ins ? k_iter_fused<true, true, false>
+                                                                : k_iter_fused<false, true, false>)
+                   : (xs ? k_iter_fused<true, false, true> : ins ? k_iter_fused<true, false, false>
+                                                                 : k_iter_fused<false, false, false>);
+    const size_t dyn = (xs ? 2 : ins ? 1 : 0) * sizeof(float) * (size_t)c->n_instr;
     if (dyn > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;

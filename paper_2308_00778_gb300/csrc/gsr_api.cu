@@ -746,13 +746,13 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     bool x0_dev = false;
     int r0_parts = 0;  // mixed solve from a warm start on binary32 storage: the start's residual is ready
     double ms_warm = 0.0;
+    gsr_net *net = nullptr;
     if (prm.warm != GSR_WARM_NONE) {
         if ((e = cudaEventRecord(c->ev_w0, c->own)) != cudaSuccess) return cuda_fail(c, e, "warm start");
         gsr_status rw = ensure_workspace(c);
         if (rw != GSR_OK) return rw;
         if (!c->ws.x0w && (e = cudaMalloc(&c->ws.x0w, sizeof(double) * (size_t)c->n_cols)) != cudaSuccess)
             return cuda_fail(c, e, "warm-start vector");
-        gsr_net *net = nullptr;
         if (prm.warm == GSR_WARM_LEARNED) {
             if (!c->warm_net || c->warm_path != prm.weights_path) {
                 if (c->warm_net) gsr_net_destroy(c->warm_net);
@@ -795,5 +795,8 @@ GSR_API gsr_status gsr_lsqr_solve(gsr_ctx *c, const gsr_solve_params *params, co
     // the caller's stream continues after the solve's last kernel
     if (cudaEventRecord(c->ev, c->own) == cudaSuccess) cudaStreamWaitEvent((cudaStream_t)stream, c->ev, 0);
     cudaGetLastError();
+    // the solve has synchronised: a network convolution whose tensor-core wait ran out has reported it
+    if (net && net_take_fault(net) && (rc == GSR_OK || rc == GSR_ETIMEOUT))
+        return fail(c, GSR_ECUDA, "warm start: a tensor-core wait of the network timed out");
     return rc;
 }

@@ -295,6 +295,8 @@ void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_c
 // r0_parts (may be null): for binary32 storage the residual of x0 is also left in ws.u32, in
 // binary32, with its per-block sums of squares in ws.part_u (*r0_parts partials; 0 when not)
 gsr_status warm_start_dev(gsr_ctx *c, gsr_net *net, double *x0, cudaStream_t s, int *r0_parts);
+// a convolution of the net found its tensor-core wait run out since the last look (then cleared)
+bool net_take_fault(gsr_net *n);
 // mixed-precision solver (mixed.cu)
 gsr_status residual_f32(gsr_ctx *c, const double *x, float *r, cudaStream_t s);
 // window: the attitude gathers read the context's window copy (split_launch with window built it);

@@ -2,11 +2,13 @@
 // attitude knots (6 -> 64 -> 64 -> 64 -> 64 -> 64 -> 3 channels, kernel 5, zero
 // padding 2, ReLU after the first five), trained and evaluated on the GPU.
 //
-// Each convolution is an implicit GEMM on the BF16 tensor cores
-// (mma.sync.m16n8k16, FP32 accumulation):
+// Each convolution is an implicit GEMM on the BF16 tensor cores with FP32 accumulation:
 //   forward      out[p][co]   = sum_{t,ci} W[co][ci][t] in[p+t-2][ci]        M = positions, N = co, K = 5*Cin
 //   backward x   dIn[p][ci]   = sum_{t,co} W[co][ci][4-t] dOut[p+t-2][co]    the same kernel, flipped weights
 //   backward W   dW[co][t,ci] = sum_p dOut[p][co] in[p+t-2][ci]               M = co, N = 5*Cin, K = positions
+// The forward and backward-data products (k_conv) issue tcgen05 MMAs from shared memory into a
+// TMEM accumulator (tc.cuh); the weight gradient (k_conv_wgrad, training only) uses warp-level
+// mma.sync fragments.
 // Activations are position-major bf16 [B][L][C] with C padded to a multiple
 // of 16 (the first layer's 6 input channels and the last layer's 3 output
 // channels to 16). FP32 master weights are updated with Adam and copied to
@@ -22,6 +24,7 @@
 
 #include "../../include/gsr_warm.h"
 #include "gsr_internal.cuh"
+#include "tc.cuh"
 
 #define GSR_API extern "C" __attribute__((visibility("default")))
 
@@ -60,93 +63,149 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 // ---------------------------------------------------------------- convolution (forward / backward-data)
 enum { CONV_RELU = 0, CONV_LAST = 1, CONV_BWD = 2, CONV_RAW = 3 };
 
-constexpr int CONV_POS = 64;  // positions per block (4 warps x 16)
+// The convolution as one tcgen05 MMA chain per CTA: M = 128 positions (one TMEM lane each), N =
+// COUT, K = 5 CIN in steps of 16 (one tap and 16 input channels per MMA). The CTA stages its 132
+// input rows (positions p0-2 .. p0+129, zero outside [0, L)) and the weights in shared memory as
+// 8-row x 16-byte core matrices, so that the operand of tap t is the input block shifted by t rows
+// (16 bytes further on): no im2col copy. One thread issues the 5 CIN/16 MMAs; their completion
+// arrives on an mbarrier; every warp then reads its 32 rows of the FP32 accumulator from TMEM.
+constexpr int CONV_POS = 128;               // positions per CTA: the MMA's M
+constexpr uint32_t CONV_TMEM_COLS = 128;    // accumulator columns allocated (>= COUT, a power of two)
+constexpr uint64_t CONV_WAIT_NS = 1000000000ull;  // the longest wait for the MMAs (1 s), then a fault
 
-// in: bf16 [B][L][CIN]; Bm: bf16 [COUT][5*CIN]. MODE:
+template <int CIN, int COUT>
+struct ConvSmem {
+    static constexpr int ROWS = CONV_POS + 4;                 // input rows p0-2 .. p0+CONV_POS+1
+    static constexpr int K = KW * CIN;
+    static constexpr uint32_t A_CHUNK = ROWS * 16;            // one 8-channel column of the input rows
+    static constexpr uint32_t A_BYTES = (CIN / 8) * A_CHUNK;
+    static constexpr uint32_t B_CHUNK = COUT * 16;            // one 8-wide K column of the weights
+    static constexpr uint32_t B_BYTES = (K / 8) * B_CHUNK;
+    static constexpr uint32_t B_OFF = (A_BYTES + 127) / 128 * 128;
+    static constexpr uint32_t CTRL_OFF = (B_OFF + B_BYTES + 127) / 128 * 128;  // mbarrier, TMEM address
+    static constexpr uint32_t USED = CTRL_OFF + 16;
+    // at least 72 KB: at most 3 CTAs per SM, whose 3 x 128 TMEM columns fit the SM's 512, so the
+    // allocation never waits for another CTA
+    static constexpr uint32_t BYTES = USED > 73728 ? USED : 73728;
+};
+
+// in: bf16 [B][L][CIN]; Bm: bf16 [COUT][5*CIN] (tap-major K). MODE:
 //   CONV_RELU: out16 = bf16(relu(acc + bias))                     [B][L][COUT]
 //   CONV_LAST: out32 = acc + bias (fp32)                          [B][L][COUT]
 //   CONV_BWD : v = acc * (mask > 0): out32 = v, out16 = bf16(v)   [B][L][COUT]
 //   CONV_RAW : out32 = acc (fp32)                                  [B][L][COUT]
+// fault: set to 1 when the MMAs did not complete within CONV_WAIT_NS (outputs of the CTA unwritten).
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16 *__restrict__ in, int64_t L,
                                               const __nv_bfloat16 *__restrict__ Bm, const float *__restrict__ bias,
                                               const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ out16,
-                                              float *__restrict__ out32)
+                                              float *__restrict__ out32, int32_t *__restrict__ fault)
 {
-    constexpr int K = KW * CIN;
-    constexpr int IS = CIN + 8;  // padded row strides (bank-conflict-free fragment loads)
-    constexpr int BS = K + 8;
-    constexpr int NT = COUT / 8;
-    extern __shared__ __align__(16) unsigned char conv_smem[];
-    __nv_bfloat16 *s_in = reinterpret_cast<__nv_bfloat16 *>(conv_smem);  // (CONV_POS + 4) * IS
-    __nv_bfloat16 *s_b = s_in + (CONV_POS + 4) * IS;                       // COUT * BS
+    using SM = ConvSmem<CIN, COUT>;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= (int)CONV_TMEM_COLS, "MMA shape");
+    extern __shared__ __align__(1024) unsigned char conv_smem[];
+    unsigned char *sA = conv_smem;
+    unsigned char *sB = conv_smem + SM::B_OFF;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(conv_smem + SM::CTRL_OFF);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(conv_smem + SM::CTRL_OFF + 8);
+    const int warp = threadIdx.x >> 5;
     const int64_t b = blockIdx.y;
     const int64_t p0 = (int64_t)blockIdx.x * CONV_POS;
     const __nv_bfloat16 *inb = in + b * L * CIN;
-    // stage the input rows p0-2 .. p0+65 (zero outside [0, L)) and the weights
-    for (int i = threadIdx.x; i < (CONV_POS + 4) * CIN; i += blockDim.x) {
-        const int r = i / CIN, c = i % CIN;
+    if (warp == 0) tc::tmem_alloc(tslot, CONV_TMEM_COLS);
+    if (threadIdx.x == 32) tc::mbar_init(mbar, 1);
+    // input rows: row r (position p0 - 2 + r), channels 8j .. 8j+7 at sA + j A_CHUNK + 16 r
+    constexpr int CJ = CIN / 8;
+    for (int i = threadIdx.x; i < SM::ROWS * CJ; i += blockDim.x) {
+        const int r = i / CJ, j = i % CJ;
         const int64_t p = p0 - 2 + r;
-        s_in[r * IS + c] = (p >= 0 && p < L) ? inb[p * CIN + c] : __float2bfloat16_rn(0.f);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (p >= 0 && p < L) v = *reinterpret_cast<const uint4 *>(inb + p * CIN + 8 * j);
+        *reinterpret_cast<uint4 *>(sA + j * SM::A_CHUNK + r * 16) = v;
     }
-    for (int i = threadIdx.x; i < COUT * K; i += blockDim.x) s_b[(i / K) * BS + (i % K)] = Bm[i];
+    // weights: output channel n, K columns 8j .. 8j+7 at sB + j B_CHUNK + 16 n
+    constexpr int KJ = SM::K / 8;
+    for (int i = threadIdx.x; i < COUT * KJ; i += blockDim.x) {
+        const int n = i / KJ, j = i % KJ;
+        *reinterpret_cast<uint4 *>(sB + j * SM::B_CHUNK + n * 16) =
+            *reinterpret_cast<const uint4 *>(Bm + (int64_t)n * SM::K + 8 * j);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const int wr = warp * 16;  // first position (relative to p0) of this warp's 16 rows
-    float acc[NT][4];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-    for (int t = 0; t < KW; ++t) {
-#pragma unroll
-        for (int c0 = 0; c0 < CIN; c0 += 16) {
-            // A: rows = positions wr..wr+15 at tap t (smem row wr + r + t), cols = channels c0..c0+15
-            const __nv_bfloat16 *ra = s_in + (wr + g + t) * IS + c0 + 2 * tq;
-            const __nv_bfloat16 *rb = s_in + (wr + g + 8 + t) * IS + c0 + 2 * tq;
-            uint32_t a[4];
-            a[0] = *reinterpret_cast<const uint32_t *>(ra);
-            a[1] = *reinterpret_cast<const uint32_t *>(rb);
-            a[2] = *reinterpret_cast<const uint32_t *>(ra + 8);
-            a[3] = *reinterpret_cast<const uint32_t *>(rb + 8);
-            const int k0 = t * CIN + c0;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const __nv_bfloat16 *bb = s_b + (n * 8 + g) * BS + k0 + 2 * tq;
-                uint32_t bf[2];
-                bf[0] = *reinterpret_cast<const uint32_t *>(bb);
-                bf[1] = *reinterpret_cast<const uint32_t *>(bb + 8);
-                mma_bf16(acc[n], a, bf);
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    if (threadIdx.x == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(CONV_POS, COUT);
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll 1
+        for (int t = 0; t < KW; ++t)
+#pragma unroll 1
+            for (int c = 0; c < CIN / 16; ++c) {
+                // A: positions p0 .. p0+127 at tap t (input rows t .. t+127), channels 16c .. 16c+15
+                const uint64_t ad = tc::smem_desc(a0 + 2 * c * SM::A_CHUNK + 16 * t, SM::A_CHUNK, 128);
+                // B: K columns t CIN + 16c .. +15 of every output channel
+                const uint64_t bd = tc::smem_desc(b0 + ((t * CIN + 16 * c) / 8) * SM::B_CHUNK, SM::B_CHUNK, 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, t > 0 || c > 0);
             }
-        }
+        tc::mma_commit(mbar);
     }
-    // epilogue: C fragment (row g / g+8 = position, col 2tq / 2tq+1 = channel)
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t p = p0 + wr + g + 8 * h;
+    // the same verdict for every thread: the TMEM loads below are warp-collective
+    const bool ok = __syncthreads_and(tc::mbar_wait(mbar, 0, CONV_WAIT_NS));
+    tc::fence_after_sync();
+    if (ok) {
+        const int m = threadIdx.x;  // accumulator row = TMEM lane = position p0 + m
+        const int64_t p = p0 + m;
+        const int64_t o = (b * L + p) * COUT;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int n0 = 0; n0 < COUT; n0 += 16) {
+            float v[16];
+            tc::tmem_ld16(lane_addr + (uint32_t)n0, v);
             if (p >= L) continue;
+            if (MODE == CONV_RELU || MODE == CONV_LAST) {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int co = n * 8 + 2 * tq + e;
-                float v = acc[n][2 * h + e];
-                const int64_t o = (b * L + p) * COUT + co;
-                if (MODE == CONV_RELU) {
-                    v += bias[co];
-                    out16[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
-                } else if (MODE == CONV_LAST) {
-                    out32[o] = v + bias[co];
-                } else if (MODE == CONV_RAW) {
-                    out32[o] = v;
-                } else {
-                    v = (__bfloat162float(mask[o]) > 0.f) ? v : 0.f;
-                    out32[o] = v;
-                    out16[o] = __float2bfloat16_rn(v);
+                for (int e = 0; e < 16; ++e) v[e] += bias[n0 + e];
+            }
+            if (MODE == CONV_BWD) {
+                const uint4 *mk = reinterpret_cast<const uint4 *>(mask + o + n0);
+                const uint4 mv[2] = {mk[0], mk[1]};
+                const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(mv);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = __bfloat162float(mb[e]) > 0.f ? v[e] : 0.f;
+            }
+            if (MODE == CONV_RELU || MODE == CONV_BWD) {
+                uint4 w[2];
+                uint32_t *wp = reinterpret_cast<uint32_t *>(w);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float lo = v[2 * e], hi = v[2 * e + 1];
+                    if (MODE == CONV_RELU) {
+                        lo = lo > 0.f ? lo : 0.f;
+                        hi = hi > 0.f ? hi : 0.f;
+                    }
+                    wp[e] = pack2(__float2bfloat16_rn(lo), __float2bfloat16_rn(hi));
                 }
+                uint4 *dst = reinterpret_cast<uint4 *>(out16 + o + n0);
+                dst[0] = w[0];
+                dst[1] = w[1];
+            }
+            if (MODE != CONV_RELU) {
+                float4 *dst = reinterpret_cast<float4 *>(out32 + o + n0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
+    } else if (threadIdx.x == 0) {
+        atomicExch(fault, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        // after a timeout, give the MMAs one more bounded wait before their TMEM is released
+        if (!ok) tc::mbar_wait(mbar, 0, CONV_WAIT_NS);
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, CONV_TMEM_COLS);
     }
 }
 
@@ -390,6 +449,9 @@ struct gsr_net {
     float *d32 = nullptr;             // output gradient fp32 [pos][64]
     __nv_bfloat16 *d16a = nullptr, *d16b = nullptr;  // output gradients bf16 [pos][64] (ping-pong)
     double *loss = nullptr;
+    // set by a convolution whose tensor-core wait ran out (mapped pinned word and its device alias);
+    // read and cleared by the next call on the net, and by a solve that ran the net
+    int32_t *fault_h = nullptr, *fault_d = nullptr;
     int step = 0;
     std::string err;
 };
@@ -451,23 +513,23 @@ static cudaError_t refresh_operands(gsr_net *n, bool update, float lr, cudaStrea
 
 template <int CIN, int COUT, int MODE>
 static void conv_launch(dim3 grid, const __nv_bfloat16 *in, int64_t L, const __nv_bfloat16 *Bm, const float *bias,
-                        const __nv_bfloat16 *mask, __nv_bfloat16 *out16, float *out32, cudaStream_t s)
+                        const __nv_bfloat16 *mask, __nv_bfloat16 *out16, float *out32, int32_t *fault, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(__nv_bfloat16) * ((CONV_POS + 4) * (CIN + 8) + COUT * (KW * CIN + 8));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-    k_conv<CIN, COUT, MODE><<<grid, 128, smem, s>>>(in, L, Bm, bias, mask, out16, out32);
+    constexpr uint32_t smem = ConvSmem<CIN, COUT>::BYTES;
+    // the opt-in above 48 KB of shared memory (per device: set on every launch)
+    cudaFuncSetAttribute(k_conv<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_conv<CIN, COUT, MODE><<<grid, 128, smem, s>>>(in, L, Bm, bias, mask, out16, out32, fault);
 }
 
 // forward of the whole net on act[0] (already packed); fills act[1..5] and y8
 static cudaError_t net_forward_packed(gsr_net *n, int64_t B, int64_t L, cudaStream_t s)
 {
     const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
-    conv_launch<16, 64, CONV_RELU>(grid, n->act[0], L, n->Bf[0], n->b[0], nullptr, n->act[1], nullptr, s);
+    conv_launch<16, 64, CONV_RELU>(grid, n->act[0], L, n->Bf[0], n->b[0], nullptr, n->act[1], nullptr, n->fault_d, s);
     for (int l = 1; l < NLAYER - 1; ++l)
-        conv_launch<64, 64, CONV_RELU>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, n->act[l + 1], nullptr, s);
+        conv_launch<64, 64, CONV_RELU>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, n->act[l + 1], nullptr, n->fault_d, s);
     conv_launch<64, 16, CONV_LAST>(grid, n->act[NLAYER - 1], L, n->Bf[NLAYER - 1], n->b[NLAYER - 1], nullptr,
-                                   nullptr, n->y8, s);
+                                   nullptr, n->y8, n->fault_d, s);
     return cudaGetLastError();
 }
 
@@ -500,9 +562,9 @@ static void backward_layer(gsr_net *n, int l, const __nv_bfloat16 *dcur, __nv_bf
     if (l > 0) {
         const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
         if (l == NLAYER - 1)
-            conv_launch<16, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, s);
+            conv_launch<16, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, n->fault_d, s);
         else
-            conv_launch<64, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, s);
+            conv_launch<64, 64, CONV_BWD>(grid, dcur, L, n->Bb[l], nullptr, n->act[l], dnext, n->d32, n->fault_d, s);
     }
 }
 
@@ -538,7 +600,7 @@ static cudaError_t layer_fwd_t(gsr_net *n, int l, const float *in, int64_t B, in
     const int64_t P = B * L;
     k_pack_any<<<grid_n(P * CINP), 256, 0, s>>>(in, P, CH(l), CINP, n->act[l], nullptr);
     const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
-    conv_launch<CINP, COUTP, CONV_LAST>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, nullptr, n->d32, s);
+    conv_launch<CINP, COUTP, CONV_LAST>(grid, n->act[l], L, n->Bf[l], n->b[l], nullptr, nullptr, n->d32, n->fault_d, s);
     k_unpack_any<<<grid_n(P * CH(l + 1)), 256, 0, s>>>(n->d32, P, CH(l + 1), COUTP, out);
     return cudaGetLastError();
 }
@@ -563,7 +625,7 @@ static cudaError_t layer_bwd_t(gsr_net *n, int l, const float *in, const float *
         return e;
     if (din) {  // the flipped-weight product, unmasked, fp32 (after the bias gradient has read d32)
         const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
-        conv_launch<COUTP, CINP, CONV_RAW>(grid, n->d16a, L, n->Bb[l], nullptr, nullptr, nullptr, n->d32, s);
+        conv_launch<COUTP, CINP, CONV_RAW>(grid, n->d16a, L, n->Bb[l], nullptr, nullptr, nullptr, n->d32, n->fault_d, s);
         k_unpack_any<<<grid_n(P * CH(l)), 256, 0, s>>>(n->d32, P, CH(l), CINP, din);
     }
     // leave the accumulators zero for training
@@ -577,6 +639,23 @@ static gsr_status net_fail(gsr_net *n, gsr_status st, const std::string &m)
 {
     if (n) n->err = m;
     return st;
+}
+
+// true (and cleared) when a convolution launched earlier on this net found its tensor-core wait
+// run out; the word is written by kernels that have finished, so a caller that synchronised after
+// the launches sees all of them
+bool net_take_fault(gsr_net *n)
+{
+    if (!n || !n->fault_h) return false;
+    volatile int32_t *f = n->fault_h;
+    if (*f == 0) return false;
+    *f = 0;
+    return true;
+}
+
+static gsr_status net_fault_status(gsr_net *n)
+{
+    return net_take_fault(n) ? net_fail(n, GSR_ECUDA, "an earlier call's tensor-core wait timed out") : GSR_OK;
 }
 
 }  // namespace gsr
@@ -598,6 +677,7 @@ GSR_API gsr_status gsr_net_destroy(gsr_net *n)
         cudaFree(n->Bb[l]);
     }
     cudaFree(n->loss);
+    cudaFreeHost(n->fault_h);
     cudaGetLastError();
     delete n;
     return GSR_OK;
@@ -625,6 +705,10 @@ GSR_API gsr_status gsr_net_create(gsr_net **out, int32_t device)
         if (e == cudaSuccess && (e = cudaMalloc(&n->Bb[l], os)) == cudaSuccess) e = cudaMemset(n->Bb[l], 0, os);
     }
     if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
+    if (e == cudaSuccess && (e = cudaHostAlloc(&n->fault_h, sizeof(int32_t), cudaHostAllocMapped)) == cudaSuccess) {
+        *n->fault_h = 0;
+        e = cudaHostGetDevicePointer(&n->fault_d, n->fault_h, 0);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         gsr_net_destroy(n);
@@ -684,6 +768,7 @@ GSR_API gsr_status gsr_net_get_params(gsr_net *n, float *params, int64_t count)
 GSR_API gsr_status gsr_net_forward(gsr_net *n, const float *in, int64_t batch, int64_t len, float *out, void *stream)
 {
     if (!n || !in || !out || batch < 1 || len < 1) return GSR_EINVAL;
+    if (const gsr_status f = net_fault_status(n); f != GSR_OK) return f;
     cudaError_t e = cudaSetDevice(n->device);
     if (e == cudaSuccess) e = net_forward_dev(n, in, batch, len, out, (cudaStream_t)stream);
     if (e != cudaSuccess) {
@@ -698,6 +783,7 @@ GSR_API gsr_status gsr_net_train_step(gsr_net *n, const float *in, const float *
                                       float lr, double *loss, void *stream)
 {
     if (!n || !in || !target || batch < 1 || len < 1 || !(lr >= 0.f)) return GSR_EINVAL;
+    if (const gsr_status f = net_fault_status(n); f != GSR_OK) return f;
     cudaError_t e = cudaSetDevice(n->device);
     if (e == cudaSuccess) e = net_train_dev(n, in, target, batch, len, lr, loss, (cudaStream_t)stream);
     if (e != cudaSuccess) {
@@ -715,6 +801,7 @@ GSR_API gsr_status gsr_net_gradients(gsr_net *n, const float *in, const float *t
                                      float *grads, int64_t count, double *loss, void *stream)
 {
     if (!n || !in || !target || !grads || batch < 1 || len < 1) return GSR_EINVAL;
+    if (const gsr_status f = net_fault_status(n); f != GSR_OK) return f;
     if (count != total_params()) return net_fail(n, GSR_EINVAL, "parameter count mismatch");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(n->device);
@@ -758,13 +845,14 @@ GSR_API gsr_status gsr_net_gradients(gsr_net *n, const float *in, const float *t
         cudaGetLastError();
         return net_fail(n, GSR_ECUDA, std::string("gradients: ") + cudaGetErrorString(e));
     }
-    return GSR_OK;
+    return net_fault_status(n);  // this call's own convolutions have finished
 }
 
 GSR_API gsr_status gsr_net_layer_forward(gsr_net *n, int32_t layer, const float *in, int64_t batch, int64_t len,
                                          float *out, void *stream)
 {
     if (!n || !in || !out || batch < 1 || len < 1 || layer < 0 || layer >= NLAYER) return GSR_EINVAL;
+    if (const gsr_status f = net_fault_status(n); f != GSR_OK) return f;
     const cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(n->device);
     if (e == cudaSuccess) e = net_reserve(n, batch * len);
@@ -788,6 +876,7 @@ GSR_API gsr_status gsr_net_layer_backward(gsr_net *n, int32_t layer, const float
                                           int64_t len, float *din, float *dW, float *db, void *stream)
 {
     if (!n || !in || !dout || !dW || !db || batch < 1 || len < 1 || layer < 0 || layer >= NLAYER) return GSR_EINVAL;
+    if (const gsr_status f = net_fault_status(n); f != GSR_OK) return f;
     const cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(n->device);
     if (e == cudaSuccess) e = net_reserve(n, batch * len);
