@@ -714,9 +714,9 @@ def measure_workload(env, args, name, headline_mode):
     return out
 
 
-# whether the library's default (gsr_solve_params.inner_fused = 0) runs the inner iterations of a form-3
-# system as the fused pass (it does not: the fused pass is opt-in, inner_fused = 1)
-FUSED_DEFAULT = False
+# whether the library's default (gsr_solve_params.inner_fused = 1) runs the inner iterations of a form-3
+# system as the fused pass (it does)
+FUSED_DEFAULT = True
 
 # stars of the CPU baseline's sample per workload (about 10-30 s of oracle work on the host cores)
 CPU_SAMPLE_STARS = {"c5": 80_000, "c3": 100_000, "c2": 100_000}

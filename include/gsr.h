@@ -308,6 +308,22 @@ gsr_status gsr_residual_static(gsr_ctx *ctx, const double *x, float *r, void *st
  */
 gsr_status gsr_fp64_fma_rate(int32_t device, double *tflops);
 
+/*
+ * gsr_tc_wait_check -- exercises the tensor-core kernels' bounded wait on its
+ * timeout path: one CTA of 128 threads allocates 32 TMEM columns, waits on an
+ * mbarrier that nothing arrives on for limit_ms, records whether the wait
+ * gave up, releases the TMEM and exits (what the network's convolution does
+ * when its MMAs have not completed within 1 s: it sets its net's fault word,
+ * which the next call on the net, or the solve that ran it, reports as
+ * GSR_ECUDA). Synchronous, on the default stream of `device`; the context
+ * stays usable afterwards.
+ *   limit_ms   in (0, 2000].
+ *   timed_out  1 if the wait gave up (the expected result), 0 if it completed.
+ *   waited_ms  the kernel's duration (CUDA events).
+ * Errors: GSR_EINVAL (bad limit or null output), GSR_ECUDA.
+ */
+gsr_status gsr_tc_wait_check(int32_t device, double limit_ms, int32_t *timed_out, double *waited_ms);
+
 typedef struct {
     int32_t itnlim;     /* maximum LSQR iterations (>= 0)                               */
     double atol, btol;  /* Paige-Saunders tolerances (0 disables the test)              */
@@ -341,9 +357,9 @@ typedef struct {
                                aprod 2 (gsr_aprod2_plan passes 3): each inner iteration's
                                aprod 1 and aprod 2 in one pass over the row tiles, the new u's
                                contributions to A^T u added while its coefficients are in
-                               registers (4-6% faster per iteration on 2e8-5e8 rows, but
-                               latency-bound at one block per SM). 1 = on; 0 (default) or
-                               -1 = the two separate passes                                  */
+                               registers (13% faster per iteration than the two passes on
+                               5e8 rows). 1 (default) = on; 0 or -1 = the two separate
+                               passes                                                        */
 } gsr_solve_params;
 
 typedef struct {

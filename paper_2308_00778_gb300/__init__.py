@@ -16,6 +16,7 @@ from .gsr import (  # noqa: F401
     gsr_net_gradients, gsr_net_get_params, gsr_net_last_error, gsr_net_load, gsr_net_num_params, gsr_net_save,
     gsr_net_set_params, gsr_net_train_step, gsr_warm_features, gsr_warm_start, gsr_net_layer_forward,
     gsr_net_layer_backward, gsr_net_apply_gradients, gsr_fp64_fma_rate, dfma_probe_tflops, gsr_aprod12_f32,
+    gsr_tc_wait_check, tc_wait_check,
 )
 
 #: trained warm-start network shipped with the package (``python -m paper_2308_00778_gb300.train``

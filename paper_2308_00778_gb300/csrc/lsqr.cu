@@ -558,7 +558,7 @@ void default_params(gsr_solve_params *p)
     p->max_outer = 0;
     p->inner_itn_next = 0;
     p->refine_grad = 0;
-    p->inner_fused = 0;
+    p->inner_fused = 1;
 }
 
 // p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in

@@ -108,6 +108,7 @@ def lib():
             "gsr_residual_static": (I32, [P, P, P, P]),
             "gsr_default_params": (None, [ctypes.POINTER(SolveParams)]),
             "gsr_fp64_fma_rate": (I32, [I32, P]),
+            "gsr_tc_wait_check": (I32, [I32, ctypes.c_double, P, P]),
             "gsr_net_num_params": (I64, []),
             "gsr_net_create": (I32, [ctypes.POINTER(P), I32]),
             "gsr_net_destroy": (I32, [P]),
@@ -306,6 +307,19 @@ def gsr_warm_start(ctx, net, x0, stream=0):
 
 def gsr_fp64_fma_rate(device, tflops_ptr):
     return lib().gsr_fp64_fma_rate(device, tflops_ptr or None)
+
+
+def gsr_tc_wait_check(device, limit_ms, timed_out_ptr, waited_ms_ptr):
+    return lib().gsr_tc_wait_check(device, limit_ms, timed_out_ptr or None, waited_ms_ptr or None)
+
+
+def tc_wait_check(device=0, limit_ms=20.0):
+    """(timed_out, waited_ms) of the tensor-core kernels' bounded wait run out on purpose."""
+    t, w = ctypes.c_int32(), ctypes.c_double()
+    st = gsr_tc_wait_check(device, limit_ms, ctypes.addressof(t), ctypes.addressof(w))
+    if st != 0:
+        raise GsrError(st, "gsr_tc_wait_check failed")
+    return t.value, w.value
 
 
 def dfma_probe_tflops(device=0) -> float:

@@ -100,7 +100,7 @@ def test_layer_forward_backward_vs_mirrored_oracle(layer):
     net = g.Net()
     net.set_params(flat)
     cin, cout = LAYERS[layer]
-    B, L = 2, 131  # three 64-position blocks, the last one ragged
+    B, L = 2, 300  # three 128-position CTAs of the convolution, the last one ragged
     x = rng.standard_normal((B, L, cin)).astype(np.float32)
     if layer > 0:
         x = np.maximum(x, 0.0)  # the output of the previous layer's ReLU
@@ -223,3 +223,24 @@ def test_save_load_roundtrip(tmp_path):
         net2.load(tmp_path / "bad.bin")
     net.close()
     net2.close()
+
+
+def test_tensor_core_wait_gives_up_and_the_context_stays_usable():
+    """The tensor-core kernels' bounded wait run out on purpose (an mbarrier nothing arrives on, 20 ms):
+    the kernel reports the timeout, releases its TMEM and ends; a network forward on the same device
+    afterwards is correct (it allocates TMEM again)."""
+    timed_out, ms = g.tc_wait_check(0, 20.0)
+    assert timed_out == 1
+    assert 20.0 <= ms < 1000.0, ms
+    rng = np.random.default_rng(9)
+    flat = _flat(_random_params(rng))
+    ps = _unflat(flat)
+    net = g.Net()
+    net.set_params(flat)
+    x = rng.standard_normal((1, 300, 6)).astype(np.float32)
+    out = torch.zeros((1, 300, 3), dtype=torch.float32, device="cuda")
+    net.forward(torch.tensor(x, device="cuda"), out)
+    torch.cuda.synchronize()
+    y, _ = oracle.net_forward(ps, x.astype(np.float64), mirrored=True)
+    assert _rel(out.cpu().numpy(), y) <= 2e-3
+    net.close()
