@@ -53,7 +53,9 @@ __global__ void k_split_window(const double *__restrict__ x, int64_t att0, int32
 
 // ATTW: the attitude pairs come from the window copy (two 16-byte loads per axis and row instead of
 // four 8-byte gathers); the terms and their order are the same, so the result is bitwise the same.
-template <bool SV = false, bool ATTW = false, bool R64 = false>
+// XS: the block copies the instrumental pairs to shared memory first and gathers them there (a random
+// 8-byte gather from global memory costs the L1 data pipe about a pass per lane); again the same terms.
+template <bool SV = false, bool ATTW = false, bool R64 = false, bool XS = false>
 __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2 *__restrict__ xhl,
                                                   const double *__restrict__ b64, float *__restrict__ r_out,
                                                   double *__restrict__ part, double *__restrict__ r64)
@@ -68,6 +70,12 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float2 *__restrict__ xt = xhl + S.att0;
     const float2 *__restrict__ xi = xhl + S.instr0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sm_xi = reinterpret_cast<float2 *>(smem_raw);
+    if constexpr (XS) {
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) sm_xi[i] = xi[i];
+        __syncthreads();
+    }
     float2 xg[MG];
 #pragma unroll
     for (int q = 0; q < MG; ++q) xg[q] = q < S.n_glob ? xhl[S.glob0 + q] : make_float2(0.f, 0.f);
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
                     const float2 xv = xhl[j < G.ni ? S.instr0 + ic[j][i] : 0];
                     acc_term(a[A_INS + j][i], j < G.ni ? xv : zero2, sh[i], c[i]);
                 } else {
-                    acc_term(a[A_INS + j][i], xi[ic[j][i]], sh[i], c[i]);
+                    acc_term(a[A_INS + j][i], XS ? sm_xi[ic[j][i]] : xi[ic[j][i]], sh[i], c[i]);
                 }
             }
 #pragma unroll
@@ -258,19 +266,35 @@ __global__ void k_correct(double *__restrict__ x, const double *__restrict__ p, 
 }
 
 // Launch (or, with grid_out, only size) the residual kernel. Allocates nothing.
+static constexpr size_t kResidualXsBudget = 200 * 1024;  // bytes of instrumental pairs in shared memory
+
 cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b64, float *r,
                             double *part, cudaStream_t s, int *grid_out, bool window, double *r64)
 {
     // a section variant runs the run-time-geometry instance; a wide attitude block the window instance;
     // r64: the instance that also keeps the residual in binary64
     const bool w = window && att_window(c);
+    // the window instance keeps the instrumental pairs in shared memory where they fit (it runs one
+    // block per SM either way)
+    const size_t dxs = sizeof(float2) * (size_t)c->n_instr;
+    const bool xs = w && dxs <= kResidualXsBudget;
     auto kern = c->sv ? (r64 ? k_residual<true, false, true> : k_residual<true>)
-                      : w ? (r64 ? k_residual<false, true, true> : k_residual<false, true>)
-                          : (r64 ? k_residual<false, false, true> : k_residual<false>);
+                : xs  ? (r64 ? k_residual<false, true, true, true> : k_residual<false, true, false, true>)
+                : w   ? (r64 ? k_residual<false, true, true> : k_residual<false, true>)
+                      : (r64 ? k_residual<false, false, true> : k_residual<false>);
     // the grid (and so the number of partial sums) is the instance without r64's, whichever runs
-    auto sized = c->sv ? k_residual<true> : w ? k_residual<false, true> : k_residual<false>;
+    auto sized = c->sv ? k_residual<true>
+                 : xs  ? k_residual<false, true, false, true>
+                 : w   ? k_residual<false, true>
+                       : k_residual<false>;
+    const size_t dyn = xs ? dxs : 0;
+    if (dyn > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(sized, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sized, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sized, kThreads, dyn) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * c->sm_count;
     blocks = std::min<int64_t>(blocks, (c->n_tiles + (kThreads / 32) - 1) / (kThreads / 32));
@@ -280,7 +304,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b
         *grid_out = (int)blocks;
         return cudaSuccess;
     }
-    kern<<<(unsigned)blocks, kThreads, 0, s>>>(view<float>(c), xhl, b64, r, part, r64);
+    kern<<<(unsigned)blocks, kThreads, dyn, s>>>(view<float>(c), xhl, b64, r, part, r64);
     return cudaGetLastError();
 }
 
