@@ -186,8 +186,12 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
 // Add a warp's per-lane partial sums of the na (5 in the standard row)
 // astrometric columns of star k: the 32 x 5 partials go through a per-warp
 // shared-memory buffer and lanes 0..na-1 each sum one column (31 adds per
-// column instead of a 5-step shuffle tree per value on every lane).
+// column instead of a 5-step shuffle tree per value on every lane). Column j
+// sits at j * WSTRIDE with WSTRIDE = 33 words: the summing lanes then read
+// different banks (with 32 they read one bank, a 5-way conflict on every load).
 // Warp-collective.
+constexpr int WSTRIDE = 33;
+
 template <typename AT>
 __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT *__restrict__ wbuf,
                                                 double *__restrict__ z, int na = NASTRO)
@@ -195,14 +199,14 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NASTRO; ++j) {
-        wbuf[j * 32 + lane] = acc[j];
+        wbuf[j * WSTRIDE + lane] = acc[j];
         acc[j] = (AT)0;
     }
     __syncwarp();
     if (lane < na) {
         AT t = (AT)0;
 #pragma unroll 8
-        for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
+        for (int l = 0; l < 32; ++l) t += wbuf[lane * WSTRIDE + l];
         atomicAdd(z + (int64_t)na * k + lane, (double)t);
     }
     __syncwarp();
@@ -245,7 +249,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     constexpr int T = Tile<VT>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm32[32];
-    __shared__ AT wred[8][NASTRO * 32];
+    __shared__ AT wred[8][NASTRO * WSTRIDE];
     if (LSQR && st->done) return;
     // block-private columns: the instrumental ones, then (ATT) the attitude ones at n_instr + a*n_dfa + k
     const int32_t ncol = ATT ? S.n_instr + NAXES * S.n_dfa : S.n_instr;
@@ -813,7 +817,7 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
     constexpr int T = Tile<float>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm64[64];
-    __shared__ float wred[8][NASTRO * 32];
+    __shared__ float wred[8][NASTRO * WSTRIDE];
     if (LSQR && st->done) return;
     const float coef = LSQR ? (float)st->coef_u : coef_arg;
     static_assert(!XS || INSTR_SMEM, "x in shared memory follows the block's sums");
@@ -1205,7 +1209,11 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
         }
         if constexpr (F32) e = aprod2_star_launch<VT, UT, AT, true, MODE, LS, true>(c, y, x, x2, st, s);
     } else if (sizeof(AT) * (size_t)c->n_instr * (MODE == A2_BOTH ? 2 : 1) <=
-               (MODE == A2_BOTH ? kSmemBudgetBoth : kSmemBudget)) {
+               (MODE == A2_BOTH || sizeof(VT) == 8 ? kSmemBudgetBoth : kSmemBudget)) {
+        // binary64 storage: up to one block per SM's worth of shared sums (on 1e8 rows with 20,000
+        // instrumental columns, 160 KB of shared binary64 sums at one block per SM ran 8.49 ms against
+        // 10.20 ms for global binary64 atomics at two blocks per SM; with binary32 storage the same
+        // change made the binary64 products slower, 53.4 -> 59.4 ms on 5e8 rows)
         e = aprod2_star_launch<VT, UT, AT, true, MODE, LS>(c, y, x, x2, st, s);
     } else {
         e = aprod2_star_launch<VT, UT, AT, false, MODE, LS>(c, y, x, x2, st, s);

@@ -117,8 +117,11 @@ __global__ void k_rest_guess(const double *__restrict__ z, const double *__restr
 static constexpr int NNORM = 20;
 
 // Add a warp's per-lane partial sums of the 20 normal-equation values of star
-// k to N (through a per-warp shared buffer: lanes 0..19 each sum one value).
-// Warp-collective.
+// k to N (through a per-warp shared buffer: lanes 0..19 each sum one value;
+// value j at j * NSTRIDE, 33 elements apart, so that the summing lanes do not
+// all read one bank). Warp-collective.
+constexpr int NSTRIDE = 33;
+
 template <typename NT>
 __device__ __forceinline__ void flush_normal_run(NT (&acc)[NNORM], int64_t k, NT *__restrict__ wbuf,
                                                  NT *__restrict__ N)
@@ -126,14 +129,14 @@ __device__ __forceinline__ void flush_normal_run(NT (&acc)[NNORM], int64_t k, NT
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < NNORM; ++j) {
-        wbuf[j * 32 + lane] = acc[j];
+        wbuf[j * NSTRIDE + lane] = acc[j];
         acc[j] = (NT)0;
     }
     __syncwarp();
     if (lane < NNORM) {
         NT t = (NT)0;
 #pragma unroll 8
-        for (int l = 0; l < 32; ++l) t += wbuf[lane * 32 + l];
+        for (int l = 0; l < 32; ++l) t += wbuf[lane * NSTRIDE + l];
         atomicAdd(N + NNORM * k + lane, t);
     }
     __syncwarp();
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(256) k_astro_normal(SysView<VT> S, const RT *_
     const int na = SV ? S.na : NASTRO;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
-    __shared__ NT wred[8][NNORM * 32];
+    __shared__ NT wred[8][NNORM * NSTRIDE];
     const int lane = threadIdx.x & 31;
     NT *wbuf = wred[threadIdx.x >> 5];
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
