@@ -73,3 +73,29 @@ def test_gpu_arm_sequential_line():
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
     assert cpu["single_thread"]["cores"] == 1 and cpu["single_thread"]["value"] > 0
+
+
+def test_launch_share_model_counts():
+    """The benchmark's per-step launch counts (roofline.launch_share_ms) as the launch lists show them:
+    the inner iterations as fused passes or as aprod 1 + aprod 2, one LSQR start per refinement step plus
+    one norm pass (the warm start's A^T b pass gives the norms), one aprod 1 for a warm start, one residual
+    per step after the first; binary64: one aprod 1 per iteration (+1 warm), iterations + 2 aprod 2."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class G:
+        GSR_MIXED = 1
+
+    class E:
+        g = G
+
+    t = {"aprod1_f32": 1.0, "aprod2_f32": 10.0, "residual_df": 100.0, "aprod12_f32": 1000.0,
+         "aprod1_f64": 1.0, "aprod2_f64": 10.0}
+    meta = {"outer": 2, "inner_iterations": [5, 7], "fused": True}
+    _, sh = bench.dominant_kernel(E, meta, {"mode": 1, "warm": 1}, t)
+    assert sh == {"aprod12_f32": 12000.0, "aprod1_f32": 1.0, "aprod2_f32": 30.0, "residual_df": 100.0}
+    meta["fused"] = False
+    _, sh = bench.dominant_kernel(E, meta, {"mode": 1}, t)
+    assert sh == {"aprod1_f32": 12.0, "aprod2_f32": 150.0, "residual_df": 100.0}
+    _, sh = bench.dominant_kernel(E, {"iterations": 13}, {"mode": 0, "warm": 2}, t)
+    assert sh == {"aprod1_f64": 14.0, "aprod2_f64": 150.0}
