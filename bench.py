@@ -253,7 +253,7 @@ def cpu_baseline(gsrgen, oracle, cfg, damp, n9, full_rows, sample_stars):
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)
-REF_SAMPLE_STARS = 25_000  # 6.25e6 rows of the default workload: one oracle solve to 1e-9 in ~6 s
+REF_SAMPLE_STARS = 18_000  # 4.5e6 rows of the default workload: one oracle solve to 1e-9 in ~6 s
 
 
 def run_reference(args):
