@@ -972,9 +972,6 @@ static constexpr size_t kSmemBudget = 100 * 1024;  // bytes of block-private acc
 // the pass that sums products and squares together (the warm start's, once per solve) keeps its
 // block-private accumulators in shared memory up to one block per SM
 static constexpr size_t kSmemBudgetBoth = 200 * 1024;
-// aprod 1 of a wide attitude block, and of binary64 storage, keeps x of the instrumental columns in
-// shared memory
-static constexpr bool kAprod1Xs = true;
 
 template <typename KernelT>
 static int persistent_blocks(const gsr_ctx *c, KernelT kern, size_t dyn_smem)
@@ -1045,7 +1042,7 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
                 if (e != cudaSuccess) return e;
             }
             const size_t dxs = sizeof(XT) * (size_t)c->n_instr;
-            if (kAprod1Xs && dxs <= kSmemBudget) {
+            if (dxs <= kSmemBudget) {
                 if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, true, true>, dxs);
                 return pick(k_aprod1<VT, XT, UT, AT, false, false, true, true>, dxs);
             }
@@ -1057,7 +1054,7 @@ static cudaError_t aprod1_t(const gsr_ctx *c, const void *x, void *y, const Lsqr
         // binary64 storage (one block per SM at its registers): x of the instrumental columns in shared
         // memory where it fits
         const size_t dxs = sizeof(XT) * (size_t)c->n_instr;
-        if (kAprod1Xs && dxs <= kSmemBudgetBoth) {
+        if (dxs <= kSmemBudgetBoth) {
             if (st) return pick(k_aprod1<VT, XT, UT, AT, true, false, false, true>, dxs);
             return pick(k_aprod1<VT, XT, UT, AT, false, false, false, true>, dxs);
         }
