@@ -10,6 +10,9 @@ The oracle cannot run over the whole system at these sizes, so:
   run on a system made of those stars' rows (the generator's host twin draws them);
 * the whole of both products through the adjoint identity <A x, u> = <x, A^T u> of the
   binary64-arithmetic aprods, to 1e-12 of <|A||x|, |u|>;
+* the fused inner-iteration pass (both products from one read of each tile) the same
+  way: its new u on the sampled stars' rows and their astrometric columns against the
+  oracle, every entry of its A^T u against the binary64 aprod 2 of the same u;
 * every entry of the binary32 aprod 2 against the binary64 one, within the binary32
   bounds: 2e3 u of |A|^T|u| as in the small-size tests, plus, for the attitude,
   instrumental and global columns, the longest run of terms one lane adds in binary32
@@ -173,3 +176,31 @@ def _check(cfg, dev, sp, ctx, cabs, count, cmax):
     bound[a0:t0 + cfg.n_instr] += count * 2.0 ** -20 * cmax * umax
     err = (z - z64).abs()
     assert bool(torch.all(err <= bound)), float(torch.max(err / bound.clamp_min(1e-300)))
+    del z64, w64, err, bound
+
+    # the fused inner-iteration pass (y <- A x + coef y, then z += A^T y with the new y from the same read
+    # of each tile), the solver's dominant kernel on these shapes: the new y on the sampled stars' rows and
+    # the astrometric entries of their columns against the oracle, every entry of z against the
+    # binary64-arithmetic aprod 2 of the GPU's own new y, with the bounds above
+    assert ctx.aprod2_plan()["passes"] == 3
+    coef = -0.75
+    y1 = u.clone()
+    z1 = torch.zeros(nc, dtype=torch.float64, device=dev)
+    ctx.aprod12_f32(xd, y1, z1, coef)
+    want = oracle.aprod1(sub, xs, coef * us)
+    scale = oracle.aprod1(sabs, np.abs(xs), np.abs(coef * us))
+    y1s = y1[rows_d].double().cpu().numpy()
+    assert np.all(np.abs(y1s - want) <= 25 * EPS32 * scale), np.max(np.abs(y1s - want) / scale)
+    want2 = oracle.aprod2(sub, y1s, np.zeros(sub.n_cols))[:5 * len(stars)]
+    scale2 = oracle.aprod2(sabs, np.abs(y1s), np.zeros(sub.n_cols))[:5 * len(stars)]
+    got2 = z1[astro_cols].cpu().numpy()
+    assert np.all(np.abs(got2 - want2) <= 2e3 * EPS32 * scale2)
+    y164 = y1.double()
+    z164 = torch.zeros(nc, dtype=torch.float64, device=dev)
+    ctx.aprod2(y164, z164)
+    w164 = torch.zeros(nc, dtype=torch.float64, device=dev)
+    cabs.aprod2(y164.abs(), w164)
+    bound1 = 2e3 * EPS32 * w164 + 1e-13 * w164
+    bound1[a0:] += k_lane * EPS32 * w164[a0:]
+    err1 = (z1 - z164).abs()
+    assert bool(torch.all(err1 <= bound1)), float(torch.max(err1 / bound1.clamp_min(1e-300)))
