@@ -14,6 +14,14 @@
  * W[cout][cin][5] then the bias[cout] (gsr_net_num_params() values in all).
  * Sequence tensors are position-major fp32 [batch][len][channels] in device
  * memory. Conventions (status codes, streams) as in gsr.h.
+ *
+ * The forward and backward-data convolutions run as tcgen05 MMAs into a TMEM
+ * accumulator; each CTA waits at most 1 s for its MMAs. A convolution whose
+ * wait runs out writes nothing, releases its TMEM and sets the net's fault
+ * word: the next call on the net (forward, train_step, gradients, layer
+ * calls), or gsr_lsqr_solve when its learned warm start ran the net, returns
+ * GSR_ECUDA for it (gsr_net_gradients, which synchronises, also reports its
+ * own). gsr_tc_wait_check (gsr.h) exercises that path.
  */
 #ifndef GSR_WARM_H
 #define GSR_WARM_H
