@@ -166,7 +166,7 @@ struct gsr_ctx {
     // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)
     float *attw = nullptr;
     float *xwin = nullptr;
-    float4 *xhlwin = nullptr;  // the double-float residual's window copy (3 n_dfa x 2 float4), with xwin
+    float4 *xhlwin = nullptr;  // the double-float residual's window copy (3 n_dfa x 2 float4), wide blocks
     int64_t *star_ptr = nullptr;     // device copy
     std::vector<int64_t> star_ptr_h; // host copy
     int32_t max_obs = 0;             // longest star
@@ -252,12 +252,16 @@ inline bool att_red(const gsr_ctx *c)
 {
     return c->prec == GSR_FP32 && !c->sv && c->fx_valid && !att_fused(c) && c->attw;
 }
-// the binary32 aprod 1 gathers the attitude unknowns through the window copy (one 16-byte load per axis)
+// the binary32 aprod 1 gathers the attitude unknowns through the window copy (one 16-byte load per axis;
+// every binary32 standard-row context: c2 0.394 -> 0.366 ms, c5 14.5 -> 10.9 ms)
 inline bool att_window(const gsr_ctx *c) { return c->prec == GSR_FP32 && !c->sv && c->xwin; }
+// the double-float residual gathers the attitude pairs through their window copy (wide blocks only)
+inline bool res_window(const gsr_ctx *c) { return c->prec == GSR_FP32 && !c->sv && c->xhlwin; }
 // the inner solves take the fused iteration pass (set per solve from gsr_solve_params.inner_fused)
 inline bool iter_fused(const gsr_ctx *c) { return c->fused_inner && att_red(c) && att_window(c); }
-// attitude columns above which the binary32 aprod 1 uses the window copy: beyond ~16K binary32 values
-// the gathered attitude vector no longer stays in L1 beside the streamed tiles
+// attitude columns above which the double-float residual uses the window copy of the pairs: beyond ~16K
+// the gathered pairs no longer stay in L1 beside the streamed tiles (below, the window made it slower:
+// c2, 9,000 columns, 0.550 -> 0.608 ms)
 constexpr int64_t ATT_WINDOW_MIN_COLS = 16384;
 // max |y| word of the fixed-point sums (nullptr when they are off)
 inline uint32_t *fx_ymax(const gsr_ctx *c) { return c->fx_bits > 0 ? c->fx_word + 2 * (size_t)c->fx_nc : nullptr; }

@@ -273,7 +273,7 @@ cudaError_t residual_launch(const gsr_ctx *c, const float2 *xhl, const double *b
 {
     // a section variant runs the run-time-geometry instance; a wide attitude block the window instance;
     // r64: the instance that also keeps the residual in binary64
-    const bool w = window && att_window(c);
+    const bool w = window && res_window(c);
     // the window instance keeps the instrumental pairs in shared memory where they fit (it runs one
     // block per SM either way)
     const size_t dxs = sizeof(float2) * (size_t)c->n_instr;
@@ -322,7 +322,7 @@ cudaError_t split_launch(const gsr_ctx *c, const double *x, float2 *out, int64_t
 {
     if (n <= 0) return cudaSuccess;
     k_split<<<col_grid(c, n), kThreads, 0, s>>>(x, out, n);
-    if (window && att_window(c))
+    if (window && res_window(c))
         k_split_window<<<col_grid(c, (int64_t)NAXES * c->n_dfa), kThreads, 0, s>>>(
             x, (int64_t)c->n_astro * c->n_stars, c->n_dfa, c->xhlwin);
     return cudaGetLastError();
