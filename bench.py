@@ -68,7 +68,7 @@ FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # captures of the benchmark's standalone launches (bench.py --profile), by the workload whose shape the
 # capture had; a launch's traffic is this figure times its rows. Sources under profiles/.
 TRAFFIC_PER_ROW = {
-    "c2": {"aprod1_f32": 117.3, "aprod2_f32": 120.8, "residual_df": 121.4, "aprod1_f64": 221.4,
+    "c2": {"aprod1_f32": 117.4, "aprod2_f32": 120.8, "residual_df": 121.4, "aprod1_f64": 221.4,
            "aprod2_f64": 274.9},   # profiles/traffic_aprod_c2.md
     "c5": {"aprod1_f32": 117.5, "aprod2_f32": 116.8, "residual_df": 121.7, "aprod12_f32": 120.7,
            "aprod1_f64": 221.4, "aprod2_f64": 269.3},  # profiles/traffic_aprod_c5shape.md
