@@ -6,9 +6,9 @@
 //   forward      out[p][co]   = sum_{t,ci} W[co][ci][t] in[p+t-2][ci]        M = positions, N = co, K = 5*Cin
 //   backward x   dIn[p][ci]   = sum_{t,co} W[co][ci][4-t] dOut[p+t-2][co]    the same kernel, flipped weights
 //   backward W   dW[co][t,ci] = sum_p dOut[p][co] in[p+t-2][ci]               M = co, N = 5*Cin, K = positions
-// The forward and backward-data products (k_conv) issue tcgen05 MMAs from shared memory into a
-// TMEM accumulator (tc.cuh); the weight gradient (k_conv_wgrad, training only) uses warp-level
-// mma.sync fragments.
+// All three products issue tcgen05 MMAs from shared memory into a TMEM accumulator (tc.cuh): the
+// forward and backward-data ones (k_conv) over 128 positions per CTA, the weight gradient
+// (k_conv_wgrad) over chunks of 64 positions accumulated in TMEM.
 // Activations are position-major bf16 [B][L][C] with C padded to a multiple
 // of 16 (the first layer's 6 input channels and the last layer's 3 output
 // channels to 16). FP32 master weights are updated with Adam and copied to
@@ -43,16 +43,6 @@ static int64_t total_params()
     int64_t n = 0;
     for (int l = 0; l < NLAYER; ++l) n += layer_wsize(l) + CH(l + 1);
     return n;
-}
-
-// ---------------------------------------------------------------- MMA helper
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
@@ -210,90 +200,161 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16 *__restrict__ 
 }
 
 // ---------------------------------------------------------------- backward weights
-// dW[co][t*CIN + ci] += sum_p dout[p][co] * in[p+t-2][ci] over a block's positions.
-// Block: 4 warps; warp w covers output rows (co) 16*(w % MT) and a range of
-// n-tiles; gridDim.y splits the 5*CIN columns into chunks of NCH n-tiles.
-constexpr int WG_POS = 64;  // positions per chunk
+// dW[co][t*CIN + ci] += sum_p dout[p][co] in[p+t-2][ci] as tcgen05 MMAs: M = 128 of the 5 CIN
+// (tap, channel) rows (blockIdx.y picks the M tile), N = COUT, K = positions, 64 per chunk. A CTA
+// stages a chunk's input and output-gradient rows position-major, transposes them into K-major core
+// matrices (A[m][k] = in[p0+k+t-2][ci], B[n][k] = dout[p0+k][n]), issues 4 MMAs of K = 16 and waits
+// for them (bounded) before the next chunk; its FP32 accumulator (TMEM) is added into dW with atomics
+// at the end. Positions past L have zero output gradient, so they add nothing.
+constexpr int WG_POS = 64;  // positions per chunk (the MMAs' K per chunk)
+
+template <int CIN, int COUT>
+struct WgradSmem {
+    static constexpr uint32_t A_CHUNK = 128 * 16;                 // one 8-position column of A
+    static constexpr uint32_t A_BYTES = (WG_POS / 8) * A_CHUNK;
+    static constexpr uint32_t B_CHUNK = COUT * 16;                // one 8-position column of B
+    static constexpr uint32_t B_OFF = A_BYTES;
+    static constexpr uint32_t B_BYTES = (WG_POS / 8) * B_CHUNK;
+    static constexpr uint32_t IN_OFF = B_OFF + B_BYTES;           // input rows p0-2 .. p0+65, [pos][ch]
+    static constexpr uint32_t IN_BYTES = (WG_POS + 4) * CIN * 2;
+    static constexpr uint32_t D_OFF = (IN_OFF + IN_BYTES + 15) / 16 * 16;  // output-gradient rows, [pos][co]
+    static constexpr uint32_t D_BYTES = WG_POS * COUT * 2;
+    static constexpr uint32_t CTRL_OFF = (D_OFF + D_BYTES + 15) / 16 * 16;
+    static constexpr uint32_t USED = CTRL_OFF + 16;
+    static constexpr uint32_t BYTES = USED > 73728 ? USED : 73728;  // at most 3 CTAs (TMEM) per SM
+};
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) k_conv_wgrad(const __nv_bfloat16 *__restrict__ in,
                                                     const __nv_bfloat16 *__restrict__ dout, int64_t B, int64_t L,
-                                                    float *__restrict__ dW)
+                                                    float *__restrict__ dW, int32_t *__restrict__ fault)
 {
-    constexpr int K = KW * CIN;          // columns of dW
-    constexpr int MP = COUT < 16 ? 16 : COUT;  // rows padded to the MMA's 16
-    constexpr int MT = MP / 16;          // m-tiles
-    constexpr int NCH = 10;              // n-tiles per grid.y chunk (80 columns)
-    constexpr int WPM = 4 / MT;          // warps sharing one m-tile
-    constexpr int NPW = (NCH + WPM - 1) / WPM;  // n-tiles per warp
-    constexpr int DS = MP + 8, IS = CIN + 8;
-    __shared__ __align__(16) __nv_bfloat16 s_d[WG_POS * DS];
-    __shared__ __align__(16) __nv_bfloat16 s_in[(WG_POS + 4) * IS];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const int mt = warp % MT;
-    const int nt0 = blockIdx.y * NCH + (warp / MT) * NPW;
-    float acc[NPW][4];
-#pragma unroll
-    for (int n = 0; n < NPW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const int64_t chunks_per_seq = (L + WG_POS - 1) / WG_POS;
-    const int64_t n_chunks = B * chunks_per_seq;
+    using SM = WgradSmem<CIN, COUT>;
+    constexpr int K5 = KW * CIN;
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= (int)CONV_TMEM_COLS, "MMA shape");
+    extern __shared__ __align__(1024) unsigned char wg_smem[];
+    unsigned char *sA = wg_smem;
+    unsigned char *sB = wg_smem + SM::B_OFF;
+    const __nv_bfloat16 *s_in = reinterpret_cast<const __nv_bfloat16 *>(wg_smem + SM::IN_OFF);
+    const __nv_bfloat16 *s_d = reinterpret_cast<const __nv_bfloat16 *>(wg_smem + SM::D_OFF);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(wg_smem + SM::CTRL_OFF);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(wg_smem + SM::CTRL_OFF + 8);
+    const int warp = threadIdx.x >> 5;
+    const int mt = blockIdx.y;
+    if (warp == 0) tc::tmem_alloc(tslot, CONV_TMEM_COLS);
+    if (threadIdx.x == 32) tc::mbar_init(mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int64_t cps = (L + WG_POS - 1) / WG_POS;
+    const int64_t n_chunks = B * cps;
+    uint32_t phase = 0;
+    bool any = false, ok = true;
     for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const int64_t b = ch / chunks_per_seq;
-        const int64_t p0 = (ch % chunks_per_seq) * WG_POS;
-        __syncthreads();
-        for (int i = threadIdx.x; i < WG_POS * MP; i += blockDim.x) {
-            const int r = i / MP, c = i % MP;
-            const int64_t p = p0 + r;
-            s_d[r * DS + c] =
-                (p < L && c < COUT) ? dout[(b * L + p) * COUT + c] : __float2bfloat16_rn(0.f);
+        if (any) {  // the previous chunk's MMAs read shared memory: wait for them before restaging
+            ok = __syncthreads_and(tc::mbar_wait(mbar, phase, CONV_WAIT_NS));
+            if (!ok) break;  // phase still names the uncompleted one, for the last wait below
+            phase ^= 1u;
+            tc::fence_after_sync();
         }
-        for (int i = threadIdx.x; i < (WG_POS + 4) * CIN; i += blockDim.x) {
-            const int r = i / CIN, c = i % CIN;
-            const int64_t p = p0 - 2 + r;
-            s_in[r * IS + c] = (p >= 0 && p < L) ? in[(b * L + p) * CIN + c] : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k0 = 0; k0 < WG_POS; k0 += 16) {
-            // A[m][k] = dout[k0 + k][16 mt + m] (m = co row, k = position)
-            uint32_t a[4];
-            const int m0 = 16 * mt;
-            a[0] = pack2(s_d[(k0 + 2 * tq) * DS + m0 + g], s_d[(k0 + 2 * tq + 1) * DS + m0 + g]);
-            a[1] = pack2(s_d[(k0 + 2 * tq) * DS + m0 + g + 8], s_d[(k0 + 2 * tq + 1) * DS + m0 + g + 8]);
-            a[2] = pack2(s_d[(k0 + 2 * tq + 8) * DS + m0 + g], s_d[(k0 + 2 * tq + 9) * DS + m0 + g]);
-            a[3] = pack2(s_d[(k0 + 2 * tq + 8) * DS + m0 + g + 8], s_d[(k0 + 2 * tq + 9) * DS + m0 + g + 8]);
-#pragma unroll
-            for (int n = 0; n < NPW; ++n) {
-                const int nt = nt0 + n;
-                if ((warp / MT) * NPW + n >= NCH || nt * 8 >= K) continue;
-                // B[k][j] = in[k0 + k + t - 2][ci] with column j = n*8 + g -> (t, ci)
-                const int col = nt * 8 + g;
-                const int t = col / CIN, ci = col % CIN;
-                uint32_t bf[2];
-                bf[0] = pack2(s_in[(k0 + 2 * tq + t) * IS + ci], s_in[(k0 + 2 * tq + 1 + t) * IS + ci]);
-                bf[1] = pack2(s_in[(k0 + 2 * tq + 8 + t) * IS + ci], s_in[(k0 + 2 * tq + 9 + t) * IS + ci]);
-                mma_bf16(acc[n], a, bf);
+        const int64_t b = ch / cps;
+        const int64_t p0 = (ch % cps) * WG_POS;
+        // position-major staging: input rows p0-2 .. p0+WG_POS+1 and output-gradient rows p0 .. p0+63
+        {
+            uint4 *si = reinterpret_cast<uint4 *>(wg_smem + SM::IN_OFF);
+            constexpr int CJ = CIN / 8;
+            for (int i = threadIdx.x; i < (WG_POS + 4) * CJ; i += blockDim.x) {
+                const int r = i / CJ, j = i % CJ;
+                const int64_t p = p0 - 2 + r;
+                si[i] = (p >= 0 && p < L) ? *reinterpret_cast<const uint4 *>(in + (b * L + p) * CIN + 8 * j)
+                                          : make_uint4(0u, 0u, 0u, 0u);
+            }
+            uint4 *sd = reinterpret_cast<uint4 *>(wg_smem + SM::D_OFF);
+            constexpr int NJ = COUT / 8;
+            for (int i = threadIdx.x; i < WG_POS * NJ; i += blockDim.x) {
+                const int r = i / NJ, j = i % NJ;
+                const int64_t p = p0 + r;
+                sd[i] = p < L ? *reinterpret_cast<const uint4 *>(dout + (b * L + p) * COUT + 8 * j)
+                              : make_uint4(0u, 0u, 0u, 0u);
             }
         }
-    }
-    // flush: C rows = co (16 mt + g / + 8), cols = (nt*8 + 2tq + e)
+        __syncthreads();
+        // K-major core matrices: row m (or n), 8 consecutive positions per 16 bytes
+        for (int i = threadIdx.x; i < 128 * (WG_POS / 8); i += blockDim.x) {
+            const int m = i % 128, j = i / 128;
+            const int mg = mt * 128 + m;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (mg < K5) {
+                const int t = mg / CIN, ci = mg % CIN;
 #pragma unroll
-    for (int n = 0; n < NPW; ++n) {
-        const int nt = nt0 + n;
-        if ((warp / MT) * NPW + n >= NCH || nt * 8 >= K) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int co = 16 * mt + g + 8 * h;
-            if (co >= COUT) continue;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int col = nt * 8 + 2 * tq + e;
-                const float v = acc[n][2 * h + e];
-                if (v != 0.f) atomicAdd(dW + (int64_t)co * K + col, v);
+                for (int q = 0; q < 4; ++q)
+                    w[q] = pack2(s_in[(8 * j + 2 * q + t) * CIN + ci], s_in[(8 * j + 2 * q + 1 + t) * CIN + ci]);
             }
+            *reinterpret_cast<uint4 *>(sA + j * SM::A_CHUNK + m * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
+        for (int i = threadIdx.x; i < COUT * (WG_POS / 8); i += blockDim.x) {
+            const int n = i % COUT, j = i / COUT;
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                w[q] = pack2(s_d[(8 * j + 2 * q) * COUT + n], s_d[(8 * j + 2 * q + 1) * COUT + n]);
+            *reinterpret_cast<uint4 *>(sB + j * SM::B_CHUNK + n * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (threadIdx.x == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll 1
+            for (int j = 0; j < WG_POS / 16; ++j) {
+                const uint64_t ad = tc::smem_desc(a0 + 2 * j * SM::A_CHUNK, SM::A_CHUNK, 128);
+                const uint64_t bd = tc::smem_desc(b0 + 2 * j * SM::B_CHUNK, SM::B_CHUNK, 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, any || j > 0);
+            }
+            tc::mma_commit(mbar);
+        }
+        any = true;
     }
+    if (any && ok) ok = __syncthreads_and(tc::mbar_wait(mbar, phase, CONV_WAIT_NS));
+    tc::fence_after_sync();
+    if (any && ok) {
+        const int mg = mt * 128 + (int)threadIdx.x;  // accumulator row = TMEM lane
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int n0 = 0; n0 < COUT; n0 += 16) {
+            float v[16];
+            tc::tmem_ld16(lane_addr + (uint32_t)n0, v);
+            if (mg >= K5) continue;
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                if (v[e] != 0.f) atomicAdd(dW + (int64_t)(n0 + e) * K5 + mg, v[e]);
+        }
+    } else if (any && threadIdx.x == 0) {
+        atomicExch(fault, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        // after a timeout, give the MMAs one more bounded wait before their TMEM is released
+        if (any && !ok) tc::mbar_wait(mbar, phase, CONV_WAIT_NS);
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, CONV_TMEM_COLS);
+    }
+}
+
+template <int CIN, int COUT>
+static void wgrad_launch(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, int64_t B, int64_t L, float *dW,
+                         int32_t *fault, cudaStream_t s)
+{
+    constexpr uint32_t smem = WgradSmem<CIN, COUT>::BYTES;
+    cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t n_chunks = B * ((L + WG_POS - 1) / WG_POS);
+    const dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>(n_chunks, 1), 128),
+                    (unsigned)((KW * CIN + 127) / 128));
+    k_conv_wgrad<CIN, COUT><<<grid, 128, smem, s>>>(in, dout, B, L, dW, fault);
 }
 
 // db[co] += sum over positions of the fp32 output gradient
@@ -549,15 +610,13 @@ static void backward_layer(gsr_net *n, int l, const __nv_bfloat16 *dcur, __nv_bf
                            cudaStream_t s)
 {
     const int64_t P = B * L;
-    const int cin = CHP(l), cout = CHP(l + 1);
-    const unsigned wg = (unsigned)std::min<int64_t>(std::max<int64_t>((P + WG_POS - 1) / WG_POS, 1), 1024);
-    const dim3 gw(wg, (unsigned)((KW * cin / 8 + 9) / 10));
+    const int cout = CHP(l + 1);
     if (l == 0)
-        k_conv_wgrad<16, 64><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+        wgrad_launch<16, 64>(n->act[l], dcur, B, L, n->dW[l], n->fault_d, s);
     else if (l == NLAYER - 1)
-        k_conv_wgrad<64, 16><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+        wgrad_launch<64, 16>(n->act[l], dcur, B, L, n->dW[l], n->fault_d, s);
     else
-        k_conv_wgrad<64, 64><<<gw, 128, 0, s>>>(n->act[l], dcur, B, L, n->dW[l]);
+        wgrad_launch<64, 64>(n->act[l], dcur, B, L, n->dW[l], n->fault_d, s);
     k_bias_grad<<<grid_n(P * CH(l + 1)), 256, sizeof(float) * CH(l + 1), s>>>(n->d32, P, CH(l + 1), cout, n->db[l]);
     if (l > 0) {
         const dim3 grid((unsigned)((L + CONV_POS - 1) / CONV_POS), (unsigned)B);
@@ -616,9 +675,7 @@ static cudaError_t layer_bwd_t(gsr_net *n, int l, const float *in, const float *
     k_pack_any<<<grid_n(P * CINP), 256, 0, s>>>(in, P, CH(l), CINP, n->act[l], nullptr);
     // the output gradient in bf16 for both products, in fp32 for the bias gradient
     k_pack_any<<<grid_n(P * COUTP), 256, 0, s>>>(dout, P, CH(l + 1), COUTP, n->d16a, n->d32);
-    const unsigned wg = (unsigned)std::min<int64_t>(std::max<int64_t>((P + WG_POS - 1) / WG_POS, 1), 1024);
-    k_conv_wgrad<CINP, COUTP><<<dim3(wg, (unsigned)((KW * CINP / 8 + 9) / 10)), 128, 0, s>>>(n->act[l], n->d16a, B, L,
-                                                                                         n->dW[l]);
+    wgrad_launch<CINP, COUTP>(n->act[l], n->d16a, B, L, n->dW[l], n->fault_d, s);
     k_bias_grad<<<grid_n(P * CH(l + 1)), 256, sizeof(float) * CH(l + 1), s>>>(n->d32, P, CH(l + 1), COUTP, n->db[l]);
     k_unpack_dw<<<grid_n(layer_wsize(l)), 256, 0, s>>>(n->dW[l], CH(l), CH(l + 1), CINP, dW);
     if ((e = cudaMemcpyAsync(db, n->db[l], sizeof(float) * CH(l + 1), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
