@@ -15,8 +15,8 @@
  * Sequence tensors are position-major fp32 [batch][len][channels] in device
  * memory. Conventions (status codes, streams) as in gsr.h.
  *
- * The forward and backward-data convolutions run as tcgen05 MMAs into a TMEM
- * accumulator; each CTA waits at most 1 s for its MMAs. A convolution whose
+ * The convolution products (forward, backward-data, weight gradient) run as
+ * tcgen05 MMAs into TMEM accumulators; each CTA waits at most 1 s for its MMAs. A convolution whose
  * wait runs out writes nothing, releases its TMEM and sets the net's fault
  * word: the next call on the net (forward, train_step, gradients, layer
  * calls), or gsr_lsqr_solve when its learned warm start ran the net, returns
