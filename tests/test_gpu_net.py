@@ -244,3 +244,41 @@ def test_tensor_core_wait_gives_up_and_the_context_stays_usable():
     y, _ = oracle.net_forward(ps, x.astype(np.float64), mirrored=True)
     assert _rel(out.cpu().numpy(), y) <= 2e-3
     net.close()
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 129])
+def test_layer_products_at_short_and_ragged_lengths(L):
+    """The convolution products where the zero padding and the tile edges meet: sequences of 1, 2
+    and 5 positions (every tap reaches past an end) and 129 (one position into a second tile of 128);
+    forward, din, dW and db of a 64 -> 64 layer against the oracle at the per-layer bounds."""
+    layer = 2
+    rng = np.random.default_rng(40 + L)
+    flat = _flat(_random_params(rng))
+    ps = _unflat(flat)
+    net = g.Net()
+    net.set_params(flat)
+    cin, cout = LAYERS[layer]
+    B = 3
+    x = np.maximum(rng.standard_normal((B, L, cin)), 0.0).astype(np.float32)
+    dout = (rng.standard_normal((B, L, cout)) * 1e-2).astype(np.float32)
+    xd, dd = torch.tensor(x, device="cuda"), torch.tensor(dout, device="cuda")
+    out = torch.zeros((B, L, cout), dtype=torch.float32, device="cuda")
+    din = torch.zeros((B, L, cin), dtype=torch.float32, device="cuda")
+    dW = torch.zeros((cout, cin, 5), dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    net.layer_forward(layer, xd, out)
+    net.layer_backward(layer, xd, dd, din, dW, db)
+    torch.cuda.synchronize()
+    W, bias = ps[layer]
+    x64, d64 = x.astype(np.float64), dout.astype(np.float64)
+    u = 2.0 ** -23
+    ref = oracle.conv_fwd(x64, W, bias, relu=False, mirrored=True)
+    mag = oracle.conv_fwd(np.abs(x64), np.abs(W), np.abs(bias), relu=False, mirrored=True)
+    assert np.all(np.abs(out.cpu().numpy().astype(np.float64) - ref) <= (5 * cin + 1) * u * mag + 1e-30)
+    rin, rW, rb = oracle.conv_bwd(x64, d64, W, mirrored=True)
+    min_, mW, mb = oracle.conv_bwd(np.abs(x64), np.abs(d64), np.abs(W), mirrored=True)
+    gin, gW, gb = (t.cpu().numpy().astype(np.float64) for t in (din, dW, db))
+    assert np.all(np.abs(gin - rin) <= 5 * cout * u * min_ + 1e-30)
+    assert np.all(np.abs(gW - rW) <= (B * L + 64) * u * mW + 1e-30)
+    assert np.all(np.abs(gb - rb) <= B * L * u * mb + 1e-30)
+    net.close()
