@@ -496,12 +496,15 @@ def dominant_kernel(env, meta, kw, t):
         # one aprod 1 over the other columns); the warm start's A^T b pass also gives the column norms, so
         # it stands in for the norm pass (profiles/launches_c5.md)
         n_res = m - 1
+        # the last iteration of each inner solve (run to its limit) is a closing one: aprod 1 alone
+        closed = m if meta.get("closing") else 0
         if meta.get("fused"):  # the inner iterations take the fused pass; the starts, the norms and A^T b the aprod 2
-            share = {"aprod12_f32": its * t["aprod12_f32"], "aprod1_f32": warm_aprod2 * t["aprod1_f32"],
+            share = {"aprod12_f32": (its - closed) * t["aprod12_f32"],
+                     "aprod1_f32": (warm_aprod2 + closed) * t["aprod1_f32"],
                      "aprod2_f32": (m + 1) * t["aprod2_f32"], "residual_df": n_res * t["residual_df"]}
         else:
             share = {"aprod1_f32": (its + warm_aprod2) * t["aprod1_f32"],
-                     "aprod2_f32": (its + m + 1) * t["aprod2_f32"],
+                     "aprod2_f32": (its - closed + m + 1) * t["aprod2_f32"],
                      "residual_df": n_res * t["residual_df"]}
     else:
         k = meta["iterations"]
@@ -632,7 +635,8 @@ def measure_workload(env, args, name, headline_mode):
             _, m, k1, k2 = min(cands)
             legs[nm] = (ctx32, mixed_kw(k1, m, warm, k2),
                         {"outer": m, "inner_iterations": [k1] + [k2] * (m - 1),
-                         "start": nm.split("_")[1] if warm else "x0 = 0", "fused": fused_inner})
+                         "start": nm.split("_")[1] if warm else "x0 = 0", "fused": fused_inner,
+                         "closing": CLOSE_DEFAULT})
 
     # ---- timed region: every solver, the same K steps after W warm-up steps each
     time_legs({nm: leg for nm, leg in legs.items() if nm not in solvers})
@@ -718,6 +722,9 @@ def measure_workload(env, args, name, headline_mode):
 # whether the library's default (gsr_solve_params.inner_fused = 1) runs the inner iterations of a form-3
 # system as the fused pass (it does)
 FUSED_DEFAULT = True
+# whether the library's default (gsr_solve_params.inner_close = 1) ends each inner solve that runs to its
+# iteration limit with a closing iteration (aprod 1 and the x update, no aprod 2) (it does)
+CLOSE_DEFAULT = True
 
 # stars of the CPU baseline's sample per workload (about 10-30 s of oracle work on the host cores)
 CPU_SAMPLE_STARS = {"c5": 80_000, "c3": 100_000, "c2": 100_000}

@@ -85,6 +85,7 @@ struct GraphCache {
     int k = 0;
     bool var = false, inner32 = false;
     int fused = 0;
+    bool close = false;  // the last iteration is a closing one (no aprod 2)
 };
 
 struct Workspace {
@@ -290,10 +291,12 @@ gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32 = false, 
 LsqrState initial_state(const gsr_solve_params *prm);
 // defer_fin: leave the final state's download (into ws.fin_h) pending on s, for a caller that
 // synchronises s itself after more work; *fin is then not written. start64 (inner32 only): the
-// start's aprod 2 reads the binary64 right-hand side in ws.u with binary64 products and sums
+// start's aprod 2 reads the binary64 right-hand side in ws.u with binary64 products and sums. close:
+// a solve that reaches its iteration limit ends with a closing iteration (aprod 1 and the x update;
+// the limit's estimates that need alpha_{k+1} keep the previous iteration's values)
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
-                    bool defer_fin = false, bool start64 = false);
+                    bool defer_fin = false, bool start64 = false, bool close = false);
 void fill_info(gsr_solve_info *info, const LsqrState &fin, std::chrono::steady_clock::time_point t0);
 // warm start (warm.cu)
 // r0_parts (may be null): for binary32 storage the residual of x0 is also left in ws.u32, in

@@ -75,10 +75,16 @@ __global__ void k_precond_finish(double *__restrict__ colsq, double *__restrict_
 // first warp of the block that finishes k_colA last; thread 0 writes. Binary64
 // divides and square roots are slow on this GPU (about 0.34 us each when
 // dependent), so each rotation takes one reciprocal and multiplies by it.
+// CLOSE: the last iteration of a solve that has reached its iteration limit, run
+// without the aprod 2 (k_colA_close): the x update needs only beta_{k+1}, through
+// rho_k and phi_k, so alpha_{k+1} is not formed. It enters theta and rhobar of the
+// next step and the |A^T r| estimate; the first two are not used again, the last
+// keeps the previous iteration's value, and the tests that read it are not made.
+template <bool CLOSE = false>
 __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_beta, const double *__restrict__ part_v,
                             const double *__restrict__ part_w, int n_part, int32_t *__restrict__ flag)
 {
-    const double ssq_v = warp_sum_partials(part_v, n_part);
+    const double ssq_v = CLOSE ? 0.0 : warp_sum_partials(part_v, n_part);
     const double ssq_w = warp_sum_partials(part_w, n_part);
     if (threadIdx.x != 0) return;
     st->colb_skip = 0;
@@ -88,7 +94,7 @@ __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_
     double anorm = st->anorm;
     if (beta > 0.0) {
         anorm = sqrt(anorm * anorm + alpha * alpha + beta * beta + dampsq);
-        alpha = sqrt(ssq_v);
+        alpha = CLOSE ? 0.0 : sqrt(ssq_v);
     }
     const double inv_bnorm = 1.0 / st->bnorm;  // off the critical path
     // rotation eliminating damp
@@ -132,7 +138,7 @@ __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_
     const double res1 = phibar * phibar;
     const double res2 = st->res2 + psi * psi;
     const double rnorm = sqrt(res1 + res2);
-    const double arnorm = alpha * fabs(tau);
+    const double arnorm = CLOSE ? st->arnorm : alpha * fabs(tau);
     const double r1sq = rnorm * rnorm - dampsq * st->xxnorm;
     double r1norm = sqrt(fabs(r1sq));
     if (r1sq < 0.0) r1norm = -r1norm;
@@ -145,17 +151,17 @@ __device__ void scalar_step(LsqrState *__restrict__ st, double beta, double inv_
     const double tt1 = test1 / (1.0 + anx);
     const double rtol = st->btol + st->atol * anx;
     int istop = 0;
-    if (itn >= st->itnlim) istop = 7;
+    if (itn >= st->itnlim || CLOSE) istop = 7;
     if (1.0 + test3 <= 1.0) istop = 6;
-    if (1.0 + test2 <= 1.0) istop = 5;
+    if (!CLOSE && 1.0 + test2 <= 1.0) istop = 5;
     if (1.0 + tt1 <= 1.0) istop = 4;
     if (test3 <= st->ctol) istop = 3;
-    if (test2 <= st->atol) istop = 2;
-    if (arnorm <= st->artol * st->arnorm0) istop = 2;
+    if (!CLOSE && test2 <= st->atol) istop = 2;
+    if (!CLOSE && arnorm <= st->artol * st->arnorm0) istop = 2;
     if (test1 <= rtol) istop = 1;
     const bool bad = !(isfinite(alpha) && isfinite(rho) && isfinite(phi) && isfinite(theta) && isfinite(rnorm));
     // store
-    st->alpha = alpha;
+    if (!CLOSE) st->alpha = alpha;
     st->anorm = anorm;
     st->rhobar = rhobar_n;
     st->phibar = phibar;
@@ -278,6 +284,66 @@ __global__ void k_colA(const double *__restrict__ part_u, int n_part_u, double *
     __threadfence();
     if (threadIdx.x < 32) scalar_step(st, beta, s_ib, part_v, part_w, gridDim.x, flag);
     if (threadIdx.x == 0) *counter = 0;
+}
+
+// colA of a closing iteration (the last of a solve that runs to its iteration limit; no aprod 2
+// before it): beta from the aprod 1 partials, the per-block sums of squares of w (the condition
+// estimate), and the closing scalar step by the block that finishes last. v, w and z are not
+// touched (z stays zero). ymax_reset as in k_colA: the aprod 1 has built max |y|, which nothing
+// reads in this iteration.
+__global__ void k_colA_close(const double *__restrict__ part_u, int n_part_u, const double *__restrict__ w,
+                             int64_t n, LsqrState *__restrict__ st, double *__restrict__ part_w,
+                             uint32_t *__restrict__ counter, int32_t *__restrict__ flag,
+                             uint32_t *__restrict__ ymax_reset)
+{
+    __shared__ double sm64[64];
+    __shared__ double s_beta, s_ib;
+    __shared__ int s_last;
+    if (ymax_reset && blockIdx.x == 0 && threadIdx.x == 0) *ymax_reset = 0u;
+    if (st->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->colb_skip = 1;
+        return;
+    }
+    if (threadIdx.x < 32) {
+        const double ssq = warp_sum_partials(part_u, n_part_u);
+        if (threadIdx.x == 0) {
+            s_beta = sqrt(ssq);
+            s_ib = 1.0 / s_beta;
+        }
+    }
+    double sw = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double wj = w[j];
+        sw = fma(wj, wj, sw);
+    }
+    const double2 t = block_sum2(0.0, sw, sm64);  // synchronises the block (s_beta is then visible)
+    if (threadIdx.x == 0) {
+        part_w[blockIdx.x] = t.y;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double beta = s_beta;
+    if (threadIdx.x < 32) scalar_step<true>(st, beta, s_ib, nullptr, part_w, gridDim.x, flag);
+    if (threadIdx.x == 0) *counter = 0;
+}
+
+// colB of a closing iteration: x += t1 w, var += (w / rho)^2 (v and w are not needed again)
+__global__ void k_colB_close(const double *__restrict__ w, double *__restrict__ x, double *__restrict__ var, int64_t n,
+                             const LsqrState *__restrict__ st)
+{
+    if (st->colb_skip) return;
+    const double t1 = st->t1, ir = st->inv_rho;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double wj = w[j];
+        x[j] = fma(t1, wj, x[j]);
+        if (var) {
+            const double d = wj * ir;
+            var[j] = fma(d, d, var[j]);
+        }
+    }
 }
 
 // The start of LSQR: beta_1 u_1 = b, alpha_1 v_1 = A~^T u_1, w_1 = v_1, x_0 = 0,
@@ -484,18 +550,22 @@ void drop_graphs(gsr_ctx *c)
 // with the scalar step, colB: 4 or 5 kernels each), captured on first use and cached on
 // the context (kernel arguments are the context's fixed buffers; the iteration state lives
 // in device memory); dropped when a reload changes the fixed-point kernel choice.
+// close: the graph's last iteration is a closing one (aprod 1, k_colA_close, k_colB_close), for the
+// last launch of a solve whose iteration limit is a multiple of k.
 static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner32, cudaStream_t s,
-                                   cudaGraphExec_t *out)
+                                   cudaGraphExec_t *out, bool close = false)
 {
     Workspace &ws = c->ws;
     const int fused = inner32 && iter_fused(c) ? c->fused_inner : 0;
     for (auto &gc : ws.graphs) {
-        if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32 && gc.fused == fused) {
+        if (gc.exec && gc.k == k && gc.var == want_var && gc.inner32 == inner32 && gc.fused == fused &&
+            gc.close == close) {
             *out = gc.exec;
             return cudaSuccess;
         }
     }
-    int gu = aprod1_grid(c, inner32);
+    const int gu1 = aprod1_grid(c, inner32);  // the partials of a standalone aprod 1 (closing iteration)
+    int gu = gu1;
     if (fused) launch_iter_fused(c, nullptr, nullptr, nullptr, nullptr, nullptr, s, &gu);
     const int gc = colab_grid(c, c->n_cols);
     // the fused binary32 aprod 2 leaves the max |y| word to colA (the attitude pass clears it otherwise)
@@ -508,6 +578,14 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < k && e == cudaSuccess; ++i) {
+        if (close && i == k - 1) {  // the x update from beta_{k+1}: aprod 1 only
+            if ((e = launch_aprod1(c, pv, u, ws.st, ws.part_u, s, inner32)) != cudaSuccess) break;
+            k_colA_close<<<gc, kColThreads, 0, s>>>(ws.part_u, gu1, ws.w, c->n_cols, ws.st, ws.part_w, ws.counter,
+                                                    ws.flag_d, inner32 ? fx_ymax(c) : nullptr);
+            k_colB_close<<<gc, kColThreads, 0, s>>>(ws.w, ws.x, want_var ? ws.var : nullptr, c->n_cols, ws.st);
+            e = cudaGetLastError();
+            break;
+        }
         if (fused) {  // both products in one pass over the tiles
             if ((e = launch_iter_fused(c, (const float *)pv, (float *)u, ws.z, ws.st, ws.part_u, s)) != cudaSuccess)
                 break;
@@ -532,6 +610,7 @@ static cudaError_t iteration_graph(gsr_ctx *c, int k, bool want_var, bool inner3
     gcache.var = want_var;
     gcache.inner32 = inner32;
     gcache.fused = fused;
+    gcache.close = close;
     ws.graphs.push_back(gcache);
     *out = exec;
     return cudaSuccess;
@@ -559,6 +638,7 @@ void default_params(gsr_solve_params *p)
     p->inner_itn_next = 0;
     p->refine_grad = 0;
     p->inner_fused = 1;
+    p->inner_close = 1;
 }
 
 // p = 1/|A_:,j| into ws.p. f32: squares and per-block partial sums in
@@ -586,7 +666,7 @@ gsr_status precond_pass(gsr_ctx *c, bool use, cudaStream_t s, bool f32, const vo
 // the scaled solution in ws.x and the final scalars in *fin.
 gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_var, int n_part_u, int graph_k,
                     double timeout_s, std::chrono::steady_clock::time_point t0, cudaStream_t s, LsqrState *fin,
-                    bool defer_fin, bool start64)
+                    bool defer_fin, bool start64, bool close)
 {
     using clk = std::chrono::steady_clock;
     Workspace &ws = c->ws;
@@ -610,8 +690,17 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     int k = graph_k > 0 ? graph_k : 8;
     if (k > init.itnlim && init.itnlim > 0) k = init.itnlim;
     if (k < 1) k = 1;
-    cudaGraphExec_t exec = nullptr;
+    if (close && graph_k <= 0 && init.itnlim > 0) {
+        // the largest divisor of the limit up to k, so that the last launch ends on the limit
+        int d = k;
+        while (init.itnlim % d) --d;
+        if (2 * d >= k) k = d;
+    }
+    close = close && init.itnlim > 0 && init.itnlim % k == 0;
+    cudaGraphExec_t exec = nullptr, exec_close = nullptr;
     if ((e = iteration_graph(c, k, want_var, inner32, s, &exec)) != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    if (close && (e = iteration_graph(c, k, want_var, inner32, s, &exec_close, true)) != cudaSuccess)
+        return cuda_fail(c, e, "graph capture");
     // No host round trip between the start and the first launch, nor after the last one: errors of the
     // start surface at the next synchronisation, and the graph's kernels skip their work once the
     // device-side state says the solve has stopped. The host waits between launches only to read the
@@ -620,7 +709,7 @@ gsr_status run_lsqr(gsr_ctx *c, const LsqrState &init, bool inner32, bool want_v
     int launched = 0;
     const int max_launch = init.itnlim > 0 ? (init.itnlim + k - 1) / k : 0;
     while (launched < max_launch) {
-        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+        if ((e = cudaGraphLaunch(close && launched == max_launch - 1 ? exec_close : exec, s)) != cudaSuccess) {
             status = cuda_fail(c, e, "graph launch");
             break;
         }

@@ -407,7 +407,7 @@ gsr_status mixed_solve(gsr_ctx *c, const gsr_solve_params *prm, const double *x0
         // one host synchronisation per refinement step: the inner solve's final state and the
         // correction's norms come back together
         status = run_lsqr(c, init, true, false, nr > 0 ? n_part : 0, prm->graph_k, prm->timeout_s, t0, s, &fin,
-                          true, start64);
+                          true, start64, prm->inner_close > 0);
         if (status != GSR_OK && status != GSR_ETIMEOUT) return status;
         if ((e = cudaMemsetAsync(ws.blk, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(c, e, "memset");
         k_correct<<<gcor, kThreads, 0, s>>>(ws.xo, ws.p, ws.x, nc, att0, instr0, glob0, ws.blk);

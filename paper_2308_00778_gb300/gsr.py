@@ -55,6 +55,7 @@ class SolveParams(ctypes.Structure):
         ("inner_itn_next", ctypes.c_int32),
         ("refine_grad", ctypes.c_int32),
         ("inner_fused", ctypes.c_int32),
+        ("inner_close", ctypes.c_int32),
     ]
 
 

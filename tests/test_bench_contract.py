@@ -77,7 +77,8 @@ def test_gpu_arm_sequential_line():
 
 def test_launch_share_model_counts():
     """The benchmark's per-step launch counts (roofline.launch_share_ms) as the launch lists show them:
-    the inner iterations as fused passes or as aprod 1 + aprod 2, one LSQR start per refinement step plus
+    the inner iterations as fused passes or as aprod 1 + aprod 2 (the closing iteration that ends each
+    inner solve as an aprod 1 alone), one LSQR start per refinement step plus
     one norm pass (the warm start's A^T b pass gives the norms), one aprod 1 for a warm start, one residual
     per step after the first; binary64: one aprod 1 per iteration (+1 warm), iterations + 2 aprod 2."""
     sys.path.insert(0, ROOT)
@@ -97,5 +98,12 @@ def test_launch_share_model_counts():
     meta["fused"] = False
     _, sh = bench.dominant_kernel(E, meta, {"mode": 1}, t)
     assert sh == {"aprod1_f32": 12.0, "aprod2_f32": 150.0, "residual_df": 100.0}
+    # closing iterations: the last inner iteration of each refinement step is an aprod 1 alone
+    meta = {"outer": 2, "inner_iterations": [5, 7], "fused": True, "closing": True}
+    _, sh = bench.dominant_kernel(E, meta, {"mode": 1, "warm": 1}, t)
+    assert sh == {"aprod12_f32": 10000.0, "aprod1_f32": 3.0, "aprod2_f32": 30.0, "residual_df": 100.0}
+    meta["fused"] = False
+    _, sh = bench.dominant_kernel(E, meta, {"mode": 1}, t)
+    assert sh == {"aprod1_f32": 12.0, "aprod2_f32": 130.0, "residual_df": 100.0}
     _, sh = bench.dominant_kernel(E, {"iterations": 13}, {"mode": 0, "warm": 2}, t)
     assert sh == {"aprod1_f64": 14.0, "aprod2_f64": 150.0}

@@ -419,3 +419,40 @@ def test_wide_attitude_windows_at_the_edge_knots():
     rscale = oracle.aprod1(_abs_sys(s), np.abs(xs), np.abs(b).copy())
     assert np.all(np.abs(rd.cpu().numpy() - r_ref) <= u * np.abs(r_ref) + 2.0 ** -40 * rscale)
     ctx.close()
+
+
+@pytest.mark.parametrize("name,fused", [("c1", 1), ("wide", 1), ("wide", -1)])
+def test_closing_iteration_gives_the_same_iterate(name, fused):
+    """An inner solve that runs to its iteration limit m ends with a closing iteration (aprod 1 and the
+    x update; inner_close 1): LSQR's x_m = x_{m-1} + (phi_m / rho_m) w_m needs beta_{m+1}, not v_{m+1}.
+    One refinement step of m inner iterations from x0 = 0, closing against every iteration in full
+    (inner_close 0), for m = 4 and 5 (one graph of m iterations each) and m = 12 (two graphs of 6): the
+    two differ only by the rounding of the last binary32 aprod 1 and its norm, far below the last LSQR
+    step |x_m - x_{m-1}| that a wrong closing update would miss or repeat. c1 takes the one-pass
+    shared-memory aprod 2; 'wide' (20,000 knots per axis) the fused pass (1) or the two passes (-1)."""
+    cfg = {"c1": gsrgen.workloads()["c1"].cfg, "wide": gsrgen.make_cfg(54, 3000, 100, 20000, 3000)}[name]
+    h, s, b, ctx = _setup32(cfg)
+    kw = dict(mode=g.GSR_MIXED, damp=1e-6, max_outer=1, refine_tol=-1.0, inner_tol=1e-30, atol=0.0, btol=0.0,
+              conlim=0.0, inner_fused=fused)
+    res = {}
+    for m in (3, 4, 5, 11, 12):
+        for close in (0, 1):
+            if close and m in (3, 11):
+                continue
+            x = torch.zeros(s.n_cols, dtype=torch.float64, device="cuda")
+            info = ctx.solve(x, inner_itn=m, inner_close=close, **kw)
+            assert info["itn"] == m and info["outer_itn"] == 1 and info["istop"] == 7, info
+            res[m, close] = x.cpu().numpy()
+    for m in (4, 5, 12):
+        step = np.linalg.norm(res[m, 0] - res[m - 1, 0])
+        assert step > 0.0
+        assert np.linalg.norm(res[m, 1] - res[m, 0]) <= 1e-3 * step, (m, step)
+    # the whole refinement with closing inner solves still reaches 1e-9 of the oracle's solution
+    xo, _ = oracle.lsqr(s, b, 2000, 1e-14, 1e-14, 0.0, 1e-6)
+    x = np.zeros(s.n_cols)
+    info = ctx.solve(x, mode=g.GSR_MIXED, damp=1e-6, inner_itn=10, max_outer=8, inner_tol=1e-30, atol=0.0,
+                     btol=0.0, inner_fused=fused)
+    assert info["itn"] == 10 * info["outer_itn"], info
+    errs = block_errors(x, xo, s)
+    assert max(errs.values()) <= 1e-9, (errs, info)
+    ctx.close()
