@@ -131,11 +131,13 @@ __global__ void __launch_bounds__(256) k_aprod1(SysView<VT> S, const XT *__restr
 #pragma unroll
                 for (int j = 1; j < NASTRO; ++j) v = fma(a[j][i], (AT)__ldg(xa + j), v);
             }
+            float4 wv[NAXES];
+            if constexpr (ATTW) att_window_load(S.xw, kn[i], wv);
 #pragma unroll
             for (int ax = 0; ax < NAXES; ++ax) {
                 if constexpr (ATTW) {
-                    // the axis's 4 consecutive unknowns in one 16-byte load of the window copy
-                    const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
+                    // the axis's 4 consecutive unknowns from the window copy
+                    const float4 w = wv[ax];
                     v = fma(a[A_ATT + NPARAXIS * ax + 0][i], (AT)w.x, v);
                     v = fma(a[A_ATT + NPARAXIS * ax + 1][i], (AT)w.y, v);
                     v = fma(a[A_ATT + NPARAXIS * ax + 2][i], (AT)w.z, v);
@@ -625,16 +627,17 @@ __global__ void k_att_fold(SysView<float> S, double *__restrict__ z, double *__r
     }
 }
 
-// the window copy of the binary32 attitude unknowns: xw[a n_dfa + k] = x[att0 + a n_dfa + k .. +3]
-// (zero past the axis's end)
+// the window copy of the binary32 attitude unknowns, knot-major in 64-byte records:
+// xw[4 k + a] = x[att0 + a n_dfa + k .. +3] (zero past the axis's end), xw[4 k + 3] unused, so that a
+// row's axes 0 and 1 are one 32-byte load and axis 2 a 16-byte one (att_window_load)
 __global__ void k_att_window(const float *__restrict__ x, int64_t att0, int32_t n_dfa, float4 *__restrict__ xw)
 {
     const int64_t nat = (int64_t)NAXES * n_dfa;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nat; c += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t k = (int32_t)(c % n_dfa);
+        const int32_t a = (int32_t)(c / n_dfa), k = (int32_t)(c % n_dfa);
         const float *xa = x + att0 + c;
-        xw[c] = make_float4(xa[0], k + 1 < n_dfa ? xa[1] : 0.f, k + 2 < n_dfa ? xa[2] : 0.f,
-                            k + 3 < n_dfa ? xa[3] : 0.f);
+        xw[4 * (int64_t)k + a] = make_float4(xa[0], k + 1 < n_dfa ? xa[1] : 0.f, k + 2 < n_dfa ? xa[2] : 0.f,
+                                             k + 3 < n_dfa ? xa[3] : 0.f);
     }
 }
 
@@ -865,9 +868,11 @@ __device__ __forceinline__ void iter_fused_body(const SysView<float> &S, const f
                 float v = a[0][i] * __ldg(xa);
 #pragma unroll
                 for (int j = 1; j < NASTRO; ++j) v = fmaf(a[j][i], __ldg(xa + j), v);
+                float4 wv[NAXES];
+                att_window_load(S.xw, kn[i], wv);
 #pragma unroll
                 for (int ax = 0; ax < NAXES; ++ax) {
-                    const float4 w = __ldg(S.xw + (int64_t)ax * S.n_dfa + kn[i]);
+                    const float4 w = wv[ax];
                     v = fmaf(a[A_ATT + NPARAXIS * ax + 0][i], w.x, v);
                     v = fmaf(a[A_ATT + NPARAXIS * ax + 1][i], w.y, v);
                     v = fmaf(a[A_ATT + NPARAXIS * ax + 2][i], w.z, v);

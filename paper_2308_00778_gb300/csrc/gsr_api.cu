@@ -444,9 +444,10 @@ static gsr_status create_ctx(gsr_ctx **out, int64_t n_stars, int32_t obs_per_sta
         return e == cudaErrorMemoryAllocation ? GSR_ENOMEM : GSR_ECUDA;
     }
     // the window copies of the binary32 attitude unknowns: binary32 for aprod 1 and the fused pass (one
-    // 16-byte window per axis and row), double-float pairs for the residual of a wide attitude block
+    // 16-byte window per axis and row, knot-major in 64-byte records), double-float pairs for the
+    // residual of a wide attitude block
     if (value_precision == GSR_FP32 && !sv &&
-        ((e = cudaMalloc(&c->xwin, sizeof(float) * 4 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess ||
+        ((e = cudaMalloc(&c->xwin, sizeof(float4) * 4 * (size_t)n_dfa)) != cudaSuccess ||
          ((int64_t)NAXES * n_dfa > ATT_WINDOW_MIN_COLS &&
           (e = cudaMalloc(&c->xhlwin, sizeof(float4) * 2 * (size_t)NAXES * (size_t)n_dfa)) != cudaSuccess))) {
         cudaGetLastError();

@@ -51,7 +51,7 @@ __global__ void k_split_window(const double *__restrict__ x, int64_t att0, int32
     }
 }
 
-// ATTW: the attitude pairs come from the window copy (two 16-byte loads per axis and row instead of
+// ATTW: the attitude pairs come from the window copy (one 32-byte load per axis and row instead of
 // four 8-byte gathers); the terms and their order are the same, so the result is bitwise the same.
 // XS: the block copies the instrumental pairs to shared memory first and gathers them there (a random
 // 8-byte gather from global memory costs the L1 data pipe about a pass per lane); again the same terms.
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(256) k_residual(SysView<float> S, const float2
             if constexpr (ATTW) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    const float4 *w = S.xw2 + 2 * ((int64_t)ax * S.n_dfa + kn[i]);
-                    const float4 p = __ldg(w), q = __ldg(w + 1);
+                    float4 p, q;  // the pairs of columns k, k+1 and k+2, k+3: one 32-byte load
+                    ldg_v8(S.xw2 + 2 * ((int64_t)ax * S.n_dfa + kn[i]), p, q);
                     acc_term(a[A_ATT + NPARAXIS * ax + 0][i], make_float2(p.x, p.y), sh[i], c[i]);
                     acc_term(a[A_ATT + NPARAXIS * ax + 1][i], make_float2(p.z, p.w), sh[i], c[i]);
                     acc_term(a[A_ATT + NPARAXIS * ax + 2][i], make_float2(q.x, q.y), sh[i], c[i]);

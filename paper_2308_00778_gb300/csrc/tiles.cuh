@@ -31,6 +31,23 @@ __device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes)
     if ((threadIdx.x & 31) == 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)bytes));
 }
 
+// One 32-byte read-only load (p 32-byte aligned): two consecutive float4 in one request, where two
+// 16-byte loads of the same sector would make two.
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// A row's three attitude windows from the knot-major window copy (64 bytes per knot: axes 0 and 1 in
+// one 32-byte load, axis 2 in a 16-byte one: two requests instead of three)
+__device__ __forceinline__ void att_window_load(const float4 *__restrict__ xw, int32_t k, float4 (&w)[3])
+{
+    ldg_v8(xw + 4 * (int64_t)k, w[0], w[1]);
+    w[2] = __ldg(xw + 4 * (int64_t)k + 2);
+}
+
 template <typename VT>
 struct Tile {
     static constexpr int R = 16 / (int)sizeof(VT);                   // rows per lane
