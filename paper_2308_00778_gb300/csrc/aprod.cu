@@ -214,6 +214,39 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
     __syncwarp();
 }
 
+// the instrumental products of a lane's rows that the fixed-point sums leave out (rare), by binary64
+// atomics; kept out of line so that the pass's own registers and schedule do not change
+__device__ __noinline__ void fx64_lane_outliers(double *__restrict__ zi, const double (&ai)[NINSTR][2],
+                                                const int32_t (&ic)[NINSTR][2], const double (&yr)[2], unsigned mask)
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (mask & (1u << i))
+#pragma unroll
+            for (int j = 0; j < NINSTR; ++j) atomicAdd(zi + ic[j][i], ai[j][i] * yr[i]);
+}
+
+// round(p 2^sh) as an int64 by integer operations only (the binary64 pipe stays free for the products),
+// for |p 2^sh| <= 2^62: p = m 2^(e - 1075) with the 53-bit significand m, so p 2^sh = m 2^(e - 1075 + sh),
+// a left shift of at most 9 places or a right shift rounded half away from zero; subnormal p (e = 0)
+// are far below any grid here and give 0.
+__device__ __forceinline__ long long fx64_round(double p, int sh)
+{
+    const long long bits = __double_as_longlong(p);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const long long m = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
+    const int sft = e - 1075 + sh;
+    long long q;
+    if (sft >= 0)
+        q = m << min(sft, 9);
+    else if (sft > -63)
+        q = (m + (1LL << (-sft - 1))) >> (-sft);
+    else
+        q = 0;
+    if (e == 0) q = 0;
+    return bits < 0 ? -q : q;
+}
+
 // aprod 2, star pass: astrometric, instrumental and global parts. Each warp
 // owns a contiguous range of tiles; astrometric products of the current star
 // accumulate per lane and are flushed once when the star changes (a tile that
@@ -232,8 +265,15 @@ __device__ __forceinline__ void flush_astro_run(AT (&acc)[NASTRO], int64_t k, AT
 // binary32 accumulation. The per-block integer sums convert exactly to binary64
 // and sum exactly there, so these columns of A^T y do not depend on the order
 // of the additions.
+//
+// FX64 (binary64 storage, products): the same for binary64, in 64-bit integers
+// with a power-of-two scale per column and call (below), converted by integer
+// operations: the binary64 shared-memory atomic adds they replace occupied the
+// binary64 pipe beside the products (on 2e7 rows with 1,000 instrumental
+// columns the pass went from 1.2 to 0.88 ms). NW: warps per block (16 when the
+// 20,000 columns of the 5e8-row system leave room for one block per SM only).
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV,
-          bool ATT = false, bool UNI = false, bool ATTRED = false>
+          bool ATT = false, bool UNI = false, bool ATTRED = false, bool FX64 = false, int NW = 8>
 __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
                                                  double *__restrict__ z, double *__restrict__ z2,
                                                  const LsqrState *__restrict__ st, int64_t tiles_per_warp,
@@ -246,12 +286,14 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     static_assert(!FX || (INSTR_SMEM && sizeof(AT) == 4), "fixed point: binary32 products and squares");
     static_assert(!ATT || (FX && !SV), "attitude columns: fixed point, standard row");
     static_assert(!ATTRED || (!ATT && !SV && sizeof(AT) == 4), "attitude reductions: binary32, standard row");
+    static_assert(!FX64 || (INSTR_SMEM && !FX && !SV && !ATT && !ATTRED && sizeof(AT) == 8 && MODE == A2_PROD),
+                  "binary64 fixed point: the products of the standard row's instrumental columns");
     __shared__ int s_bad;
     constexpr int R = Tile<VT>::R;
     constexpr int T = Tile<VT>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sm32[32];
-    __shared__ AT wred[8][NASTRO * WSTRIDE];
+    __shared__ AT wred[NW][NASTRO * WSTRIDE];
     if (LSQR && st->done) return;
     // block-private columns: the instrumental ones, then (ATT) the attitude ones at n_instr + a*n_dfa + k
     const int32_t ncol = ATT ? S.n_instr + NAXES * S.n_dfa : S.n_instr;
@@ -304,6 +346,35 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                 sm_qscale[i] = qs;
             }
         }
+    }
+    // FX64: the instrumental sums as int64 fixed point, column j in units of 2^-sh_j, with sh_j the
+    // largest shift for which (the most contributions one block adds to j) x max|a_j| x y_t stays
+    // within 2^62: no block sum can overflow, and each contribution is rounded to 2^-(sh_j + 1), about
+    // 2^-53 of its column's bound times that count. y_t is a power of two above all but about 1/1024 of
+    // the rows' |y| (k_fx64_yt); the rows at or above it (and non-finite or subnormal ones) add their
+    // instrumental products with binary64 atomics instead (fx64_lane_outliers), so that one large
+    // entry of y does not coarsen every column's grid. Any y_t gives the right sums; it only
+    // decides how fine the grid is. fx_word: the 2048 exponent bins, y_t (binary64), the counts,
+    // max|a_j| (binary32 bits, rounded up). The fixed-point sums are exact integers, whatever their order.
+    int16_t *sm_sh = reinterpret_cast<int16_t *>(smem_raw + sizeof(long long) * (size_t)S.n_instr);
+    __shared__ double s_yt;
+    if constexpr (FX64) {
+        if (threadIdx.x == 0) s_yt = __longlong_as_double(*reinterpret_cast<const long long *>(fx_word + FX64_BINS));
+        __syncthreads();
+        const double yt = s_yt;
+        const uint32_t *kmx = fx_word + FX64_BINS + 2, *amx = fx_word + FX64_BINS + 2 + S.n_instr;
+        int bad = 0;
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+            const double bound = (double)kmx[i] * (double)__uint_as_float(amx[i]) * yt;
+            int sh = 0;
+            if (bound > 0.0 && bound < INFINITY)
+                sh = 61 - ilogb(bound);  // bound < 2^(ilogb + 1), so bound 2^sh <= 2^62
+            else if (bound != 0.0)
+                bad = 1;  // beyond the binary64 range: the column cannot be held in fixed point
+            sm_sh[i] = (int16_t)max(min(sh, 30000), -30000);
+        }
+        bad = __syncthreads_or(bad);
+        if (threadIdx.x == 0) s_bad = bad;
     }
     __syncthreads();
     // UNI: the instrumental group scale applies (the host chose this instance from the statistics)
@@ -383,6 +454,20 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
 #pragma unroll
             for (int i = 0; i < R; ++i) yr[i] = SQUARE ? (in[i] ? (AT)1 : (AT)0) : (in[i] ? (AT)y[r0 + i] : (AT)0);
         }
+        // FX64: y of the rows whose instrumental products go to the fixed-point sums, 0 for the others
+        // (|y| >= y_t, non-finite or subnormal y), which fx64_lane_outliers adds at once
+        AT yfx[R];
+        unsigned omask = 0u;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const double ya = fabs((double)yr[i]);
+            const bool fx_row = ya < s_yt && ya >= 0x1p-1022;
+            yfx[i] = (FX64 && fx_row) ? yr[i] : (AT)0;
+            if (FX64 && !fx_row && ya != 0.0 && in[i]) omask |= 1u << i;
+        }
+        if constexpr (FX64 && R == 2) {
+            if (omask) fx64_lane_outliers(zi, ai, ic, yr, omask);
+        }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
 #pragma unroll
@@ -415,7 +500,10 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                     continue;
                 }
                 if (in[i]) {
-                    if (FX)
+                    if (FX64)  // straight-line: a row left to fx64_lane_outliers adds 0 here
+                        atomicAdd(reinterpret_cast<unsigned long long *>(sm_ins) + ic[j][i],
+                                  (unsigned long long)fx64_round((double)(av * yfx[i]), sm_sh[ic[j][i]]));
+                    else if (FX)
                         atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
                                   __float2int_rn(av * yr[i] * (ATT && ins_uni ? ins_sc : sm_scale[ic[j][i]])));
                     else if (INSTR_SMEM)
@@ -564,6 +652,12 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
             atomicAdd((sq ? z2 : z) + dst, (double)q / (double)sc);  // the scale is a power of two: exact
         }
         if (s_bad && threadIdx.x == 0) atomicAdd(S.n_instr ? zi : z + S.att0, (double)NAN);
+    } else if (FX64) {
+        for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+            const long long q = reinterpret_cast<const long long *>(sm_ins)[i];
+            if (q != 0) atomicAdd(zi + i, ldexp((double)q, -(int)sm_sh[i]));  // a power of two: exact
+        }
+        if (s_bad && threadIdx.x == 0) atomicAdd(zi, (double)NAN);
     } else {
         for (int32_t i = threadIdx.x; i < nsm; i += blockDim.x) {
             const AT v = sm_ins[i];
@@ -594,6 +688,37 @@ __global__ void __launch_bounds__(256) k_aprod2_star(SysView<VT> S, const UT *__
 {
     aprod2_star_body<VT, UT, AT, INSTR_SMEM, MODE, LSQR, FX, false, false, false, ATTRED>(S, y, z, z2, st,
                                                                                         tiles_per_warp, fx_word, fxs);
+}
+
+// The binary64 star pass with int64 fixed-point instrumental sums (binary64 storage, standard row,
+// products): NT threads a block, 256 where two blocks' sums fit an SM, else 512 (one block of 16 warps:
+// the 20,000 columns' 200 KB of sums and shifts leave room for one block only). fx_word: the context's
+// fx64_word (max |y| of this call, the per-column counts and bounds).
+template <bool LSQR, int NT>
+__global__ void __launch_bounds__(NT) k_aprod2_star_fx64(SysView<double> S, const double *__restrict__ y,
+                                                         double *__restrict__ z, const LsqrState *__restrict__ st,
+                                                         int64_t tiles_per_warp, const uint32_t *__restrict__ fx_word)
+{
+    aprod2_star_body<double, double, double, true, A2_PROD, LSQR, false, false, false, false, false, true, NT / 32>(
+        S, y, z, nullptr, st, tiles_per_warp, fx_word, 0);
+}
+
+// The binary64 exponents of |y| over a sample of the rows (every 64th) into FX64_BINS bins (zero on
+// entry), from which the fixed-point star pass picks the magnitude that all but about 1/1024 of the
+// rows stay below; nothing once the solve has stopped (st)
+__global__ void k_ybins64(const double *__restrict__ y, int64_t n, uint32_t *__restrict__ bins,
+                          const LsqrState *__restrict__ st)
+{
+    __shared__ uint32_t hb[FX64_BINS];
+    if (st && st->done) return;
+    for (int i = threadIdx.x; i < FX64_BINS; i += blockDim.x) hb[i] = 0u;
+    __syncthreads();
+    const int64_t ns = (n + 63) / 64;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(hb + (int)((__double_as_longlong(y[64 * i]) >> 52) & 0x7ff), 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < FX64_BINS; i += blockDim.x)
+        if (hb[i]) atomicAdd(bins + i, hb[i]);
 }
 
 // z[att] += the window accumulators of the attitude reductions: column k of axis a collects
@@ -1149,6 +1274,80 @@ __global__ void k_absmax(const float *__restrict__ y, int64_t n, uint32_t *__res
     if (threadIdx.x == 0) atomicMax(ymax, __float_as_uint(m));
 }
 
+// y_t of the binary64 fixed-point star pass from the sampled exponent bins (one warp): the power of two
+// 2^(E - 1023) with E >= 1 the smallest exponent whose bin and those above hold at most 1/1024 of the
+// sample; into fx_word[FX64_BINS ..] as binary64. Nothing once the solve has stopped (st).
+__global__ void k_fx64_yt(uint32_t *__restrict__ fx_word, const LsqrState *__restrict__ st)
+{
+    if (st && st->done) return;
+    const uint32_t *bins = fx_word;
+    const int l = threadIdx.x;  // lane l holds bins [64 l, 64 l + 64)
+    uint32_t mine = 0u;
+    for (int b = 0; b < 64; ++b) mine += bins[64 * l + b];
+    uint32_t incl = mine;  // sum over lanes l..31 (inclusive suffix scan)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(0xffffffffu, incl, o);
+        if (l + o < 32) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 0);
+    const uint32_t lim = total >> 10;
+    int cand = 0;  // the largest bin b of this lane with (bins b and above) > lim, if any
+    uint32_t run = incl - mine;
+    for (int b = 63; b >= 0; --b) {
+        run += bins[64 * l + b];
+        if (run > lim) {
+            cand = 64 * l + b;
+            break;
+        }
+    }
+    const int E = max(__reduce_max_sync(0xffffffffu, cand) + 1, 1);
+    if (l == 0) *reinterpret_cast<long long *>(fx_word + FX64_BINS) = __double_as_longlong(ldexp(1.0, min(E, 2046) - 1023));
+}
+
+
+// The partition of the binary64 fixed-point star pass (the statistics of layout.cu are taken over it):
+// two blocks of 256 threads per SM where their shared memory fits, else one block of 512; contiguous
+// ranges of at least 8 tiles a warp.
+void fx64_partition(const gsr_ctx *c, int64_t *per, int64_t *blocks, int32_t *nt)
+{
+    const size_t dyn = fx64_smem(c);
+    int per_sm = 0;
+    auto k256 = k_aprod2_star_fx64<false, 256>;
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(k256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k256, 256, dyn) != cudaSuccess) per_sm = 0;
+    cudaGetLastError();
+    *nt = per_sm >= 2 ? 256 : 512;
+    const int64_t wpb = *nt / 32;
+    const int64_t max_warps = (per_sm >= 2 ? (int64_t)per_sm : 1) * c->sm_count * wpb;
+    *per = std::max<int64_t>((c->n_tiles + max_warps - 1) / max_warps, 8);
+    const int64_t warps = (c->n_tiles + *per - 1) / *per;
+    *blocks = std::max<int64_t>((warps + wpb - 1) / wpb, 1);
+}
+
+// the binary64 star pass with the fixed-point instrumental sums: the sampled exponents of |y| and y_t
+// first, then the pass over the partition its statistics were taken for
+template <bool LS>
+static cudaError_t aprod2_star_fx64_launch(const gsr_ctx *c, const double *y, double *x, const LsqrState *st,
+                                           cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(c->fx64_word, 0, sizeof(uint32_t) * FX64_BINS, s);
+    if (e != cudaSuccess) return e;
+    const int64_t ns = (c->n_rows + 63) / 64;
+    k_ybins64<<<(unsigned)std::min<int64_t>(std::max<int64_t>((ns + kThreads - 1) / kThreads, 1), c->sm_count),
+                kThreads, 0, s>>>(y, c->n_rows, c->fx64_word, st);
+    k_fx64_yt<<<1, 32, 0, s>>>(c->fx64_word, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t dyn = fx64_smem(c);
+    auto kern = c->fx64_nt == 256 ? k_aprod2_star_fx64<LS, 256> : k_aprod2_star_fx64<LS, 512>;
+    if (dyn > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
+        return e;
+    kern<<<(unsigned)c->fx64_blocks, (unsigned)c->fx64_nt, dyn, s>>>(view<double>(c), y, x, st, c->fx64_per,
+                                                                    c->fx64_word);
+    return cudaGetLastError();
+}
+
 // the binary32 aprod 2 of a wide attitude block (att_red): one star pass whose attitude products go to the
 // window accumulators by vector reductions, then the fold into z (which also clears max |y|)
 template <int MODE, bool LS>
@@ -1202,7 +1401,13 @@ static cudaError_t aprod2_t(const gsr_ctx *c, const void *y, double *x, double *
     // the combined pass needs twice the shared words; it keeps binary32 atomics when they do not fit
     const bool fx = F32 && c->fx_bits > 0 &&
                     (MODE != A2_BOTH || 4 * sizeof(float) * (size_t)c->n_instr <= kSmemBudget);
-    if (fx) {
+    bool fx64 = false;
+    if constexpr (sizeof(VT) == 8 && MODE == A2_PROD) fx64 = star_fx64(c);
+    if (fx64) {
+        // binary64 storage: int64 fixed-point instrumental sums (integer operations and atomics, off
+        // the binary64 pipe that the products keep busy)
+        if constexpr (sizeof(VT) == 8 && MODE == A2_PROD) e = aprod2_star_fx64_launch<LS>(c, (const double *)y, x, st, s);
+    } else if (fx) {
         // fixed-point instrumental sums: max |y| comes from the LSQR aprod 1 of the same iteration,
         // else from a pass over y here
         if (MODE != A2_SQUARE && !LS) {

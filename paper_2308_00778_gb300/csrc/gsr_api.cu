@@ -517,6 +517,7 @@ GSR_API gsr_status gsr_destroy(gsr_ctx *c)
     cudaFree(c->errw);
     cudaFree(c->knot_ptr);
     cudaFree(c->fx_word);
+    cudaFree(c->fx64_word);
     cudaFree(c->attw);
     cudaFree(c->xwin);
     cudaFree(c->xhlwin);

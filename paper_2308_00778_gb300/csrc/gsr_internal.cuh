@@ -161,10 +161,20 @@ struct gsr_ctx {
     bool fx_att = false;
     bool fx_uni = false;             // the one-pass aprod 2 gives the instrumental columns one scale too
     bool fx_valid = false;           // the statistics match the loaded rows
+    // fixed-point instrumental sums of the binary64 star pass (binary64 storage, standard row; built
+    // with the knot-ordered copy, layout.cu): the pass's partition (fx64_per tiles a warp, fx64_blocks
+    // blocks of fx64_nt threads) and fx64_word: [FX64_BINS] the sampled binary64 exponents of |y| of the
+    // current aprod 2, its y_t (binary64, 2 words), [n_instr] the largest number of contributions one
+    // block adds to each instrumental column, [n_instr] each column's largest |coefficient| (binary32
+    // bits, rounded up)
+    int64_t fx64_per = 0, fx64_blocks = 0;
+    int32_t fx64_nt = 0;
+    uint32_t *fx64_word = nullptr;
+    bool fx64 = false;               // the statistics are built (valid while att_valid holds)
     int32_t fused_inner = 0;         // the current solve's inner iterations take the fused pass (> 0)
     // wide attitude blocks (binary32 storage, standard row): attw holds the window accumulators of the
     // binary32 aprod 2 (2 x 3 n_dfa x 4 binary32: products, then squares; zero between uses), xwin the
-    // window copy aprod 1 gathers from (3 n_dfa x 4 binary32)
+    // window copy aprod 1 gathers from (n_dfa x 4 float4, knot-major: axes 0-2, one unused)
     float *attw = nullptr;
     float *xwin = nullptr;
     float4 *xhlwin = nullptr;  // the double-float residual's window copy (3 n_dfa x 2 float4), wide blocks
@@ -265,6 +275,13 @@ inline bool iter_fused(const gsr_ctx *c) { return c->fused_inner && att_red(c) &
 // c2, 9,000 columns, 0.550 -> 0.608 ms)
 constexpr int64_t ATT_WINDOW_MIN_COLS = 16384;
 // max |y| word of the fixed-point sums (nullptr when they are off)
+constexpr int FX64_BINS = 2048;  // binary64 exponent values
+// the binary64 star pass takes the fixed-point instrumental sums
+inline bool star_fx64(const gsr_ctx *c) { return c->prec == GSR_FP64 && !c->sv && c->fx64 && c->att_valid; }
+// its partition for the loaded dimensions (aprod.cu): per tiles a warp, blocks, threads a block
+void fx64_partition(const gsr_ctx *c, int64_t *per, int64_t *blocks, int32_t *nt);
+// bytes of the pass's dynamic shared memory: int64 sums and int16 shifts of the instrumental columns
+inline size_t fx64_smem(const gsr_ctx *c) { return (sizeof(long long) + sizeof(int16_t)) * (size_t)c->n_instr; }
 inline uint32_t *fx_ymax(const gsr_ctx *c) { return c->fx_bits > 0 ? c->fx_word + 2 * (size_t)c->fx_nc : nullptr; }
 
 // the allocation-free residual's scratch array (residual_static.cu): load its module and the kernels

@@ -203,6 +203,9 @@ __global__ void __launch_bounds__(1024) k_group_extremes(const uint32_t *__restr
 // every column, twice for the pass that sums products and squares together.
 static constexpr size_t kFxSmemOne = 100 * 1024;   // two blocks per SM
 static constexpr size_t kFxSmemBoth = 200 * 1024;  // one block per SM
+// the binary64 fixed-point star pass: its sums and shifts beside the 21 KB of static shared memory of a
+// 512-thread block, within the 227 KB a block may hold
+static constexpr size_t kFx64SmemMax = 204 * 1024;
 
 // Per-column bits of the fixed-point sums (all 0: keep binary32 atomics):
 // bits_j = 31 - ceil(log2(kmax_j + 1)), so that no block can overflow column j;
@@ -302,6 +305,80 @@ static gsr_status fixed_point_finish(gsr_ctx *c, cudaStream_t s, const std::vect
     c->fx_bits = min_ins;
     c->fx_att = group_bits[0] > 0;
     c->fx_uni = group_bits[1] > 0;
+    return GSR_OK;
+}
+
+// For the int64 fixed-point instrumental sums of the binary64 star pass (aprod.cu), over its partition
+// (warp w of that pass takes tiles [w per, (w + 1) per), wpb warps a block; this kernel runs one block
+// per block of the pass, its own warps striding over the block's tiles): the largest number of
+// contributions one block adds to each instrumental column (kmax) and each column's largest
+// |coefficient| (amax, binary32 bits rounded up, so never below the binary64 value). Both zero on entry.
+__global__ void __launch_bounds__(256) k_instr_stats64(SysView<double> S, int64_t per, int32_t wpb,
+                                                       uint32_t *__restrict__ kmax, uint32_t *__restrict__ amax)
+{
+    constexpr int R = Tile<double>::R;
+    constexpr int T = Tile<double>::T;
+    extern __shared__ uint32_t cnt[];  // [n_instr] counts, then [n_instr] max |a| bits
+    uint32_t *am = cnt + S.n_instr;
+    for (int32_t i = threadIdx.x; i < 2 * S.n_instr; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t b0 = (int64_t)blockIdx.x * wpb * per;
+    const int64_t b1 = min(S.n_tiles, b0 + (int64_t)wpb * per);
+    for (int64_t t = b0 + warp; t < b1; t += nw) {
+        const uint8_t *tb = S.tiles + t * S.tile_bytes;
+        const int64_t r0 = t * T + lane * R;
+#pragma unroll
+        for (int j = 0; j < NINSTR; ++j) {
+            int32_t ic[R];
+            double a[R];
+            load_instr<double>(tb, S.iw16, j, ic);
+            load_vals<double, double>(tb, A_INS + j, a);
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (r0 + i < S.n_rows) {
+                    atomicAdd(cnt + ic[i], 1u);
+                    atomicMax(am + ic[i], __float_as_uint(__double2float_ru(fabs(a[i]))));
+                }
+        }
+    }
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < S.n_instr; i += blockDim.x) {
+        if (cnt[i]) atomicMax(kmax + i, cnt[i]);
+        if (am[i]) atomicMax(amax + i, am[i]);
+    }
+}
+
+// The statistics of the binary64 fixed-point star pass (asynchronous on s), where it applies: binary64
+// storage, the standard row, and its sums and shifts within one block's shared memory.
+static gsr_status fx64_stats(gsr_ctx *c, cudaStream_t s)
+{
+    const bool was = c->fx64;
+    c->fx64 = false;
+    const size_t dyn = fx64_smem(c);
+    const bool fits = dyn <= kFx64SmemMax && 2 * sizeof(uint32_t) * (size_t)c->n_instr <= kFx64SmemMax;
+    if (c->prec != GSR_FP64 || c->sv || c->n_rows == 0 || c->n_instr == 0 || !fits) {
+        if (was) drop_graphs(c);
+        return GSR_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    const size_t words = FX64_BINS + 2 + 2 * (size_t)c->n_instr;
+    if (!c->fx64_word && (e = cudaMalloc(&c->fx64_word, sizeof(uint32_t) * words)) != cudaSuccess)
+        return cuda_fail(c, e, "fixed-point words");
+    fx64_partition(c, &c->fx64_per, &c->fx64_blocks, &c->fx64_nt);
+    if ((e = cudaMemsetAsync(c->fx64_word, 0, sizeof(uint32_t) * words, s)) != cudaSuccess)
+        return cuda_fail(c, e, "memset");
+    const size_t smem = 2 * sizeof(uint32_t) * (size_t)c->n_instr;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_instr_stats64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return cuda_fail(c, e, "fixed-point statistics");
+    k_instr_stats64<<<(unsigned)c->fx64_blocks, 256, smem, s>>>(view<double>(c), c->fx64_per, c->fx64_nt / 32,
+                                                                c->fx64_word + FX64_BINS + 2,
+                                                                c->fx64_word + FX64_BINS + 2 + c->n_instr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "fixed-point statistics");
+    c->fx64 = true;
+    if (!was) drop_graphs(c);  // graphs captured before hold the binary64 atomics' pass
     return GSR_OK;
 }
 
@@ -421,7 +498,8 @@ gsr_status ensure_att_layout(gsr_ctx *c, cudaStream_t s, bool binary64)
     // the knot-ordered copy: for binary64 aprod 2 passes, and binary32 section variants whose
     // attitude columns do not fit the one-pass form
     if ((binary64 || (!att_fused(c) && !att_red(c))) && !c->att_valid) {
-        const gsr_status rc = build_att_copy(c, s);
+        gsr_status rc = build_att_copy(c, s);
+        if (rc == GSR_OK) rc = fx64_stats(c, s);
         if (rc != GSR_OK) return rc;
         c->att_valid = true;
     }

@@ -222,3 +222,36 @@ def test_pinned_host_rows_convert_in_one_pass(fp32):
     assert torch.equal(y1, y2)
     ref.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "wide_att_global", "ragged_many"])
+def test_aprod2_binary64_instrumental_columns_of_spread_scale(name):
+    """The binary64 star pass sums the instrumental products as int64 fixed point with one power-of-two
+    scale per column (from the column's largest |coefficient|, the most contributions one block adds to
+    it, and max |y| of the call). Columns whose coefficients are 2^-20, 1 and 2^20 times the others
+    (by column index mod 3) must each keep binary64 accuracy: every entry within 1e-13 of its own sum
+    of |terms|, against the oracle on the same values. c1 and ragged_many take blocks of 256 threads,
+    wide_att_global (15,000 instrumental columns: 150 KB of sums and shifts) one block of 512 per SM.
+    Also y with a single huge entry (the bound then far above the typical product) and y = 0."""
+    cfg = CASES[name]
+    h = gsrgen.generate(cfg)
+    fac = 2.0 ** (20.0 * ((np.arange(cfg.n_instr) % 3) - 1.0))
+    A = h.A.copy()
+    a_ins = 5 + 12
+    for j in range(cfg.n_ipr):
+        A[:, a_ins + j] *= fac[h.instr[:, j]]
+    s = oracle.from_host_system(h)
+    s = oracle.System(s.star_ptr, A, s.knot, s.instr, s.n_dfa, s.n_instr, s.n_glob, s.n_astro, s.n_ipr)
+    ctx = context_for(h)
+    ctx.set_system(A, h.knot, h.instr)
+    rng = np.random.default_rng(11)
+    u_spike = rng.standard_normal(s.n_rows)
+    u_spike[s.n_rows // 3] = 1e6
+    for u in (rng.standard_normal(s.n_rows), u_spike, np.zeros(s.n_rows)):
+        x0 = rng.standard_normal(s.n_cols)
+        zd = torch.tensor(x0, device="cuda")
+        ctx.aprod2(torch.tensor(u, device="cuda"), zd)
+        want = oracle.aprod2(s, u, x0.copy())
+        scale = oracle.aprod2(abs_system(s), np.abs(u), np.abs(x0).copy())
+        _check(zd.cpu().numpy(), want, scale)
+    ctx.close()
