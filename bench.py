@@ -68,10 +68,11 @@ FLOPS_PER_ROW = 48  # 24 multiply-adds per row in each aprod
 # captures of the benchmark's standalone launches (bench.py --profile), by the workload whose shape the
 # capture had; a launch's traffic is this figure times its rows. Sources under profiles/.
 TRAFFIC_PER_ROW = {
+    # (the binary64 aprod 2 changed after its 2e7-row capture: no current figure)
     "c2": {"aprod1_f32": 117.4, "aprod2_f32": 120.8, "residual_df": 121.4, "aprod1_f64": 221.4,
-           "aprod2_f64": 274.9},   # profiles/traffic_aprod_c2.md
-    "c5": {"aprod1_f32": 117.5, "aprod2_f32": 116.8, "residual_df": 121.7, "aprod12_f32": 120.7,
-           "aprod1_f64": 221.4, "aprod2_f64": 269.3},  # profiles/traffic_aprod_c5shape.md
+           "aprod2_f64": None},   # profiles/traffic_aprod_c2.md
+    "c5": {"aprod1_f32": 117.6, "aprod2_f32": 116.7, "residual_df": 121.8, "aprod12_f32": 120.5,
+           "aprod1_f64": 221.4, "aprod2_f64": 269.2},  # profiles/traffic_aprod_c5shape.md
 }
 # the workload each capture stands for (a smaller case of the same shape)
 TRAFFIC_SHAPE = {"c2": "c2", "c5": "c5"}
