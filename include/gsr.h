@@ -367,8 +367,10 @@ typedef struct {
                                step). x is the same iterate up to rounding; that solve's
                                |A~^T r| estimate (gsr_solve_info.arnorm) is the one of the
                                iteration before. 1 (default) = on; 0 or -1 = every iteration
-                               in full. Applies when graph_k is 0 (automatic) or divides the
-                               inner iteration limit                                          */
+                               in full. Applies when the limit is a multiple of the iterations
+                               per graph launch: graph_k if set, else the largest divisor of
+                               the limit up to 8 when that is at least half of min(8, limit)
+                               (every limit up to 8, and 10, 12, 14, 15, 16, 18, 20, 21, ...) */
 } gsr_solve_params;
 
 typedef struct {
