@@ -45,8 +45,12 @@ def _static_call(L, ctx, xd, r):
     return free0, torch.cuda.mem_get_info()[0]
 
 
-def test_static_residual_allocates_nothing_and_matches_gsr_residual():
-    cfg = gsrgen.make_cfg(71, 3000, (40, 160), 700, 300, att_kind=1)
+@pytest.mark.parametrize("n_dfa", [700, 6000])
+def test_static_residual_allocates_nothing_and_matches_gsr_residual(n_dfa):
+    # 6000 knots per axis: a wide attitude block, where gsr_residual reads the attitude pairs through the
+    # context's window copy and the instrumental pairs from shared memory; the entry point here gathers
+    # them from its own array, the same terms in the same order
+    cfg = gsrgen.make_cfg(71, 3000, (40, 160), n_dfa, 300, att_kind=1)
     h = gsrgen.generate(cfg, fp32=True)
     s = oracle.from_host_system(h)
     b = oracle.rhs(s, h.x_true, h.eps)
