@@ -456,14 +456,19 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
         }
         // FX64: y of the rows whose instrumental products go to the fixed-point sums, 0 for the others
         // (|y| >= y_t, non-finite or subnormal y), which fx64_lane_outliers adds at once
+        // (the tests on the bits of |y|: non-negative binary64 values, NaN above infinity, order as
+        // integers, so the binary64 pipe stays with the products)
         AT yfx[R];
         unsigned omask = 0u;
+        if constexpr (FX64) {
+            const unsigned long long yt_bits = (unsigned long long)__double_as_longlong(s_yt);
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const double ya = fabs((double)yr[i]);
-            const bool fx_row = ya < s_yt && ya >= 0x1p-1022;
-            yfx[i] = (FX64 && fx_row) ? yr[i] : (AT)0;
-            if (FX64 && !fx_row && ya != 0.0 && in[i]) omask |= 1u << i;
+            for (int i = 0; i < R; ++i) {
+                const unsigned long long ya = (unsigned long long)__double_as_longlong((double)yr[i]) & 0x7fffffffffffffffull;
+                const bool fx_row = ya < yt_bits && ya >= 0x0010000000000000ull;  // 2^-1022 <= |y| < y_t
+                yfx[i] = fx_row ? yr[i] : (AT)0;
+                if (!fx_row && ya != 0ull && in[i]) omask |= 1u << i;
+            }
         }
         if constexpr (FX64 && R == 2) {
             if (omask) fx64_lane_outliers(zi, ai, ic, yr, omask);
