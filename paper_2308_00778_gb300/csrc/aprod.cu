@@ -226,25 +226,22 @@ __device__ __noinline__ void fx64_lane_outliers(double *__restrict__ zi, const d
             for (int j = 0; j < NINSTR; ++j) atomicAdd(zi + ic[j][i], ai[j][i] * yr[i]);
 }
 
-// round(p 2^sh) as an int64 by integer operations only (the binary64 pipe stays free for the products),
-// for |p 2^sh| <= 2^62: p = m 2^(e - 1075) with the 53-bit significand m, so p 2^sh = m 2^(e - 1075 + sh),
-// a left shift of at most 9 places or a right shift rounded half away from zero; subnormal p (e = 0)
-// are far below any grid here and give 0.
-__device__ __forceinline__ long long fx64_round(double p, int sh)
+// round(a y 2^sh) as an int64 from the exact product of the significands (a 53 x 53-bit integer
+// multiply), for |a y 2^sh| <= 2^62: a y 2^sh = ma my 2^-t with t = 2150 - ea - ey - sh >= 42 (ea, ey the
+// biased exponents, 1 for subnormals), rounded half away from zero by a right shift of t places. No
+// binary64 operation: the product never passes through a rounded binary64 value.
+__device__ __forceinline__ long long fx64_mulround(double a, double y, int sh)
 {
-    const long long bits = __double_as_longlong(p);
-    const int e = (int)((bits >> 52) & 0x7ff);
-    const long long m = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
-    const int sft = e - 1075 + sh;
-    long long q;
-    if (sft >= 0)
-        q = m << min(sft, 9);
-    else if (sft > -63)
-        q = (m + (1LL << (-sft - 1))) >> (-sft);
-    else
-        q = 0;
-    if (e == 0) q = 0;
-    return bits < 0 ? -q : q;
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+    const int ea = (int)((ba >> 52) & 0x7ff), ey = (int)((by >> 52) & 0x7ff);
+    const unsigned long long ma = (ba & 0xfffffffffffffull) | (ea ? 0x10000000000000ull : 0ull);
+    const unsigned long long my = (by & 0xfffffffffffffull) | (ey ? 0x10000000000000ull : 0ull);
+    const int t = 2150 - max(ea, 1) - max(ey, 1) - sh;
+    const unsigned __int128 p = (unsigned __int128)ma * my;
+    unsigned long long q = 0ull;
+    if (t > 0 && t < 128) q = (unsigned long long)((p + ((unsigned __int128)1 << (t - 1))) >> t);
+    return ((ba ^ by) >> 63) ? -(long long)q : (long long)q;
 }
 
 // aprod 2, star pass: astrometric, instrumental and global parts. Each warp
@@ -267,11 +264,12 @@ __device__ __forceinline__ long long fx64_round(double p, int sh)
 // of the additions.
 //
 // FX64 (binary64 storage, products): the same for binary64, in 64-bit integers
-// with a power-of-two scale per column and call (below), converted by integer
-// operations: the binary64 shared-memory atomic adds they replace occupied the
-// binary64 pipe beside the products (on 2e7 rows with 1,000 instrumental
-// columns the pass went from 1.2 to 0.88 ms). NW: warps per block (16 when the
-// 20,000 columns of the 5e8-row system leave room for one block per SM only).
+// with a power-of-two scale per column and call (below), each product formed
+// and rounded by integer operations (fx64_mulround): the binary64 shared-memory
+// atomic adds they replace, and the products themselves, occupied the binary64
+// pipe (on 2e7 rows with 1,000 instrumental columns the whole aprod 2 went from
+// 1.70 to 1.29 ms). NW: warps per block (16 when the 20,000 columns of the
+// 5e8-row system leave room for one block per SM only).
 template <typename VT, typename UT, typename AT, bool INSTR_SMEM, int MODE, bool LSQR, bool FX, bool SV,
           bool ATT = false, bool UNI = false, bool ATTRED = false, bool FX64 = false, int NW = 8>
 __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT *__restrict__ y,
@@ -350,11 +348,11 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
     // FX64: the instrumental sums as int64 fixed point, column j in units of 2^-sh_j, with sh_j the
     // largest shift for which (the most contributions one block adds to j) x max|a_j| x y_t stays
     // within 2^62: no block sum can overflow, and each contribution is rounded to 2^-(sh_j + 1), about
-    // 2^-53 of its column's bound times that count. y_t is a power of two above all but about 1/1024 of
-    // the rows' |y| (k_fx64_yt); the rows at or above it (and non-finite or subnormal ones) add their
-    // instrumental products with binary64 atomics instead (fx64_lane_outliers), so that one large
-    // entry of y does not coarsen every column's grid. Any y_t gives the right sums; it only
-    // decides how fine the grid is. fx_word: the 2048 exponent bins, y_t (binary64), the counts,
+    // 2^-53 of its column's bound times that count (from the exact product, fx64_mulround). y_t is a
+    // power of two above all but about 1/1024 of the rows' |y| (k_fx64_yt); the rows at or above it
+    // (and non-finite or subnormal ones) add their instrumental products with binary64 atomics instead
+    // (fx64_lane_outliers), so that one large entry of y does not coarsen every column's grid. Any y_t
+    // gives the right sums; it only decides how fine the grid is. fx_word: the 2048 exponent bins, y_t (binary64), the counts,
     // max|a_j| (binary32 bits, rounded up). The fixed-point sums are exact integers, whatever their order.
     int16_t *sm_sh = reinterpret_cast<int16_t *>(smem_raw + sizeof(long long) * (size_t)S.n_instr);
     __shared__ double s_yt;
@@ -507,7 +505,7 @@ __device__ __forceinline__ void aprod2_star_body(const SysView<VT> &S, const UT 
                 if (in[i]) {
                     if (FX64)  // straight-line: a row left to fx64_lane_outliers adds 0 here
                         atomicAdd(reinterpret_cast<unsigned long long *>(sm_ins) + ic[j][i],
-                                  (unsigned long long)fx64_round((double)(av * yfx[i]), sm_sh[ic[j][i]]));
+                                  (unsigned long long)fx64_mulround((double)av, (double)yfx[i], sm_sh[ic[j][i]]));
                     else if (FX)
                         atomicAdd(reinterpret_cast<int *>(sm_ins) + ic[j][i],
                                   __float2int_rn(av * yr[i] * (ATT && ins_uni ? ins_sc : sm_scale[ic[j][i]])));
