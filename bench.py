@@ -72,7 +72,7 @@ TRAFFIC_PER_ROW = {
     "c2": {"aprod1_f32": 117.4, "aprod2_f32": 120.8, "residual_df": 121.4, "aprod1_f64": 221.4,
            "aprod2_f64": None},   # profiles/traffic_aprod_c2.md
     "c5": {"aprod1_f32": 117.6, "aprod2_f32": 116.7, "residual_df": 121.8, "aprod12_f32": 120.5,
-           "aprod1_f64": 221.4, "aprod2_f64": 269.2},  # profiles/traffic_aprod_c5shape.md
+           "aprod1_f64": 221.4, "aprod2_f64": 269.4},  # profiles/traffic_aprod_c5shape.md
 }
 # the workload each capture stands for (a smaller case of the same shape)
 TRAFFIC_SHAPE = {"c2": "c2", "c5": "c5"}
