@@ -181,9 +181,17 @@ gsr_status gsr_aprod1(gsr_ctx *ctx, const double *x, double *y, void *stream);
  * Runs on stream. Partial sums (per star segment, per attitude knot run,
  * per block for the instrumental and global unknowns) are added with atomic
  * adds, so the low bits of the results can differ from run to run (the sums
- * are reordered). The first call after the rows change builds the
- * knot-ordered attitude copy (52 B a row for binary32 storage, 100 B for
- * binary64, plus temporaries while it is sorted) and synchronises stream.
+ * are reordered). With binary64 storage and the standard row, the
+ * instrumental products are summed per block as 64-bit fixed point: each is
+ * rounded once, exactly from the product of the two significands, to a grid
+ * of about 2^-53 of (its column's max |coefficient| x the most terms one
+ * block adds to that column x y_t), where y_t is a power of two above all
+ * but about 1/1024 of the |y_i| (rows at or above it add theirs in binary64);
+ * the block sums are exact, whatever their order. The first call after the
+ * rows change builds the knot-ordered attitude copy (52 B a row for binary32
+ * storage, 100 B for binary64, plus temporaries while it is sorted) and, for
+ * binary64 storage, the statistics of the fixed-point sums, and synchronises
+ * stream.
  * Errors: GSR_EINVAL (null vector), GSR_ESTATE (rows not loaded),
  * GSR_ENOMEM, GSR_ECUDA.
  */
